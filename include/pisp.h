@@ -1,0 +1,215 @@
+/*
+ * pisp.h - C ABI of the perturbation-induced static pivoting solver.
+ *
+ * Method (arXiv 2311.11833): the K diagonally perturbed systems
+ *     (A + t_k D) x_k = b,   k = 0..K-1                    (Sec. III-A, Eq. xap / xam)
+ * are factored WITHOUT pivoting, all K in the same launches, and their
+ * solutions are combined as
+ *     x_hat = sum_k beta_k x_k                             (Eq. x_star, Remark 2)
+ * with weights chosen so that the Neumann-series terms (A^{-1} D)^j A^{-1} b,
+ * j = 1..K-1, cancel (Eq. neumann_2, Eq. gam).  For the paper's symmetric
+ * shift set t = {+-alpha*eps}, alpha = 1..m, these per-solve weights are
+ * half the paper's beta = (Gamma_m^T)^{-1} e_1 for each +- pair (Alg. 1).
+ *
+ * Conventions for every entry point:
+ *  - Return value: PISP_OK (0) or one of the PISP_ERR_* codes below;
+ *    pisp_last_error(h) gives a message for the last failing call.
+ *  - Array arguments marked "device" are caller-owned device memory on the
+ *    handle's device; "host" arrays are caller-owned host memory.  The
+ *    library owns only its handle, the symbolic structure and its workspace
+ *    (factors, per-perturbation solutions), all freed by pisp_destroy.
+ *  - Work is enqueued on the stream given to pisp_create and is ordered on
+ *    it; only pisp_get_status and pisp_solve_host synchronise the stream.
+ *  - A handle is not thread-safe; use one handle per host thread.
+ *  - Instances: the matrix is the block diagonal of G independent instances
+ *    of sizes n[0..G-1]; N = sum n[g].  All vectors are row-major [N][R]
+ *    FP64 (R right-hand sides per instance row), values are the CSR values
+ *    of the concatenated instances, in the order of the pattern given to
+ *    pisp_analyze.
+ */
+#ifndef PISP_H
+#define PISP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PISP_OK = 0,
+  PISP_ERR_INVALID_ARG = 1,  /* bad pointer, size or pattern */
+  PISP_ERR_NOT_ANALYZED = 2, /* pisp_analyze has not succeeded yet */
+  PISP_ERR_NOT_FACTORED = 3, /* no successful pisp_factor_perturbed yet */
+  PISP_ERR_ZERO_PIVOT = 4,   /* an exact zero pivot was met (see status) */
+  PISP_ERR_NONFINITE = 5,    /* a pivot became Inf/NaN (see status) */
+  PISP_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
+  PISP_ERR_BOUNDS = 7,       /* an index check failed */
+  PISP_ERR_CUDA = 8,         /* a CUDA runtime call failed */
+  PISP_ERR_OOM = 9,          /* device allocation failed */
+  PISP_ERR_UNSUPPORTED = 10  /* a size outside what the kernels handle */
+};
+
+enum { PISP_FP32 = 32, PISP_FP64 = 64 };
+
+#define PISP_K_MAX 16
+
+typedef struct pisp_handle pisp_handle;
+
+typedef struct pisp_options {
+  int32_t ordering;     /* 0 = minimum degree on A + A^T (default), 1 = as given
+                           (both followed by an elimination-tree postorder) */
+  int32_t relax_small;  /* supernode amalgamation: merge while pivot block <= this (default 8) */
+  double relax_zeros;   /* ... or while explicit zeros <= this fraction (default 0.05) */
+} pisp_options;
+
+typedef struct pisp_stats {
+  int64_t N;             /* total unknowns */
+  int64_t nnzA;          /* entries of A (all instances) */
+  int64_t nnzL;          /* structural strictly-lower entries of L (= those of U) */
+  int64_t nnzF_stored;   /* factor entries stored per perturbation, incl. amalgamation zeros */
+  int64_t front_elems;   /* sum of squared front sizes (workspace per perturbation) */
+  int32_t G;             /* instances */
+  int32_t n_supernodes;
+  int32_t n_levels;      /* height of the assembly forest */
+  int32_t max_front;
+  int32_t etree_height;  /* height of the column elimination tree */
+  int32_t K;             /* perturbations of the last factorisation */
+  int32_t precision;     /* PISP_FP32 / PISP_FP64 of the last factorisation */
+  int32_t gpu_launches;  /* kernels launched by the last factor + solve calls */
+  double flops_factor;   /* per perturbation */
+  double flops_solve;    /* per perturbation per RHS (forward + back) */
+  double analyze_ms;     /* host time of pisp_analyze */
+} pisp_stats;
+
+/* Creates a handle bound to `device` and to `stream` (a cudaStream_t; NULL =
+ * the legacy default stream).  *h receives the handle.  device = -1 makes a
+ * host-only handle: pisp_analyze and the pisp_get_stats / pisp_get_perm /
+ * pisp_get_supernodes queries work without a GPU, numeric calls fail with
+ * PISP_ERR_INVALID_ARG. */
+int pisp_create(pisp_handle** h, int device, void* stream);
+
+/* Frees the handle and all library-owned device memory. */
+int pisp_destroy(pisp_handle* h);
+
+/* Rebinds the handle to another stream of the same device. */
+int pisp_set_stream(pisp_handle* h, void* stream);
+
+/* Message for the last failing call on h (or for a NULL handle). */
+const char* pisp_last_error(const pisp_handle* h);
+
+/* Symbolic phase (host).  Static pivot order of Sec. II-C: a fill-reducing
+ * symmetric ordering of A + A^T, elimination tree, supernodes and the level
+ * schedule of the assembly forest, computed once per pattern and reused by
+ * every factorisation.
+ *   G        number of instances (>= 1)
+ *   n        host [G] instance sizes (>= 0)
+ *   row_ptr  host [N+1] global CSR row pointer, row_ptr[0] = 0
+ *   col_idx  host [nnz] global column indices; each row's columns must lie in
+ *            its own instance's block; duplicates are summed
+ *   opt      host, may be NULL for defaults
+ * The pattern is copied; the host arrays may be freed afterwards. */
+int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row_ptr,
+                 const int32_t* col_idx, const pisp_options* opt);
+
+/* Alg. 1 steps 1-2 (factor part): forms P (A + t_k D) P^T for every shift in
+ * the fixed pivot order and factors all K perturbations pivot-free, level by
+ * level of the assembly forest, all K (and all instances) in the same launches.
+ *   values    device FP64 [nnz], CSR order of the analysed pattern
+ *   D         device FP64 [N], the diagonal perturbation matrix
+ *   t         host FP64 [K], distinct signed shifts (eps * alpha with sign)
+ *   K         1..PISP_K_MAX
+ *   precision PISP_FP32 or PISP_FP64: type in which factors are stored and
+ *             eliminated
+ * Pivot failures do not abort: they are recorded per (instance, k) and read
+ * with pisp_get_status. */
+int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
+                          const double* t, int32_t K, int32_t precision);
+
+/* Alg. 1 steps 2-4 (solve part): for every perturbation k and RHS r solves
+ * (A + t_k D) x_k = b with the pivot-free factors, then writes
+ *     x[i][r] = sum_k w_k x_k[i][r]       (FP64 accumulation)
+ *   b        device FP64 [N][R]
+ *   R        right-hand sides, >= 1
+ *   w        host FP64 [K] weights, or NULL for the weights of pisp_weights(t)
+ *   x        device FP64 [N][R] output (may not alias b)
+ *   sweeps   FP64 residual corrections of each perturbed solution:
+ *            x_k += (L_k U_k)^{-1} (b - (A + t_k D) x_k), computed in FP64
+ *            against the original values; 0 keeps the plain solve.  With FP32
+ *            factors this makes every x_k (and so x) agree with the FP64
+ *            definition to working accuracy.
+ * The per-perturbation solutions are kept in the handle for pisp_combine and
+ * pisp_adjoint. */
+int pisp_solve(pisp_handle* h, const double* b, int32_t R, const double* w, double* x,
+               int32_t sweeps);
+
+/* Re-combines the kept per-perturbation solutions of the last pisp_solve with
+ * other weights (Eq. x_star):  x = sum_k w_k x_k.
+ *   w  host FP64 [K] or NULL for pisp_weights(t);   x device FP64 [N][R]. */
+int pisp_combine(pisp_handle* h, const double* w, double* x);
+
+/* Alg. 1 step 5 turned into a correction: `iters` times
+ *     r = b - A x (FP64, original values);  x += sum_k beta_k (A + t_k D)^{-1} r
+ * with each inner perturbed solve done with `sweeps` residual corrections.
+ * Converges to A^{-1} b when the Neumann series converges (eps * max|alpha| *
+ * rho(A^{-1} D) < 1, Sec. II-B).
+ *   values device FP64 [nnz]; b device FP64 [N][R]; x device FP64 [N][R] in/out;
+ *   R must equal the R of the last pisp_solve. */
+int pisp_refine(pisp_handle* h, const double* b, double* x, int32_t R, int32_t iters,
+                int32_t sweeps);
+
+/* Reverse mode of x = sum_k beta_k (A + t_k D)^{-1} b for the last pisp_solve:
+ *   lambda_k = (A + t_k D)^{-T} g,  grad_b = sum_k beta_k lambda_k,
+ *   grad_values[e] = - sum_k beta_k sum_r lambda_k[i_e][r] x_k[j_e][r]
+ * on A's pattern (D held fixed), using the same factors transposed.
+ *   g           device FP64 [N][R] = dL/dx
+ *   grad_b      device FP64 [N][R] output, or NULL
+ *   grad_values device FP64 [nnz] output, or NULL
+ *   w           host FP64 [K] or NULL (pisp_weights(t)): the combination used
+ *               in the forward pass. */
+int pisp_adjoint(pisp_handle* h, const double* g, const double* w, double* grad_b,
+                 double* grad_values);
+
+/* Host helper: per-solve weights for distinct shifts t[K] (Remark 2 written
+ * for arbitrary shifts): beta_k = prod_{l != k} t_l / (t_l - t_k), the unique
+ * solution of sum_k beta_k t_k^j = [j == 0], j = 0..K-1. */
+int pisp_weights(const double* t, int32_t K, double* beta);
+
+/* Synchronises the stream and copies host [G*K] status codes of the last
+ * factorisation: 0 ok, PISP_ERR_ZERO_PIVOT or PISP_ERR_NONFINITE.  If
+ * first_bad_col is not NULL it receives host [G*K] the first failing
+ * permuted column (or -1).  Returns the worst code. */
+int pisp_get_status(pisp_handle* h, int32_t* per_instance_k, int32_t* first_bad_col);
+
+/* Statistics of the analysed pattern and the last factorisation. */
+int pisp_get_stats(const pisp_handle* h, pisp_stats* out);
+
+/* Copies the symbolic permutation: host perm[N] with perm[new] = old. */
+int pisp_get_perm(const pisp_handle* h, int32_t* perm);
+
+/* Supernode partition for structure checks: host arrays of n_supernodes
+ * entries (c0, c1: permuted column range; ms: update rows) and host rows[]
+ * of sum(ms) entries (the update-row lists, permuted indices).  Any pointer
+ * may be NULL to query sizes through pisp_get_stats only. */
+int pisp_get_supernodes(const pisp_handle* h, int32_t* c0, int32_t* c1, int32_t* ms,
+                        int32_t* rows);
+
+/* Copies the factor of perturbation k of the front owning permuted column
+ * range [c0, c1): host FP64 out[F*F] column-major with L (unit, strictly
+ * lower part), U (upper part incl. the diagonal) of the pivot block, L21 and
+ * U12 in place and the Schur complement in the trailing block.  F is written
+ * to *F_out.  Synchronises the stream.  For factor-level tests. */
+int pisp_get_front(pisp_handle* h, int32_t supernode, int32_t k, double* out, int32_t* F_out);
+
+/* End-to-end convenience: host buffers, copies inside.  Factor + solve +
+ * combine of `values`, `D`, `b` given in host memory; x written to host.
+ * Synchronises the stream. */
+int pisp_solve_host(pisp_handle* h, const double* values_host, const double* D_host,
+                    const double* t, int32_t K, int32_t precision, const double* b_host,
+                    int32_t R, double* x_host, int32_t sweeps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PISP_H */

@@ -1,0 +1,632 @@
+// C ABI of libpisp: handle, symbolic upload, level plans and the host-side
+// orchestration of the level-scheduled factor / solve launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pisp.h"
+#include "pisp_internal.h"
+#include "symbolic.h"
+
+namespace {
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~Buf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  // grow-only device buffer; returns false on allocation failure
+  bool ensure(size_t want) {
+    want = std::max<size_t>(want, 256);
+    if (want <= bytes) return true;
+    release();
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return false;
+    }
+    bytes = want;
+    return true;
+  }
+  template <typename T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+std::string g_last_error;  // for calls without a valid handle
+
+}  // namespace
+
+struct pisp_handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  bool analyzed = false, factored = false, solved = false;
+  pisp::Symbolic sym;
+  double analyze_ms = 0.0;
+  // device symbolic
+  Buf c0, ns, ms, inst, front_off, vec_off, row_off, child_off, child, amap_off, amap_src,
+      amap_dst, rows, emap, perm, iperm, row_inst, row_ptr, col;
+  pisp::SymDev sd{};
+  // level plans (depend on the factor precision)
+  int plan_precision = 0;
+  std::vector<pisp::LevelPlan> plans;
+  std::vector<int32_t> h_small, h_big, h_all;
+  std::vector<pisp::BigFrontHost> h_bigF;
+  Buf d_small, d_big, d_all;
+  // numeric state
+  int32_t K = 0, precision = 0;
+  double t[PISP_K_MAX] = {}, beta[PISP_K_MAX] = {}, w_last[PISP_K_MAX] = {};
+  Buf fronts, vals, D, status, badcol;
+  // solve state
+  int32_t R = 0;
+  Buf V, X, Y, Rk, Lam, X2, rtmp, dtmp;
+  // host-buffer entry point staging
+  Buf in_vals, in_D, in_b, out_x;
+  int launches = 0;
+};
+
+namespace {
+
+int fail(pisp_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg; else g_last_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(h, PISP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+int set_device(pisp_handle* h) {
+  if (h->device < 0)
+    return fail(h, PISP_ERR_INVALID_ARG, "host-only handle (device -1): numeric calls need a device");
+  int cur = -1;
+  CK(cudaGetDevice(&cur));
+  if (cur != h->device) CK(cudaSetDevice(h->device));
+  return PISP_OK;
+}
+
+template <typename T>
+int upload(pisp_handle* h, Buf& b, const std::vector<T>& v) {
+  if (!b.ensure(v.size() * sizeof(T))) return fail(h, PISP_ERR_OOM, "device allocation failed");
+  if (!v.empty()) CK(cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return PISP_OK;
+}
+
+#define TRY(x)            \
+  do {                    \
+    int rc_ = (x);        \
+    if (rc_) return rc_;  \
+  } while (0)
+
+// Groups the supernodes of every level by front size: small fronts into
+// shared-memory classes, big fronts into the blocked path, and all fronts into
+// solve classes.
+int build_plans(pisp_handle* h, int precision) {
+  const pisp::Symbolic& S = h->sym;
+  const int limit = pisp::small_front_limit(precision);
+  const int fcls[5] = {16, 32, 64, 128, limit};
+  const int scls[4] = {32, 128, 512, INT_MAX};
+  h->plans.assign(S.n_levels, pisp::LevelPlan());
+  h->h_small.clear();
+  h->h_big.clear();
+  h->h_all.clear();
+  h->h_bigF.clear();
+  for (int l = 0; l < S.n_levels; ++l) {
+    pisp::LevelPlan& lp = h->plans[l];
+    std::vector<int32_t> lst(S.level_sn.begin() + S.level_off[l],
+                             S.level_sn.begin() + S.level_off[l + 1]);
+    std::sort(lst.begin(), lst.end(), [&](int32_t a, int32_t b) {
+      const int fa = S.sn[a].F(), fb = S.sn[b].F();
+      return fa != fb ? fa < fb : a < b;
+    });
+    int lo = 0;
+    for (int c = 0; c < 5; ++c) {
+      pisp::LevelPlan::Group G{(int64_t)h->h_small.size(), 0, 0};
+      for (int32_t s : lst) {
+        const int F = S.sn[s].F();
+        if (F > lo && F <= fcls[c]) {
+          h->h_small.push_back(s);
+          ++G.count;
+          G.maxF = std::max(G.maxF, F);
+        }
+      }
+      if (G.count) lp.groups[lp.n_groups++] = G;
+      lo = fcls[c];
+    }
+    lp.big_off = (int64_t)h->h_big.size();
+    for (int32_t s : lst) {
+      const int F = S.sn[s].F();
+      if (F > limit) {
+        h->h_big.push_back(s);
+        h->h_bigF.push_back({F, S.sn[s].ns()});
+        ++lp.big_count;
+        lp.big_maxF = std::max(lp.big_maxF, F);
+        lp.big_maxns = std::max(lp.big_maxns, S.sn[s].ns());
+      }
+    }
+    lo = 0;
+    for (int c = 0; c < 4; ++c) {
+      pisp::LevelPlan::Group G{(int64_t)h->h_all.size(), 0, 0};
+      for (int32_t s : lst) {
+        const int F = S.sn[s].F();
+        if (F > lo && F <= scls[c]) {
+          h->h_all.push_back(s);
+          ++G.count;
+          G.maxF = std::max(G.maxF, F);
+        }
+      }
+      if (G.count) lp.sgroups[lp.n_sgroups++] = G;
+      lo = scls[c];
+    }
+  }
+  TRY(upload(h, h->d_small, h->h_small));
+  TRY(upload(h, h->d_big, h->h_big));
+  TRY(upload(h, h->d_all, h->h_all));
+  h->plan_precision = precision;
+  return PISP_OK;
+}
+
+int set_weights(pisp_handle* h, const double* w, double* out) {
+  if (w) {
+    for (int k = 0; k < h->K; ++k) {
+      if (!std::isfinite(w[k])) return fail(h, PISP_ERR_INVALID_ARG, "non-finite weight");
+      out[k] = w[k];
+    }
+  } else {
+    for (int k = 0; k < h->K; ++k) out[k] = h->beta[k];
+  }
+  return PISP_OK;
+}
+
+pisp::Shifts make_shifts(const pisp_handle* h, const double* w) {
+  pisp::Shifts sh{};
+  sh.K = h->K;
+  for (int k = 0; k < h->K; ++k) {
+    sh.t[k] = h->t[k];
+    sh.w[k] = w[k];
+  }
+  return sh;
+}
+
+size_t esize(int precision) { return precision == PISP_FP32 ? 4 : 8; }
+
+int count(pisp_handle* h, int n) {
+  if (n < 0) {
+    cudaError_t e = cudaGetLastError();
+    return fail(h, PISP_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
+  }
+  h->launches += n;
+  return PISP_OK;
+}
+
+// forward + backward over all levels; `rhs` broadcast [N][R] (original order)
+// or per-perturbation [N][K][R] (permuted order); results to `out`
+// (and added to `acc` when given).
+int solve_pass(pisp_handle* h, bool trans, const double* rhs, int rhs_mode, double* out,
+               double* acc, int32_t R) {
+  const int L = h->sym.n_levels;
+  for (int l = 0; l < L; ++l)
+    TRY(count(h, pisp::launch_forward_level(h->precision, trans, h->sd, h->plans[l],
+                                            h->d_all.as<int32_t>(), h->fronts.p, rhs, rhs_mode,
+                                            h->V.p, R, h->K, h->stream)));
+  for (int l = L - 1; l >= 0; --l)
+    TRY(count(h, pisp::launch_backward_level(h->precision, trans, h->sd, h->plans[l],
+                                             h->d_all.as<int32_t>(), h->fronts.p, h->V.p, out,
+                                             acc, R, h->K, h->stream)));
+  return PISP_OK;
+}
+
+// Per-perturbation solves of `rhs` (broadcast, original order) into X_out,
+// followed by `sweeps` FP64 residual corrections of every x_k.
+int solve_core(pisp_handle* h, const double* rhs, double* X_out, int32_t R, int32_t sweeps,
+               const pisp::Shifts& sh) {
+  TRY(solve_pass(h, false, rhs, pisp::RHS_BROADCAST, X_out, nullptr, R));
+  for (int it = 0; it < sweeps; ++it) {
+    TRY(count(h, pisp::launch_residual_per_k(h->sd, h->vals.as<double>(), h->D.as<double>(), sh,
+                                             rhs, X_out, R, h->Rk.as<double>(), h->stream)));
+    TRY(solve_pass(h, false, h->Rk.as<double>(), pisp::RHS_PER_K, h->Y.as<double>(), X_out, R));
+  }
+  return PISP_OK;
+}
+
+int ensure_solve_buffers(pisp_handle* h, int32_t R) {
+  const size_t nkr = (size_t)h->sym.N * h->K * R * sizeof(double);
+  const size_t v = (size_t)h->K * R * h->sym.vec_off.back() * esize(h->precision);
+  if (!h->V.ensure(v) || !h->X.ensure(nkr) || !h->Y.ensure(nkr) || !h->Rk.ensure(nkr))
+    return fail(h, PISP_ERR_OOM, "device allocation failed (solve workspace)");
+  return PISP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pisp_last_error(const pisp_handle* h) {
+  return h ? h->err.c_str() : g_last_error.c_str();
+}
+
+int pisp_create(pisp_handle** out, int device, void* stream) {
+  if (!out) return fail(nullptr, PISP_ERR_INVALID_ARG, "null output pointer");
+  *out = nullptr;
+  if (device != -1) {
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev)
+      return fail(nullptr, PISP_ERR_CUDA, "no such CUDA device");
+  }
+  pisp_handle* h = new pisp_handle();
+  h->device = device;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  *out = h;
+  return PISP_OK;
+}
+
+int pisp_destroy(pisp_handle* h) {
+  if (!h) return PISP_OK;
+  if (h->device < 0) {
+    delete h;
+    return PISP_OK;
+  }
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != h->device) cudaSetDevice(h->device);
+  delete h;
+  if (cur >= 0) cudaSetDevice(cur);
+  return PISP_OK;
+}
+
+int pisp_set_stream(pisp_handle* h, void* stream) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  return PISP_OK;
+}
+
+int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row_ptr,
+                 const int32_t* col_idx, const pisp_options* opt) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  if (G < 1 || !n || !row_ptr) return fail(h, PISP_ERR_INVALID_ARG, "bad instance description");
+  int64_t N = 0;
+  for (int g = 0; g < G; ++g) N += n[g] < 0 ? 0 : n[g];
+  if (row_ptr[N] > 0 && !col_idx) return fail(h, PISP_ERR_INVALID_ARG, "null col_idx");
+  if (h->device >= 0) TRY(set_device(h));
+  pisp::SymbolicOptions so;
+  if (opt) {
+    so.ordering = opt->ordering;
+    if (opt->relax_small >= 0) so.relax_small = opt->relax_small;
+    if (opt->relax_zeros >= 0) so.relax_zeros = opt->relax_zeros;
+  }
+  h->analyzed = h->factored = h->solved = false;
+  h->plan_precision = 0;
+  const auto t0 = std::chrono::steady_clock::now();
+  std::string msg = pisp::analyze(G, n, row_ptr, col_idx, so, h->sym);
+  h->analyze_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (!msg.empty()) return fail(h, PISP_ERR_INVALID_ARG, msg);
+  const pisp::Symbolic& S = h->sym;
+  if (S.max_front > 46340) return fail(h, PISP_ERR_UNSUPPORTED, "front larger than 46340");
+  if (h->device < 0) {  // host-only handle: symbolic structure for inspection only
+    h->analyzed = true;
+    return PISP_OK;
+  }
+  // upload the structure
+  const int nS = (int)S.sn.size();
+  std::vector<int32_t> c0(nS), ns(nS), ms(nS), inst(nS), child_off(nS + 1);
+  std::vector<int64_t> row_off(nS);
+  for (int s = 0; s < nS; ++s) {
+    c0[s] = S.sn[s].c0;
+    ns[s] = S.sn[s].ns();
+    ms[s] = S.sn[s].ms;
+    inst[s] = S.sn[s].instance;
+    row_off[s] = S.sn[s].row_off;
+  }
+  for (int s = 0; s <= nS; ++s) child_off[s] = (int32_t)S.child_off[s];
+  std::vector<int32_t> row_inst(S.N);
+  for (int g = 0; g < G; ++g)
+    for (int64_t i = S.inst_off[g]; i < S.inst_off[g + 1]; ++i) row_inst[i] = g;
+  std::vector<int64_t> rp(row_ptr, row_ptr + S.N + 1);
+  std::vector<int32_t> cl(col_idx ? col_idx : nullptr, col_idx ? col_idx + S.nnzA : nullptr);
+  TRY(upload(h, h->c0, c0));
+  TRY(upload(h, h->ns, ns));
+  TRY(upload(h, h->ms, ms));
+  TRY(upload(h, h->inst, inst));
+  TRY(upload(h, h->front_off, S.front_off));
+  TRY(upload(h, h->vec_off, S.vec_off));
+  TRY(upload(h, h->row_off, row_off));
+  TRY(upload(h, h->child_off, child_off));
+  TRY(upload(h, h->child, S.child));
+  TRY(upload(h, h->amap_off, S.amap_off));
+  TRY(upload(h, h->amap_src, S.amap_src));
+  TRY(upload(h, h->amap_dst, S.amap_dst));
+  TRY(upload(h, h->rows, S.rows));
+  TRY(upload(h, h->emap, S.emap));
+  TRY(upload(h, h->perm, S.perm));
+  TRY(upload(h, h->iperm, S.iperm));
+  TRY(upload(h, h->row_inst, row_inst));
+  TRY(upload(h, h->row_ptr, rp));
+  TRY(upload(h, h->col, cl));
+  pisp::SymDev& sd = h->sd;
+  sd.c0 = h->c0.as<int32_t>();
+  sd.ns = h->ns.as<int32_t>();
+  sd.ms = h->ms.as<int32_t>();
+  sd.inst = h->inst.as<int32_t>();
+  sd.front_off = h->front_off.as<int64_t>();
+  sd.vec_off = h->vec_off.as<int64_t>();
+  sd.row_off = h->row_off.as<int64_t>();
+  sd.child_off = h->child_off.as<int32_t>();
+  sd.child = h->child.as<int32_t>();
+  sd.amap_off = h->amap_off.as<int64_t>();
+  sd.amap_src = h->amap_src.as<int32_t>();
+  sd.amap_dst = h->amap_dst.as<int32_t>();
+  sd.rows = h->rows.as<int32_t>();
+  sd.emap = h->emap.as<int32_t>();
+  sd.perm = h->perm.as<int32_t>();
+  sd.iperm = h->iperm.as<int32_t>();
+  sd.row_inst = h->row_inst.as<int32_t>();
+  sd.row_ptr = h->row_ptr.as<int64_t>();
+  sd.col = h->col.as<int32_t>();
+  sd.N = S.N;
+  sd.S = nS;
+  h->analyzed = true;
+  return PISP_OK;
+}
+
+int pisp_weights(const double* t, int32_t K, double* beta) {
+  if (!t || !beta || K < 1 || K > PISP_K_MAX)
+    return fail(nullptr, PISP_ERR_INVALID_ARG, "pisp_weights: bad arguments");
+  for (int k = 0; k < K; ++k) {
+    if (!std::isfinite(t[k])) return fail(nullptr, PISP_ERR_INVALID_ARG, "non-finite shift");
+    for (int l = 0; l < k; ++l)
+      if (t[l] == t[k]) return fail(nullptr, PISP_ERR_INVALID_ARG, "shifts must be distinct");
+  }
+  // Lagrange basis polynomial of node t_k evaluated at 0: the unique weights
+  // with sum_k beta_k t_k^j = [j == 0] for j < K.
+  for (int k = 0; k < K; ++k) {
+    long double p = 1.0L;
+    for (int l = 0; l < K; ++l)
+      if (l != k) p *= (long double)t[l] / ((long double)t[l] - (long double)t[k]);
+    beta[k] = (double)p;
+  }
+  return PISP_OK;
+}
+
+int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
+                          const double* t, int32_t K, int32_t precision) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  if (!h->analyzed) return fail(h, PISP_ERR_NOT_ANALYZED, "pisp_analyze has not succeeded");
+  if (K < 1 || K > PISP_K_MAX || !t) return fail(h, PISP_ERR_INVALID_ARG, "K must be in 1..16");
+  if (precision != PISP_FP32 && precision != PISP_FP64)
+    return fail(h, PISP_ERR_INVALID_ARG, "precision must be PISP_FP32 or PISP_FP64");
+  const pisp::Symbolic& S = h->sym;
+  if ((S.nnzA > 0 && !values) || (S.N > 0 && !D)) return fail(h, PISP_ERR_INVALID_ARG, "null values or D");
+  if (S.max_front > pisp::max_solve_front(precision) || S.max_front > pisp::max_big_front(precision))
+    return fail(h, PISP_ERR_UNSUPPORTED, "front too large for this precision");
+  double beta[PISP_K_MAX];
+  if (pisp_weights(t, K, beta) != PISP_OK) return fail(h, PISP_ERR_INVALID_ARG, g_last_error);
+  TRY(set_device(h));
+  h->factored = h->solved = false;
+  if (h->plan_precision != precision) TRY(build_plans(h, precision));
+  h->K = K;
+  h->precision = precision;
+  for (int k = 0; k < K; ++k) {
+    h->t[k] = t[k];
+    h->beta[k] = beta[k];
+  }
+  if (!h->fronts.ensure((size_t)K * S.front_elems * esize(precision)) ||
+      !h->vals.ensure(S.nnzA * sizeof(double)) || !h->D.ensure(S.N * sizeof(double)) ||
+      !h->status.ensure((size_t)S.G * K * sizeof(int32_t)) ||
+      !h->badcol.ensure((size_t)S.G * K * sizeof(int32_t)))
+    return fail(h, PISP_ERR_OOM, "device allocation failed (factor workspace)");
+  if (S.nnzA) CK(cudaMemcpyAsync(h->vals.p, values, S.nnzA * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  if (S.N) CK(cudaMemcpyAsync(h->D.p, D, S.N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemsetAsync(h->status.p, 0, (size_t)S.G * K * sizeof(int32_t), h->stream));
+  CK(cudaMemsetAsync(h->badcol.p, 0x7f, (size_t)S.G * K * sizeof(int32_t), h->stream));
+  h->launches = 0;
+  const pisp::Shifts sh = make_shifts(h, h->beta);
+  for (int l = 0; l < S.n_levels; ++l)
+    TRY(count(h, pisp::launch_factor_level(precision, h->sd, h->plans[l], h->d_small.as<int32_t>(),
+                                           h->d_big.as<int32_t>(), h->h_bigF.data(),
+                                           h->vals.as<double>(), h->D.as<double>(), sh,
+                                           h->fronts.p, h->status.as<int32_t>(),
+                                           h->badcol.as<int32_t>(), h->stream)));
+  h->factored = true;
+  return PISP_OK;
+}
+
+int pisp_solve(pisp_handle* h, const double* b, int32_t R, const double* w, double* x,
+               int32_t sweeps) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  if (!h->factored) return fail(h, PISP_ERR_NOT_FACTORED, "no factorisation");
+  if (R < 1 || sweeps < 0) return fail(h, PISP_ERR_INVALID_ARG, "R must be >= 1, sweeps >= 0");
+  if (h->sym.N > 0 && (!b || !x)) return fail(h, PISP_ERR_INVALID_ARG, "null b or x");
+  if (b == x && b) return fail(h, PISP_ERR_INVALID_ARG, "x may not alias b");
+  TRY(set_device(h));
+  TRY(set_weights(h, w, h->w_last));
+  TRY(ensure_solve_buffers(h, R));
+  const pisp::Shifts sh = make_shifts(h, h->w_last);
+  TRY(solve_core(h, b, h->X.as<double>(), R, sweeps, sh));
+  TRY(count(h, pisp::launch_combine(h->sd, h->X.as<double>(), sh, R, x, h->stream)));
+  TRY(count(h, pisp::launch_fill_nan_failed(h->sd, h->status.as<int32_t>(), h->K, R, x, h->stream)));
+  h->R = R;
+  h->solved = true;
+  return PISP_OK;
+}
+
+int pisp_combine(pisp_handle* h, const double* w, double* x) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  if (!h->solved) return fail(h, PISP_ERR_NOT_FACTORED, "pisp_solve has not run");
+  if (h->sym.N > 0 && !x) return fail(h, PISP_ERR_INVALID_ARG, "null x");
+  TRY(set_device(h));
+  double ww[PISP_K_MAX];
+  TRY(set_weights(h, w, ww));
+  const pisp::Shifts sh = make_shifts(h, ww);
+  TRY(count(h, pisp::launch_combine(h->sd, h->X.as<double>(), sh, h->R, x, h->stream)));
+  TRY(count(h, pisp::launch_fill_nan_failed(h->sd, h->status.as<int32_t>(), h->K, h->R, x, h->stream)));
+  return PISP_OK;
+}
+
+int pisp_refine(pisp_handle* h, const double* b, double* x, int32_t R, int32_t iters,
+                int32_t sweeps) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  if (!h->factored) return fail(h, PISP_ERR_NOT_FACTORED, "no factorisation");
+  if (R < 1 || iters < 0 || sweeps < 0) return fail(h, PISP_ERR_INVALID_ARG, "bad R/iters/sweeps");
+  if (h->sym.N > 0 && (!b || !x)) return fail(h, PISP_ERR_INVALID_ARG, "null b or x");
+  TRY(set_device(h));
+  TRY(ensure_solve_buffers(h, R));
+  const size_t nkr = (size_t)h->sym.N * h->K * R * sizeof(double);
+  const size_t nr = (size_t)h->sym.N * R * sizeof(double);
+  if (!h->X2.ensure(nkr) || !h->rtmp.ensure(nr) || !h->dtmp.ensure(nr))
+    return fail(h, PISP_ERR_OOM, "device allocation failed (refine workspace)");
+  const pisp::Shifts sh = make_shifts(h, h->beta);
+  for (int it = 0; it < iters; ++it) {
+    TRY(count(h, pisp::launch_residual(h->sd, h->vals.as<double>(), b, x, R, h->rtmp.as<double>(), h->stream)));
+    TRY(solve_core(h, h->rtmp.as<double>(), h->X2.as<double>(), R, sweeps, sh));
+    TRY(count(h, pisp::launch_combine(h->sd, h->X2.as<double>(), sh, R, h->dtmp.as<double>(), h->stream)));
+    TRY(count(h, pisp::launch_axpy((int64_t)h->sym.N * R, h->dtmp.as<double>(), x, h->stream)));
+  }
+  TRY(count(h, pisp::launch_fill_nan_failed(h->sd, h->status.as<int32_t>(), h->K, R, x, h->stream)));
+  return PISP_OK;
+}
+
+int pisp_adjoint(pisp_handle* h, const double* g, const double* w, double* grad_b,
+                 double* grad_values) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  if (!h->solved) return fail(h, PISP_ERR_NOT_FACTORED, "pisp_solve has not run");
+  if (h->sym.N > 0 && !g) return fail(h, PISP_ERR_INVALID_ARG, "null g");
+  TRY(set_device(h));
+  double ww[PISP_K_MAX];
+  TRY(set_weights(h, w, ww));
+  const int32_t R = h->R;
+  if (!h->Lam.ensure((size_t)h->sym.N * h->K * R * sizeof(double)))
+    return fail(h, PISP_ERR_OOM, "device allocation failed (adjoint workspace)");
+  const pisp::Shifts sh = make_shifts(h, ww);
+  TRY(solve_pass(h, true, g, pisp::RHS_BROADCAST, h->Lam.as<double>(), nullptr, R));
+  if (grad_b) TRY(count(h, pisp::launch_combine(h->sd, h->Lam.as<double>(), sh, R, grad_b, h->stream)));
+  if (grad_values)
+    TRY(count(h, pisp::launch_grad_values(h->sd, h->Lam.as<double>(), h->X.as<double>(), sh, R,
+                                          grad_values, h->stream)));
+  return PISP_OK;
+}
+
+int pisp_get_status(pisp_handle* h, int32_t* per_instance_k, int32_t* first_bad_col) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  if (!h->factored) return fail(h, PISP_ERR_NOT_FACTORED, "no factorisation");
+  TRY(set_device(h));
+  const size_t n = (size_t)h->sym.G * h->K;
+  std::vector<int32_t> st(n), bc(n);
+  CK(cudaMemcpyAsync(st.data(), h->status.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(bc.data(), h->badcol.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  int worst = PISP_OK;
+  for (size_t q = 0; q < n; ++q) {
+    int code = PISP_OK;
+    if (st[q] & 1) code = PISP_ERR_ZERO_PIVOT;
+    else if (st[q] & 2) code = PISP_ERR_NONFINITE;
+    if (per_instance_k) per_instance_k[q] = code;
+    if (first_bad_col) first_bad_col[q] = code ? bc[q] : -1;
+    if (code == PISP_ERR_ZERO_PIVOT || (code && worst == PISP_OK)) worst = code;
+  }
+  return worst;
+}
+
+int pisp_get_stats(const pisp_handle* h, pisp_stats* o) {
+  if (!h || !o) return PISP_ERR_INVALID_ARG;
+  if (!h->analyzed) return PISP_ERR_NOT_ANALYZED;
+  const pisp::Symbolic& S = h->sym;
+  std::memset(o, 0, sizeof(*o));
+  o->N = S.N;
+  o->nnzA = S.nnzA;
+  o->nnzL = S.nnzL;
+  o->nnzF_stored = S.nnzF_stored;
+  o->front_elems = S.front_elems;
+  o->G = S.G;
+  o->n_supernodes = (int32_t)S.sn.size();
+  o->n_levels = S.n_levels;
+  o->max_front = S.max_front;
+  o->etree_height = S.etree_height;
+  o->K = h->K;
+  o->precision = h->precision;
+  o->gpu_launches = h->launches;
+  o->flops_factor = S.flops_factor;
+  o->flops_solve = S.flops_solve;
+  o->analyze_ms = h->analyze_ms;
+  return PISP_OK;
+}
+
+int pisp_get_perm(const pisp_handle* h, int32_t* perm) {
+  if (!h || !perm) return PISP_ERR_INVALID_ARG;
+  if (!h->analyzed) return PISP_ERR_NOT_ANALYZED;
+  std::copy(h->sym.perm.begin(), h->sym.perm.end(), perm);
+  return PISP_OK;
+}
+
+int pisp_get_supernodes(const pisp_handle* h, int32_t* c0, int32_t* c1, int32_t* ms,
+                        int32_t* rows) {
+  if (!h) return PISP_ERR_INVALID_ARG;
+  if (!h->analyzed) return PISP_ERR_NOT_ANALYZED;
+  const auto& S = h->sym;
+  for (size_t s = 0; s < S.sn.size(); ++s) {
+    if (c0) c0[s] = S.sn[s].c0;
+    if (c1) c1[s] = S.sn[s].c1;
+    if (ms) ms[s] = S.sn[s].ms;
+  }
+  if (rows) std::copy(S.rows.begin(), S.rows.end(), rows);
+  return PISP_OK;
+}
+
+int pisp_get_front(pisp_handle* h, int32_t s, int32_t k, double* out, int32_t* F_out) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  if (!h->factored) return fail(h, PISP_ERR_NOT_FACTORED, "no factorisation");
+  if (s < 0 || s >= (int32_t)h->sym.sn.size() || k < 0 || k >= h->K)
+    return fail(h, PISP_ERR_INVALID_ARG, "supernode or k out of range");
+  TRY(set_device(h));
+  const int64_t F = h->sym.sn[s].F();
+  if (F_out) *F_out = (int32_t)F;
+  if (!out) return PISP_OK;
+  const size_t es = esize(h->precision);
+  const size_t off = ((size_t)h->K * h->sym.front_off[s] + (size_t)k * F * F) * es;
+  std::vector<unsigned char> buf(F * F * es);
+  CK(cudaMemcpyAsync(buf.data(), (const char*)h->fronts.p + off, buf.size(), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int64_t q = 0; q < F * F; ++q)
+    out[q] = es == 4 ? (double)reinterpret_cast<const float*>(buf.data())[q]
+                     : reinterpret_cast<const double*>(buf.data())[q];
+  return PISP_OK;
+}
+
+int pisp_solve_host(pisp_handle* h, const double* values_host, const double* D_host,
+                    const double* t, int32_t K, int32_t precision, const double* b_host,
+                    int32_t R, double* x_host, int32_t sweeps) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  if (!h->analyzed) return fail(h, PISP_ERR_NOT_ANALYZED, "pisp_analyze has not succeeded");
+  if (R < 1) return fail(h, PISP_ERR_INVALID_ARG, "R must be >= 1");
+  const pisp::Symbolic& S = h->sym;
+  if ((S.nnzA && !values_host) || (S.N && (!D_host || !b_host || !x_host)))
+    return fail(h, PISP_ERR_INVALID_ARG, "null host buffer");
+  TRY(set_device(h));
+  const size_t nv = S.nnzA * sizeof(double), nd = S.N * sizeof(double);
+  const size_t nb = (size_t)S.N * R * sizeof(double);
+  if (!h->in_vals.ensure(nv) || !h->in_D.ensure(nd) || !h->in_b.ensure(nb) || !h->out_x.ensure(nb))
+    return fail(h, PISP_ERR_OOM, "device allocation failed (host staging)");
+  if (nv) CK(cudaMemcpyAsync(h->in_vals.p, values_host, nv, cudaMemcpyHostToDevice, h->stream));
+  if (nd) CK(cudaMemcpyAsync(h->in_D.p, D_host, nd, cudaMemcpyHostToDevice, h->stream));
+  if (nb) CK(cudaMemcpyAsync(h->in_b.p, b_host, nb, cudaMemcpyHostToDevice, h->stream));
+  TRY(pisp_factor_perturbed(h, h->in_vals.as<double>(), h->in_D.as<double>(), t, K, precision));
+  TRY(pisp_solve(h, h->in_b.as<double>(), R, nullptr, h->out_x.as<double>(), sweeps));
+  if (nb) CK(cudaMemcpyAsync(x_host, h->out_x.p, nb, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return PISP_OK;
+}
+
+}  // extern "C"

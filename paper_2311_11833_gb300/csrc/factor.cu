@@ -1,0 +1,393 @@
+// Pivot-free multifrontal LU of all K perturbed matrices (Alg. 1, steps 1-2).
+//
+// Each supernode s owns a dense front of size F = ns + ms per perturbation k:
+//   1. assembly: P (A + t_k D) P^T entries that belong to s, plus the
+//      Schur complements (update blocks) of its children (extend-add);
+//   2. ns steps of right-looking elimination WITHOUT pivoting: the pivot
+//      order is the static one fixed by the symbolic phase (Sec. II-C).
+// Fronts at the same level of the assembly forest are independent; one
+// launch covers all of them, all K perturbations (grid.y / grid.z) and all
+// instances of a batch.  Small fronts are factored in shared memory, one CTA
+// per (front, k); large fronts use a blocked right-looking scheme in global
+// memory (panel factorisation, row-block triangular solve, tiled update).
+//
+// Storage: front s of perturbation k occupies F*F contiguous elements
+// (column-major) at K*front_off[s] + k*F*F.  After factorisation it holds
+// L11\U11, L21, U12 and the Schur complement F22 that the parent reads.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+
+#include "pisp_internal.h"
+
+namespace pisp {
+namespace {
+
+constexpr int kSmemCap = 225 * 1024;  // dynamic shared memory budget per CTA
+constexpr int kStatusZero = 1;        // status bits: exact zero pivot
+constexpr int kStatusNonfinite = 2;   //              Inf / NaN pivot
+
+template <typename T>
+__device__ __forceinline__ void check_pivot(T piv, const SymDev& sd, int s, int k, int K,
+                                            int col, int32_t* status, int32_t* badcol) {
+  const double p = (double)piv;
+  int code = 0;
+  if (!isfinite(p)) code = kStatusNonfinite;
+  else if (p == 0.0) code = kStatusZero;
+  if (code) {
+    const int g = sd.inst[s];
+    atomicOr(&status[g * K + k], code);
+    atomicMin(&badcol[g * K + k], col);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Small fronts: whole front in shared memory, one CTA per (front, k).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_front_small(SymDev sd, const int32_t* __restrict__ list,
+                              const double* __restrict__ vals, const double* __restrict__ D,
+                              Shifts sh, T* __restrict__ fronts, int32_t* status,
+                              int32_t* badcol) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* f = reinterpret_cast<T*>(smraw);
+  const int s = list[blockIdx.x];
+  const int k = blockIdx.y;
+  const int K = sh.K;
+  const int ns = sd.ns[s], ms = sd.ms[s], F = ns + ms;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int FF = F * F;
+  for (int q = tid; q < FF; q += nt) f[q] = T(0);
+  __syncthreads();
+  // 1a. entries of A owned by this front (duplicates add up)
+  const int64_t a0 = sd.amap_off[s], a1 = sd.amap_off[s + 1];
+  for (int64_t q = a0 + tid; q < a1; q += nt) atomicAdd(&f[sd.amap_dst[q]], (T)vals[sd.amap_src[q]]);
+  // 1b. the perturbation t_k D on the pivot diagonal
+  const double tk = sh.t[k];
+  const int c0 = sd.c0[s];
+  for (int c = tid; c < ns; c += nt) atomicAdd(&f[c * (F + 1)], (T)(tk * D[sd.perm[c0 + c]]));
+  __syncthreads();
+  // 1c. extend-add of the children's Schur complements, one child at a time
+  for (int ci = sd.child_off[s]; ci < sd.child_off[s + 1]; ++ci) {
+    const int c = sd.child[ci];
+    const int cns = sd.ns[c], cms = sd.ms[c], cF = cns + cms;
+    const T* cf = fronts + (int64_t)K * sd.front_off[c] + (int64_t)k * cF * cF;
+    const int32_t* em = sd.emap + sd.row_off[c];
+    const int n2 = cms * cms;
+    for (int q = tid; q < n2; q += nt) {
+      const int a = q % cms, b = q / cms;
+      f[em[a] + em[b] * F] += cf[(cns + a) + (int64_t)(cns + b) * cF];
+    }
+    __syncthreads();
+  }
+  // 2. ns steps of pivot-free elimination
+  for (int p = 0; p < ns; ++p) {
+    const T piv = f[p * (F + 1)];
+    if (tid == 0) check_pivot(piv, sd, s, k, K, c0 + p, status, badcol);
+    const int m = F - p - 1;
+    for (int i = tid; i < m; i += nt) f[(p + 1 + i) + p * F] /= piv;
+    __syncthreads();
+    const int m2 = m * m;
+    for (int q = tid; q < m2; q += nt) {
+      const int i = p + 1 + q % m, j = p + 1 + q / m;
+      f[i + j * F] -= f[i + p * F] * f[p + j * F];
+    }
+    __syncthreads();
+  }
+  T* out = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * FF;
+  for (int q = tid; q < FF; q += nt) out[q] = f[q];
+}
+
+// ---------------------------------------------------------------------------
+// Big fronts, step 1: assembly, one CTA per (column tile, front, k).  Each
+// CTA owns TW columns, so children are added in a fixed order: the result is
+// deterministic.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t lower_bound_col(const int32_t* dst, int64_t lo, int64_t hi,
+                                                   int F, int j) {
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (dst[mid] / F < j) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int lower_bound_i(const int32_t* a, int n, int x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_assemble_big(SymDev sd, const int32_t* __restrict__ list,
+                                                      const double* __restrict__ vals,
+                                                      const double* __restrict__ D, Shifts sh,
+                                                      T* __restrict__ fronts, int TW) {
+  const int s = list[blockIdx.y];
+  const int k = blockIdx.z;
+  const int K = sh.K;
+  const int ns = sd.ns[s], ms = sd.ms[s], F = ns + ms;
+  const int j0 = blockIdx.x * TW;
+  if (j0 >= F) return;
+  const int j1 = min(F, j0 + TW);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  T* f = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * F * F;
+  const int64_t nz = (int64_t)F * (j1 - j0);
+  for (int64_t q = tid; q < nz; q += nt) f[(int64_t)j0 * F + q] = T(0);
+  __syncthreads();
+  const int64_t a0 = sd.amap_off[s], a1 = sd.amap_off[s + 1];
+  const int64_t lo = lower_bound_col(sd.amap_dst, a0, a1, F, j0);
+  const int64_t hi = lower_bound_col(sd.amap_dst, lo, a1, F, j1);
+  for (int64_t q = lo + tid; q < hi; q += nt) atomicAdd(&f[sd.amap_dst[q]], (T)vals[sd.amap_src[q]]);
+  const double tk = sh.t[k];
+  const int c0 = sd.c0[s];
+  for (int c = j0 + tid; c < min(j1, ns); c += nt)
+    atomicAdd(&f[(int64_t)c * (F + 1)], (T)(tk * D[sd.perm[c0 + c]]));
+  __syncthreads();
+  for (int ci = sd.child_off[s]; ci < sd.child_off[s + 1]; ++ci) {
+    const int c = sd.child[ci];
+    const int cns = sd.ns[c], cms = sd.ms[c], cF = cns + cms;
+    const int32_t* em = sd.emap + sd.row_off[c];
+    const int b0 = lower_bound_i(em, cms, j0);
+    const int b1 = lower_bound_i(em, cms, j1);
+    if (b1 > b0) {
+      const T* cf = fronts + (int64_t)K * sd.front_off[c] + (int64_t)k * cF * cF;
+      const int n2 = (b1 - b0) * cms;
+      for (int q = tid; q < n2; q += nt) {
+        const int a = q % cms, b = b0 + q / cms;
+        f[em[a] + (int64_t)em[b] * F] += cf[(cns + a) + (int64_t)(cns + b) * cF];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Big fronts, step 2: factor the panel of columns [p0, p0+NB) (rows p0..F-1)
+// in shared memory, then solve the row block U[p0:p0+NB, p0+NB:F] with the
+// panel's unit lower triangle.  One CTA per (front, k).
+// ---------------------------------------------------------------------------
+template <typename T, int NB>
+__global__ void __launch_bounds__(512) k_panel_big(SymDev sd, const int32_t* __restrict__ list,
+                                                   int K, T* __restrict__ fronts, int p0,
+                                                   int32_t* status, int32_t* badcol) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* P = reinterpret_cast<T*>(smraw);
+  const int s = list[blockIdx.x];
+  const int k = blockIdx.y;
+  const int ns = sd.ns[s], F = ns + sd.ms[s];
+  if (p0 >= ns) return;
+  const int nbe = min(NB, ns - p0);
+  const int Mr = F - p0;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  T* f = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * F * F;
+  const int np = Mr * nbe;
+  for (int q = tid; q < np; q += nt) {
+    const int i = q % Mr, c = q / Mr;
+    P[q] = f[(p0 + i) + (int64_t)(p0 + c) * F];
+  }
+  __syncthreads();
+  const int c0 = sd.c0[s];
+  for (int c = 0; c < nbe; ++c) {
+    const T piv = P[c + c * Mr];
+    if (tid == 0) check_pivot(piv, sd, s, k, K, c0 + p0 + c, status, badcol);
+    for (int i = c + 1 + tid; i < Mr; i += nt) P[i + c * Mr] /= piv;
+    __syncthreads();
+    const int h = Mr - c - 1, w = nbe - c - 1;
+    const int n2 = h * w;
+    for (int q = tid; q < n2; q += nt) {
+      const int i = c + 1 + q % h, cc = c + 1 + q / h;
+      P[i + cc * Mr] -= P[i + c * Mr] * P[c + cc * Mr];
+    }
+    __syncthreads();
+  }
+  for (int q = tid; q < np; q += nt) {
+    const int i = q % Mr, c = q / Mr;
+    f[(p0 + i) + (int64_t)(p0 + c) * F] = P[q];
+  }
+  // row block of U: columns j >= p0 + nbe
+  for (int j = p0 + nbe + tid; j < F; j += nt) {
+    T* col = f + (int64_t)j * F + p0;
+    T u[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) u[q] = (q < nbe) ? col[q] : T(0);
+#pragma unroll
+    for (int q = 1; q < NB; ++q) {
+      T a = u[q];
+#pragma unroll
+      for (int r = 0; r < NB - 1; ++r)
+        if (r < q) a -= P[q + r * Mr] * u[r];
+      u[q] = a;
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+      if (q < nbe) col[q] = u[q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Big fronts, step 3: trailing update C -= L_panel * U_panel on 64x64 tiles.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_update_big(SymDev sd, const int32_t* __restrict__ list,
+                                                    int K, T* __restrict__ fronts, int p0,
+                                                    int nb) {
+  const int s = list[blockIdx.y];
+  const int k = blockIdx.z;
+  const int ns = sd.ns[s], F = ns + sd.ms[s];
+  if (p0 >= ns) return;
+  const int nbe = min(nb, ns - p0);
+  const int t0 = p0 + nbe;
+  const int m = F - t0;
+  if (m <= 0) return;
+  const int tpd = (m + 63) / 64;
+  if ((int)blockIdx.x >= tpd * tpd) return;
+  const int i0 = t0 + (blockIdx.x % tpd) * 64;
+  const int j0 = t0 + (blockIdx.x / tpd) * 64;
+  T* f = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * F * F;
+  __shared__ T As[32][64];
+  __shared__ T Bs[32][65];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 64 * 32; e += 256) {
+    const int r = e % 64, q = e / 64;
+    As[q][r] = (q < nbe && i0 + r < F) ? f[(i0 + r) + (int64_t)(p0 + q) * F] : T(0);
+  }
+  for (int e = tid; e < 64 * 32; e += 256) {
+    const int q = e % 32, c = e / 32;
+    Bs[q][c] = (q < nbe && j0 + c < F) ? f[(p0 + q) + (int64_t)(j0 + c) * F] : T(0);
+  }
+  __syncthreads();
+  const int tx = tid % 16, ty = tid / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int q = 0; q < nbe; ++q) {
+    T a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = As[q][tx + 16 * i];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = Bs[q][ty + 16 * j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = i0 + tx + 16 * i, c = j0 + ty + 16 * j;
+      if (r < F && c < F) f[r + (int64_t)c * F] -= acc[i][j];
+    }
+}
+
+template <typename T>
+int small_threads(int maxF) {
+  if (maxF <= 16) return 64;
+  if (maxF <= 32) return 128;
+  if (maxF <= 96) return 256;
+  return 512;
+}
+
+template <typename T>
+void set_smem_attrs() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_front_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  cudaFuncSetAttribute(k_panel_big<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  cudaFuncSetAttribute(k_panel_big<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  cudaFuncSetAttribute(k_panel_big<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  cudaFuncSetAttribute(k_panel_big<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  done = true;
+}
+
+template <typename T, int NB>
+int run_panels(const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,
+               const BigFrontHost* bh, int K, T* fr, int32_t* status, int32_t* badcol,
+               cudaStream_t st) {
+  int launches = 0;
+  for (int p0 = 0; p0 < lp.big_maxns; p0 += NB) {
+    int maxMr = 0, mmax = 0;
+    for (int b = 0; b < lp.big_count; ++b) {
+      if (p0 >= bh[b].ns) continue;
+      maxMr = std::max(maxMr, bh[b].F - p0);
+      mmax = std::max(mmax, bh[b].F - p0 - std::min(NB, bh[b].ns - p0));
+    }
+    if (maxMr == 0) continue;
+    const size_t smem = (size_t)maxMr * NB * sizeof(T);
+    k_panel_big<T, NB><<<dim3(lp.big_count, K), 512, smem, st>>>(sd, d_big, K, fr, p0, status, badcol);
+    ++launches;
+    if (mmax > 0) {
+      const int tpd = (mmax + 63) / 64;
+      k_update_big<T><<<dim3(tpd * tpd, lp.big_count, K), 256, 0, st>>>(sd, d_big, K, fr, p0, NB);
+      ++launches;
+    }
+  }
+  return launches;
+}
+
+template <typename T>
+int factor_level_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_small,
+                      const int32_t* d_big, const BigFrontHost* bh, const double* vals,
+                      const double* D, const Shifts& sh, void* fronts, int32_t* status,
+                      int32_t* badcol, cudaStream_t st) {
+  set_smem_attrs<T>();
+  T* fr = reinterpret_cast<T*>(fronts);
+  const int K = sh.K;
+  int launches = 0;
+  for (int g = 0; g < lp.n_groups; ++g) {
+    const auto& G = lp.groups[g];
+    if (G.count == 0) continue;
+    const size_t smem = (size_t)G.maxF * G.maxF * sizeof(T);
+    k_front_small<T><<<dim3(G.count, K), small_threads<T>(G.maxF), smem, st>>>(
+        sd, d_small + G.off, vals, D, sh, fr, status, badcol);
+    ++launches;
+  }
+  if (lp.big_count > 0) {
+    const int TW = 32;
+    const int big = lp.big_count;
+    const int32_t* lst = d_big + lp.big_off;
+    k_assemble_big<T><<<dim3((lp.big_maxF + TW - 1) / TW, big, K), 256, 0, st>>>(
+        sd, lst, vals, D, sh, fr, TW);
+    ++launches;
+    const BigFrontHost* b = bh + lp.big_off;
+    if ((size_t)lp.big_maxF * 32 * sizeof(T) <= (size_t)kSmemCap)
+      launches += run_panels<T, 32>(sd, lp, lst, b, K, fr, status, badcol, st);
+    else if ((size_t)lp.big_maxF * 16 * sizeof(T) <= (size_t)kSmemCap)
+      launches += run_panels<T, 16>(sd, lp, lst, b, K, fr, status, badcol, st);
+    else if ((size_t)lp.big_maxF * 8 * sizeof(T) <= (size_t)kSmemCap)
+      launches += run_panels<T, 8>(sd, lp, lst, b, K, fr, status, badcol, st);
+    else
+      launches += run_panels<T, 4>(sd, lp, lst, b, K, fr, status, badcol, st);
+  }
+  if (cudaGetLastError() != cudaSuccess) return -1;
+  return launches;
+}
+
+}  // namespace
+
+int small_front_limit(int precision) { return precision == PISP_FP32 ? 224 : 160; }
+
+int max_big_front(int precision) {
+  return kSmemCap / (4 * (precision == PISP_FP32 ? 4 : 8));
+}
+
+int launch_factor_level(int precision, const SymDev& sd, const LevelPlan& lp,
+                        const int32_t* d_small, const int32_t* d_big,
+                        const BigFrontHost* big_host, const double* vals, const double* D,
+                        const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol,
+                        cudaStream_t st) {
+  if (precision == PISP_FP32)
+    return factor_level_impl<float>(sd, lp, d_small, d_big, big_host, vals, D, sh, fronts,
+                                    status, badcol, st);
+  return factor_level_impl<double>(sd, lp, d_small, d_big, big_host, vals, D, sh, fronts, status,
+                                   badcol, st);
+}
+
+}  // namespace pisp

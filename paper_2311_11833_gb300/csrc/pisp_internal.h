@@ -1,0 +1,103 @@
+// Internal declarations shared by the CUDA translation units of libpisp.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/pisp.h"
+
+namespace pisp {
+
+// Device view of the symbolic structure (all arrays live on the device).
+struct SymDev {
+  const int32_t* c0;         // [S] first permuted column of each supernode
+  const int32_t* ns;         // [S] pivots
+  const int32_t* ms;         // [S] update rows
+  const int32_t* inst;       // [S] instance of each supernode
+  const int64_t* front_off;  // [S+1] prefix of F^2
+  const int64_t* vec_off;    // [S+1] prefix of F
+  const int64_t* row_off;    // [S] offset into rows/emap
+  const int32_t* child_off;  // [S+1]
+  const int32_t* child;      // children, ascending
+  const int64_t* amap_off;   // [S+1]
+  const int32_t* amap_src;   // A value index
+  const int32_t* amap_dst;   // position i + j*F in the front
+  const int32_t* rows;       // update rows (permuted global index)
+  const int32_t* emap;       // position of each update row in the parent front
+  const int32_t* perm;       // [N] perm[new] = old
+  const int32_t* iperm;      // [N] iperm[old] = new
+  const int32_t* row_inst;   // [N] instance of each original row
+  const int64_t* row_ptr;    // [N+1] CSR of A (original order)
+  const int32_t* col;        // [nnz]
+  int64_t N;
+  int32_t S;
+};
+
+// Shifts and combination weights, passed by value to kernels.
+struct Shifts {
+  double t[PISP_K_MAX];
+  double w[PISP_K_MAX];
+  int32_t K;
+};
+
+// One level of the assembly forest, split by front size.
+struct LevelPlan {
+  // small fronts (factored in shared memory), grouped by size class
+  struct Group {
+    int64_t off;    // offset into the device list of small fronts
+    int32_t count;  // fronts in the group
+    int32_t maxF;   // largest front in the group
+  };
+  Group groups[8];
+  int32_t n_groups = 0;
+  // big fronts (blocked factorisation in global memory)
+  int64_t big_off = 0;
+  int32_t big_count = 0;
+  int32_t big_maxF = 0;
+  int32_t big_maxns = 0;
+  // every front of the level for the solves, grouped by size class
+  Group sgroups[8];
+  int32_t n_sgroups = 0;
+};
+
+// Host copies needed to size the launches of the big-front path.
+struct BigFrontHost {
+  int32_t F, ns;
+};
+
+// ---- factor (factor.cu) ----
+// Returns the number of kernels launched (>= 0) or -1 on a launch error.
+int launch_factor_level(int precision, const SymDev& sd, const LevelPlan& lp,
+                        const int32_t* d_small, const int32_t* d_big,
+                        const BigFrontHost* big_host, const double* vals, const double* D,
+                        const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol,
+                        cudaStream_t st);
+// largest front (in elements of the given precision) the shared-memory path takes
+int small_front_limit(int precision);
+// largest front the blocked path can take (its panel must fit in shared memory)
+int max_big_front(int precision);
+// largest front the solve kernels can take
+int max_solve_front(int precision);
+
+// ---- solve (solve.cu) ----
+enum RhsMode { RHS_BROADCAST = 0, RHS_PER_K = 1 };
+int launch_forward_level(int precision, bool trans, const SymDev& sd, const LevelPlan& lp,
+                         const int32_t* d_all, const void* fronts, const double* rhs,
+                         int rhs_mode, void* V, int32_t R, int32_t K, cudaStream_t st);
+int launch_backward_level(int precision, bool trans, const SymDev& sd, const LevelPlan& lp,
+                          const int32_t* d_all, const void* fronts, const void* V, double* out,
+                          double* acc, int32_t R, int32_t K, cudaStream_t st);
+int launch_combine(const SymDev& sd, const double* X, const Shifts& sh, int32_t R, double* x,
+                   cudaStream_t st);
+int launch_residual_per_k(const SymDev& sd, const double* vals, const double* D,
+                          const Shifts& sh, const double* b, const double* X, int32_t R,
+                          double* Rk, cudaStream_t st);
+int launch_residual(const SymDev& sd, const double* vals, const double* b, const double* x,
+                    int32_t R, double* r, cudaStream_t st);
+int launch_axpy(int64_t n, const double* y, double* x, cudaStream_t st);
+int launch_grad_values(const SymDev& sd, const double* Lam, const double* X, const Shifts& sh,
+                       int32_t R, double* grad, cudaStream_t st);
+int launch_fill_nan_failed(const SymDev& sd, const int32_t* status, int32_t K, int32_t R,
+                           double* x, cudaStream_t st);
+
+}  // namespace pisp

@@ -1,0 +1,414 @@
+// Host-side symbolic analysis: ordering, elimination tree, supernodes,
+// assembly-tree levels and the index maps the GPU kernels use.
+//
+// The pivot sequence is fixed here once per sparsity pattern (Sec. II-C:
+// static pivoting "computed once, and perpetually reused"); the perturbation
+// A + t_k D of Sec. III-A changes values only, so every perturbation and
+// every later set of values reuses this structure.
+#include "symbolic.h"
+
+#include <algorithm>
+#include <cstdio>
+#include <numeric>
+#include <set>
+#include <utility>
+
+namespace pisp {
+
+// --------------------------------------------------------------------------
+// Minimum degree on the quotient graph.  Eliminated nodes become "elements"
+// (cliques of their remaining neighbours); a variable's degree is bounded by
+// |Lp| - 1 + |its variable neighbours| + sum over its other elements of the
+// part not already in Lp (an upper bound on the exact external degree, as in
+// approximate minimum degree).  Elements whose variables all lie in the new
+// element are absorbed.  Ties go to the lowest index, so the ordering is
+// deterministic.
+// --------------------------------------------------------------------------
+std::vector<int32_t> minimum_degree(int32_t n, const std::vector<int32_t>& xadj,
+                                    const std::vector<int32_t>& adj) {
+  std::vector<std::vector<int32_t>> vadj(n), eadj(n), le(n);
+  std::vector<char> state(n, 0);  // 0 variable, 1 live element, 2 absorbed
+  std::vector<int32_t> deg(n), mark(n, -1), w(n, 0), wstamp(n, -1);
+  std::set<std::pair<int32_t, int32_t>> pq;
+  for (int32_t i = 0; i < n; ++i) {
+    vadj[i].assign(adj.begin() + xadj[i], adj.begin() + xadj[i + 1]);
+    deg[i] = (int32_t)vadj[i].size();
+    pq.insert({deg[i], i});
+  }
+  std::vector<int32_t> perm;
+  perm.reserve(n);
+  int32_t live = n;
+  std::vector<int32_t> Lp, nv, ne;
+  for (int32_t step = 0; step < n; ++step) {
+    auto it = pq.begin();
+    const int32_t p = it->second;
+    pq.erase(it);
+    perm.push_back(p);
+    --live;
+    Lp.clear();
+    mark[p] = step;
+    for (int32_t v : vadj[p])
+      if (state[v] == 0 && mark[v] != step) { mark[v] = step; Lp.push_back(v); }
+    for (int32_t e : eadj[p]) {
+      if (state[e] != 1) continue;
+      for (int32_t v : le[e])
+        if (state[v] == 0 && mark[v] != step) { mark[v] = step; Lp.push_back(v); }
+      state[e] = 2;
+      std::vector<int32_t>().swap(le[e]);
+    }
+    state[p] = 1;
+    le[p] = Lp;
+    std::vector<int32_t>().swap(vadj[p]);
+    std::vector<int32_t>().swap(eadj[p]);
+    // |Le \ Lp| for every live element touching Lp
+    for (int32_t i : Lp)
+      for (int32_t e : eadj[i]) {
+        if (state[e] != 1 || e == p) continue;
+        if (wstamp[e] != step) { wstamp[e] = step; w[e] = (int32_t)le[e].size(); }
+        --w[e];
+      }
+    for (int32_t i : Lp)
+      for (int32_t e : eadj[i])
+        if (state[e] == 1 && e != p && wstamp[e] == step && w[e] == 0) {
+          state[e] = 2;  // aggressive absorption: Le is inside Lp
+          std::vector<int32_t>().swap(le[e]);
+        }
+    const int32_t lp = (int32_t)Lp.size();
+    for (int32_t i : Lp) {
+      nv.clear();
+      for (int32_t v : vadj[i])
+        if (state[v] == 0 && mark[v] != step) nv.push_back(v);
+      vadj[i].swap(nv);
+      ne.clear();
+      int64_t d = (int64_t)lp - 1 + (int64_t)vadj[i].size();
+      for (int32_t e : eadj[i])
+        if (state[e] == 1 && e != p) {
+          ne.push_back(e);
+          d += (wstamp[e] == step) ? w[e] : (int64_t)le[e].size();
+        }
+      ne.push_back(p);
+      eadj[i].swap(ne);
+      if (d > live - 1) d = live - 1;
+      pq.erase({deg[i], i});
+      deg[i] = (int32_t)d;
+      pq.insert({deg[i], i});
+    }
+  }
+  return perm;
+}
+
+namespace {
+
+struct LocalSn {
+  int32_t c0, c1;
+  std::vector<int32_t> rows;  // local permuted rows > c1-1, ascending
+  int64_t zeros = 0;
+  int32_t level = 0;
+};
+
+int32_t pos_in_front(const Supernode& s, const int32_t* rows, int32_t x) {
+  if (x >= s.c0 && x < s.c1) return x - s.c0;
+  const int32_t* b = rows + s.row_off;
+  const int32_t* e = b + s.ms;
+  const int32_t* f = std::lower_bound(b, e, x);
+  if (f == e || *f != x) return -1;
+  return s.ns() + (int32_t)(f - b);
+}
+
+}  // namespace
+
+std::string analyze(int32_t G, const int32_t* n, const int64_t* row_ptr,
+                    const int32_t* col, const SymbolicOptions& opt, Symbolic& S) {
+  S = Symbolic();
+  if (G < 1) return "G must be >= 1";
+  S.G = G;
+  S.inst_off.assign(G + 1, 0);
+  for (int32_t g = 0; g < G; ++g) {
+    if (n[g] < 0) return "negative instance size";
+    S.inst_off[g + 1] = S.inst_off[g] + n[g];
+  }
+  S.N = S.inst_off[G];
+  if (S.N >= (int64_t)1 << 31) return "too many unknowns (limit 2^31-1)";
+  if (row_ptr[0] != 0) return "row_ptr[0] must be 0";
+  for (int64_t i = 0; i < S.N; ++i)
+    if (row_ptr[i + 1] < row_ptr[i]) return "row_ptr must be non-decreasing";
+  S.nnzA = row_ptr[S.N];
+  if (S.nnzA >= (int64_t)1 << 31) return "too many nonzeros (limit 2^31-1)";
+  S.inst_nnz_off.assign(G + 1, 0);
+  for (int32_t g = 0; g <= G; ++g) S.inst_nnz_off[g] = row_ptr[S.inst_off[g]];
+  S.perm.assign(S.N, 0);
+  S.iperm.assign(S.N, 0);
+  S.col_sn.assign(S.N, -1);
+
+  for (int32_t g = 0; g < G; ++g) {
+    const int32_t ng = n[g];
+    const int64_t off = S.inst_off[g];
+    if (ng == 0) continue;
+    // symmetric adjacency of A + A^T without the diagonal (local indices)
+    std::vector<int32_t> cnt(ng + 1, 0);
+    for (int32_t i = 0; i < ng; ++i)
+      for (int64_t e = row_ptr[off + i]; e < row_ptr[off + i + 1]; ++e) {
+        const int64_t j = (int64_t)col[e] - off;
+        if (j < 0 || j >= ng) return "column index outside its instance block";
+        if (j != i) { ++cnt[i + 1]; ++cnt[j + 1]; }
+      }
+    std::vector<int32_t> xadj(ng + 1, 0);
+    for (int32_t i = 0; i < ng; ++i) xadj[i + 1] = xadj[i] + cnt[i + 1];
+    std::vector<int32_t> adj(xadj[ng]);
+    std::vector<int32_t> fill(xadj.begin(), xadj.end() - 1);
+    for (int32_t i = 0; i < ng; ++i)
+      for (int64_t e = row_ptr[off + i]; e < row_ptr[off + i + 1]; ++e) {
+        const int32_t j = (int32_t)(col[e] - off);
+        if (j != i) { adj[fill[i]++] = j; adj[fill[j]++] = i; }
+      }
+    // sort + unique each list
+    {
+      std::vector<int32_t> x2(ng + 1, 0), a2;
+      a2.reserve(adj.size());
+      for (int32_t i = 0; i < ng; ++i) {
+        auto b = adj.begin() + xadj[i], e = adj.begin() + xadj[i + 1];
+        std::sort(b, e);
+        auto u = std::unique(b, e);
+        a2.insert(a2.end(), b, u);
+        x2[i + 1] = (int32_t)a2.size();
+      }
+      xadj.swap(x2);
+      adj.swap(a2);
+    }
+    std::vector<int32_t> pl;
+    if (opt.ordering == 0) {
+      pl = minimum_degree(ng, xadj, adj);
+    } else {
+      pl.resize(ng);
+      std::iota(pl.begin(), pl.end(), 0);
+    }
+    std::vector<int32_t> ipl(ng);
+    for (int32_t i = 0; i < ng; ++i) ipl[pl[i]] = i;
+    // elimination tree of the permuted pattern
+    std::vector<int32_t> parent(ng, -1), anc(ng, -1);
+    for (int32_t j = 0; j < ng; ++j) {
+      const int32_t o = pl[j];
+      for (int32_t q = xadj[o]; q < xadj[o + 1]; ++q) {
+        int32_t r = ipl[adj[q]];
+        if (r >= j) continue;
+        while (anc[r] != -1 && anc[r] != j) { const int32_t t = anc[r]; anc[r] = j; r = t; }
+        if (anc[r] == -1) { anc[r] = j; parent[r] = j; }
+      }
+    }
+    // postorder (children visited in ascending order)
+    std::vector<int32_t> head(ng, -1), next(ng, -1);
+    for (int32_t j = ng - 1; j >= 0; --j)
+      if (parent[j] >= 0) { next[j] = head[parent[j]]; head[parent[j]] = j; }
+    std::vector<int32_t> post;
+    post.reserve(ng);
+    std::vector<int32_t> stack;
+    for (int32_t r = 0; r < ng; ++r) {
+      if (parent[r] != -1) continue;
+      stack.push_back(r);
+      while (!stack.empty()) {
+        const int32_t v = stack.back();
+        if (head[v] >= 0) {
+          const int32_t c = head[v];
+          head[v] = next[c];
+          stack.push_back(c);
+        } else {
+          stack.pop_back();
+          post.push_back(v);
+        }
+      }
+    }
+    std::vector<int32_t> ipost(ng);
+    for (int32_t k = 0; k < ng; ++k) ipost[post[k]] = k;
+    std::vector<int32_t> pf(ng), ipf(ng), par(ng);
+    for (int32_t k = 0; k < ng; ++k) {
+      pf[k] = pl[post[k]];
+      par[k] = parent[post[k]] >= 0 ? ipost[parent[post[k]]] : -1;
+    }
+    for (int32_t k = 0; k < ng; ++k) ipf[pf[k]] = k;
+    // column structures of L (rows > j) by merging children
+    std::vector<std::vector<int32_t>> st(ng);
+    std::vector<int32_t> mk(ng, -1), height(ng, 0);
+    std::vector<std::vector<int32_t>> kids(ng);
+    for (int32_t j = 0; j < ng; ++j)
+      if (par[j] >= 0) kids[par[j]].push_back(j);
+    for (int32_t j = 0; j < ng; ++j) {
+      std::vector<int32_t>& s = st[j];
+      mk[j] = j;
+      const int32_t o = pf[j];
+      for (int32_t q = xadj[o]; q < xadj[o + 1]; ++q) {
+        const int32_t i = ipf[adj[q]];
+        if (i > j && mk[i] != j) { mk[i] = j; s.push_back(i); }
+      }
+      for (int32_t c : kids[j]) {
+        height[j] = std::max(height[j], height[c] + 1);
+        for (int32_t i : st[c])
+          if (i > j && mk[i] != j) { mk[i] = j; s.push_back(i); }
+      }
+      std::sort(s.begin(), s.end());
+      S.nnzL += (int64_t)s.size();
+      S.etree_height = std::max(S.etree_height, height[j] + 1);
+    }
+    // maximal supernodes: j-1 joins j when struct(j-1) = {j} u struct(j)
+    std::vector<LocalSn> fund;
+    for (int32_t j = 0; j < ng; ++j) {
+      const bool join = j > 0 && par[j - 1] == j && st[j - 1].size() == st[j].size() + 1;
+      if (join) {
+        fund.back().c1 = j + 1;
+      } else {
+        LocalSn s;
+        s.c0 = j;
+        s.c1 = j + 1;
+        fund.push_back(std::move(s));
+      }
+    }
+    for (auto& s : fund) s.rows = st[s.c1 - 1];
+    std::vector<std::vector<int32_t>>().swap(st);
+    // relaxed amalgamation of last-child chains
+    std::vector<LocalSn> merged;
+    for (auto& p : fund) {
+      LocalSn cur = std::move(p);
+      while (!merged.empty()) {
+        LocalSn& c = merged.back();
+        if (c.c1 != cur.c0) break;
+        const int32_t pc = par[c.c1 - 1];
+        if (pc < cur.c0 || pc >= cur.c1) break;
+        const int64_t nsc = c.c1 - c.c0, nsp = cur.c1 - cur.c0;
+        const int64_t msc = (int64_t)c.rows.size(), msp = (int64_t)cur.rows.size();
+        const int64_t z = c.zeros + cur.zeros + nsc * (nsp + msp - msc);
+        const int64_t ns = nsc + nsp;
+        const double E = (double)ns * (ns + 1) / 2.0 + (double)ns * msp;
+        if (!(ns <= opt.relax_small || (double)z <= opt.relax_zeros * E)) break;
+        cur.c0 = c.c0;
+        cur.zeros = z;
+        merged.pop_back();
+      }
+      merged.push_back(std::move(cur));
+    }
+    // supernode parents and levels (children precede parents)
+    std::vector<int32_t> lsn(ng, -1);
+    for (int32_t s = 0; s < (int32_t)merged.size(); ++s)
+      for (int32_t j = merged[s].c0; j < merged[s].c1; ++j) lsn[j] = s;
+    const int32_t base = (int32_t)S.sn.size();
+    for (int32_t s = 0; s < (int32_t)merged.size(); ++s) {
+      const LocalSn& L = merged[s];
+      Supernode sn;
+      sn.c0 = (int32_t)(L.c0 + off);
+      sn.c1 = (int32_t)(L.c1 + off);
+      sn.instance = g;
+      sn.ms = (int32_t)L.rows.size();
+      sn.row_off = (int64_t)S.rows.size();
+      for (int32_t r : L.rows) S.rows.push_back((int32_t)(r + off));
+      const int32_t pc = par[L.c1 - 1];
+      sn.parent = pc >= 0 ? base + lsn[pc] : -1;
+      S.sn.push_back(sn);
+    }
+    for (int32_t s = base; s < (int32_t)S.sn.size(); ++s) {
+      const int32_t p = S.sn[s].parent;
+      if (p >= 0) S.sn[p].level = std::max(S.sn[p].level, S.sn[s].level + 1);
+    }
+    for (int32_t k = 0; k < ng; ++k) {
+      S.perm[off + k] = (int32_t)(pf[k] + off);
+      S.iperm[off + pf[k]] = (int32_t)(k + off);
+      S.col_sn[off + k] = base + lsn[k];
+    }
+  }
+
+  const int32_t nS = (int32_t)S.sn.size();
+  S.emap.assign(S.rows.size(), 0);
+  S.front_off.assign(nS + 1, 0);
+  S.vec_off.assign(nS + 1, 0);
+  S.child_off.assign(nS + 1, 0);
+  for (int32_t s = 0; s < nS; ++s) {
+    const Supernode& sn = S.sn[s];
+    const int64_t F = sn.F(), ns = sn.ns(), ms = sn.ms;
+    S.front_off[s + 1] = S.front_off[s] + F * F;
+    S.vec_off[s + 1] = S.vec_off[s] + F;
+    S.max_front = std::max<int32_t>(S.max_front, (int32_t)F);
+    S.nnzF_stored += ns * (ns + 2 * ms);
+    for (int64_t p = 0; p < ns; ++p) {
+      const double r = (double)(F - p - 1);
+      S.flops_factor += r + 2.0 * r * r;
+    }
+    S.flops_solve += 2.0 * ((double)ns * ns + 2.0 * ns * ms);
+    if (sn.parent >= 0) {
+      ++S.child_off[sn.parent + 1];
+      const Supernode& P = S.sn[sn.parent];
+      for (int32_t a = 0; a < sn.ms; ++a) {
+        const int32_t pos = pos_in_front(P, S.rows.data(), S.rows[sn.row_off + a]);
+        if (pos < 0) return "internal error: child row missing from parent front";
+        S.emap[sn.row_off + a] = pos;
+      }
+    }
+  }
+  S.front_elems = S.front_off[nS];
+  for (int32_t s = 0; s < nS; ++s) S.child_off[s + 1] += S.child_off[s];
+  S.child.assign(S.child_off[nS], 0);
+  {
+    std::vector<int64_t> f(S.child_off.begin(), S.child_off.end() - 1);
+    for (int32_t s = 0; s < nS; ++s)
+      if (S.sn[s].parent >= 0) S.child[f[S.sn[s].parent]++] = s;
+  }
+  // levels
+  int32_t L = 0;
+  for (const auto& sn : S.sn) L = std::max(L, sn.level + 1);
+  S.n_levels = L;
+  S.level_off.assign(L + 1, 0);
+  for (const auto& sn : S.sn) ++S.level_off[sn.level + 1];
+  for (int32_t l = 0; l < L; ++l) S.level_off[l + 1] += S.level_off[l];
+  S.level_sn.assign(nS, 0);
+  {
+    std::vector<int64_t> f(S.level_off.begin(), S.level_off.end() - 1);
+    for (int32_t s = 0; s < nS; ++s) S.level_sn[f[S.sn[s].level]++] = s;
+  }
+  // assembly map: every entry of A lands in the front of the supernode that
+  // owns column min(pi, pj); sorted by (supernode, front column, front row)
+  std::vector<int32_t> dst_of(S.nnzA);
+  std::vector<int32_t> sn_of(S.nnzA);
+  for (int64_t i = 0; i < S.N; ++i) {
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      const int32_t pi = S.iperm[i], pj = S.iperm[col[e]];
+      const int32_t s = S.col_sn[std::min(pi, pj)];
+      const Supernode& sn = S.sn[s];
+      const int32_t r = pos_in_front(sn, S.rows.data(), pi);
+      const int32_t c = pos_in_front(sn, S.rows.data(), pj);
+      if (r < 0 || c < 0) return "internal error: entry outside its front";
+      sn_of[e] = s;
+      dst_of[e] = r + c * sn.F();
+    }
+  }
+  S.amap_off.assign(nS + 1, 0);
+  for (int64_t e = 0; e < S.nnzA; ++e) ++S.amap_off[sn_of[e] + 1];
+  for (int32_t s = 0; s < nS; ++s) S.amap_off[s + 1] += S.amap_off[s];
+  S.amap_src.assign(S.nnzA, 0);
+  S.amap_dst.assign(S.nnzA, 0);
+  {
+    std::vector<int64_t> f(S.amap_off.begin(), S.amap_off.end() - 1);
+    for (int64_t e = 0; e < S.nnzA; ++e) {
+      const int64_t q = f[sn_of[e]]++;
+      S.amap_src[q] = (int32_t)e;
+      S.amap_dst[q] = dst_of[e];
+    }
+    // order each supernode's entries by (column, row) of the front
+    std::vector<std::pair<int32_t, int32_t>> tmp;
+    for (int32_t s = 0; s < nS; ++s) {
+      const int32_t F = S.sn[s].F();
+      tmp.clear();
+      for (int64_t q = S.amap_off[s]; q < S.amap_off[s + 1]; ++q)
+        tmp.push_back({S.amap_dst[q], S.amap_src[q]});
+      std::sort(tmp.begin(), tmp.end(), [F](const std::pair<int32_t, int32_t>& a,
+                                             const std::pair<int32_t, int32_t>& b) {
+        const int32_t ca = a.first / F, cb = b.first / F;
+        if (ca != cb) return ca < cb;
+        if (a.first != b.first) return a.first < b.first;
+        return a.second < b.second;
+      });
+      for (int64_t q = S.amap_off[s], k = 0; q < S.amap_off[s + 1]; ++q, ++k) {
+        S.amap_dst[q] = tmp[k].first;
+        S.amap_src[q] = tmp[k].second;
+      }
+    }
+  }
+  return std::string();
+}
+
+}  // namespace pisp

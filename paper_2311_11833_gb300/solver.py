@@ -1,0 +1,248 @@
+"""Python front end of libpisp: the same calls as include/pisp.h.
+
+PyTorch provides device memory, the stream and autograd; every arithmetic
+step runs in the CUDA library.  There is no CPU fallback: without libpisp.so
+or without a CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import FP32, FP64, PispOptions, PispStats, check
+
+_PREC = {"fp32": FP32, "fp64": FP64, FP32: FP32, FP64: FP64, torch.float32: FP32, torch.float64: FP64}
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _host_f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _dev_f64(t: torch.Tensor, name: str, shape=None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.contiguous()
+
+
+def weights(t: Sequence[float]) -> np.ndarray:
+    """pisp_weights: per-solve weights prod_{l != k} t_l / (t_l - t_k)."""
+    lib = _lib.load()
+    tt = _host_f64(t)
+    out = np.zeros(len(tt))
+    check(lib.pisp_weights(tt.ctypes.data_as(ctypes.c_void_p), len(tt), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+class Solver:
+    """One analysed sparsity pattern (G instances, block diagonal) on one device.
+
+    row_ptr / col describe the concatenated CSR pattern (global indices);
+    `n` is the list of instance sizes (an int for a single instance).
+    """
+
+    def __init__(self, n, row_ptr, col, device: int | None = None, ordering: int = 0,
+                 relax_small: int = -1, relax_zeros: float = -1.0):
+        self._lib = _lib.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libpisp needs a CUDA device")
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        sizes = np.atleast_1d(np.asarray(n, dtype=np.int32))
+        self.G = len(sizes)
+        self.sizes = sizes
+        self.N = int(sizes.sum())
+        rp = np.ascontiguousarray(np.asarray(row_ptr, dtype=np.int64))
+        cl = np.ascontiguousarray(np.asarray(col, dtype=np.int32))
+        if rp.shape != (self.N + 1,):
+            raise ValueError("row_ptr must have N + 1 entries")
+        self.nnz = int(rp[-1])
+        self._row_ptr, self._col = rp, cl
+        h = ctypes.c_void_p()
+        check(self._lib.pisp_create(ctypes.byref(h), self.device, None))
+        self._h = h
+        opt = PispOptions(ordering, relax_small, relax_zeros)
+        check(self._lib.pisp_analyze(self._h, self.G, sizes.ctypes.data_as(ctypes.c_void_p),
+                                     rp.ctypes.data_as(ctypes.c_void_p),
+                                     cl.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opt)), self._h)
+        self.K = 0
+        self.t = None
+        self.precision = None
+        self.R = 0
+
+    # ------------------------------------------------------------- plumbing --
+    def _sync_stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        check(self._lib.pisp_set_stream(self._h, ctypes.c_void_p(s)), self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pisp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ ABI --
+    def factor(self, values: torch.Tensor, D: torch.Tensor, t: Sequence[float], precision="fp64"):
+        """pisp_factor_perturbed: pivot-free LU of P (A + t_k D) P^T for all k."""
+        values = _dev_f64(values, "values", (self.nnz,))
+        D = _dev_f64(D, "D", (self.N,))
+        tt = _host_f64(t)
+        prec = _PREC[precision]
+        self._sync_stream()
+        check(self._lib.pisp_factor_perturbed(self._h, _ptr(values), _ptr(D),
+                                              tt.ctypes.data_as(ctypes.c_void_p), len(tt), prec), self._h)
+        self.K, self.t, self.precision = len(tt), tt, prec
+        return self
+
+    def solve(self, b: torch.Tensor, weights=None, sweeps: int = 0, out: torch.Tensor | None = None):
+        """pisp_solve: x = sum_k w_k (A + t_k D)^{-1} b; b is [N] or [N, R]."""
+        vec = b.dim() == 1
+        b2 = _dev_f64(b, "b").reshape(self.N, -1)
+        R = b2.shape[1]
+        x = out if out is not None else torch.empty_like(b2)
+        w = None if weights is None else _host_f64(weights)
+        self._sync_stream()
+        check(self._lib.pisp_solve(self._h, _ptr(b2), R,
+                                   None if w is None else w.ctypes.data_as(ctypes.c_void_p),
+                                   _ptr(x), int(sweeps)), self._h)
+        self.R = R
+        return x.reshape(-1) if vec else x
+
+    def combine(self, weights=None, out: torch.Tensor | None = None):
+        """pisp_combine: re-weights the kept per-perturbation solutions."""
+        x = out if out is not None else torch.empty((self.N, self.R), dtype=torch.float64,
+                                                    device=f"cuda:{self.device}")
+        w = None if weights is None else _host_f64(weights)
+        self._sync_stream()
+        check(self._lib.pisp_combine(self._h, None if w is None else w.ctypes.data_as(ctypes.c_void_p),
+                                     _ptr(x)), self._h)
+        return x
+
+    def refine(self, b: torch.Tensor, x: torch.Tensor, iters: int = 1, sweeps: int = 0):
+        """pisp_refine: x += sum_k beta_k (A + t_k D)^{-1} (b - A x), in place."""
+        vec = b.dim() == 1
+        b2 = _dev_f64(b, "b").reshape(self.N, -1)
+        if not x.is_contiguous():
+            raise ValueError("x must be contiguous")
+        x2 = x.reshape(self.N, -1)
+        self._sync_stream()
+        check(self._lib.pisp_refine(self._h, _ptr(b2), _ptr(x2), b2.shape[1], int(iters), int(sweeps)),
+              self._h)
+        return x.reshape(-1) if vec else x
+
+    def adjoint(self, g: torch.Tensor, weights=None, need_b=True, need_values=True):
+        """pisp_adjoint: (dL/db, dL/dvalues) for dL/dx = g of the last solve."""
+        g2 = _dev_f64(g, "g").reshape(self.N, -1)
+        gb = torch.empty_like(g2) if need_b else None
+        gv = torch.empty(self.nnz, dtype=torch.float64, device=g2.device) if need_values else None
+        w = None if weights is None else _host_f64(weights)
+        self._sync_stream()
+        check(self._lib.pisp_adjoint(self._h, _ptr(g2), None if w is None else w.ctypes.data_as(ctypes.c_void_p),
+                                     _ptr(gb), _ptr(gv)), self._h)
+        if gb is not None and g.dim() == 1:
+            gb = gb.reshape(-1)
+        return gb, gv
+
+    def status(self):
+        """pisp_get_status: (worst code, per-(instance, k) codes, first failing columns)."""
+        st = np.zeros(self.G * self.K, dtype=np.int32)
+        bc = np.zeros(self.G * self.K, dtype=np.int32)
+        self._sync_stream()
+        worst = self._lib.pisp_get_status(self._h, st.ctypes.data_as(ctypes.c_void_p),
+                                          bc.ctypes.data_as(ctypes.c_void_p))
+        if worst not in (0, 4, 5):
+            check(worst, self._h)
+        return worst, st.reshape(self.G, self.K), bc.reshape(self.G, self.K)
+
+    def stats(self) -> dict:
+        s = PispStats()
+        check(self._lib.pisp_get_stats(self._h, ctypes.byref(s)), self._h)
+        return s.as_dict()
+
+    def perm(self) -> np.ndarray:
+        p = np.zeros(self.N, dtype=np.int32)
+        check(self._lib.pisp_get_perm(self._h, p.ctypes.data_as(ctypes.c_void_p)), self._h)
+        return p
+
+    def supernodes(self):
+        S = self.stats()["n_supernodes"]
+        c0 = np.zeros(S, np.int32)
+        c1 = np.zeros(S, np.int32)
+        ms = np.zeros(S, np.int32)
+        check(self._lib.pisp_get_supernodes(self._h, c0.ctypes.data_as(ctypes.c_void_p),
+                                            c1.ctypes.data_as(ctypes.c_void_p),
+                                            ms.ctypes.data_as(ctypes.c_void_p), None), self._h)
+        rows = np.zeros(int(ms.sum()), np.int32)
+        check(self._lib.pisp_get_supernodes(self._h, None, None, None,
+                                            rows.ctypes.data_as(ctypes.c_void_p)), self._h)
+        return c0, c1, ms, rows
+
+    def front(self, s: int, k: int) -> np.ndarray:
+        F = ctypes.c_int32()
+        check(self._lib.pisp_get_front(self._h, s, k, None, ctypes.byref(F)), self._h)
+        out = np.zeros(F.value * F.value)
+        self._sync_stream()
+        check(self._lib.pisp_get_front(self._h, s, k, out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(F)),
+              self._h)
+        return out.reshape(F.value, F.value, order="F")
+
+    def solve_host(self, values: np.ndarray, D: np.ndarray, t, b: np.ndarray, precision="fp64",
+                   sweeps: int = 0, out: np.ndarray | None = None) -> np.ndarray:
+        """pisp_solve_host: end to end from host buffers (copies included)."""
+        vals = _host_f64(values)
+        DD = _host_f64(D)
+        tt = _host_f64(t)
+        bb = _host_f64(b).reshape(self.N, -1)
+        x = out if out is not None else np.empty_like(bb)
+        self._sync_stream()
+        check(self._lib.pisp_solve_host(self._h, vals.ctypes.data_as(ctypes.c_void_p),
+                                        DD.ctypes.data_as(ctypes.c_void_p),
+                                        tt.ctypes.data_as(ctypes.c_void_p), len(tt), _PREC[precision],
+                                        bb.ctypes.data_as(ctypes.c_void_p), bb.shape[1],
+                                        x.ctypes.data_as(ctypes.c_void_p), int(sweeps)), self._h)
+        self.K, self.t, self.precision, self.R = len(tt), tt, _PREC[precision], bb.shape[1]
+        return x
+
+
+class _PerturbedSolve(torch.autograd.Function):
+    """x = sum_k beta_k (A + t_k D)^{-1} b with gradients for values and b.
+
+    The backward pass reuses the K factors of the forward pass transposed
+    (pisp_adjoint); D and t are held fixed.
+    """
+
+    @staticmethod
+    def forward(ctx, values, b, solver, D, t, precision, sweeps):
+        solver.factor(values.detach(), D, t, precision)
+        x = solver.solve(b.detach(), sweeps=sweeps)
+        ctx.solver = solver
+        ctx.vec = b.dim() == 1
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        s = ctx.solver
+        need_v, need_b = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        gb, gv = s.adjoint(gx.contiguous(), need_b=need_b, need_values=need_v)
+        return gv, gb, None, None, None, None, None
+
+
+def solve(solver: Solver, values: torch.Tensor, b: torch.Tensor, D: torch.Tensor, t, precision="fp64",
+          sweeps: int = 0) -> torch.Tensor:
+    """Differentiable perturbed solve + combine (autograd through pisp_adjoint)."""
+    return _PerturbedSolve.apply(values, b, solver, D, t, precision, sweeps)

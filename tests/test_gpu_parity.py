@@ -1,0 +1,337 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances: FP64 factors must match the oracle's x_hat (same A, D, t, beta)
+to a relative error <= 1e-10 per right-hand side.  FP32 factors with FP64
+residual sweeps must reach the same bound; without sweeps they are checked
+against a bound derived from single-precision rounding (see below).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import pfgen
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def pisp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2311_11833_gb300 as p
+    return p
+
+
+def _dev(a):
+    import torch
+    return torch.tensor(np.asarray(a), dtype=torch.float64, device="cuda")
+
+
+def _concat(insts):
+    rp, cols, vals, off = [0], [], [], 0
+    for I in insts:
+        rp.extend((I.row_ptr[1:] + rp[-1]).tolist())
+        cols.append(I.col + off)
+        vals.append(I.val)
+        off += I.n
+    return ([I.n for I in insts], np.array(rp, np.int64), np.concatenate(cols).astype(np.int32),
+            np.concatenate(vals), np.concatenate([I.D for I in insts]))
+
+
+def _solver(pisp, insts, **kw):
+    sizes, rp, col, val, D = _concat(insts)
+    return pisp.Solver(sizes, rp, col, **kw), val, D
+
+
+def _oracle_xhat(inst, t, b):
+    return oracle.x_hat(oracle.to_scipy(inst), inst.D, t, b)
+
+
+def _maxrel(x, ref):
+    return float(np.max(oracle.rel_err(x, ref)))
+
+
+# ------------------------------------------------------------------ FP64 --
+def test_plain_fp64_matches_oracle(pisp):
+    inst = pfgen.make_instance("plain")
+    t = pfgen.symmetric_shifts(4)
+    b = pfgen.rhs(inst.n, 1, 1)
+    s, val, D = _solver(pisp, [inst])
+    s.factor(_dev(val), _dev(D), t, "fp64")
+    x = s.solve(_dev(b)).cpu().numpy()
+    assert _maxrel(x, _oracle_xhat(inst, t, b)) <= TOL64
+    worst, st, _ = s.status()
+    assert worst == 0 and not st.any()
+
+
+def test_plain_literal_one_sided_shifts(pisp):
+    inst = pfgen.make_instance("plain")
+    t = pfgen.one_sided_shifts(4)
+    b = pfgen.rhs(inst.n, 2, 2)
+    s, val, D = _solver(pisp, [inst])
+    s.factor(_dev(val), _dev(D), t, "fp64")
+    x = s.solve(_dev(b)).cpu().numpy()
+    assert _maxrel(x, _oracle_xhat(inst, t, b)) <= TOL64
+
+
+@pytest.mark.parametrize("n,K,R,density", [(1, 1, 1, 1.0), (2, 2, 3, 1.0), (7, 3, 1, 0.4),
+                                           (33, 4, 5, 0.15), (100, 6, 17, 0.05),
+                                           (257, 8, 2, 0.02), (64, 16, 1, 0.1)])
+def test_random_systems_fp64(pisp, n, K, R, density):
+    inst = pfgen.random_sparse(n, density, seed=10 + n)
+    t = pfgen.symmetric_shifts(K, 0.01) if K % 2 == 0 else pfgen.one_sided_shifts(K, 0.01)
+    b = pfgen.rhs(n, R, n)
+    s, val, D = _solver(pisp, [inst])
+    s.factor(_dev(val), _dev(D), t, "fp64")
+    x = s.solve(_dev(b)).cpu().numpy()
+    assert _maxrel(x, _oracle_xhat(inst, t, b)) <= TOL64
+
+
+def test_factor_entries_match_pivot_free_lu(pisp):
+    """The pivot-free factor is unique: front entries equal dense Doolittle's."""
+    inst = pfgen.make_instance("plain")
+    t = pfgen.symmetric_shifts(4)
+    s, val, D = _solver(pisp, [inst])
+    s.factor(_dev(val), _dev(D), t, "fp64")
+    perm = s.perm()
+    c0, c1, ms, rows = s.supernodes()
+    A = oracle.to_dense(inst)
+    roff = np.concatenate([[0], np.cumsum(ms)])
+    for k in (0, 3):
+        L, U = oracle.pivot_free_lu(A, inst.D, t[k], perm)
+        scale = np.abs(U).max()
+        for sn in range(len(c0)):
+            idx = np.concatenate([np.arange(c0[sn], c1[sn]), rows[roff[sn]:roff[sn + 1]]])
+            ns = c1[sn] - c0[sn]
+            Fr = s.front(sn, k)
+            LU = np.tril(L[np.ix_(idx, idx[:ns])], -1) + np.triu(U[np.ix_(idx, idx[:ns])])
+            np.testing.assert_allclose(Fr[:, :ns], LU, rtol=0, atol=1e-12 * scale)
+            np.testing.assert_allclose(Fr[:ns, ns:], U[np.ix_(idx[:ns], idx[ns:])], rtol=0,
+                                       atol=1e-12 * scale)
+
+
+def test_precision_config_fp64_big_fronts(pisp):
+    """2000-bus grid: its top fronts exceed the shared-memory path (blocked path)."""
+    inst = pfgen.make_instance("precision")
+    t = pfgen.symmetric_shifts(6)
+    b = pfgen.rhs(inst.n, 3, 2)
+    s, val, D = _solver(pisp, [inst])
+    assert s.stats()["max_front"] > 160
+    s.factor(_dev(val), _dev(D), t, "fp64")
+    x = s.solve(_dev(b)).cpu().numpy()
+    assert _maxrel(x, _oracle_xhat(inst, t, b)) <= TOL64
+
+
+def test_batched_uneven_instances_fp64(pisp):
+    insts = [pfgen.make_instance("batching", g) for g in (1, 3, 5, 9, 13)]
+    insts.append(pfgen.random_sparse(5, 0.5, seed=3))
+    t = pfgen.symmetric_shifts(4)
+    R = 3
+    s, val, D = _solver(pisp, insts)
+    s.factor(_dev(val), _dev(D), t, "fp64")
+    N = sum(I.n for I in insts)
+    b = pfgen.rhs(N, R, 5)
+    x = s.solve(_dev(b)).cpu().numpy()
+    off = 0
+    for I in insts:
+        ref = _oracle_xhat(I, t, b[off:off + I.n])
+        assert _maxrel(x[off:off + I.n], ref) <= TOL64
+        off += I.n
+
+
+# ------------------------------------------------------------------ FP32 --
+def test_fp32_without_sweeps_within_single_precision_bound(pisp):
+    """Plain FP32 solve: error bounded by c * n * u32 * kappa-ish growth."""
+    inst = pfgen.make_instance("plain")
+    t = pfgen.symmetric_shifts(4)
+    b = pfgen.rhs(inst.n, 4, 3)
+    s, val, D = _solver(pisp, [inst])
+    s.factor(_dev(val), _dev(D), t, "fp32")
+    x = s.solve(_dev(b)).cpu().numpy()
+    err = _maxrel(x, _oracle_xhat(inst, t, b))
+    # sum |beta| * kappa_1(A + tD) * u32 with kappa_1 ~ 1.5e4 here: ~5e-3 bound
+    assert 1e-12 < err < 5e-3
+
+
+@pytest.mark.parametrize("cfg,sweeps", [("plain", 3), ("precision", 3)])
+def test_fp32_with_sweeps_reaches_fp64(pisp, cfg, sweeps):
+    inst = pfgen.make_instance(cfg)
+    K = pfgen.CONFIGS[cfg]["K"]
+    t = pfgen.symmetric_shifts(K)
+    b = pfgen.rhs(inst.n, 4, 4)
+    s, val, D = _solver(pisp, [inst])
+    s.factor(_dev(val), _dev(D), t, "fp32")
+    x = s.solve(_dev(b), sweeps=sweeps).cpu().numpy()
+    assert _maxrel(x, _oracle_xhat(inst, t, b)) <= TOL64
+
+
+# ------------------------------------------------------- refine / combine --
+def test_refine_matches_oracle(pisp):
+    inst = pfgen.make_instance("plain")
+    t = pfgen.symmetric_shifts(4)
+    b = pfgen.rhs(inst.n, 2, 6)
+    s, val, D = _solver(pisp, [inst])
+    s.factor(_dev(val), _dev(D), t, "fp64")
+    bt = _dev(b)
+    x = s.solve(bt)
+    s.refine(bt, x, iters=2)
+    A = oracle.to_scipy(inst)
+    ref = oracle.refine(A, inst.D, t, b, oracle.x_hat(A, inst.D, t, b), iters=2)
+    assert _maxrel(x.cpu().numpy(), ref) <= TOL64
+    # inside the convergence region the correction approaches x*
+    xs = oracle.x_star(A, b)
+    assert _maxrel(x.cpu().numpy(), xs) < 0.1 * _maxrel(oracle.x_hat(A, inst.D, t, b), xs)
+
+
+def test_combine_reweights(pisp):
+    inst = pfgen.random_sparse(40, 0.1, seed=8)
+    t = pfgen.symmetric_shifts(4)
+    b = pfgen.rhs(40, 2, 8)
+    s, val, D = _solver(pisp, [inst])
+    s.factor(_dev(val), _dev(D), t, "fp64")
+    s.solve(_dev(b))
+    w = np.array([1.0, 0.0, 0.0, 0.0])
+    x0 = s.combine(w).cpu().numpy()
+    ref = oracle.perturbed_solutions(oracle.to_scipy(inst), inst.D, t[:1], b)[0]
+    assert _maxrel(x0, ref) <= TOL64
+
+
+def test_solve_host_matches_device(pisp):
+    inst = pfgen.make_instance("plain")
+    t = pfgen.symmetric_shifts(4)
+    b = pfgen.rhs(inst.n, 3, 9)
+    s, val, D = _solver(pisp, [inst])
+    xh = s.solve_host(val, D, t, b, "fp64")
+    assert _maxrel(xh, _oracle_xhat(inst, t, b)) <= TOL64
+
+
+# ------------------------------------------------------------- adjoint --
+def test_adjoint_matches_oracle(pisp):
+    inst = pfgen.make_instance("plain")
+    t = pfgen.symmetric_shifts(4)
+    R = 3
+    b = pfgen.rhs(inst.n, R, 10)
+    W = pfgen.rhs(inst.n, R, 11)
+    s, val, D = _solver(pisp, [inst])
+    s.factor(_dev(val), _dev(D), t, "fp64")
+    s.solve(_dev(b))
+    gb, gv = s.adjoint(_dev(W))
+    rb, rv = oracle.adjoint(oracle.to_scipy(inst), inst.D, t, b, W)
+    assert _maxrel(gb.cpu().numpy(), rb) <= TOL64
+    assert np.linalg.norm(gv.cpu().numpy() - rv) <= TOL64 * np.linalg.norm(rv)
+
+
+def test_autograd_finite_differences(pisp):
+    """dL/dvalues and dL/db of L = sum(w * x) against central differences of the GPU forward."""
+    import torch
+    inst = pfgen.random_sparse(30, 0.15, seed=12)
+    t = pfgen.symmetric_shifts(4)
+    R = 2
+    s, val, D = _solver(pisp, [inst])
+    vals = _dev(val).requires_grad_(True)
+    b = _dev(pfgen.rhs(30, R, 12)).requires_grad_(True)
+    Dt = _dev(D)
+    w = _dev(pfgen.rhs(30, R, 13))
+    x = pisp.solve(s, vals, b, Dt, t, "fp64")
+    (x * w).sum().backward()
+    gv, gb = vals.grad.cpu().numpy(), b.grad.cpu().numpy()
+
+    def L(v, bb):
+        with torch.no_grad():
+            return float((pisp.solve(s, v, bb, Dt, t, "fp64") * w).sum())
+
+    h = 1e-6
+    rng = np.random.default_rng(0)
+    for e in rng.choice(len(val), 6, replace=False):
+        vp, vm = vals.detach().clone(), vals.detach().clone()
+        step = h * max(1.0, abs(val[e]))
+        vp[e] += step
+        vm[e] -= step
+        fd = (L(vp, b.detach()) - L(vm, b.detach())) / (2 * step)
+        assert fd == pytest.approx(gv[e], rel=1e-5, abs=1e-8)
+    for i, r in ((0, 0), (17, 1)):
+        bp, bm = b.detach().clone(), b.detach().clone()
+        bp[i, r] += h
+        bm[i, r] -= h
+        fd = (L(vals.detach(), bp) - L(vals.detach(), bm)) / (2 * h)
+        assert fd == pytest.approx(gb[i, r], rel=1e-5, abs=1e-8)
+
+
+# ------------------------------------------------------------- failures --
+def test_zero_pivot_status_and_nan_isolation(pisp):
+    """An exact zero pivot in one perturbation of one instance is reported and isolated."""
+    n = 6
+    a = np.array([2.0, 3.0, -1.5, 4.0, 2.5, 1.0])
+    bad = pfgen.Instance(n=n, row_ptr=np.arange(n + 1, dtype=np.int64), col=np.arange(n, dtype=np.int32),
+                         val=a.copy(), D=np.ones(n), meta={})
+    good = pfgen.random_sparse(9, 0.3, seed=4)
+    t = np.array([0.5, -2.0])           # a[0] + t[1] * D[0] == 0 exactly
+    s, val, D = _solver(pisp, [bad, good])
+    s.factor(_dev(val), _dev(D), t, "fp64")
+    worst, st, col = s.status()
+    assert worst == 4
+    assert st[0, 1] == 4 and st[0, 0] == 0 and not st[1].any()
+    perm = s.perm()
+    assert perm[col[0, 1]] == 0
+    b = pfgen.rhs(n + 9, 1, 1)
+    x = s.solve(_dev(b)).cpu().numpy()
+    assert np.all(np.isnan(x[:n])) and np.all(np.isfinite(x[n:]))
+    assert _maxrel(x[n:], _oracle_xhat(good, t, b[n:])) <= TOL64
+
+
+def test_nonfinite_values_reported(pisp):
+    inst = pfgen.random_sparse(12, 0.3, seed=5)
+    val = inst.val.copy()
+    val[3] = np.nan
+    s, _, D = _solver(pisp, [inst])
+    s.factor(_dev(val), _dev(D), pfgen.symmetric_shifts(2), "fp64")
+    worst, st, _ = s.status()
+    assert worst == 5 and np.all(st == 5)
+
+
+def test_invalid_arguments_raise(pisp):
+    inst = pfgen.random_sparse(5, 0.5, seed=1)
+    s, val, D = _solver(pisp, [inst])
+    with pytest.raises(pisp.PispError):
+        s.solve(_dev(np.ones(5)))                    # before factor
+    with pytest.raises(pisp.PispError):
+        s.factor(_dev(val), _dev(D), [0.1, 0.1], "fp64")   # repeated shift
+    with pytest.raises(pisp.PispError):
+        s.factor(_dev(val), _dev(D), np.linspace(0.01, 0.2, 17), "fp64")  # K > 16
+
+
+# ------------------------------------------------------- full-size samples --
+def test_full_precision_config_fp32_sweeps_all_rhs(pisp):
+    """The 2000-bus workload at its full size (K = 6, R = 16), FP32 factors."""
+    inst = pfgen.make_instance("precision")
+    c = pfgen.CONFIGS["precision"]
+    t = pfgen.symmetric_shifts(c["K"])
+    b = pfgen.rhs(inst.n, c["R"], 1)
+    s, val, D = _solver(pisp, [inst])
+    s.factor(_dev(val), _dev(D), t, "fp32")
+    x = s.solve(_dev(b), sweeps=3).cpu().numpy()
+    err = oracle.rel_err(x, _oracle_xhat(inst, t, b))
+    assert err.shape == (c["R"],) and np.all(err <= TOL64)
+
+
+def test_full_batching_config_sampled(pisp):
+    """All 256 grids in one factor/solve; sampled instances checked against the oracle."""
+    c = pfgen.CONFIGS["batching"]
+    insts = [pfgen.make_instance("batching", g) for g in range(c["G"])]
+    t = pfgen.symmetric_shifts(c["K"])
+    s, val, D = _solver(pisp, insts)
+    s.factor(_dev(val), _dev(D), t, "fp32")
+    N = sum(I.n for I in insts)
+    b = pfgen.rhs(N, c["R"], 3)
+    x = s.solve(_dev(b), sweeps=3).cpu().numpy()
+    offs = np.concatenate([[0], np.cumsum([I.n for I in insts])])
+    for g in (0, 7, 100, 255):
+        I = insts[g]
+        sl = slice(offs[g], offs[g + 1])
+        assert _maxrel(x[sl], _oracle_xhat(I, t, b[sl])) <= TOL64
+    assert np.all(np.isfinite(x))
