@@ -1,0 +1,463 @@
+#!/usr/bin/env python
+"""Throughput benchmark: combined solves/s of perturbation-induced static pivoting.
+
+A step is one pass of the whole hot path over one batch of synthetic
+power-flow Jacobians already resident in HBM: perturb + pivot-free factor of
+all K shifted matrices, forward/backward solves of R right-hand sides, FP64
+residual sweeps (FP32 factors) and the expansion-weighted FP64 combine.  The
+metric counts combined solutions x_hat (instances x RHS) per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...    # the CPU oracle on bounded samples
+
+Workloads (pfgen.CONFIGS): precision (default: 2000-bus grid, K = 6, R = 16,
+FP32 factors + FP64 sweeps/combine), plain, batching, differentiation, scale.
+Under torchrun every rank solves its own independent replica of the workload
+(weak scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import pfgen  # noqa: E402
+
+METRIC = "combined solves/s (K perturbed LUs + expansion) vs plain GPU path at rel err <=1e-10"
+UNIT = "solves/s"
+TOL = 1e-10
+L2_BYTES = 129 * 1024 * 1024
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
+# kernel family from the ncu capture summarised under profiles/ (None when the
+# kernel changed since the counters were taken).
+TRAFFIC_PER_LAUNCH = {}
+
+BENCH = {
+    "plain": dict(precision="fp64", sweeps=0),
+    "precision": dict(precision="fp32", sweeps=3),
+    "batching": dict(precision="fp32", sweeps=3),
+    "differentiation": dict(precision="fp64", sweeps=0),
+    "scale": dict(precision="fp32", sweeps=3),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="pisp", choices=["pisp", "reference"])
+    ap.add_argument("--workload", default="precision", choices=list(pfgen.CONFIGS))
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
+    ap.add_argument("--sweeps", type=int, default=None)
+    ap.add_argument("--eps", type=float, default=1e-2)
+    ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of a CUDA graph")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed arm only (no plain-FP64 arm, e2e, CPU baseline or oracle check)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- inputs --
+def workload_instances(name: str, rank: int):
+    c = pfgen.CONFIGS[name]
+    if name == "batching":
+        sizes = pfgen.batch_sizes(c["G"])
+        insts = [pfgen.grid_jacobian(int(sizes[g]), None, 1000 * c["index"] + g + 100_000 * rank)
+                 for g in range(c["G"])]
+    else:
+        insts = [pfgen.grid_jacobian(c["N"], c.get("n_pv"), 1000 * c["index"] + 100_000 * rank)]
+    return insts
+
+
+def concat(insts):
+    rp, cols, vals, off = [0], [], [], 0
+    for I in insts:
+        rp.extend((I.row_ptr[1:] + rp[-1]).tolist())
+        cols.append(I.col + off)
+        vals.append(I.val)
+        off += I.n
+    return ([I.n for I in insts], np.array(rp, np.int64), np.concatenate(cols).astype(np.int32),
+            np.concatenate(vals), np.concatenate([I.D for I in insts]))
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- GPU arms --
+class Arm:
+    """One configured solver with device-resident inputs and a step function."""
+
+    def __init__(self, pisp, torch, insts, K, R, eps, precision, sweeps, workload, dev):
+        self.torch = torch
+        self.insts = insts
+        sizes, rp, col, val, D = concat(insts)
+        t0 = time.perf_counter()
+        self.s = pisp.Solver(sizes, rp, col, device=dev.index)
+        self.analyze_ms = (time.perf_counter() - t0) * 1e3
+        self.N = sum(sizes)
+        self.K, self.R, self.precision, self.sweeps = K, R, precision, sweeps
+        self.t = pfgen.symmetric_shifts(K, eps)
+        self.vals = torch.tensor(val, device=dev)
+        self.D = torch.tensor(D, device=dev)
+        self.b_host = pfgen.rhs(self.N, R, 1)
+        self.b = torch.tensor(self.b_host, device=dev)
+        self.x = torch.empty_like(self.b)
+        self.adjoint = workload == "differentiation"
+        if self.adjoint:
+            self.g = torch.tensor(pfgen.rhs(self.N, R, 2), device=dev)
+            self.gb = torch.empty_like(self.b)
+            self.gv = torch.empty_like(self.vals)
+        self.graph = None
+
+    def step(self):
+        s = self.s
+        s.factor(self.vals, self.D, self.t, self.precision)
+        s.solve(self.b, sweeps=self.sweeps, out=self.x)
+        if self.adjoint:
+            self.s._sync_stream()
+            import ctypes
+            from paper_2311_11833_gb300._lib import check
+            check(s._lib.pisp_adjoint(s._h, ctypes.c_void_p(self.g.data_ptr()), None,
+                                      ctypes.c_void_p(self.gb.data_ptr()),
+                                      ctypes.c_void_p(self.gv.data_ptr())), s._h)
+
+    def capture(self, profile: bool):
+        torch = self.torch
+        self.step()                      # allocate workspaces before capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        st = torch.cuda.Stream()
+        st.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(st):
+            if profile:
+                self.s.profile(True)
+            with torch.cuda.graph(g, stream=st):
+                self.step()
+            if profile:
+                self.s.profile(False)
+        torch.cuda.current_stream().wait_stream(st)
+        torch.cuda.synchronize()
+        self.graph = g
+
+    def run(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.step()
+
+
+def oracle_err(arm, sample_rhs=2, sample_inst=3):
+    """Max relative error of the last x against the CPU oracle on a sample."""
+    import oracle
+    x = arm.x.cpu().numpy()
+    offs = np.concatenate([[0], np.cumsum([I.n for I in arm.insts])])
+    G = len(arm.insts)
+    pick = sorted(set([0, G // 2, G - 1][:sample_inst]))
+    cols = list(range(min(sample_rhs, arm.R)))
+    err = 0.0
+    for g in pick:
+        I = arm.insts[g]
+        sl = slice(offs[g], offs[g + 1])
+        ref = oracle.x_hat(oracle.to_scipy(I), I.D, arm.t, arm.b_host[sl][:, cols])
+        err = max(err, float(np.max(oracle.rel_err(x[sl][:, cols], ref))))
+    return err
+
+
+def cpu_baseline(insts, K, R, eps, budget_s=12.0):
+    """The oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    t = pfgen.symmetric_shifts(K, eps)
+    done_units, elapsed, calls = 0.0, 0.0, 0
+    g = 0
+    t0 = time.perf_counter()
+    while elapsed < budget_s and calls < len(insts) * K:
+        I = insts[g % len(insts)]
+        A = oracle.to_scipy(I)
+        b = pfgen.rhs(I.n, R, 1)
+        oracle.x_hat(A, I.D, t, b)
+        done_units += R
+        calls += K
+        g += 1
+        elapsed = time.perf_counter() - t0
+    return {"value": done_units / elapsed, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{g} instance(s) x {R} RHS x {K} perturbed GEPP solves + combine, "
+                      f"{elapsed:.1f} s of CPU work (numpy/LAPACK, BLAS threads = host cores)"}
+
+
+def run_pisp(args, rank, world, local_rank):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2311_11833_gb300 as pisp
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    c = pfgen.CONFIGS[args.workload]
+    bcfg = BENCH[args.workload]
+    precision = args.precision or bcfg["precision"]
+    sweeps = bcfg["sweeps"] if args.sweeps is None else args.sweeps
+    if precision == "fp64" and args.sweeps is None:
+        sweeps = 0
+    K, R = c["K"], c["R"]
+    insts = workload_instances(args.workload, rank)
+    arm = Arm(pisp, torch, insts, K, R, args.eps, precision, sweeps, args.workload, dev)
+    G = len(insts)
+    units = G * R
+    use_graph = not args.no_graph
+    for _ in range(args.warmup):
+        arm.step()
+    torch.cuda.synchronize()
+    if use_graph:
+        arm.capture(profile=True)
+        for _ in range(max(3, args.warmup)):
+            arm.run()
+    torch.cuda.synchronize()
+    arm.s.profile_reset()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))                      # evict L2 between steps (outside the events)
+        if not use_graph:
+            arm.s.profile(True)                    # fresh bracket list for this eager step
+        ev[i][0].record()
+        arm.run()
+        ev[i][1].record()
+        ev[i][1].synchronize()
+        arm.s.profile_collect()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop() if clocks else None
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        tdist.barrier()
+    value = units * world * args.steps / (total_ms / 1e3)
+    prof = arm.s.profile_read()
+    stats = arm.s.stats()
+    if not use_graph:
+        arm.s.profile(False)
+    if rank != 0:
+        return None
+    # roofline of the dominant kernel family
+    peak, peak_kind = load_peaks()
+    fam = max(prof, key=lambda f: prof[f]["ms"])
+    pf = prof[fam]
+    achieved = pf["bytes"] / (pf["ms"] / 1e3) / 1e9 if pf["ms"] > 0 else 0.0
+    traffic = TRAFFIC_PER_LAUNCH.get(fam)
+    roofline = {"bound": "hbm", "kernel": fam, "achieved": round(achieved, 2), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 5), "peak_source": peak_kind,
+                "traffic": traffic,
+                "algorithmic_bytes_per_launch": pf["bytes"] / max(1, pf["launches"]),
+                "avg_launch_us": 1e3 * pf["ms"] / max(1, pf["launches"]),
+                "share_of_step": round(pf["ms"] / total_ms, 4) if world == 1 else None}
+    families = {f: {"ms_per_step": round(v["ms"] / args.steps, 4),
+                    "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 2) if v["ms"] > 0 else 0.0,
+                    "launches_per_step": v["launches"] / args.steps} for f, v in prof.items()}
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if precision == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "instances": G, "N": arm.N, "nnzA": int(stats["nnzA"]),
+                   "K": K, "R": R, "shifts": "symmetric +-eps*alpha", "eps": args.eps,
+                   "factor_precision": precision, "combine_precision": "fp64", "sweeps": sweeps,
+                   "graph": use_graph, "l2": "flushed between steps (256 MB write outside the events)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "families": families,
+        "gpu_launches": int(stats["gpu_launches"]) * args.steps,
+        "analyze_ms": round(arm.analyze_ms, 2),
+        "wall_s_timed_region": round(wall, 3),
+        "structure": {k: stats[k] for k in ("nnzL", "nnzF_stored", "n_supernodes", "n_levels",
+                                            "max_front", "etree_height")},
+    }
+    if clk:
+        out["clocks"] = clk
+    if not args.quick:
+        out["max_rel_err_vs_oracle"] = oracle_err(arm)
+        # plain FP64 single-instance path: FP64 factors, no sweeps, instances
+        # one after another, eager launches, no graph
+        plain_ms = []
+        plain_err = 0.0
+        arms = [Arm(pisp, torch, [I], K, R, args.eps, "fp64", 0, args.workload, dev)
+                for I in (insts if G <= 8 else insts)]
+        n_plain_steps = 5 if G > 1 else min(args.steps, 20)
+        for a in arms:
+            a.step()
+        torch.cuda.synchronize()
+        for i in range(n_plain_steps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for a in arms:
+                a.step()
+            e1.record()
+            e1.synchronize()
+            plain_ms.append(e0.elapsed_time(e1))
+        plain_err = max(oracle_err(a) for a in arms[:1])
+        pv = units / (statistics.mean(plain_ms) / 1e3)
+        out["plain_fp64_path"] = {"value": round(pv, 2), "ms_per_step": round(statistics.mean(plain_ms), 4),
+                                  "steps": n_plain_steps, "max_rel_err_vs_oracle": plain_err,
+                                  "speedup_of_value": round(value / world / pv, 3)}
+        del arms
+        # end to end through the public API with host buffers (pinned), copies inside
+        sizes, rp, col, val, D = concat(insts)
+        hv = torch.tensor(val).pin_memory().numpy()
+        hD = torch.tensor(D).pin_memory().numpy()
+        hb = torch.tensor(arm.b_host).pin_memory().numpy()
+        hx = torch.empty(arm.b_host.shape, dtype=torch.float64).pin_memory().numpy()
+        e2e_steps = min(args.steps, 20)
+        arm.s.solve_host(hv, hD, arm.t, hb, precision, sweeps, out=hx)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            arm.s.solve_host(hv, hD, arm.t, hb, precision, sweeps, out=hx)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        out["e2e"] = {"value": round(units * world / e2e_s, 2), "unit": UNIT,
+                      "h2d_bytes_per_step": int(hv.nbytes + hD.nbytes + hb.nbytes),
+                      "d2h_bytes_per_step": int(hx.nbytes), "ms_per_step": round(e2e_s * 1e3, 4),
+                      "path": "pisp_solve_host: pinned host buffers, H2D + factor + solve + D2H, eager"}
+        out["cpu_baseline"] = cpu_baseline(insts, K, R, args.eps)
+    return out
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle timed on the host cores: each step one perturbed GEPP solve."""
+    if rank != 0:
+        return None
+    import oracle
+    c = pfgen.CONFIGS[args.workload]
+    K, R = c["K"], c["R"]
+    insts = workload_instances(args.workload, 0)
+    t = pfgen.symmetric_shifts(K, args.eps)
+    beta = oracle.weights_float(list(t))
+    G = len(insts)
+    mats = {}
+
+    def one(i):
+        # step i: perturbed solve k = i % K of instance (i // K) % G, folded into x_hat
+        g, k = (i // K) % G, i % K
+        if g not in mats:
+            mats[g] = (oracle.to_scipy(insts[g]), pfgen.rhs(insts[g].n, R, 1))
+        A, b = mats[g]
+        xk = oracle.perturbed_solutions(A, insts[g].D, [t[k]], b)[0]
+        return beta[k] * xk
+
+    for i in range(args.warmup):
+        one(i)
+    times = []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        one(args.warmup + i)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps * R / K / total      # K perturbed solves make R combined solves
+    return {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "instances": G, "K": K, "R": R, "eps": args.eps},
+        "impl": "reference",
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "each step one perturbed partial-pivoting solve (1/K of a combined "
+                                   "solve of R RHS) of the workload's instances, numpy/scipy FP64"},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as tdist
+            torch.cuda.set_device(local_rank)
+            tdist.init_process_group("nccl")
+        out = run_pisp(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -208,6 +208,40 @@ int pisp_solve_host(pisp_handle* h, const double* values_host, const double* D_h
                     const double* t, int32_t K, int32_t precision, const double* b_host,
                     int32_t R, double* x_host, int32_t sweeps);
 
+/* ---- profiling: CUDA events on the handle's stream around each kernel
+ * family of each level, for per-family device time and achieved bandwidth.
+ * Families: */
+enum {
+  PISP_PROF_FACTOR_SMALL = 0, /* shared-memory front factorisation */
+  PISP_PROF_FACTOR_BIG = 1,   /* blocked front factorisation (assembly, panels, updates) */
+  PISP_PROF_FORWARD = 2,      /* forward substitution */
+  PISP_PROF_BACKWARD = 3,     /* backward substitution */
+  PISP_PROF_RESIDUAL = 4,     /* FP64 residuals of the sweeps */
+  PISP_PROF_COMBINE = 5,      /* expansion-weighted combine */
+  PISP_PROF_FAMILIES = 6
+};
+
+/* on != 0: start recording brackets (forgets the previous recording); the
+ * brackets recorded during a stream capture are replayed with the graph.
+ * on == 0: stop recording. */
+int pisp_profile(pisp_handle* h, int32_t on);
+
+/* Synchronises the stream and adds the elapsed time, algorithmic bytes and
+ * kernel launches of every recorded bracket to the per-family totals. */
+int pisp_profile_collect(pisp_handle* h);
+
+/* Per-family totals since the last pisp_profile_reset: device milliseconds,
+ * algorithmic bytes (minimum data each family must move) and launches.  Any
+ * output pointer may be NULL. */
+int pisp_profile_read(pisp_handle* h, int32_t family, double* ms, double* bytes,
+                      int64_t* launches);
+
+/* Clears the per-family totals. */
+int pisp_profile_reset(pisp_handle* h);
+
+/* Name of a family ("factor_small", ...), "" if out of range. */
+const char* pisp_profile_name(int32_t family);
+
 #ifdef __cplusplus
 }
 #endif

@@ -61,7 +61,13 @@ _SIGS = {
     "pisp_get_front": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, P(c_int32)]),
     "pisp_solve_host": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
                                   c_void_p, c_int32, c_void_p, c_int32]),
+    "pisp_profile": (c_int32, [c_void_p, c_int32]),
+    "pisp_profile_collect": (c_int32, [c_void_p]),
+    "pisp_profile_read": (c_int32, [c_void_p, c_int32, P(c_double), P(c_double), P(c_int64)]),
+    "pisp_profile_reset": (c_int32, [c_void_p]),
+    "pisp_profile_name": (ctypes.c_char_p, [c_int32]),
 }
+PROF_FAMILIES = 6
 
 _lib = None
 

@@ -73,9 +73,25 @@ struct pisp_handle {
   // host-buffer entry point staging
   Buf in_vals, in_D, in_b, out_x;
   int launches = 0;
+  // profiling: CUDA events bracketing each kernel family per level
+  struct Bracket {
+    int fam, e0, e1, launches;
+    double bytes;
+  };
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;
+  int prof_next = 0;
+  std::vector<Bracket> prof_br;
+  double prof_ms[PISP_PROF_FAMILIES] = {}, prof_bytes[PISP_PROF_FAMILIES] = {};
+  int64_t prof_launches[PISP_PROF_FAMILIES] = {};
+  ~pisp_handle() {
+    for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
+  }
 };
 
 namespace {
+
+size_t esize(int precision) { return precision == PISP_FP32 ? 4 : 8; }
 
 int fail(pisp_handle* h, int code, const std::string& msg) {
   if (h) h->err = msg; else g_last_error = msg;
@@ -171,6 +187,26 @@ int build_plans(pisp_handle* h, int precision) {
       if (G.count) lp.sgroups[lp.n_sgroups++] = G;
       lo = scls[c];
     }
+    // algorithmic bytes per perturbation: what each kernel family must read
+    // and write at least (values, indices, factor entries, vectors)
+    const double p = (double)esize(precision);
+    for (int32_t s : lst) {
+      const pisp::Supernode& sn = S.sn[s];
+      const double F = sn.F(), ns = sn.ns(), ms = sn.ms;
+      double child = 0, childv = 0;
+      for (int64_t q = S.child_off[s]; q < S.child_off[s + 1]; ++q) {
+        const double cms = S.sn[S.child[q]].ms;
+        child += cms * cms * p + cms * 4;
+        childv += cms;
+      }
+      const double amap = (double)(S.amap_off[s + 1] - S.amap_off[s]);
+      const double fac = amap * 16 + ns * 12 + child + F * F * p;
+      if (sn.F() > limit) lp.bytes_fbig += fac + 2 * F * F * p; else lp.bytes_fsmall += fac;
+      lp.bytes_fwd_a += ns * 4 + childv * 4 + (ns * F - ns * (ns + 1) / 2) * p;
+      lp.bytes_fwd_b += ns * 8 + childv * p + F * p;
+      lp.bytes_bwd_a += ms * 4 + (ns * (ns + 1) / 2 + ns * ms) * p;
+      lp.bytes_bwd_b += ms * 8 + ns * p + ns * 8;
+    }
   }
   TRY(upload(h, h->d_small, h->h_small));
   TRY(upload(h, h->d_big, h->h_big));
@@ -201,7 +237,40 @@ pisp::Shifts make_shifts(const pisp_handle* h, const double* w) {
   return sh;
 }
 
-size_t esize(int precision) { return precision == PISP_FP32 ? 4 : 8; }
+const char* kFamilyNames[PISP_PROF_FAMILIES] = {"factor_small", "factor_big", "forward",
+                                                "backward",     "residual",   "combine"};
+
+// Event record that also works inside a stream capture: there it must become
+// an event-record node of the graph (external record) to be timed on replay.
+void record_event(pisp_handle* h, cudaEvent_t e) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(h->stream, &cs);
+  cudaEventRecordWithFlags(e, h->stream,
+                           cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                               : cudaEventRecordDefault);
+}
+
+// Records a start event of a profiling bracket; returns its index or -1.
+int prof_begin(pisp_handle* h) {
+  if (!h->prof_on) return -1;
+  if (h->prof_next + 2 > (int)h->prof_ev.size()) {
+    for (int q = 0; q < 64; ++q) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      h->prof_ev.push_back(e);
+    }
+  }
+  const int i = h->prof_next;
+  h->prof_next += 2;
+  record_event(h, h->prof_ev[i]);
+  return i;
+}
+
+void prof_end(pisp_handle* h, int i, int fam, double bytes, int launches) {
+  if (i < 0 || launches <= 0) return;
+  record_event(h, h->prof_ev[i + 1]);
+  h->prof_br.push_back({fam, i, i + 1, launches, bytes});
+}
 
 int count(pisp_handle* h, int n) {
   if (n < 0) {
@@ -218,14 +287,23 @@ int count(pisp_handle* h, int n) {
 int solve_pass(pisp_handle* h, bool trans, const double* rhs, int rhs_mode, double* out,
                double* acc, int32_t R) {
   const int L = h->sym.n_levels;
-  for (int l = 0; l < L; ++l)
-    TRY(count(h, pisp::launch_forward_level(h->precision, trans, h->sd, h->plans[l],
-                                            h->d_all.as<int32_t>(), h->fronts.p, rhs, rhs_mode,
-                                            h->V.p, R, h->K, h->stream)));
-  for (int l = L - 1; l >= 0; --l)
-    TRY(count(h, pisp::launch_backward_level(h->precision, trans, h->sd, h->plans[l],
-                                             h->d_all.as<int32_t>(), h->fronts.p, h->V.p, out,
-                                             acc, R, h->K, h->stream)));
+  for (int l = 0; l < L; ++l) {
+    const pisp::LevelPlan& lp = h->plans[l];
+    const int pb = prof_begin(h);
+    const int n = pisp::launch_forward_level(h->precision, trans, h->sd, lp, h->d_all.as<int32_t>(),
+                                             h->fronts.p, rhs, rhs_mode, h->V.p, R, h->K, h->stream);
+    TRY(count(h, n));
+    prof_end(h, pb, PISP_PROF_FORWARD, h->K * (lp.bytes_fwd_a + lp.bytes_fwd_b * R), n);
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    const pisp::LevelPlan& lp = h->plans[l];
+    const int pb = prof_begin(h);
+    const int n = pisp::launch_backward_level(h->precision, trans, h->sd, lp, h->d_all.as<int32_t>(),
+                                              h->fronts.p, h->V.p, out, acc, R, h->K, h->stream);
+    TRY(count(h, n));
+    prof_end(h, pb, PISP_PROF_BACKWARD,
+             h->K * (lp.bytes_bwd_a + lp.bytes_bwd_b * R) + (acc ? 16.0 * h->sym.N * h->K * R / L : 0.0), n);
+  }
   return PISP_OK;
 }
 
@@ -234,9 +312,14 @@ int solve_pass(pisp_handle* h, bool trans, const double* rhs, int rhs_mode, doub
 int solve_core(pisp_handle* h, const double* rhs, double* X_out, int32_t R, int32_t sweeps,
                const pisp::Shifts& sh) {
   TRY(solve_pass(h, false, rhs, pisp::RHS_BROADCAST, X_out, nullptr, R));
+  const double N = (double)h->sym.N, KR = (double)h->K * R;
   for (int it = 0; it < sweeps; ++it) {
-    TRY(count(h, pisp::launch_residual_per_k(h->sd, h->vals.as<double>(), h->D.as<double>(), sh,
-                                             rhs, X_out, R, h->Rk.as<double>(), h->stream)));
+    const int pb = prof_begin(h);
+    const int n = pisp::launch_residual_per_k(h->sd, h->vals.as<double>(), h->D.as<double>(), sh,
+                                              rhs, X_out, R, h->Rk.as<double>(), h->stream);
+    TRY(count(h, n));
+    prof_end(h, pb, PISP_PROF_RESIDUAL,
+             h->sym.nnzA * 12.0 + N * 20.0 + N * R * 8.0 + 2.0 * N * KR * 8.0, n);
     TRY(solve_pass(h, false, h->Rk.as<double>(), pisp::RHS_PER_K, h->Y.as<double>(), X_out, R));
   }
   return PISP_OK;
@@ -434,12 +517,22 @@ int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
   CK(cudaMemsetAsync(h->badcol.p, 0x7f, (size_t)S.G * K * sizeof(int32_t), h->stream));
   h->launches = 0;
   const pisp::Shifts sh = make_shifts(h, h->beta);
-  for (int l = 0; l < S.n_levels; ++l)
-    TRY(count(h, pisp::launch_factor_level(precision, h->sd, h->plans[l], h->d_small.as<int32_t>(),
-                                           h->d_big.as<int32_t>(), h->h_bigF.data(),
-                                           h->vals.as<double>(), h->D.as<double>(), sh,
-                                           h->fronts.p, h->status.as<int32_t>(),
-                                           h->badcol.as<int32_t>(), h->stream)));
+  for (int l = 0; l < S.n_levels; ++l) {
+    const pisp::LevelPlan& lp = h->plans[l];
+    int pb = prof_begin(h);
+    int n = pisp::launch_factor_small(precision, h->sd, lp, h->d_small.as<int32_t>(),
+                                      h->vals.as<double>(), h->D.as<double>(), sh, h->fronts.p,
+                                      h->status.as<int32_t>(), h->badcol.as<int32_t>(), h->stream);
+    TRY(count(h, n));
+    prof_end(h, pb, PISP_PROF_FACTOR_SMALL, K * lp.bytes_fsmall, n);
+    if (lp.big_count == 0) continue;
+    pb = prof_begin(h);
+    n = pisp::launch_factor_big(precision, h->sd, lp, h->d_big.as<int32_t>(), h->h_bigF.data(),
+                                h->vals.as<double>(), h->D.as<double>(), sh, h->fronts.p,
+                                h->status.as<int32_t>(), h->badcol.as<int32_t>(), h->stream);
+    TRY(count(h, n));
+    prof_end(h, pb, PISP_PROF_FACTOR_BIG, K * lp.bytes_fbig, n);
+  }
   h->factored = true;
   return PISP_OK;
 }
@@ -456,7 +549,10 @@ int pisp_solve(pisp_handle* h, const double* b, int32_t R, const double* w, doub
   TRY(ensure_solve_buffers(h, R));
   const pisp::Shifts sh = make_shifts(h, h->w_last);
   TRY(solve_core(h, b, h->X.as<double>(), R, sweeps, sh));
-  TRY(count(h, pisp::launch_combine(h->sd, h->X.as<double>(), sh, R, x, h->stream)));
+  const int pb = prof_begin(h);
+  const int n = pisp::launch_combine(h->sd, h->X.as<double>(), sh, R, x, h->stream);
+  TRY(count(h, n));
+  prof_end(h, pb, PISP_PROF_COMBINE, (double)h->sym.N * R * 8.0 * (h->K + 1) + h->sym.N * 4.0, n);
   TRY(count(h, pisp::launch_fill_nan_failed(h->sd, h->status.as<int32_t>(), h->K, R, x, h->stream)));
   h->R = R;
   h->solved = true;
@@ -627,6 +723,61 @@ int pisp_solve_host(pisp_handle* h, const double* values_host, const double* D_h
   if (nb) CK(cudaMemcpyAsync(x_host, h->out_x.p, nb, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return PISP_OK;
+}
+
+int pisp_profile(pisp_handle* h, int32_t on) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  if (on) {
+    TRY(set_device(h));
+    while (h->prof_ev.size() < 2048) {  // events exist before any stream capture
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      h->prof_ev.push_back(e);
+    }
+    h->prof_on = true;
+    h->prof_next = 0;
+    h->prof_br.clear();
+  } else {
+    h->prof_on = false;
+  }
+  return PISP_OK;
+}
+
+int pisp_profile_collect(pisp_handle* h) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  TRY(set_device(h));
+  CK(cudaStreamSynchronize(h->stream));
+  for (const auto& b : h->prof_br) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->prof_ev[b.e0], h->prof_ev[b.e1]));
+    h->prof_ms[b.fam] += ms;
+    h->prof_bytes[b.fam] += b.bytes;
+    h->prof_launches[b.fam] += b.launches;
+  }
+  return PISP_OK;
+}
+
+int pisp_profile_read(pisp_handle* h, int32_t family, double* ms, double* bytes,
+                      int64_t* launches) {
+  if (!h || family < 0 || family >= PISP_PROF_FAMILIES)
+    return fail(h, PISP_ERR_INVALID_ARG, "bad profiling family");
+  if (ms) *ms = h->prof_ms[family];
+  if (bytes) *bytes = h->prof_bytes[family];
+  if (launches) *launches = h->prof_launches[family];
+  return PISP_OK;
+}
+
+int pisp_profile_reset(pisp_handle* h) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  for (int f = 0; f < PISP_PROF_FAMILIES; ++f) {
+    h->prof_ms[f] = h->prof_bytes[f] = 0.0;
+    h->prof_launches[f] = 0;
+  }
+  return PISP_OK;
+}
+
+const char* pisp_profile_name(int32_t family) {
+  return (family >= 0 && family < PISP_PROF_FAMILIES) ? kFamilyNames[family] : "";
 }
 
 }  // extern "C"

@@ -333,10 +333,9 @@ int run_panels(const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,
 }
 
 template <typename T>
-int factor_level_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_small,
-                      const int32_t* d_big, const BigFrontHost* bh, const double* vals,
-                      const double* D, const Shifts& sh, void* fronts, int32_t* status,
-                      int32_t* badcol, cudaStream_t st) {
+int factor_small_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_small,
+                      const double* vals, const double* D, const Shifts& sh, void* fronts,
+                      int32_t* status, int32_t* badcol, cudaStream_t st) {
   set_smem_attrs<T>();
   T* fr = reinterpret_cast<T*>(fronts);
   const int K = sh.K;
@@ -349,6 +348,18 @@ int factor_level_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_sm
         sd, d_small + G.off, vals, D, sh, fr, status, badcol);
     ++launches;
   }
+  if (cudaGetLastError() != cudaSuccess) return -1;
+  return launches;
+}
+
+template <typename T>
+int factor_big_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,
+                    const BigFrontHost* bh, const double* vals, const double* D, const Shifts& sh,
+                    void* fronts, int32_t* status, int32_t* badcol, cudaStream_t st) {
+  set_smem_attrs<T>();
+  T* fr = reinterpret_cast<T*>(fronts);
+  const int K = sh.K;
+  int launches = 0;
   if (lp.big_count > 0) {
     const int TW = 32;
     const int big = lp.big_count;
@@ -378,16 +389,22 @@ int max_big_front(int precision) {
   return kSmemCap / (4 * (precision == PISP_FP32 ? 4 : 8));
 }
 
-int launch_factor_level(int precision, const SymDev& sd, const LevelPlan& lp,
-                        const int32_t* d_small, const int32_t* d_big,
-                        const BigFrontHost* big_host, const double* vals, const double* D,
+int launch_factor_small(int precision, const SymDev& sd, const LevelPlan& lp,
+                        const int32_t* d_small, const double* vals, const double* D,
                         const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol,
                         cudaStream_t st) {
   if (precision == PISP_FP32)
-    return factor_level_impl<float>(sd, lp, d_small, d_big, big_host, vals, D, sh, fronts,
-                                    status, badcol, st);
-  return factor_level_impl<double>(sd, lp, d_small, d_big, big_host, vals, D, sh, fronts, status,
-                                   badcol, st);
+    return factor_small_impl<float>(sd, lp, d_small, vals, D, sh, fronts, status, badcol, st);
+  return factor_small_impl<double>(sd, lp, d_small, vals, D, sh, fronts, status, badcol, st);
+}
+
+int launch_factor_big(int precision, const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,
+                      const BigFrontHost* big_host, const double* vals, const double* D,
+                      const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol,
+                      cudaStream_t st) {
+  if (precision == PISP_FP32)
+    return factor_big_impl<float>(sd, lp, d_big, big_host, vals, D, sh, fronts, status, badcol, st);
+  return factor_big_impl<double>(sd, lp, d_big, big_host, vals, D, sh, fronts, status, badcol, st);
 }
 
 }  // namespace pisp

@@ -58,6 +58,10 @@ struct LevelPlan {
   // every front of the level for the solves, grouped by size class
   Group sgroups[8];
   int32_t n_sgroups = 0;
+  // algorithmic bytes per perturbation (a + b * R) of each kernel family,
+  // used for the achieved-bandwidth figures of the profiling interface
+  double bytes_fsmall = 0, bytes_fbig = 0;
+  double bytes_fwd_a = 0, bytes_fwd_b = 0, bytes_bwd_a = 0, bytes_bwd_b = 0;
 };
 
 // Host copies needed to size the launches of the big-front path.
@@ -66,12 +70,17 @@ struct BigFrontHost {
 };
 
 // ---- factor (factor.cu) ----
-// Returns the number of kernels launched (>= 0) or -1 on a launch error.
-int launch_factor_level(int precision, const SymDev& sd, const LevelPlan& lp,
-                        const int32_t* d_small, const int32_t* d_big,
-                        const BigFrontHost* big_host, const double* vals, const double* D,
+// Each launcher returns the number of kernels launched (>= 0) or -1 on a
+// launch error.  Small fronts of one level (shared-memory path):
+int launch_factor_small(int precision, const SymDev& sd, const LevelPlan& lp,
+                        const int32_t* d_small, const double* vals, const double* D,
                         const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol,
                         cudaStream_t st);
+// Big fronts of one level (blocked path):
+int launch_factor_big(int precision, const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,
+                      const BigFrontHost* big_host, const double* vals, const double* D,
+                      const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol,
+                      cudaStream_t st);
 // largest front (in elements of the given precision) the shared-memory path takes
 int small_front_limit(int precision);
 // largest front the blocked path can take (its panel must fit in shared memory)

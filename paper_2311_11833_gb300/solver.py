@@ -219,6 +219,30 @@ class Solver:
         return x
 
 
+    # ------------------------------------------------------------ profiling --
+    def profile(self, on: bool):
+        """pisp_profile: start / stop recording CUDA-event brackets per kernel family."""
+        check(self._lib.pisp_profile(self._h, 1 if on else 0), self._h)
+
+    def profile_collect(self):
+        self._sync_stream()
+        check(self._lib.pisp_profile_collect(self._h), self._h)
+
+    def profile_reset(self):
+        check(self._lib.pisp_profile_reset(self._h), self._h)
+
+    def profile_read(self) -> dict:
+        """{family: {"ms", "bytes", "launches"}} accumulated since the last reset."""
+        out = {}
+        for f in range(_lib.PROF_FAMILIES):
+            ms, by, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+            check(self._lib.pisp_profile_read(self._h, f, ctypes.byref(ms), ctypes.byref(by),
+                                              ctypes.byref(n)), self._h)
+            out[self._lib.pisp_profile_name(f).decode()] = {"ms": ms.value, "bytes": by.value,
+                                                            "launches": n.value}
+        return out
+
+
 class _PerturbedSolve(torch.autograd.Function):
     """x = sum_k beta_k (A + t_k D)^{-1} b with gradients for values and b.
 
