@@ -61,6 +61,10 @@ typedef struct pisp_options {
                            (both followed by an elimination-tree postorder) */
   int32_t relax_small;  /* supernode amalgamation: merge while pivot block <= this (default 8) */
   double relax_zeros;   /* ... or while explicit zeros <= this fraction (default 0.05) */
+  int32_t solve_schedule; /* 0 = persistent: one launch per solve direction whose
+                             CTAs take (front, k, RHS chunk) tasks in level order
+                             and wait (boundedly) for their dependencies;
+                             1 = one launch per level and front-size class */
 } pisp_options;
 
 typedef struct pisp_stats {
@@ -178,7 +182,9 @@ int pisp_weights(const double* t, int32_t K, double* beta);
 /* Synchronises the stream and copies host [G*K] status codes of the last
  * factorisation: 0 ok, PISP_ERR_ZERO_PIVOT or PISP_ERR_NONFINITE.  If
  * first_bad_col is not NULL it receives host [G*K] the first failing
- * permuted column (or -1).  Returns the worst code. */
+ * permuted column (or -1).  Returns the worst code, or PISP_ERR_TIMEOUT if a
+ * bounded dependency wait of a persistent solve gave up since the last
+ * factorisation (its results are then not valid). */
 int pisp_get_status(pisp_handle* h, int32_t* per_instance_k, int32_t* first_bad_col);
 
 /* Statistics of the analysed pattern and the last factorisation. */

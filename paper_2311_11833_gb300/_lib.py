@@ -26,7 +26,8 @@ K_MAX = 16
 
 
 class PispOptions(ctypes.Structure):
-    _fields_ = [("ordering", c_int32), ("relax_small", c_int32), ("relax_zeros", c_double)]
+    _fields_ = [("ordering", c_int32), ("relax_small", c_int32), ("relax_zeros", c_double),
+                ("solve_schedule", c_int32)]
 
 
 class PispStats(ctypes.Structure):

@@ -55,7 +55,12 @@ struct pisp_handle {
   double analyze_ms = 0.0;
   // device symbolic
   Buf c0, ns, ms, inst, front_off, vec_off, row_off, child_off, child, amap_off, amap_src,
-      amap_dst, rows, emap, perm, iperm, row_inst, row_ptr, col;
+      amap_dst, rows, emap, perm, iperm, row_inst, row_ptr, col, parent;
+  // persistent solve schedule (depends on K and R)
+  int32_t schedule = 0;
+  int32_t units_K = 0, units_R = 0;
+  int32_t n_units_f = 0, n_units_b = 0, units_maxF = 0;
+  Buf units_f, units_b, ticket, done, serr, nch;
   pisp::SymDev sd{};
   // level plans (depend on the factor precision)
   int plan_precision = 0;
@@ -134,7 +139,7 @@ int build_plans(pisp_handle* h, int precision) {
   const pisp::Symbolic& S = h->sym;
   const int limit = pisp::small_front_limit(precision);
   const int fcls[5] = {16, 32, 64, 128, limit};
-  const int scls[4] = {32, 128, 512, INT_MAX};
+  const int scls[6] = {8, 16, 32, 128, 512, INT_MAX};
   h->plans.assign(S.n_levels, pisp::LevelPlan());
   h->h_small.clear();
   h->h_big.clear();
@@ -174,7 +179,7 @@ int build_plans(pisp_handle* h, int precision) {
       }
     }
     lo = 0;
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < 6; ++c) {
       pisp::LevelPlan::Group G{(int64_t)h->h_all.size(), 0, 0};
       for (int32_t s : lst) {
         const int F = S.sn[s].F();
@@ -212,6 +217,63 @@ int build_plans(pisp_handle* h, int precision) {
   TRY(upload(h, h->d_big, h->h_big));
   TRY(upload(h, h->d_all, h->h_all));
   h->plan_precision = precision;
+  h->units_K = h->units_R = 0;
+  return PISP_OK;
+}
+
+// Work units of the persistent solve: per level, one unit per (front, k, RHS
+// chunk) for fronts wider than 32, and segment units of 256/SEG tasks for
+// the narrow ones; forward order is levels bottom-up, backward top-down.
+int build_units(pisp_handle* h, int32_t K, int32_t R) {
+  const pisp::Symbolic& S = h->sym;
+  const int segch = (R + pisp::kSolveChunk - 1) / pisp::kSolveChunk;
+  std::vector<std::vector<pisp::SolveUnit>> per_level(S.n_levels);
+  std::vector<int32_t> nch(S.sn.size(), segch);
+  int maxF = 0;
+  for (int l = 0; l < S.n_levels; ++l) {
+    const pisp::LevelPlan& lp = h->plans[l];
+    auto& U = per_level[l];
+    int nbig = 0;
+    for (int g = 0; g < lp.n_sgroups; ++g)
+      if (lp.sgroups[g].maxF > 32) nbig += lp.sgroups[g].count;
+    const int rc = pisp::pick_chunk(std::max(1, nbig), K, R);
+    const int bch = (R + rc - 1) / rc;
+    for (int g = lp.n_sgroups - 1; g >= 0; --g) {
+      const auto& G = lp.sgroups[g];
+      if (G.maxF <= 32) continue;
+      for (int q = G.count - 1; q >= 0; --q) {
+        const int32_t sn = h->h_all[G.off + q];
+        maxF = std::max(maxF, S.sn[sn].F());
+        nch[sn] = bch;
+        for (int k = 0; k < K; ++k)
+          for (int c = 0; c < bch; ++c) U.push_back({pisp::kUnitBlk, sn, k, c, rc});
+      }
+    }
+    for (int g = 0; g < lp.n_sgroups; ++g) {
+      const auto& G = lp.sgroups[g];
+      if (G.maxF > 32) continue;
+      const int seg = G.maxF <= 8 ? 8 : (G.maxF <= 16 ? 16 : 32);
+      const int kind = seg == 8 ? pisp::kUnitSeg8 : (seg == 16 ? pisp::kUnitSeg16 : pisp::kUnitSeg32);
+      const int64_t segs = (int64_t)G.count * K * segch;
+      if (segs >= INT32_MAX) return fail(h, PISP_ERR_UNSUPPORTED, "too many solve tasks");
+      for (int64_t b = 0; b < segs; b += 256 / seg)
+        U.push_back({kind, (int32_t)G.off, (int32_t)b, (int32_t)segs, 0});
+    }
+  }
+  std::vector<pisp::SolveUnit> f, b;
+  for (int l = 0; l < S.n_levels; ++l) f.insert(f.end(), per_level[l].begin(), per_level[l].end());
+  for (int l = S.n_levels - 1; l >= 0; --l) b.insert(b.end(), per_level[l].begin(), per_level[l].end());
+  TRY(upload(h, h->units_f, f));
+  TRY(upload(h, h->units_b, b));
+  TRY(upload(h, h->nch, nch));
+  if (!h->ticket.ensure(2 * sizeof(int)) || !h->serr.ensure(sizeof(int)) ||
+      !h->done.ensure((size_t)S.sn.size() * K * sizeof(int)))
+    return fail(h, PISP_ERR_OOM, "device allocation failed (solve schedule)");
+  h->n_units_f = (int32_t)f.size();
+  h->n_units_b = (int32_t)b.size();
+  h->units_maxF = maxF;
+  h->units_K = K;
+  h->units_R = R;
   return PISP_OK;
 }
 
@@ -287,6 +349,34 @@ int count(pisp_handle* h, int n) {
 int solve_pass(pisp_handle* h, bool trans, const double* rhs, int rhs_mode, double* out,
                double* acc, int32_t R) {
   const int L = h->sym.n_levels;
+  if (!trans && h->schedule == 0) {
+    if (h->units_K != h->K || h->units_R != R) TRY(build_units(h, h->K, R));
+    const size_t nd = (size_t)h->sym.sn.size() * h->K * sizeof(int);
+    double bf = 0, bb = 0;
+    for (int l = 0; l < L; ++l) {
+      bf += h->K * (h->plans[l].bytes_fwd_a + h->plans[l].bytes_fwd_b * R);
+      bb += h->K * (h->plans[l].bytes_bwd_a + h->plans[l].bytes_bwd_b * R);
+    }
+    if (acc) bb += 16.0 * h->sym.N * h->K * R;
+    CK(cudaMemsetAsync(h->ticket.p, 0, 2 * sizeof(int), h->stream));
+    CK(cudaMemsetAsync(h->done.p, 0, nd, h->stream));
+    int pb = prof_begin(h);
+    int n = pisp::launch_solve_persistent(h->precision, true, h->sd, h->units_f.as<pisp::SolveUnit>(),
+                                          h->n_units_f, h->ticket.as<int>(), h->done.as<int>(),
+                                          h->serr.as<int>(), h->nch.as<int>(), h->d_all.as<int32_t>(), h->fronts.p, rhs,
+                                          rhs_mode, h->V.p, out, acc, R, h->K, h->units_maxF, h->stream);
+    TRY(count(h, n));
+    prof_end(h, pb, PISP_PROF_FORWARD, bf, n);
+    CK(cudaMemsetAsync(h->done.p, 0, nd, h->stream));
+    pb = prof_begin(h);
+    n = pisp::launch_solve_persistent(h->precision, false, h->sd, h->units_b.as<pisp::SolveUnit>(),
+                                      h->n_units_b, h->ticket.as<int>() + 1, h->done.as<int>(),
+                                      h->serr.as<int>(), h->nch.as<int>(), h->d_all.as<int32_t>(), h->fronts.p, rhs,
+                                      rhs_mode, h->V.p, out, acc, R, h->K, h->units_maxF, h->stream);
+    TRY(count(h, n));
+    prof_end(h, pb, PISP_PROF_BACKWARD, bb, n);
+    return PISP_OK;
+  }
   for (int l = 0; l < L; ++l) {
     const pisp::LevelPlan& lp = h->plans[l];
     const int pb = prof_begin(h);
@@ -386,6 +476,8 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   if (row_ptr[N] > 0 && !col_idx) return fail(h, PISP_ERR_INVALID_ARG, "null col_idx");
   if (h->device >= 0) TRY(set_device(h));
   pisp::SymbolicOptions so;
+  h->schedule = opt ? opt->solve_schedule : 0;
+  h->units_K = h->units_R = 0;
   if (opt) {
     so.ordering = opt->ordering;
     if (opt->relax_small >= 0) so.relax_small = opt->relax_small;
@@ -405,13 +497,14 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   }
   // upload the structure
   const int nS = (int)S.sn.size();
-  std::vector<int32_t> c0(nS), ns(nS), ms(nS), inst(nS), child_off(nS + 1);
+  std::vector<int32_t> c0(nS), ns(nS), ms(nS), inst(nS), child_off(nS + 1), par(nS);
   std::vector<int64_t> row_off(nS);
   for (int s = 0; s < nS; ++s) {
     c0[s] = S.sn[s].c0;
     ns[s] = S.sn[s].ns();
     ms[s] = S.sn[s].ms;
     inst[s] = S.sn[s].instance;
+    par[s] = S.sn[s].parent;
     row_off[s] = S.sn[s].row_off;
   }
   for (int s = 0; s <= nS; ++s) child_off[s] = (int32_t)S.child_off[s];
@@ -439,6 +532,7 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   TRY(upload(h, h->row_inst, row_inst));
   TRY(upload(h, h->row_ptr, rp));
   TRY(upload(h, h->col, cl));
+  TRY(upload(h, h->parent, par));
   pisp::SymDev& sd = h->sd;
   sd.c0 = h->c0.as<int32_t>();
   sd.ns = h->ns.as<int32_t>();
@@ -459,6 +553,7 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   sd.row_inst = h->row_inst.as<int32_t>();
   sd.row_ptr = h->row_ptr.as<int64_t>();
   sd.col = h->col.as<int32_t>();
+  sd.parent = h->parent.as<int32_t>();
   sd.N = S.N;
   sd.S = nS;
   h->analyzed = true;
@@ -515,6 +610,8 @@ int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
   if (S.N) CK(cudaMemcpyAsync(h->D.p, D, S.N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaMemsetAsync(h->status.p, 0, (size_t)S.G * K * sizeof(int32_t), h->stream));
   CK(cudaMemsetAsync(h->badcol.p, 0x7f, (size_t)S.G * K * sizeof(int32_t), h->stream));
+  if (!h->serr.ensure(sizeof(int))) return fail(h, PISP_ERR_OOM, "device allocation failed");
+  CK(cudaMemsetAsync(h->serr.p, 0, sizeof(int), h->stream));
   h->launches = 0;
   const pisp::Shifts sh = make_shifts(h, h->beta);
   for (int l = 0; l < S.n_levels; ++l) {
@@ -623,7 +720,13 @@ int pisp_get_status(pisp_handle* h, int32_t* per_instance_k, int32_t* first_bad_
   std::vector<int32_t> st(n), bc(n);
   CK(cudaMemcpyAsync(st.data(), h->status.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(bc.data(), h->badcol.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  int serr = 0;
+  CK(cudaMemcpyAsync(&serr, h->serr.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (serr) {
+    h->err = "a bounded dependency wait of the persistent solve gave up";
+    return PISP_ERR_TIMEOUT;
+  }
   int worst = PISP_OK;
   for (size_t q = 0; q < n; ++q) {
     int code = PISP_OK;

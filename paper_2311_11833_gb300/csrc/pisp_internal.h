@@ -24,6 +24,7 @@ struct SymDev {
   const int32_t* amap_dst;   // position i + j*F in the front
   const int32_t* rows;       // update rows (permuted global index)
   const int32_t* emap;       // position of each update row in the parent front
+  const int32_t* parent;     // [S] parent supernode or -1
   const int32_t* perm;       // [N] perm[new] = old
   const int32_t* iperm;      // [N] iperm[old] = new
   const int32_t* row_inst;   // [N] instance of each original row
@@ -90,6 +91,29 @@ int max_solve_front(int precision);
 
 // ---- solve (solve.cu) ----
 enum RhsMode { RHS_BROADCAST = 0, RHS_PER_K = 1 };
+
+// Work unit of the persistent solve schedule.  Segment units cover 256/SEG
+// consecutive (front, k, RHS chunk) segments of one size group: a = offset of
+// the group in the level list, b = first segment, c = segments in the group.
+// Block units are one (front a, perturbation b, RHS chunk c of d right-hand
+// sides).
+enum UnitKind { kUnitSeg8 = 0, kUnitSeg16 = 1, kUnitSeg32 = 2, kUnitBlk = 3 };
+struct SolveUnit {
+  int32_t kind, a, b, c, d;
+};
+constexpr int kSolveChunk = 8;  // largest RHS chunk of a task (segment tasks use exactly 8)
+
+// One launch solving every level of the forest (forward = L, bottom-up, or
+// backward = U, top-down).  ticket (1 int) and done (S*K ints) must be zero;
+// nch[s] is the number of RHS chunks (tasks) per (front s, k); err is set to 1
+// if a bounded dependency wait gave up.
+int launch_solve_persistent(int precision, bool forward, const SymDev& sd, const SolveUnit* units,
+                            int nunits, int* ticket, int* done, int* err, const int* nch,
+                            const int32_t* d_all, const void* fronts, const double* rhs,
+                            int rhs_mode, void* V, double* out, double* acc, int32_t R, int32_t K,
+                            int32_t max_blk_F, cudaStream_t st);
+// RHS chunk for the CTAs solving one big front at a time (persistent schedule)
+int pick_chunk(int fronts_in_level, int K, int R);
 int launch_forward_level(int precision, bool trans, const SymDev& sd, const LevelPlan& lp,
                          const int32_t* d_all, const void* fronts, const double* rhs,
                          int rhs_mode, void* V, int32_t R, int32_t K, cudaStream_t st);

@@ -157,6 +157,517 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward(SymDev sd, const int
   }
 }
 
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ double load_rhs(const SymDev& sd, const double* rhs, int rhs_mode,
+                                           int col, int k, int K, int R, int r) {
+  return rhs_mode == RHS_BROADCAST ? rhs[(int64_t)sd.perm[col] * R + r]
+                                   : rhs[((int64_t)col * K + k) * R + r];
+}
+
+// ---------------------------------------------------------------------------
+// Dependency flags of the persistent schedule.  A task (front, k, RHS chunk)
+// publishes done[(s*K + k)*nch + ch] = 1 after its results are globally
+// visible; consumers spin on it with a bounded number of polls.  A wait that
+// gives up sets *err (reported as PISP_ERR_TIMEOUT) and the task proceeds, so
+// no wait can hang the GPU.
+// ---------------------------------------------------------------------------
+constexpr int64_t kWaitPolls = 1 << 22;
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// done[s*K + k] counts the finished RHS chunks of (front s, perturbation k).
+// Forward solve: a front waits until the counter of each child reaches
+// nch[child].  Backward solve: a front waits until its parent's counter
+// reaches nch[parent].
+struct Sync {
+  int* done;          // nullptr: level-synchronous launches, nothing to wait for
+  int* err;
+  const int* nch;     // [S] RHS chunks per (front, k) in the persistent schedule
+  __device__ void wait_ge(const int* f, int need) const {
+    if (ld_acquire(f) >= need) return;
+    for (int64_t i = 0; i < kWaitPolls; ++i) {
+      __nanosleep(64);
+      if (ld_acquire(f) >= need) return;
+    }
+    atomicExch(err, 1);
+  }
+  __device__ void add(int s, int k, int K) const {
+    asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(done + (int64_t)s * K + k) : "memory");
+  }
+  // forward: wait for child c of this front
+  __device__ void wait_child(int c, int k, int K) const { wait_ge(done + (int64_t)c * K + k, nch[c]); }
+  // backward: front s waits for its parent p (which publishes to itself)
+  __device__ void wait_parent(int s, int p, int k, int K) const {
+    wait_ge(done + (int64_t)p * K + k, nch[p]);
+  }
+  __device__ void publish_children(const SymDev& sd, int s, int k, int K) const { add(s, k, K); }
+};
+
+// ---------------------------------------------------------------------------
+// Fronts with F <= SEG (SEG = 8, 16 or 32): a warp is split into 32/SEG
+// segments and every segment solves one (front, k, chunk of kRW right-hand
+// sides).  Lane i of a segment owns row i of its front; the factor entries it
+// needs live in registers and the triangular solves are shuffle chains within
+// the segment.  Loops run to warp-uniform bounds (entries beyond a front are
+// zero), so segments with different fronts never diverge around a shuffle.
+// All lanes of a warp call these bodies together.
+// ---------------------------------------------------------------------------
+constexpr int kRW = 8;
+
+struct SegTask {
+  bool active;
+  int s, k, r0, nr, ch;
+};
+
+__device__ __forceinline__ SegTask seg_task(const SymDev& sd, const int32_t* list, int64_t sg,
+                                            int64_t nseg, int R, int K) {
+  SegTask t{false, 0, 0, 0, 0, 0};
+  const int nch = (R + kRW - 1) / kRW;
+  if (sg < nseg) {
+    t.active = true;
+    t.ch = (int)(sg % nch);
+    t.k = (int)((sg / nch) % K);
+    t.s = list[sg / ((int64_t)nch * K)];
+    t.r0 = t.ch * kRW;
+    t.nr = min(kRW, R - t.r0);
+  }
+  return t;
+}
+
+template <typename T, int SEG>
+__device__ __forceinline__ void seg_forward(const SymDev& sd, const SegTask& t, int sl,
+                                            T (*bw)[SEG + 1], const T* __restrict__ fronts,
+                                            const double* __restrict__ rhs, int rhs_mode,
+                                            T* __restrict__ V, int R, int K, const Sync& sy) {
+  int ns = 0, ms = 0, F = 0, c0 = 0, ch0 = 0, nchn = 0;
+  if (t.active) {
+    ns = sd.ns[t.s];
+    ms = sd.ms[t.s];
+    F = ns + ms;
+    c0 = sd.c0[t.s];
+    ch0 = sd.child_off[t.s];
+    nchn = sd.child_off[t.s + 1] - ch0;
+  }
+  const int k = t.k, r0 = t.r0, nr = t.nr;
+  const T* f = fronts + (t.active ? (int64_t)K * sd.front_off[t.s] + (int64_t)k * F * F : 0);
+#pragma unroll
+  for (int r = 0; r < kRW; ++r)
+    bw[r][sl] = (r < nr && sl < ns) ? (T)load_rhs(sd, rhs, rhs_mode, c0 + sl, k, K, R, r0 + r) : T(0);
+  T Lr[SEG];
+#pragma unroll
+  for (int c = 0; c < SEG; ++c) Lr[c] = (c < ns && sl > c && sl < F) ? f[sl + c * F] : T(0);
+  if (sy.done && sl == 0)
+    for (int ci = 0; ci < nchn; ++ci) sy.wait_child(sd.child[ch0 + ci], k, K);
+  const int nchild = __reduce_max_sync(kFull, nchn);
+  __syncwarp();
+  for (int ci = 0; ci < nchild; ++ci) {
+    if (ci < nchn) {
+      const int c = sd.child[ch0 + ci];
+      const int cns = sd.ns[c], cms = sd.ms[c], cF = cns + cms;
+      if (sl < cms) {
+        const int dst = sd.emap[sd.row_off[c] + sl];
+        const T* cv = V + (int64_t)K * R * sd.vec_off[c] + ((int64_t)k * R + r0) * cF + cns + sl;
+        T tmp[kRW];
+#pragma unroll
+        for (int r = 0; r < kRW; ++r) tmp[r] = (r < nr) ? __ldcg(cv + (int64_t)r * cF) : T(0);
+#pragma unroll
+        for (int r = 0; r < kRW; ++r)
+          if (r < nr) bw[r][dst] += tmp[r];
+      }
+    }
+    __syncwarp();
+  }
+  // right-hand sides actually present in this warp (uniform): the FP64 pipe
+  // is narrow on this GPU, so absent columns must cost nothing
+  const int nrw = __reduce_max_sync(kFull, nr);
+  T vv[kRW];
+#pragma unroll
+  for (int r = 0; r < kRW; ++r) vv[r] = bw[r][sl];
+  const int nsw = __reduce_max_sync(kFull, ns);
+#pragma unroll
+  for (int c = 0; c < SEG - 1; ++c) {
+    if (c >= nsw) break;
+#pragma unroll
+    for (int r = 0; r < kRW; ++r)
+      if (r < nrw) vv[r] -= Lr[c] * __shfl_sync(kFull, vv[r], c, SEG);
+  }
+  T* Vs = V + (t.active ? (int64_t)K * R * sd.vec_off[t.s] + ((int64_t)k * R + r0) * F : 0);
+#pragma unroll
+  for (int r = 0; r < kRW; ++r)
+    if (r < nr && sl < F) Vs[(int64_t)r * F + sl] = vv[r];
+  if (sy.done) {
+    __threadfence();
+    __syncwarp();
+    if (t.active && sl == 0) sy.add(t.s, k, K);
+  }
+}
+
+template <typename T, int SEG>
+__device__ __forceinline__ void seg_backward(const SymDev& sd, const SegTask& t, int sl,
+                                             const T* __restrict__ fronts, const T* __restrict__ V,
+                                             double* out, double* acc, int R, int K, const Sync& sy) {
+  int ns = 0, ms = 0, F = 0, c0 = 0;
+  if (t.active) {
+    ns = sd.ns[t.s];
+    ms = sd.ms[t.s];
+    F = ns + ms;
+    c0 = sd.c0[t.s];
+  }
+  const int k = t.k, r0 = t.r0, nr = t.nr;
+  const T* f = fronts + (t.active ? (int64_t)K * sd.front_off[t.s] + (int64_t)k * F * F : 0);
+  const int myrow = (sl < ms) ? sd.rows[sd.row_off[t.s] + sl] : 0;
+  const T* Vs = V + (t.active ? (int64_t)K * R * sd.vec_off[t.s] + ((int64_t)k * R + r0) * F : 0);
+  T zt[kRW], xt[kRW];
+#pragma unroll
+  for (int r = 0; r < kRW; ++r) zt[r] = (r < nr && sl < ns) ? Vs[(int64_t)r * F + sl] : T(0);
+  const T rd = (sl < ns) ? T(1) / f[sl * (F + 1)] : T(0);
+  if (sy.done && sl == 0 && t.active && ms > 0) sy.wait_parent(t.s, sd.parent[t.s], k, K);
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < kRW; ++r)
+    xt[r] = (r < nr && sl < ms) ? (T)__ldcg(out + ((int64_t)myrow * K + k) * R + r0 + r) : T(0);
+  const int nrw = __reduce_max_sync(kFull, nr);
+  const int msw = __reduce_max_sync(kFull, ms);
+  const int nsw = __reduce_max_sync(kFull, ns);
+  // update part: z -= U12 x_R, one column of U12 at a time
+#pragma unroll 4
+  for (int j = 0; j < SEG - 1; ++j) {
+    if (j >= msw) break;
+    const T u = (sl < ns && j < ms) ? f[sl + (ns + j) * F] : T(0);
+#pragma unroll
+    for (int r = 0; r < kRW; ++r)
+      if (r < nrw) zt[r] -= u * __shfl_sync(kFull, xt[r], j, SEG);
+  }
+  // back substitution with U11, one column at a time
+#pragma unroll 4
+  for (int c = SEG - 1; c >= 0; --c) {
+    if (c >= nsw) continue;
+    const T u = (sl < ns && c > sl && c < ns) ? f[sl + c * F] : T(0);
+#pragma unroll
+    for (int r = 0; r < kRW; ++r) {
+      if (r < nrw) {
+        if (sl == c) zt[r] *= rd;
+        zt[r] -= u * __shfl_sync(kFull, zt[r], c, SEG);
+      }
+    }
+  }
+  if (t.active && sl < ns) {
+    double* o = out + ((int64_t)(c0 + sl) * K + k) * R + r0;
+#pragma unroll
+    for (int r = 0; r < kRW; ++r)
+      if (r < nr) o[r] = (double)zt[r];
+    if (acc) {
+      double* a = acc + ((int64_t)(c0 + sl) * K + k) * R + r0;
+#pragma unroll
+      for (int r = 0; r < kRW; ++r)
+        if (r < nr) a[r] += (double)zt[r];
+    }
+  }
+  if (sy.done) {
+    __threadfence();
+    __syncwarp();
+    if (t.active && sl == 0) sy.publish_children(sd, t.s, k, K);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fronts with F > 32: a whole CTA per (front, k, RHS chunk), blocked by 32
+// pivots.  The 32x32 diagonal block of step b+1 is staged in shared memory
+// while step b updates the rows below it, so each step costs one global
+// latency: warps solve the diagonal block with shuffles (one warp per
+// right-hand side), then every thread updates its rows with the 32 solved
+// values, reading the factor panel with coalesced column loads.
+// ---------------------------------------------------------------------------
+constexpr int kBS = 33;  // padded row stride of a staged 32x32 block
+
+template <typename T>
+__device__ __forceinline__ void stage_block(T* dst, const T* f, int F, int p0, int nb, bool lower,
+                                            int tid, int nt) {
+  for (int q = tid; q < 32 * 32; q += nt) {
+    const int i = q & 31, c = q >> 5;
+    const bool keep = (i < nb && c < nb) && (lower ? (i > c) : (i <= c));
+    dst[i * kBS + c] = keep ? f[(p0 + i) + (int64_t)(p0 + c) * F] : T(0);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void blk_forward(const SymDev& sd, int s, int k, int r0, int nr, int ch,
+                                            unsigned char* smraw, const T* __restrict__ fronts,
+                                            const double* __restrict__ rhs, int rhs_mode,
+                                            T* __restrict__ V, int R, int K, const Sync& sy) {
+  const int ns = sd.ns[s], ms = sd.ms[s], F = ns + ms;
+  const int c0 = sd.c0[s];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  T* blk = reinterpret_cast<T*>(smraw);          // 2 x 32 x kBS
+  T* v = blk + 2 * 32 * kBS;                      // nr x F
+  const T* f = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * F * F;
+  stage_block(blk, f, F, 0, min(32, ns), true, tid, nt);
+  for (int q = tid; q < nr * ns; q += nt) {
+    const int c = q % ns, r = q / ns;
+    v[r * F + c] = (T)load_rhs(sd, rhs, rhs_mode, c0 + c, k, K, R, r0 + r);
+  }
+  for (int q = tid; q < nr * ms; q += nt) v[(q / ms) * F + ns + q % ms] = T(0);
+  const int cb = sd.child_off[s], ce = sd.child_off[s + 1];
+  if (sy.done && tid == 0)
+    for (int ci = cb; ci < ce; ++ci) sy.wait_child(sd.child[ci], k, K);
+  __syncthreads();
+  for (int ci = cb; ci < ce; ++ci) {
+    const int c = sd.child[ci];
+    const int cns = sd.ns[c], cms = sd.ms[c], cF = cns + cms;
+    const T* cv = V + (int64_t)K * R * sd.vec_off[c] + ((int64_t)k * R + r0) * cF;
+    const int32_t* em = sd.emap + sd.row_off[c];
+    for (int q = tid; q < nr * cms; q += nt) {
+      const int a = q % cms, r = q / cms;
+      v[r * F + em[a]] += __ldcg(cv + (int64_t)r * cF + cns + a);
+    }
+    __syncthreads();
+  }
+  int cur = 0;
+  for (int p0 = 0; p0 < ns; p0 += 32) {
+    const int nb = min(32, ns - p0);
+    const T* B = blk + cur * 32 * kBS;
+    for (int r = wid; r < nr; r += nw) {
+      T vi = (lane < nb) ? v[r * F + p0 + lane] : T(0);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        if (c >= nb) break;
+        vi -= B[lane * kBS + c] * __shfl_sync(kFull, vi, c);
+      }
+      if (lane < nb) v[r * F + p0 + lane] = vi;
+    }
+    __syncthreads();
+    if (p0 + 32 < ns) stage_block(blk + (cur ^ 1) * 32 * kBS, f, F, p0 + 32, min(32, ns - p0 - 32), true, tid, nt);
+    for (int i = p0 + nb + tid; i < F; i += nt) {
+      T Lc[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) Lc[c] = (c < nb) ? f[i + (int64_t)(p0 + c) * F] : T(0);
+      for (int r = 0; r < nr; ++r) {
+        const T* yb = v + r * F + p0;
+        T a = T(0);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          if (c >= nb) break;
+          a += Lc[c] * yb[c];
+        }
+        v[r * F + i] -= a;
+      }
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  T* outv = V + (int64_t)K * R * sd.vec_off[s] + ((int64_t)k * R + r0) * F;
+  for (int q = tid; q < nr * F; q += nt) outv[q] = v[q];
+  if (sy.done) {
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) sy.add(s, k, K);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void blk_backward(const SymDev& sd, int s, int k, int r0, int nr, int ch,
+                                             unsigned char* smraw, const T* __restrict__ fronts,
+                                             const T* __restrict__ V, double* out, double* acc,
+                                             int R, int K, const Sync& sy) {
+  const int ns = sd.ns[s], ms = sd.ms[s], F = ns + ms;
+  const int c0 = sd.c0[s];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  T* blk = reinterpret_cast<T*>(smraw);
+  T* xr = blk + 2 * 32 * kBS;
+  T* z = xr + nr * ms;
+  const T* f = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * F * F;
+  const int32_t* rows = sd.rows + sd.row_off[s];
+  const int last0 = ((ns - 1) / 32) * 32;        // first pivot of the bottom block
+  stage_block(blk, f, F, last0, ns - last0, false, tid, nt);
+  const T* y = V + (int64_t)K * R * sd.vec_off[s] + ((int64_t)k * R + r0) * F;
+  for (int q = tid; q < nr * ns; q += nt) {
+    const int p = q % ns, r = q / ns;
+    z[q] = y[(int64_t)r * F + p];
+  }
+  if (sy.done && tid == 0 && ms > 0) sy.wait_parent(s, sd.parent[s], k, K);
+  __syncthreads();
+  for (int q = tid; q < nr * ms; q += nt) {
+    const int j = q % ms, r = q / ms;
+    xr[q] = (T)__ldcg(out + ((int64_t)rows[j] * K + k) * R + r0 + r);
+  }
+  __syncthreads();
+  if (ms > 0) {
+    // z[r][p] -= sum_j U12[p][j] xr[r][j]; thread (p, jj) takes every JG-th j
+    const int JG = max(1, min(32, nt / ns));
+    for (int q = tid; q < ns * JG; q += nt) {
+      const int p = q % ns, jj = q / ns;
+      for (int rr = 0; rr < nr; rr += 4) {
+        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int j = jj; j < ms; j += JG) {
+          const T u = f[p + (int64_t)(ns + j) * F];
+          const T* x0 = xr + rr * ms + j;
+          a0 += u * x0[0];
+          if (rr + 1 < nr) a1 += u * x0[ms];
+          if (rr + 2 < nr) a2 += u * x0[2 * ms];
+          if (rr + 3 < nr) a3 += u * x0[3 * ms];
+        }
+        atomicAdd(&z[rr * ns + p], -a0);
+        if (rr + 1 < nr) atomicAdd(&z[(rr + 1) * ns + p], -a1);
+        if (rr + 2 < nr) atomicAdd(&z[(rr + 2) * ns + p], -a2);
+        if (rr + 3 < nr) atomicAdd(&z[(rr + 3) * ns + p], -a3);
+      }
+    }
+    __syncthreads();
+  }
+  int cur = 0;
+  for (int p0 = last0; p0 >= 0; p0 -= 32) {
+    const int nb = min(32, ns - p0);
+    const T* B = blk + cur * 32 * kBS;
+    for (int r = wid; r < nr; r += nw) {
+      T zi = (lane < nb) ? z[r * ns + p0 + lane] : T(0);
+      const T rd = (lane < nb) ? T(1) / B[lane * kBS + lane] : T(0);
+#pragma unroll
+      for (int c = 31; c >= 0; --c) {
+        if (c >= nb) continue;
+        if (lane == c) zi *= rd;
+        const T xc = __shfl_sync(kFull, zi, c);
+        if (lane < c) zi -= B[lane * kBS + c] * xc;
+      }
+      if (lane < nb) z[r * ns + p0 + lane] = zi;
+    }
+    __syncthreads();
+    if (p0 > 0) stage_block(blk + (cur ^ 1) * 32 * kBS, f, F, p0 - 32, 32, false, tid, nt);
+    for (int i = tid; i < p0; i += nt) {
+      T Uc[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) Uc[c] = (c < nb) ? f[i + (int64_t)(p0 + c) * F] : T(0);
+      for (int r = 0; r < nr; ++r) {
+        const T* xb = z + r * ns + p0;
+        T a = T(0);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          if (c >= nb) break;
+          a += Uc[c] * xb[c];
+        }
+        z[r * ns + i] -= a;
+      }
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  for (int q = tid; q < nr * ns; q += nt) {
+    const int p = q % ns, r = q / ns;
+    const int64_t o = ((int64_t)(c0 + p) * K + k) * R + r0 + r;
+    out[o] = (double)z[q];
+    if (acc) acc[o] += (double)z[q];
+  }
+  if (sy.done) {
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) sy.publish_children(sd, s, k, K);
+  }
+}
+
+// ---- level-synchronous kernels (one launch per level and size class) ----
+template <typename T, int SEG>
+__global__ void __launch_bounds__(256, 2) k_forward_seg(SymDev sd, const int32_t* __restrict__ list,
+                                                        int64_t nseg, const T* __restrict__ fronts,
+                                                        const double* __restrict__ rhs, int rhs_mode,
+                                                        T* __restrict__ V, int R, int K) {
+  __shared__ T buf[256 / SEG][kRW][SEG + 1];
+  const int64_t sg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / SEG;
+  const SegTask t = seg_task(sd, list, sg, nseg, R, K);
+  seg_forward<T, SEG>(sd, t, threadIdx.x % SEG, buf[threadIdx.x / SEG], fronts, rhs, rhs_mode, V, R,
+                      K, Sync{nullptr, nullptr, nullptr});
+}
+
+template <typename T, int SEG>
+__global__ void __launch_bounds__(256, 2) k_backward_seg(SymDev sd, const int32_t* __restrict__ list,
+                                                         int64_t nseg, const T* __restrict__ fronts,
+                                                         const T* __restrict__ V, double* out,
+                                                         double* acc, int R, int K) {
+  const int64_t sg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / SEG;
+  const SegTask t = seg_task(sd, list, sg, nseg, R, K);
+  seg_backward<T, SEG>(sd, t, threadIdx.x % SEG, fronts, V, out, acc, R, K, Sync{nullptr, nullptr, nullptr});
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSolveThreads, 2) k_forward_blk(SymDev sd, const int32_t* __restrict__ list,
+                                                                  const T* __restrict__ fronts,
+                                                                  const double* __restrict__ rhs,
+                                                                  int rhs_mode, T* __restrict__ V,
+                                                                  int R, int K, int rc) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int r0 = blockIdx.z * rc;
+  if (r0 >= R) return;
+  blk_forward<T>(sd, list[blockIdx.x], blockIdx.y, r0, min(rc, R - r0), 0, smraw, fronts, rhs,
+                 rhs_mode, V, R, K, Sync{nullptr, nullptr, nullptr});
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSolveThreads, 2) k_backward_blk(SymDev sd, const int32_t* __restrict__ list,
+                                                                   const T* __restrict__ fronts,
+                                                                   const T* __restrict__ V, double* out,
+                                                                   double* acc, int R, int K, int rc) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int r0 = blockIdx.z * rc;
+  if (r0 >= R) return;
+  blk_backward<T>(sd, list[blockIdx.x], blockIdx.y, r0, min(rc, R - r0), 0, smraw, fronts, V, out,
+                  acc, R, K, Sync{nullptr, nullptr, nullptr});
+}
+
+// ---- persistent schedule: one launch per direction -------------------------
+// CTAs take work units in ticket order (levels bottom-up for the forward
+// solve, top-down for the backward solve).  A unit only waits for units with
+// smaller tickets, which running CTAs already hold, so the schedule cannot
+// deadlock whatever the number of resident CTAs.
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(kSolveThreads, 2)
+k_solve_persistent(SymDev sd, const SolveUnit* __restrict__ units, int nunits, int* ticket,
+                   int* done, int* err, const int* __restrict__ nch, const int32_t* __restrict__ all,
+                   const T* __restrict__ fronts, const double* __restrict__ rhs, int rhs_mode,
+                   T* __restrict__ V, double* out, double* acc, int R, int K) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_unit;
+  const Sync sy{done, err, nch};
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_unit = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int u = s_unit;
+    __syncthreads();
+    if (u >= nunits) return;
+    const SolveUnit U = units[u];
+    if (U.kind == kUnitBlk) {
+      const int r0 = U.c * U.d;
+      if (FWD)
+        blk_forward<T>(sd, U.a, U.b, r0, min(U.d, R - r0), U.c, smraw, fronts, rhs, rhs_mode, V, R, K, sy);
+      else
+        blk_backward<T>(sd, U.a, U.b, r0, min(U.d, R - r0), U.c, smraw, fronts, V, out, acc, R, K, sy);
+    } else {
+      const int SEG = U.kind == kUnitSeg8 ? 8 : (U.kind == kUnitSeg16 ? 16 : 32);
+      const int64_t sg = (int64_t)U.b + tid / SEG;
+      const SegTask t = seg_task(sd, all + U.a, sg, (int64_t)U.c, R, K);
+      if (U.kind == kUnitSeg8) {
+        auto bw = reinterpret_cast<T (*)[kRW][9]>(smraw);
+        if (FWD) seg_forward<T, 8>(sd, t, tid % 8, bw[tid / 8], fronts, rhs, rhs_mode, V, R, K, sy);
+        else seg_backward<T, 8>(sd, t, tid % 8, fronts, V, out, acc, R, K, sy);
+      } else if (U.kind == kUnitSeg16) {
+        auto bw = reinterpret_cast<T (*)[kRW][17]>(smraw);
+        if (FWD) seg_forward<T, 16>(sd, t, tid % 16, bw[tid / 16], fronts, rhs, rhs_mode, V, R, K, sy);
+        else seg_backward<T, 16>(sd, t, tid % 16, fronts, V, out, acc, R, K, sy);
+      } else {
+        auto bw = reinterpret_cast<T (*)[kRW][33]>(smraw);
+        if (FWD) seg_forward<T, 32>(sd, t, tid % 32, bw[tid / 32], fronts, rhs, rhs_mode, V, R, K, sy);
+        else seg_backward<T, 32>(sd, t, tid % 32, fronts, V, out, acc, R, K, sy);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // x[perm[i]][r] = sum_k w_k X[i][k][r]   (Eq. x_star; FP64, k ascending)
 __global__ void k_combine(SymDev sd, const double* __restrict__ X, Shifts sh, int R,
                           double* __restrict__ x) {
@@ -253,6 +764,10 @@ void set_solve_attrs() {
   cudaFuncSetAttribute(k_forward<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSolveSmem);
   cudaFuncSetAttribute(k_backward<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSolveSmem);
   cudaFuncSetAttribute(k_backward<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSolveSmem);
+  cudaFuncSetAttribute(k_forward_blk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kSolveSmem + 2 * 32 * kBS * (int)sizeof(T));
+  cudaFuncSetAttribute(k_backward_blk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kSolveSmem + 2 * 32 * kBS * (int)sizeof(T));
   done = true;
 }
 
@@ -275,15 +790,28 @@ int forward_impl(bool trans, const SymDev& sd, const LevelPlan& lp, const int32_
   for (int g = 0; g < lp.n_sgroups; ++g) {
     const auto& G = lp.sgroups[g];
     if (!G.count) continue;
+    if (!trans && G.maxF <= 32) {
+      const int64_t segs = (int64_t)G.count * K * ((R + kRW - 1) / kRW);
+      const int SEG = G.maxF <= 8 ? 8 : (G.maxF <= 16 ? 16 : 32);
+      const unsigned blocks = (unsigned)((segs * SEG + 255) / 256);
+      if (SEG == 8)
+        k_forward_seg<T, 8><<<blocks, 256, 0, st>>>(sd, d_all + G.off, segs, (const T*)fronts, rhs, rhs_mode, (T*)V, R, K);
+      else if (SEG == 16)
+        k_forward_seg<T, 16><<<blocks, 256, 0, st>>>(sd, d_all + G.off, segs, (const T*)fronts, rhs, rhs_mode, (T*)V, R, K);
+      else
+        k_forward_seg<T, 32><<<blocks, 256, 0, st>>>(sd, d_all + G.off, segs, (const T*)fronts, rhs, rhs_mode, (T*)V, R, K);
+      ++launches;
+      continue;
+    }
     const int rc = pick_rc(G.count, K, R, G.maxF, sizeof(T));
     const dim3 grid(G.count, K, (R + rc - 1) / rc);
-    const size_t smem = (size_t)rc * G.maxF * sizeof(T);
+    const size_t smem = (size_t)rc * G.maxF * sizeof(T) + (trans ? 0 : 2 * 32 * kBS * sizeof(T));
     if (trans)
       k_forward<T, true><<<grid, kSolveThreads, smem, st>>>(sd, d_all + G.off, (const T*)fronts, rhs,
                                                             rhs_mode, (T*)V, R, K, rc);
     else
-      k_forward<T, false><<<grid, kSolveThreads, smem, st>>>(sd, d_all + G.off, (const T*)fronts, rhs,
-                                                             rhs_mode, (T*)V, R, K, rc);
+      k_forward_blk<T><<<grid, kSolveThreads, smem, st>>>(sd, d_all + G.off, (const T*)fronts, rhs,
+                                                          rhs_mode, (T*)V, R, K, rc);
     ++launches;
   }
   if (cudaGetLastError() != cudaSuccess) return -1;
@@ -299,15 +827,28 @@ int backward_impl(bool trans, const SymDev& sd, const LevelPlan& lp, const int32
   for (int g = 0; g < lp.n_sgroups; ++g) {
     const auto& G = lp.sgroups[g];
     if (!G.count) continue;
+    if (!trans && G.maxF <= 32) {
+      const int64_t segs = (int64_t)G.count * K * ((R + kRW - 1) / kRW);
+      const int SEG = G.maxF <= 8 ? 8 : (G.maxF <= 16 ? 16 : 32);
+      const unsigned blocks = (unsigned)((segs * SEG + 255) / 256);
+      if (SEG == 8)
+        k_backward_seg<T, 8><<<blocks, 256, 0, st>>>(sd, d_all + G.off, segs, (const T*)fronts, (const T*)V, out, acc, R, K);
+      else if (SEG == 16)
+        k_backward_seg<T, 16><<<blocks, 256, 0, st>>>(sd, d_all + G.off, segs, (const T*)fronts, (const T*)V, out, acc, R, K);
+      else
+        k_backward_seg<T, 32><<<blocks, 256, 0, st>>>(sd, d_all + G.off, segs, (const T*)fronts, (const T*)V, out, acc, R, K);
+      ++launches;
+      continue;
+    }
     const int rc = pick_rc(G.count, K, R, G.maxF, sizeof(T));
     const dim3 grid(G.count, K, (R + rc - 1) / rc);
-    const size_t smem = (size_t)rc * G.maxF * sizeof(T);
+    const size_t smem = (size_t)rc * G.maxF * sizeof(T) + (trans ? 0 : 2 * 32 * kBS * sizeof(T));
     if (trans)
       k_backward<T, true><<<grid, kSolveThreads, smem, st>>>(sd, d_all + G.off, (const T*)fronts,
                                                              (const T*)V, out, acc, R, K, rc);
     else
-      k_backward<T, false><<<grid, kSolveThreads, smem, st>>>(sd, d_all + G.off, (const T*)fronts,
-                                                              (const T*)V, out, acc, R, K, rc);
+      k_backward_blk<T><<<grid, kSolveThreads, smem, st>>>(sd, d_all + G.off, (const T*)fronts,
+                                                           (const T*)V, out, acc, R, K, rc);
     ++launches;
   }
   if (cudaGetLastError() != cudaSuccess) return -1;
@@ -319,6 +860,13 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 }  // namespace
 
 int max_solve_front(int precision) { return kSolveSmem / (precision == PISP_FP32 ? 4 : 8); }
+
+int pick_chunk(int fronts_in_level, int K, int R) {
+  const int target = 2 * 152;
+  int chunks = (target + fronts_in_level * K - 1) / std::max(1, fronts_in_level * K);
+  chunks = std::max(1, std::min(chunks, R));
+  return std::max(1, std::min((R + chunks - 1) / chunks, kSolveChunk));
+}
 
 int launch_forward_level(int precision, bool trans, const SymDev& sd, const LevelPlan& lp,
                          const int32_t* d_all, const void* fronts, const double* rhs,
@@ -334,6 +882,53 @@ int launch_backward_level(int precision, bool trans, const SymDev& sd, const Lev
   if (precision == PISP_FP32)
     return backward_impl<float>(trans, sd, lp, d_all, fronts, V, out, acc, R, K, st);
   return backward_impl<double>(trans, sd, lp, d_all, fronts, V, out, acc, R, K, st);
+}
+
+namespace {
+template <typename T>
+int persistent_impl(bool forward, const SymDev& sd, const SolveUnit* units, int nunits, int* ticket,
+                    int* done, int* err, const int* nch, const int32_t* d_all, const void* fronts, const double* rhs,
+                    int rhs_mode, void* V, double* out, double* acc, int R, int K, int max_blk_F,
+                    cudaStream_t st) {
+  if (nunits == 0) return 0;
+  static int smem_set = 0, nsm = 0, occ_f = 0, occ_b = 0;
+  const size_t seg_smem = (size_t)(256 / 8) * kRW * 9 * sizeof(T);
+  const size_t blk_smem = (size_t)(2 * 32 * kBS + kSolveChunk * std::max(max_blk_F, 1)) * sizeof(T);
+  const size_t smem = std::max(seg_smem, blk_smem);
+  if (!smem_set) {
+    cudaFuncSetAttribute(k_solve_persistent<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_solve_persistent<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    smem_set = 1;
+  }
+  if (smem > 200 * 1024) return -1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_solve_persistent<T, true>, kSolveThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_solve_persistent<T, false>, kSolveThreads, smem);
+  const int occ = std::max(1, forward ? occ_f : occ_b);
+  const int grid = std::max(1, std::min(nunits, occ * std::max(nsm, 1)));
+  if (forward)
+    k_solve_persistent<T, true><<<grid, kSolveThreads, smem, st>>>(
+        sd, units, nunits, ticket, done, err, nch, d_all, (const T*)fronts, rhs, rhs_mode, (T*)V, out, acc, R, K);
+  else
+    k_solve_persistent<T, false><<<grid, kSolveThreads, smem, st>>>(
+        sd, units, nunits, ticket, done, err, nch, d_all, (const T*)fronts, rhs, rhs_mode, (T*)V, out, acc, R, K);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+}  // namespace
+
+int launch_solve_persistent(int precision, bool forward, const SymDev& sd, const SolveUnit* units,
+                            int nunits, int* ticket, int* done, int* err, const int* nch,
+                            const int32_t* d_all, const void* fronts, const double* rhs,
+                            int rhs_mode, void* V, double* out, double* acc, int32_t R, int32_t K,
+                            int32_t max_blk_F, cudaStream_t st) {
+  if (precision == PISP_FP32)
+    return persistent_impl<float>(forward, sd, units, nunits, ticket, done, err, nch, d_all, fronts,
+                                  rhs, rhs_mode, V, out, acc, R, K, max_blk_F, st);
+  return persistent_impl<double>(forward, sd, units, nunits, ticket, done, err, nch, d_all, fronts,
+                                 rhs, rhs_mode, V, out, acc, R, K, max_blk_F, st);
 }
 
 int launch_combine(const SymDev& sd, const double* X, const Shifts& sh, int32_t R, double* x,

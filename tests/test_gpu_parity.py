@@ -115,24 +115,25 @@ def test_factor_entries_match_pivot_free_lu(pisp):
                                        atol=1e-12 * scale)
 
 
-def test_precision_config_fp64_big_fronts(pisp):
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_precision_config_fp64_big_fronts(pisp, schedule):
     """2000-bus grid: its top fronts exceed the shared-memory path (blocked path)."""
     inst = pfgen.make_instance("precision")
     t = pfgen.symmetric_shifts(6)
     b = pfgen.rhs(inst.n, 3, 2)
-    s, val, D = _solver(pisp, [inst])
+    s, val, D = _solver(pisp, [inst], solve_schedule=schedule)
     assert s.stats()["max_front"] > 160
     s.factor(_dev(val), _dev(D), t, "fp64")
     x = s.solve(_dev(b)).cpu().numpy()
     assert _maxrel(x, _oracle_xhat(inst, t, b)) <= TOL64
 
 
-def test_batched_uneven_instances_fp64(pisp):
+@pytest.mark.parametrize("schedule,R", [(0, 3), (1, 3), (0, 19)])
+def test_batched_uneven_instances_fp64(pisp, schedule, R):
     insts = [pfgen.make_instance("batching", g) for g in (1, 3, 5, 9, 13)]
     insts.append(pfgen.random_sparse(5, 0.5, seed=3))
     t = pfgen.symmetric_shifts(4)
-    R = 3
-    s, val, D = _solver(pisp, insts)
+    s, val, D = _solver(pisp, insts, solve_schedule=schedule)
     s.factor(_dev(val), _dev(D), t, "fp64")
     N = sum(I.n for I in insts)
     b = pfgen.rhs(N, R, 5)
