@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=None)
     ap.add_argument("--eps", type=float, default=1e-2)
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of a CUDA graph")
+    ap.add_argument("--factor-policy", type=int, default=0, choices=[0, 1],
+                    help="fronts wider than 64: 0 single CTA / global blocked (default), 1 CTA clusters")
     ap.add_argument("--schedule", type=int, default=0, choices=[0, 1],
                     help="solve schedule: 0 persistent (default), 1 one launch per level")
     ap.add_argument("--quick", action="store_true",
@@ -150,12 +152,14 @@ class ClockSampler:
 class Arm:
     """One configured solver with device-resident inputs and a step function."""
 
-    def __init__(self, pisp, torch, insts, K, R, eps, precision, sweeps, workload, dev, schedule=0):
+    def __init__(self, pisp, torch, insts, K, R, eps, precision, sweeps, workload, dev, schedule=0,
+                 factor_policy=0):
         self.torch = torch
         self.insts = insts
         sizes, rp, col, val, D = concat(insts)
         t0 = time.perf_counter()
-        self.s = pisp.Solver(sizes, rp, col, device=dev.index, solve_schedule=schedule)
+        self.s = pisp.Solver(sizes, rp, col, device=dev.index, solve_schedule=schedule,
+                             factor_policy=factor_policy)
         self.analyze_ms = (time.perf_counter() - t0) * 1e3
         self.N = sum(sizes)
         self.K, self.R, self.precision, self.sweeps = K, R, precision, sweeps
@@ -263,7 +267,8 @@ def run_pisp(args, rank, world, local_rank):
         sweeps = 0
     K, R = c["K"], c["R"]
     insts = workload_instances(args.workload, rank)
-    arm = Arm(pisp, torch, insts, K, R, args.eps, precision, sweeps, args.workload, dev, args.schedule)
+    arm = Arm(pisp, torch, insts, K, R, args.eps, precision, sweeps, args.workload, dev, args.schedule,
+              args.factor_policy)
     G = len(insts)
     units = G * R
     use_graph = not args.no_graph
@@ -336,7 +341,8 @@ def run_pisp(args, rank, world, local_rank):
         "config": {"workload": args.workload, "instances": G, "N": arm.N, "nnzA": int(stats["nnzA"]),
                    "K": K, "R": R, "shifts": "symmetric +-eps*alpha", "eps": args.eps,
                    "factor_precision": precision, "combine_precision": "fp64", "sweeps": sweeps,
-                   "graph": use_graph, "solve_schedule": ["persistent", "per-level"][args.schedule], "l2": "flushed between steps (256 MB write outside the events)",
+                   "graph": use_graph, "solve_schedule": ["persistent", "per-level"][args.schedule],
+                   "factor_policy": ["single-CTA/global", "clusters"][args.factor_policy], "l2": "flushed between steps (256 MB write outside the events)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "families": families,

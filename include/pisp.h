@@ -65,6 +65,11 @@ typedef struct pisp_options {
                              CTAs take (front, k, RHS chunk) tasks in level order
                              and wait (boundedly) for their dependencies;
                              1 = one launch per level and front-size class */
+  int32_t factor_policy;  /* fronts wider than 64: 0 = one CTA each while the front
+                             fits in shared memory, else a blocked global-memory
+                             factorisation (default); 1 = thread-block clusters of
+                             up to 8 CTAs holding the front in distributed shared
+                             memory wherever it fits */
 } pisp_options;
 
 typedef struct pisp_stats {

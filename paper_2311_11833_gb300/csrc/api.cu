@@ -58,6 +58,7 @@ struct pisp_handle {
       amap_dst, rows, emap, perm, iperm, row_inst, row_ptr, col, parent;
   // persistent solve schedule (depends on K and R)
   int32_t schedule = 0;
+  int32_t factor_policy = 0;
   int32_t units_K = 0, units_R = 0;
   int32_t n_units_f = 0, n_units_b = 0, units_maxF = 0;
   Buf units_f, units_b, ticket, done, serr, nch;
@@ -69,7 +70,7 @@ struct pisp_handle {
   std::vector<pisp::BigFrontHost> h_bigF;
   Buf d_small, d_big, d_all;
   // numeric state
-  int32_t K = 0, precision = 0;
+  int32_t K = 0, precision = 0, K_hint = 1, plan_K = 0;
   double t[PISP_K_MAX] = {}, beta[PISP_K_MAX] = {}, w_last[PISP_K_MAX] = {};
   Buf fronts, vals, D, status, badcol;
   // solve state
@@ -132,13 +133,21 @@ int upload(pisp_handle* h, Buf& b, const std::vector<T>& v) {
     if (rc_) return rc_;  \
   } while (0)
 
+// Factor path of a front of size F > 64: 0 = one CTA with the front in shared
+// memory, C >= 1 = a cluster of C CTAs (distributed shared memory), -1 = the
+// blocked global-memory path.  Policy 0 (default): one CTA while the front
+// fits, else the global path.  Policy 1: clusters wherever the front fits in
+// at most 8 CTAs' shared memory.
+int factor_path(const pisp_handle* h, int F, int precision) {
+  if (h->factor_policy == 1) return pisp::front_cluster_size(F, precision);
+  return F <= pisp::small_front_limit(precision) ? 0 : -1;
+}
+
 // Groups the supernodes of every level by front size: small fronts into
 // shared-memory classes, big fronts into the blocked path, and all fronts into
 // solve classes.
 int build_plans(pisp_handle* h, int precision) {
   const pisp::Symbolic& S = h->sym;
-  const int limit = pisp::small_front_limit(precision);
-  const int fcls[5] = {16, 32, 64, 128, limit};
   const int scls[6] = {8, 16, 32, 128, 512, INT_MAX};
   h->plans.assign(S.n_levels, pisp::LevelPlan());
   h->h_small.clear();
@@ -153,9 +162,11 @@ int build_plans(pisp_handle* h, int precision) {
       const int fa = S.sn[a].F(), fb = S.sn[b].F();
       return fa != fb ? fa < fb : a < b;
     });
+    // on-chip fronts: single-CTA classes up to 64, then clusters of 1..8 CTAs
+    const int fcls[3] = {16, 32, 64};
     int lo = 0;
-    for (int c = 0; c < 5; ++c) {
-      pisp::LevelPlan::Group G{(int64_t)h->h_small.size(), 0, 0};
+    for (int c = 0; c < 3; ++c) {
+      pisp::LevelPlan::Group G{(int64_t)h->h_small.size(), 0, 0, 0};
       for (int32_t s : lst) {
         const int F = S.sn[s].F();
         if (F > lo && F <= fcls[c]) {
@@ -167,10 +178,38 @@ int build_plans(pisp_handle* h, int precision) {
       if (G.count) lp.groups[lp.n_groups++] = G;
       lo = fcls[c];
     }
+    // fronts above 64: the factor path of each front (single CTA in shared
+    // memory, a cluster of C CTAs in distributed shared memory, or the blocked
+    // global-memory path) comes from the handle's factor policy
+    auto path = [&](int F) { return factor_path(h, F, precision); };
+    for (int C = 1; C <= 8; C *= 2) {
+      pisp::LevelPlan::Group G{(int64_t)h->h_small.size(), 0, 0, C};
+      for (int32_t s : lst) {
+        const int F = S.sn[s].F();
+        if (F > 64 && path(F) == C) {
+          h->h_small.push_back(s);
+          ++G.count;
+          G.maxF = std::max(G.maxF, F);
+        }
+      }
+      if (G.count) lp.groups[lp.n_groups++] = G;
+    }
+    {
+      pisp::LevelPlan::Group G{(int64_t)h->h_small.size(), 0, 0, 0};
+      for (int32_t s : lst) {
+        const int F = S.sn[s].F();
+        if (F > 64 && path(F) == 0) {
+          h->h_small.push_back(s);
+          ++G.count;
+          G.maxF = std::max(G.maxF, F);
+        }
+      }
+      if (G.count) lp.groups[lp.n_groups++] = G;
+    }
     lp.big_off = (int64_t)h->h_big.size();
     for (int32_t s : lst) {
       const int F = S.sn[s].F();
-      if (F > limit) {
+      if (F > 64 && path(F) < 0) {
         h->h_big.push_back(s);
         h->h_bigF.push_back({F, S.sn[s].ns()});
         ++lp.big_count;
@@ -180,7 +219,7 @@ int build_plans(pisp_handle* h, int precision) {
     }
     lo = 0;
     for (int c = 0; c < 6; ++c) {
-      pisp::LevelPlan::Group G{(int64_t)h->h_all.size(), 0, 0};
+      pisp::LevelPlan::Group G{(int64_t)h->h_all.size(), 0, 0, 0};
       for (int32_t s : lst) {
         const int F = S.sn[s].F();
         if (F > lo && F <= scls[c]) {
@@ -206,7 +245,8 @@ int build_plans(pisp_handle* h, int precision) {
       }
       const double amap = (double)(S.amap_off[s + 1] - S.amap_off[s]);
       const double fac = amap * 16 + ns * 12 + child + F * F * p;
-      if (sn.F() > limit) lp.bytes_fbig += fac + 2 * F * F * p; else lp.bytes_fsmall += fac;
+      if (sn.F() > 64 && path(sn.F()) < 0) lp.bytes_fbig += fac + 2 * F * F * p;
+      else lp.bytes_fsmall += fac;
       lp.bytes_fwd_a += ns * 4 + childv * 4 + (ns * F - ns * (ns + 1) / 2) * p;
       lp.bytes_fwd_b += ns * 8 + childv * p + F * p;
       lp.bytes_bwd_a += ms * 4 + (ns * (ns + 1) / 2 + ns * ms) * p;
@@ -477,6 +517,7 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   if (h->device >= 0) TRY(set_device(h));
   pisp::SymbolicOptions so;
   h->schedule = opt ? opt->solve_schedule : 0;
+  h->factor_policy = opt ? opt->factor_policy : 0;
   h->units_K = h->units_R = 0;
   if (opt) {
     so.ordering = opt->ordering;
@@ -594,7 +635,9 @@ int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
   if (pisp_weights(t, K, beta) != PISP_OK) return fail(h, PISP_ERR_INVALID_ARG, g_last_error);
   TRY(set_device(h));
   h->factored = h->solved = false;
-  if (h->plan_precision != precision) TRY(build_plans(h, precision));
+  h->K_hint = K;
+  if (h->plan_precision != precision || h->plan_K != K) TRY(build_plans(h, precision));
+  h->plan_K = K;
   h->K = K;
   h->precision = precision;
   for (int k = 0; k < K; ++k) {

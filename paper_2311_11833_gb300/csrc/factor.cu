@@ -14,6 +14,7 @@
 // Storage: front s of perturbation k occupies F*F contiguous elements
 // (column-major) at K*front_off[s] + k*F*F.  After factorisation it holds
 // L11\U11, L21, U12 and the Schur complement F22 that the parent reads.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -287,6 +288,199 @@ __global__ void __launch_bounds__(256) k_update_big(SymDev sd, const int32_t* __
     }
 }
 
+// Pivot-free LU of a panel P (rows p0..F-1, nb <= 32 columns, P[i + c*F] =
+// front(i, p0 + c), in shared memory) by one CTA.  Threads update whole rows
+// in place.  The thread that finishes row p0+c+1 during step c also copies it
+// to the other half of a double-buffered pivot row, so each pivot costs one
+// barrier.
+template <typename T>
+__device__ __forceinline__ void panel_factor_rows(T* P, int F, int p0, int nb, T (*prow)[32],
+                                                  const SymDev& sd, int s, int k, int K, int c0,
+                                                  int32_t* status, int32_t* badcol) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid < nb) prow[0][tid] = P[p0 + tid * F];
+  for (int c = 0; c < nb; ++c) {
+    __syncthreads();
+    const T* pr = prow[c & 1];
+    const int pc = p0 + c;
+    const T piv = pr[c];
+    if (tid == 0) check_pivot(piv, sd, s, k, K, c0 + pc, status, badcol);
+    for (int r = pc + 1 + tid; r < F; r += nt) {
+      const T l = P[r + c * F] / piv;
+      P[r + c * F] = l;
+      for (int j = c + 1; j < nb; ++j) P[r + j * F] -= l * pr[j];
+      if (r == pc + 1 && c + 1 < nb)
+        for (int j = 0; j < nb; ++j) prow[(c + 1) & 1][j] = P[r + j * F];
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Mid-size fronts: one thread-block cluster of C CTAs per (front, k).  The
+// front's columns are dealt out to the CTAs in widths cw (a multiple of 32)
+// and live in their shared memory for the whole factorisation.  For each
+// panel of 32 pivots the owning CTA factors it locally, one cluster barrier
+// publishes it, and every CTA copies the panel over distributed shared
+// memory, solves its part of the U row block and applies a register-tiled
+// update to its columns.  Only the owner's panel columns are ever read
+// remotely and they are not written after being factored, so one barrier per
+// panel suffices; a final barrier keeps every CTA resident until the last
+// remote read is done.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int cluster_cw(int F, int C) {
+  return (((F + C - 1) / C) + 31) / 32 * 32;
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ size_t cluster_smem(int F, int C) {
+  const size_t cw = (size_t)cluster_cw(F, C);
+  return ((size_t)F * cw + (C > 1 ? (size_t)F * 32 : 0) + 32 * 33) * sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_front_cluster(SymDev sd, const int32_t* __restrict__ list,
+                                                       int C, const double* __restrict__ vals,
+                                                       const double* __restrict__ D, Shifts sh,
+                                                       T* __restrict__ fronts, int32_t* status,
+                                                       int32_t* badcol) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int rank = (int)cl.block_rank();
+  const int s = list[blockIdx.x / C];
+  const int k = blockIdx.y;
+  const int K = sh.K;
+  const int ns = sd.ns[s], ms = sd.ms[s], F = ns + ms;
+  const int cw = cluster_cw(F, C);
+  const int j0 = min(F, rank * cw), j1 = min(F, j0 + cw);
+  const int nc = j1 - j0;
+  T* M = reinterpret_cast<T*>(smraw);                  // my columns, F x cw, ld F
+  T* Lp = M + (size_t)F * cw;                           // copy of a remote panel
+  T* L11 = Lp + (C > 1 ? (size_t)F * 32 : 0);           // 32 x 33 unit-lower block
+  __shared__ T prow[2][32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int c0 = sd.c0[s];
+  // 1. assembly of my columns
+  for (int q = tid; q < F * nc; q += nt) M[q] = T(0);
+  __syncthreads();
+  if (nc > 0) {
+    const int64_t a0 = sd.amap_off[s], a1 = sd.amap_off[s + 1];
+    const int64_t lo = lower_bound_col(sd.amap_dst, a0, a1, F, j0);
+    const int64_t hi = lower_bound_col(sd.amap_dst, lo, a1, F, j1);
+    for (int64_t q = lo + tid; q < hi; q += nt)
+      atomicAdd(&M[sd.amap_dst[q] - j0 * F], (T)vals[sd.amap_src[q]]);
+    const double tk = sh.t[k];
+    for (int c = j0 + tid; c < min(j1, ns); c += nt)
+      atomicAdd(&M[c + (c - j0) * F], (T)(tk * D[sd.perm[c0 + c]]));
+  }
+  __syncthreads();
+  for (int ci = sd.child_off[s]; ci < sd.child_off[s + 1]; ++ci) {
+    const int c = sd.child[ci];
+    const int cns = sd.ns[c], cms = sd.ms[c], cF = cns + cms;
+    const int32_t* em = sd.emap + sd.row_off[c];
+    const int b0 = lower_bound_i(em, cms, j0);
+    const int b1 = lower_bound_i(em, cms, j1);
+    if (b1 > b0) {
+      const T* cf = fronts + (int64_t)K * sd.front_off[c] + (int64_t)k * cF * cF;
+      const int n2 = (b1 - b0) * cms;
+      for (int q = tid; q < n2; q += nt) {
+        const int a = q % cms, b = b0 + q / cms;
+        M[em[a] + (em[b] - j0) * F] += cf[(cns + a) + (int64_t)(cns + b) * cF];
+      }
+    }
+    __syncthreads();
+  }
+  // 2. blocked right-looking elimination, 32 pivots per panel
+  const int tx = tid & 15, ty = tid >> 4;
+  for (int p0 = 0; p0 < ns; p0 += 32) {
+    const int nb = min(32, ns - p0);
+    const int owner = p0 / cw;
+    if (rank == owner) panel_factor_rows<T>(M + (size_t)(p0 - j0) * F, F, p0, nb, prow, sd, s, k,
+                                            K, c0, status, badcol);
+    cl.sync();
+    const int jlo = max(j0, p0 + nb);
+    if (jlo < j1) {
+      const T* Ls;                                       // Ls[i + c*F] = front(i, p0 + c)
+      if (rank == owner) {
+        Ls = M + (size_t)(p0 - j0) * F;
+      } else {
+        const T* R = cl.map_shared_rank(M, owner) + (size_t)(p0 - owner * cw) * F;
+        const int hr = F - p0;
+        for (int e = tid; e < hr * nb; e += nt) {
+          const int i = p0 + e % hr, c = e / hr;
+          Lp[i + c * F] = R[i + c * F];
+        }
+        Ls = Lp;
+      }
+      __syncthreads();
+      for (int e = tid; e < 32 * 32; e += nt) {
+        const int r = e >> 5, c = e & 31;
+        L11[r * 33 + c] = (r < nb && c < r) ? Ls[(p0 + r) + c * F] : T(0);
+      }
+      __syncthreads();
+      // (a) U row block of my columns: unit-lower triangular solve, one column per thread
+      for (int j = jlo + tid; j < j1; j += nt) {
+        T* col = M + (size_t)(j - j0) * F + p0;
+        T u[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) u[r] = (r < nb) ? col[r] : T(0);
+#pragma unroll
+        for (int r = 1; r < 32; ++r) {
+          T a = u[r];
+#pragma unroll
+          for (int c = 0; c < 31; ++c)
+            if (c < r) a -= L11[r * 33 + c] * u[c];
+          u[r] = a;
+        }
+#pragma unroll
+        for (int r = 0; r < 32; ++r)
+          if (r < nb) col[r] = u[r];
+      }
+      __syncthreads();
+      // (b) trailing update of my columns, 64 x 64 tiles, 4 x 4 per thread
+      const int r0 = p0 + nb;
+      for (int rb = r0; rb < F; rb += 64) {
+        for (int cb = jlo; cb < j1; cb += 64) {
+          T acc[4][4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+          for (int c = 0; c < nb; ++c) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+              const int i = rb + tx + 16 * a;
+              av[a] = (i < F) ? Ls[i + c * F] : T(0);
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              const int j = cb + ty + 16 * b;
+              bv[b] = (j < j1) ? M[(p0 + c) + (size_t)(j - j0) * F] : T(0);
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+              for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+          }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              const int i = rb + tx + 16 * a, j = cb + ty + 16 * b;
+              if (i < F && j < j1) M[i + (size_t)(j - j0) * F] -= acc[a][b];
+            }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  cl.sync();
+  T* out = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * F * F + (int64_t)j0 * F;
+  for (int e = tid; e < F * nc; e += nt) out[e] = M[e];
+}
+
 template <typename T>
 int small_threads(int maxF) {
   if (maxF <= 16) return 64;
@@ -300,6 +494,7 @@ void set_smem_attrs() {
   static bool done = false;
   if (done) return;
   cudaFuncSetAttribute(k_front_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  cudaFuncSetAttribute(k_front_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
   cudaFuncSetAttribute(k_panel_big<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
   cudaFuncSetAttribute(k_panel_big<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
   cudaFuncSetAttribute(k_panel_big<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
@@ -343,9 +538,29 @@ int factor_small_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_sm
   for (int g = 0; g < lp.n_groups; ++g) {
     const auto& G = lp.groups[g];
     if (G.count == 0) continue;
-    const size_t smem = (size_t)G.maxF * G.maxF * sizeof(T);
-    k_front_small<T><<<dim3(G.count, K), small_threads<T>(G.maxF), smem, st>>>(
-        sd, d_small + G.off, vals, D, sh, fr, status, badcol);
+    if (G.cluster == 0) {
+      const size_t smem = (size_t)G.maxF * G.maxF * sizeof(T);
+      k_front_small<T><<<dim3(G.count, K), small_threads<T>(G.maxF), smem, st>>>(
+          sd, d_small + G.off, vals, D, sh, fr, status, badcol);
+    } else {
+      const int C = G.cluster;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(G.count * C, K, 1);
+      cfg.blockDim = dim3(256, 1, 1);
+      cfg.dynamicSmemBytes = cluster_smem<T>(G.maxF, C);
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      const int32_t* lst = d_small + G.off;
+      if (cudaLaunchKernelEx(&cfg, k_front_cluster<T>, sd, lst, C, vals, D, sh, fr, status, badcol) !=
+          cudaSuccess)
+        return -1;
+    }
     ++launches;
   }
   if (cudaGetLastError() != cudaSuccess) return -1;
@@ -384,6 +599,15 @@ int factor_big_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,
 }  // namespace
 
 int small_front_limit(int precision) { return precision == PISP_FP32 ? 224 : 160; }
+
+int front_cluster_size(int F, int precision) {
+  if (F <= 64) return 0;
+  for (int C = 1; C <= 8; C *= 2) {
+    const size_t need = precision == PISP_FP32 ? cluster_smem<float>(F, C) : cluster_smem<double>(F, C);
+    if (need <= (size_t)kSmemCap) return C;
+  }
+  return -1;
+}
 
 int max_big_front(int precision) {
   return kSmemCap / (4 * (precision == PISP_FP32 ? 4 : 8));

@@ -45,9 +45,10 @@ struct Shifts {
 struct LevelPlan {
   // small fronts (factored in shared memory), grouped by size class
   struct Group {
-    int64_t off;    // offset into the device list of small fronts
-    int32_t count;  // fronts in the group
-    int32_t maxF;   // largest front in the group
+    int64_t off;      // offset into the device list of small fronts
+    int32_t count;    // fronts in the group
+    int32_t maxF;     // largest front in the group
+    int32_t cluster;  // 0: one CTA per (front, k); C > 0: clusters of C CTAs
   };
   Group groups[8];
   int32_t n_groups = 0;
@@ -84,6 +85,10 @@ int launch_factor_big(int precision, const SymDev& sd, const LevelPlan& lp, cons
                       cudaStream_t st);
 // largest front (in elements of the given precision) the shared-memory path takes
 int small_front_limit(int precision);
+// CTAs per cluster for a front of size F factored in distributed shared
+// memory: 0 for F <= 64 (single-CTA kernel), -1 if the front does not fit
+// (blocked path in global memory)
+int front_cluster_size(int F, int precision);
 // largest front the blocked path can take (its panel must fit in shared memory)
 int max_big_front(int precision);
 // largest front the solve kernels can take

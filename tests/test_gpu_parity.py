@@ -115,6 +115,37 @@ def test_factor_entries_match_pivot_free_lu(pisp):
                                        atol=1e-12 * scale)
 
 
+@pytest.mark.parametrize("n,density,prec,policy", [
+    (220, 0.03, "fp64", 0), (300, 0.03, "fp64", 0), (300, 0.03, "fp32", 0), (700, 0.012, "fp32", 0),
+    (220, 0.03, "fp64", 1), (300, 0.03, "fp64", 1), (300, 0.03, "fp32", 1), (420, 0.02, "fp32", 1),
+    (700, 0.012, "fp32", 1)])
+def test_factor_entries_large_fronts(pisp, n, density, prec, policy):
+    """Fronts factored in shared memory, by CTA clusters or by the blocked global path
+    equal dense Doolittle's."""
+    inst = pfgen.random_sparse(n, density, seed=n)
+    t = pfgen.symmetric_shifts(2)
+    s, val, D = _solver(pisp, [inst], factor_policy=policy)
+    s.factor(_dev(val), _dev(D), t, prec)
+    assert s.stats()["max_front"] > 100
+    perm = s.perm()
+    c0, c1, ms, rows = s.supernodes()
+    A = oracle.to_dense(inst)
+    roff = np.concatenate([[0], np.cumsum(ms)])
+    tol = 1e-11 if prec == "fp64" else 2e-4
+    for k in (0, 1):
+        L, U = oracle.pivot_free_lu(A, inst.D, t[k], perm)
+        scale = np.abs(U).max()
+        for sn in range(len(c0)):
+            idx = np.concatenate([np.arange(c0[sn], c1[sn]), rows[roff[sn]:roff[sn + 1]]])
+            ns = c1[sn] - c0[sn]
+            Fr = s.front(sn, k)
+            LU = np.tril(L[np.ix_(idx, idx[:ns])], -1) + np.triu(U[np.ix_(idx, idx[:ns])])
+            lscale = max(1.0, np.abs(LU).max())
+            np.testing.assert_allclose(Fr[:, :ns], LU, rtol=0, atol=tol * max(scale, lscale))
+            np.testing.assert_allclose(Fr[:ns, ns:], U[np.ix_(idx[:ns], idx[ns:])], rtol=0,
+                                       atol=tol * scale)
+
+
 @pytest.mark.parametrize("schedule", [0, 1])
 def test_precision_config_fp64_big_fronts(pisp, schedule):
     """2000-bus grid: its top fronts exceed the shared-memory path (blocked path)."""
