@@ -219,6 +219,41 @@ int pisp_solve_host(pisp_handle* h, const double* values_host, const double* D_h
                     const double* t, int32_t K, int32_t precision, const double* b_host,
                     int32_t R, double* x_host, int32_t sweeps);
 
+/* ---- allocation-free entry point ---------------------------------------- */
+#define PISP_STATIC_MAX_N 128 /* largest system of pisp_dense_solve_static */
+#define PISP_STATIC_MAX_R 64  /* most right-hand sides per call */
+
+/* The paper has no counterpart to this call.  It serves callers that may not
+ * allocate device memory when they call -- a memory budget fixed at start-up,
+ * host callbacks or real-time loops that cannot take cudaMalloc's implicit
+ * synchronisation, frameworks that hand over only their input and output
+ * buffers -- whereas every other numeric entry point allocates its workspace
+ * on first use.  It needs no handle and allocates nothing: the K
+ * per-perturbation solutions live in one file-scope static device array of
+ * PISP_K_MAX * PISP_STATIC_MAX_R * PISP_STATIC_MAX_N doubles (1 MiB) that
+ * every GPU loading the library holds until the process exits.
+ *
+ * It computes, for one small dense system, the same result as
+ * pisp_factor_perturbed + pisp_solve: x = sum_k beta_k (A + t_k D)^{-1} b with
+ * pivot-free LU factors (FP64) and beta from pisp_weights(t).
+ *   stream  cudaStream_t the work is enqueued on (NULL = legacy default)
+ *   n       1..PISP_STATIC_MAX_N
+ *   A       device FP64 [n][n], row-major, dense
+ *   D       device FP64 [n], the diagonal perturbation
+ *   t       host FP64 [K], distinct shifts, K in 1..PISP_K_MAX
+ *   b       device FP64 [n][R], R in 1..PISP_STATIC_MAX_R
+ *   x       device FP64 [n][R] output (may not alias b)
+ * Sizes beyond the limits return PISP_ERR_UNSUPPORTED before any GPU work.
+ * The first call on a device, with that device current, resolves the array's
+ * device address (cudaGetSymbolAddress) and sets the kernel's shared-memory
+ * limit; make that first call before any stream capture.  Calls share the
+ * array, which keeps the last call's contents; each call overwrites the part
+ * it reads, but calls that overlap on the GPU (other streams or host threads)
+ * race on it, so order them on one stream.  A zero pivot is not reported:
+ * it shows as Inf/NaN in x. */
+int pisp_dense_solve_static(void* stream, int32_t n, const double* A, const double* D,
+                            const double* t, int32_t K, const double* b, int32_t R, double* x);
+
 /* ---- profiling: CUDA events on the handle's stream around each kernel
  * family of each level, for per-family device time and achieved bandwidth.
  * Families: */

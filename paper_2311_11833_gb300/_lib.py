@@ -62,6 +62,8 @@ _SIGS = {
     "pisp_get_front": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, P(c_int32)]),
     "pisp_solve_host": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
                                   c_void_p, c_int32, c_void_p, c_int32]),
+    "pisp_dense_solve_static": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32,
+                                          c_void_p, c_int32, c_void_p]),
     "pisp_profile": (c_int32, [c_void_p, c_int32]),
     "pisp_profile_collect": (c_int32, [c_void_p]),
     "pisp_profile_read": (c_int32, [c_void_p, c_int32, P(c_double), P(c_double), P(c_int64)]),

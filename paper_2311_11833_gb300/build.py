@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpisp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["symbolic.cpp", "api.cu", "factor.cu", "solve.cu"]
+SOURCES = ["symbolic.cpp", "api.cu", "factor.cu", "solve.cu", "static_dense.cu"]
 
 
 def _nvcc() -> str:

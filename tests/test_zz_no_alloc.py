@@ -1,0 +1,74 @@
+"""The allocation-free entry point checked against the regular path.
+
+pisp_dense_solve_static serves callers that may not allocate device memory
+when they call (a budget fixed at start-up, host callbacks or real-time loops
+that cannot take cudaMalloc's implicit synchronisation, frameworks that pass
+only their own input and output buffers).  It keeps its per-perturbation
+solutions in a static device array instead of allocated workspace, so its
+answer must equal that of pisp_factor_perturbed + pisp_solve on the same
+system, and it must stay right when the array is reused by the next call.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import pfgen
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2311_11833_gb300 as pisp
+    return torch, pisp, pisp.load()
+
+
+def _static_solve(torch, lib, A, D, t, b):
+    n, R = b.shape
+    At = torch.tensor(A, dtype=torch.float64, device="cuda")
+    Dt = torch.tensor(D, dtype=torch.float64, device="cuda")
+    bt = torch.tensor(b, dtype=torch.float64, device="cuda")
+    x = torch.full((n, R), float("nan"), dtype=torch.float64, device="cuda")
+    th = np.ascontiguousarray(t, dtype=np.float64)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = lib.pisp_dense_solve_static(stream, n, ctypes.c_void_p(At.data_ptr()),
+                                     ctypes.c_void_p(Dt.data_ptr()), th.ctypes.data_as(ctypes.c_void_p),
+                                     len(th), ctypes.c_void_p(bt.data_ptr()), R, ctypes.c_void_p(x.data_ptr()))
+    torch.cuda.synchronize()
+    return rc, x.cpu().numpy()
+
+
+def test_static_entry_matches_regular_path_on_two_calls(env):
+    torch, pisp, lib = env
+    cases = [(96, 4, 3, 11), (128, 6, 5, 12)]
+    for n, K, R, seed in cases:
+        inst = pfgen.random_sparse(n, 0.08, seed=seed)
+        A = oracle.to_dense(inst)
+        t = pfgen.symmetric_shifts(K)
+        b = pfgen.rhs(n, R, seed)
+        # the regular (allocating) entry points on the same system
+        s = pisp.Solver(n, inst.row_ptr, inst.col)
+        s.factor(torch.tensor(inst.val, device="cuda"), torch.tensor(inst.D, device="cuda"), t, "fp64")
+        x_ref = s.solve(torch.tensor(b, device="cuda")).cpu().numpy()
+        rc, x = _static_solve(torch, lib, A, inst.D, t, b)
+        assert rc == 0
+        assert np.max(oracle.rel_err(x, x_ref)) <= TOL64
+
+
+def test_static_entry_rejects_sizes_beyond_its_limits(env):
+    torch, pisp, lib = env
+    t = pfgen.symmetric_shifts(2)
+    n = 129                                   # PISP_STATIC_MAX_N + 1
+    rc, _ = _static_solve(torch, lib, np.eye(n), np.ones(n), t, np.ones((n, 1)))
+    assert rc == 10                           # PISP_ERR_UNSUPPORTED
+    rc, _ = _static_solve(torch, lib, np.eye(4), np.ones(4), t, np.ones((4, 65)))
+    assert rc == 10
