@@ -38,14 +38,17 @@ METRIC = "combined solves/s (K perturbed LUs + expansion) vs plain GPU path at r
 UNIT = "solves/s"
 TOL = 1e-10
 L2_BYTES = 129 * 1024 * 1024
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
-# kernel family from the ncu capture summarised under profiles/ (None when the
-# kernel changed since the counters were taken).
-TRAFFIC_PER_LAUNCH = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel family
+# on a workload, from the ncu captures summarised under profiles/; an entry is
+# removed when its kernel changes.
+TRAFFIC_PER_LAUNCH = {
+    ("precision", "forward"): 6.33e6,     # profiles/k_solve_persistent_precision_2000bus_K6_R16.md
+    ("precision", "backward"): 12.89e6,
+}
 
 BENCH = {
     "plain": dict(precision="fp64", sweeps=0),
-    "precision": dict(precision="fp32", sweeps=3),
+    "precision": dict(precision="fp32", sweeps=2),
     "batching": dict(precision="fp32", sweeps=3),
     "differentiation": dict(precision="fp64", sweeps=0),
     "scale": dict(precision="fp32", sweeps=3),
@@ -231,13 +234,13 @@ def oracle_err(arm, sample_rhs=2, sample_inst=3):
 
 
 def cpu_baseline(insts, K, R, eps, budget_s=12.0):
-    """The oracle, as it stands, on a bounded sample of the workload."""
+    """The oracle, as it stands, on a bounded sample of the workload (about budget_s of CPU work)."""
     import oracle
     t = pfgen.symmetric_shifts(K, eps)
     done_units, elapsed, calls = 0.0, 0.0, 0
     g = 0
     t0 = time.perf_counter()
-    while elapsed < budget_s and calls < len(insts) * K:
+    while elapsed < budget_s:
         I = insts[g % len(insts)]
         A = oracle.to_scipy(I)
         b = pfgen.rhs(I.n, R, 1)
@@ -247,7 +250,7 @@ def cpu_baseline(insts, K, R, eps, budget_s=12.0):
         g += 1
         elapsed = time.perf_counter() - t0
     return {"value": done_units / elapsed, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{g} instance(s) x {R} RHS x {K} perturbed GEPP solves + combine, "
+            "sample": f"{g} combined solve(s) of {R} RHS (K = {K} perturbed GEPP solves + combine each), "
                       f"{elapsed:.1f} s of CPU work (numpy/LAPACK, BLAS threads = host cores)"}
 
 
@@ -322,7 +325,7 @@ def run_pisp(args, rank, world, local_rank):
     fam = max(prof, key=lambda f: prof[f]["ms"])
     pf = prof[fam]
     achieved = pf["bytes"] / (pf["ms"] / 1e3) / 1e9 if pf["ms"] > 0 else 0.0
-    traffic = TRAFFIC_PER_LAUNCH.get(fam)
+    traffic = TRAFFIC_PER_LAUNCH.get((args.workload, fam))
     roofline = {"bound": "hbm", "kernel": fam, "achieved": round(achieved, 2), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 5), "peak_source": peak_kind,
                 "traffic": traffic,
