@@ -367,3 +367,23 @@ def test_full_batching_config_sampled(pisp):
         sl = slice(offs[g], offs[g + 1])
         assert _maxrel(x[sl], _oracle_xhat(I, t, b[sl])) <= TOL64
     assert np.all(np.isfinite(x))
+
+
+# ------------------------------------------------------------ shift split --
+def test_shift_split_partials_sum_to_full_combine(pisp):
+    """Each rank's partial (its shifts, full-set weights) sums to the full x_hat."""
+    from paper_2311_11833_gb300 import shard
+    inst = pfgen.make_instance("plain")
+    t = pfgen.symmetric_shifts(6)
+    beta = pisp.weights(t)
+    b = _dev(pfgen.rhs(inst.n, 3, 4))
+    s, val, D = _solver(pisp, [inst])
+    vals, Dd = _dev(val), _dev(D)
+    s.factor(vals, Dd, t, "fp64")
+    full = s.solve(b).cpu().numpy()
+    total = 0
+    for r in range(4):                       # 4 ranks, one of them without shifts
+        idx = shard.shift_subset(len(t), r, 4)
+        part = shard.gpu_partial(s, vals, Dd, b, precision="fp64", sweeps=0)
+        total = total + part(t[idx], beta[idx]).cpu().numpy()
+    assert _maxrel(total, full) <= TOL64
