@@ -70,6 +70,8 @@ def parse():
                     help="fronts wider than 64: 0 single CTA / global blocked (default), 1 CTA clusters")
     ap.add_argument("--schedule", type=int, default=0, choices=[0, 1],
                     help="solve schedule: 0 persistent (default), 1 one launch per level")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time candidate library options on this workload first and use the fastest")
     ap.add_argument("--quick", action="store_true",
                     help="timed arm only (no plain-FP64 arm, e2e, CPU baseline or oracle check)")
     return ap.parse_args()
@@ -156,13 +158,13 @@ class Arm:
     """One configured solver with device-resident inputs and a step function."""
 
     def __init__(self, pisp, torch, insts, K, R, eps, precision, sweeps, workload, dev, schedule=0,
-                 factor_policy=0):
+                 factor_policy=0, options=None):
         self.torch = torch
         self.insts = insts
         sizes, rp, col, val, D = concat(insts)
         t0 = time.perf_counter()
-        self.s = pisp.Solver(sizes, rp, col, device=dev.index, solve_schedule=schedule,
-                             factor_policy=factor_policy)
+        opts = options or dict(solve_schedule=schedule, factor_policy=factor_policy)
+        self.s = pisp.Solver(sizes, rp, col, device=dev.index, **opts)
         self.analyze_ms = (time.perf_counter() - t0) * 1e3
         self.N = sum(sizes)
         self.K, self.R, self.precision, self.sweeps = K, R, precision, sweeps
@@ -270,8 +272,15 @@ def run_pisp(args, rank, world, local_rank):
         sweeps = 0
     K, R = c["K"], c["R"]
     insts = workload_instances(args.workload, rank)
+    tuned = None
+    if args.autotune:
+        from paper_2311_11833_gb300 import tune
+        sizes, rp, col, val, D = concat(insts)
+        tuned = tune.autotune(sizes, rp, col, torch.tensor(val, device=dev), torch.tensor(D, device=dev),
+                              pfgen.symmetric_shifts(K, args.eps),
+                              torch.tensor(pfgen.rhs(sum(sizes), R, 1), device=dev), precision, sweeps)
     arm = Arm(pisp, torch, insts, K, R, args.eps, precision, sweeps, args.workload, dev, args.schedule,
-              args.factor_policy)
+              args.factor_policy, options=tuned["options"] if tuned else None)
     G = len(insts)
     units = G * R
     use_graph = not args.no_graph
@@ -351,6 +360,11 @@ def run_pisp(args, rank, world, local_rank):
         "families": families,
         "gpu_launches": int(stats["gpu_launches"]) * args.steps,
         "analyze_ms": round(arm.analyze_ms, 2),
+        "autotune": ({"options": tuned["options"], "candidates": len(tuned["all"]),
+                      "best_ms": round(tuned["ms"], 4),
+                      "default_ms": round(next((r["ms"] for r in tuned["all"] if r["options"] == dict(
+                          relax_small=8, relax_zeros=0.05, factor_policy=0, solve_schedule=0)), float("nan")), 4)}
+                     if tuned else None),
         "wall_s_timed_region": round(wall, 3),
         "structure": {k: stats[k] for k in ("nnzL", "nnzF_stored", "n_supernodes", "n_levels",
                                             "max_front", "etree_height")},

@@ -387,3 +387,25 @@ def test_shift_split_partials_sum_to_full_combine(pisp):
         part = shard.gpu_partial(s, vals, Dd, b, precision="fp64", sweeps=0)
         total = total + part(t[idx], beta[idx]).cpu().numpy()
     assert _maxrel(total, full) <= TOL64
+
+
+# --------------------------------------------------------------- autotune --
+def test_autotune_picks_a_candidate_and_caches(pisp, tmp_path):
+    from paper_2311_11833_gb300 import tune
+    inst = pfgen.make_instance("plain")
+    t = pfgen.symmetric_shifts(4)
+    b = _dev(pfgen.rhs(inst.n, 2, 1))
+    cache = str(tmp_path / "tune.json")
+    opts = [dict(relax_small=8, relax_zeros=0.05, factor_policy=0, solve_schedule=0),
+            dict(relax_small=16, relax_zeros=0.1, factor_policy=1, solve_schedule=1)]
+    r = tune.autotune([inst.n], inst.row_ptr, inst.col, _dev(inst.val), _dev(inst.D), t, b, "fp64", 0,
+                      reps=2, cache=cache, options=opts)
+    assert r["options"] in opts and len(r["all"]) == 2 and r["ms"] > 0
+    again = tune.autotune([inst.n], inst.row_ptr, inst.col, _dev(inst.val), _dev(inst.D), t, b, "fp64", 0,
+                          reps=2, cache=cache, options=opts)
+    assert again["options"] == r["options"]
+    # the tuned options give the same answer
+    s, val, D = _solver(pisp, [inst], **r["options"])
+    s.factor(_dev(val), _dev(D), t, "fp64")
+    x = s.solve(b).cpu().numpy()
+    assert _maxrel(x, _oracle_xhat(inst, t, pfgen.rhs(inst.n, 2, 1))) <= TOL64
