@@ -43,6 +43,41 @@ __device__ __forceinline__ void check_pivot(T piv, const SymDev& sd, int s, int 
   }
 }
 
+// Pivot-free LU of a panel in shared memory: rows p0..F-1 of nb <= 32
+// columns, P[i + c*ld] = front(i, p0 + c).  Warps take rows; lane j of a warp
+// updates column j, so a row costs one instruction group.  The warp that
+// finishes row p0+c+1 during step c also copies it to the other half of a
+// double-buffered pivot row, so each pivot costs one block barrier.  An odd
+// ld keeps the lanes' column accesses on distinct banks.
+template <typename T>
+__device__ __forceinline__ void panel_factor_rows(T* P, int ld, int F, int p0, int nb,
+                                                  T (*prow)[32], const SymDev& sd, int s, int k,
+                                                  int K, int colbase, int32_t* status,
+                                                  int32_t* badcol) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (wid == 0 && lane < nb) prow[0][lane] = P[p0 + lane * ld];
+  for (int c = 0; c < nb; ++c) {
+    __syncthreads();
+    const T* pr = prow[c & 1];
+    const int pc = p0 + c;
+    const T piv = pr[c];
+    if (threadIdx.x == 0) check_pivot(piv, sd, s, k, K, colbase + c, status, badcol);
+    const T rp = T(1) / piv;
+    const T pj = (lane > c && lane < nb) ? pr[lane] : T(0);
+    for (int i = pc + 1 + wid; i < F; i += nw) {
+      const T l = P[i + c * ld] * rp;
+      __syncwarp();
+      if (lane == c) P[i + c * ld] = l;
+      else if (lane > c && lane < nb) P[i + lane * ld] -= l * pj;
+      if (i == pc + 1 && c + 1 < nb) {
+        __syncwarp();
+        if (lane < nb) prow[(c + 1) & 1][lane] = P[i + lane * ld];
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // Small fronts: whole front in shared memory, one CTA per (front, k).
 // ---------------------------------------------------------------------------
@@ -184,31 +219,33 @@ __global__ void __launch_bounds__(512) k_panel_big(SymDev sd, const int32_t* __r
   if (p0 >= ns) return;
   const int nbe = min(NB, ns - p0);
   const int Mr = F - p0;
+  const int ld = Mr | 1;
   const int tid = threadIdx.x, nt = blockDim.x;
   T* f = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * F * F;
   const int np = Mr * nbe;
   for (int q = tid; q < np; q += nt) {
     const int i = q % Mr, c = q / Mr;
-    P[q] = f[(p0 + i) + (int64_t)(p0 + c) * F];
+    P[i + c * ld] = f[(p0 + i) + (int64_t)(p0 + c) * F];
   }
   __syncthreads();
   const int c0 = sd.c0[s];
   for (int c = 0; c < nbe; ++c) {
-    const T piv = P[c + c * Mr];
+    const T piv = P[c + c * ld];
     if (tid == 0) check_pivot(piv, sd, s, k, K, c0 + p0 + c, status, badcol);
-    for (int i = c + 1 + tid; i < Mr; i += nt) P[i + c * Mr] /= piv;
+    const T rp = T(1) / piv;
+    for (int i = c + 1 + tid; i < Mr; i += nt) P[i + c * ld] *= rp;
     __syncthreads();
     const int h = Mr - c - 1, w = nbe - c - 1;
     const int n2 = h * w;
     for (int q = tid; q < n2; q += nt) {
       const int i = c + 1 + q % h, cc = c + 1 + q / h;
-      P[i + cc * Mr] -= P[i + c * Mr] * P[c + cc * Mr];
+      P[i + cc * ld] -= P[i + c * ld] * P[c + cc * ld];
     }
     __syncthreads();
   }
   for (int q = tid; q < np; q += nt) {
     const int i = q % Mr, c = q / Mr;
-    f[(p0 + i) + (int64_t)(p0 + c) * F] = P[q];
+    f[(p0 + i) + (int64_t)(p0 + c) * F] = P[i + c * ld];
   }
   // row block of U: columns j >= p0 + nbe
   for (int j = p0 + nbe + tid; j < F; j += nt) {
@@ -221,7 +258,7 @@ __global__ void __launch_bounds__(512) k_panel_big(SymDev sd, const int32_t* __r
       T a = u[q];
 #pragma unroll
       for (int r = 0; r < NB - 1; ++r)
-        if (r < q) a -= P[q + r * Mr] * u[r];
+        if (r < q) a -= P[q + r * ld] * u[r];
       u[q] = a;
     }
 #pragma unroll
@@ -286,34 +323,6 @@ __global__ void __launch_bounds__(256) k_update_big(SymDev sd, const int32_t* __
       const int r = i0 + tx + 16 * i, c = j0 + ty + 16 * j;
       if (r < F && c < F) f[r + (int64_t)c * F] -= acc[i][j];
     }
-}
-
-// Pivot-free LU of a panel P (rows p0..F-1, nb <= 32 columns, P[i + c*F] =
-// front(i, p0 + c), in shared memory) by one CTA.  Threads update whole rows
-// in place.  The thread that finishes row p0+c+1 during step c also copies it
-// to the other half of a double-buffered pivot row, so each pivot costs one
-// barrier.
-template <typename T>
-__device__ __forceinline__ void panel_factor_rows(T* P, int F, int p0, int nb, T (*prow)[32],
-                                                  const SymDev& sd, int s, int k, int K, int c0,
-                                                  int32_t* status, int32_t* badcol) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid < nb) prow[0][tid] = P[p0 + tid * F];
-  for (int c = 0; c < nb; ++c) {
-    __syncthreads();
-    const T* pr = prow[c & 1];
-    const int pc = p0 + c;
-    const T piv = pr[c];
-    if (tid == 0) check_pivot(piv, sd, s, k, K, c0 + pc, status, badcol);
-    for (int r = pc + 1 + tid; r < F; r += nt) {
-      const T l = P[r + c * F] / piv;
-      P[r + c * F] = l;
-      for (int j = c + 1; j < nb; ++j) P[r + j * F] -= l * pr[j];
-      if (r == pc + 1 && c + 1 < nb)
-        for (int j = 0; j < nb; ++j) prow[(c + 1) & 1][j] = P[r + j * F];
-    }
-  }
-  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -396,8 +405,8 @@ __global__ void __launch_bounds__(256) k_front_cluster(SymDev sd, const int32_t*
   for (int p0 = 0; p0 < ns; p0 += 32) {
     const int nb = min(32, ns - p0);
     const int owner = p0 / cw;
-    if (rank == owner) panel_factor_rows<T>(M + (size_t)(p0 - j0) * F, F, p0, nb, prow, sd, s, k,
-                                            K, c0, status, badcol);
+    if (rank == owner) panel_factor_rows<T>(M + (size_t)(p0 - j0) * F, F, F, p0, nb, prow, sd, s, k,
+                                            K, c0 + p0, status, badcol);
     cl.sync();
     const int jlo = max(j0, p0 + nb);
     if (jlo < j1) {
@@ -515,7 +524,7 @@ int run_panels(const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,
       mmax = std::max(mmax, bh[b].F - p0 - std::min(NB, bh[b].ns - p0));
     }
     if (maxMr == 0) continue;
-    const size_t smem = (size_t)maxMr * NB * sizeof(T);
+    const size_t smem = (size_t)(maxMr + 1) * NB * sizeof(T);
     k_panel_big<T, NB><<<dim3(lp.big_count, K), 512, smem, st>>>(sd, d_big, K, fr, p0, status, badcol);
     ++launches;
     if (mmax > 0) {
@@ -583,11 +592,11 @@ int factor_big_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,
         sd, lst, vals, D, sh, fr, TW);
     ++launches;
     const BigFrontHost* b = bh + lp.big_off;
-    if ((size_t)lp.big_maxF * 32 * sizeof(T) <= (size_t)kSmemCap)
+    if ((size_t)(lp.big_maxF + 1) * 32 * sizeof(T) <= (size_t)kSmemCap)
       launches += run_panels<T, 32>(sd, lp, lst, b, K, fr, status, badcol, st);
-    else if ((size_t)lp.big_maxF * 16 * sizeof(T) <= (size_t)kSmemCap)
+    else if ((size_t)(lp.big_maxF + 1) * 16 * sizeof(T) <= (size_t)kSmemCap)
       launches += run_panels<T, 16>(sd, lp, lst, b, K, fr, status, badcol, st);
-    else if ((size_t)lp.big_maxF * 8 * sizeof(T) <= (size_t)kSmemCap)
+    else if ((size_t)(lp.big_maxF + 1) * 8 * sizeof(T) <= (size_t)kSmemCap)
       launches += run_panels<T, 8>(sd, lp, lst, b, K, fr, status, badcol, st);
     else
       launches += run_panels<T, 4>(sd, lp, lst, b, K, fr, status, badcol, st);
@@ -610,7 +619,7 @@ int front_cluster_size(int F, int precision) {
 }
 
 int max_big_front(int precision) {
-  return kSmemCap / (4 * (precision == PISP_FP32 ? 4 : 8));
+  return kSmemCap / (4 * (precision == PISP_FP32 ? 4 : 8)) - 1;
 }
 
 int launch_factor_small(int precision, const SymDev& sd, const LevelPlan& lp,
