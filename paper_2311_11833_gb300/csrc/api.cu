@@ -55,7 +55,7 @@ struct pisp_handle {
   double analyze_ms = 0.0;
   // device symbolic
   Buf c0, ns, ms, inst, front_off, vec_off, row_off, child_off, child, amap_off, amap_src,
-      amap_dst, rows, emap, perm, iperm, row_inst, row_ptr, col, parent;
+      amap_dst, rows, emap, perm, iperm, row_inst, row_ptr, col, parent, inv_off, inv_child, inv_a;
   // persistent solve schedule (depends on K and R)
   int32_t schedule = 0;
   int32_t factor_policy = 0;
@@ -574,6 +574,9 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   TRY(upload(h, h->row_ptr, rp));
   TRY(upload(h, h->col, cl));
   TRY(upload(h, h->parent, par));
+  TRY(upload(h, h->inv_off, S.inv_off));
+  TRY(upload(h, h->inv_child, S.inv_child));
+  TRY(upload(h, h->inv_a, S.inv_a));
   pisp::SymDev& sd = h->sd;
   sd.c0 = h->c0.as<int32_t>();
   sd.ns = h->ns.as<int32_t>();
@@ -595,6 +598,9 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   sd.row_ptr = h->row_ptr.as<int64_t>();
   sd.col = h->col.as<int32_t>();
   sd.parent = h->parent.as<int32_t>();
+  sd.inv_off = h->inv_off.as<int64_t>();
+  sd.inv_child = h->inv_child.as<int32_t>();
+  sd.inv_a = h->inv_a.as<int32_t>();
   sd.N = S.N;
   sd.S = nS;
   h->analyzed = true;

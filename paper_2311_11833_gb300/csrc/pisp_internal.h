@@ -25,6 +25,9 @@ struct SymDev {
   const int32_t* rows;       // update rows (permuted global index)
   const int32_t* emap;       // position of each update row in the parent front
   const int32_t* parent;     // [S] parent supernode or -1
+  const int64_t* inv_off;    // [sum F + 1] contributions to position vec_off[s] + j
+  const int32_t* inv_child;  //   contributing child
+  const int32_t* inv_a;      //   its update-row index
   const int32_t* perm;       // [N] perm[new] = old
   const int32_t* iperm;      // [N] iperm[old] = new
   const int32_t* row_inst;   // [N] instance of each original row

@@ -341,6 +341,29 @@ std::string analyze(int32_t G, const int32_t* n, const int64_t* row_ptr,
     }
   }
   S.front_elems = S.front_off[nS];
+  // inverse of the extend-add maps (children visited in increasing id, so the
+  // contributions of each position are in child order)
+  S.inv_off.assign(S.vec_off[nS] + 1, 0);
+  for (int32_t c = 0; c < nS; ++c) {
+    const Supernode& sn = S.sn[c];
+    if (sn.parent < 0) continue;
+    for (int32_t a = 0; a < sn.ms; ++a) ++S.inv_off[S.vec_off[sn.parent] + S.emap[sn.row_off + a] + 1];
+  }
+  for (size_t q = 1; q < S.inv_off.size(); ++q) S.inv_off[q] += S.inv_off[q - 1];
+  S.inv_child.assign(S.inv_off.back(), 0);
+  S.inv_a.assign(S.inv_off.back(), 0);
+  {
+    std::vector<int64_t> f(S.inv_off.begin(), S.inv_off.end() - 1);
+    for (int32_t c = 0; c < nS; ++c) {
+      const Supernode& sn = S.sn[c];
+      if (sn.parent < 0) continue;
+      for (int32_t a = 0; a < sn.ms; ++a) {
+        const int64_t q = f[S.vec_off[sn.parent] + S.emap[sn.row_off + a]]++;
+        S.inv_child[q] = c;
+        S.inv_a[q] = a;
+      }
+    }
+  }
   for (int32_t s = 0; s < nS; ++s) S.child_off[s + 1] += S.child_off[s];
   S.child.assign(S.child_off[nS], 0);
   {

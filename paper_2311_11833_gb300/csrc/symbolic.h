@@ -55,6 +55,11 @@ struct Symbolic {
   std::vector<int32_t> amap_dst;       // i + j*F within the front
   // extend-add map: for supernode s, ms positions of its rows in the parent front
   std::vector<int32_t> emap;           // aligned with rows[]
+  // inverse extend-add map: for position j of front p (index vec_off[p] + j)
+  // the children's update rows landing there, in child order
+  std::vector<int64_t> inv_off;        // [sum F + 1]
+  std::vector<int32_t> inv_child;      // child supernode
+  std::vector<int32_t> inv_a;          // row index in the child's update part
   // children lists
   std::vector<int64_t> child_off;      // [S+1]
   std::vector<int32_t> child;          // children ids, ascending
