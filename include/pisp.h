@@ -65,11 +65,15 @@ typedef struct pisp_options {
                              CTAs take (front, k, RHS chunk) tasks in level order
                              and wait (boundedly) for their dependencies;
                              1 = one launch per level and front-size class */
-  int32_t factor_policy;  /* fronts wider than 64: 0 = one CTA each while the front
-                             fits in shared memory, else a blocked global-memory
-                             factorisation (default); 1 = thread-block clusters of
-                             up to 8 CTAs holding the front in distributed shared
-                             memory wherever it fits */
+  int32_t factor_policy;  /* fronts wider than 64: 0 (default) = one CTA each while
+                             the front fits in shared memory, larger fronts by a
+                             blocked factorisation in global memory (one panel
+                             launch and one tiled-update launch per 32 pivots);
+                             1 = thread-block clusters of up to 8 CTAs holding the
+                             front in distributed shared memory wherever it fits;
+                             2 = as 0 but larger fronts as a tile DAG (column-block
+                             assembly, panel and update tasks in one persistent
+                             launch per level, with look-ahead) */
 } pisp_options;
 
 typedef struct pisp_stats {

@@ -68,7 +68,9 @@ struct pisp_handle {
   std::vector<pisp::LevelPlan> plans;
   std::vector<int32_t> h_small, h_big, h_all;
   std::vector<pisp::BigFrontHost> h_bigF;
-  Buf d_small, d_big, d_all;
+  std::vector<pisp::DagTask> h_dag;
+  int32_t dag_max_flags = 0;
+  Buf d_small, d_big, d_all, d_dag, dag_ticket, dag_flags;
   // numeric state
   int32_t K = 0, precision = 0, K_hint = 1, plan_K = 0;
   double t[PISP_K_MAX] = {}, beta[PISP_K_MAX] = {}, w_last[PISP_K_MAX] = {};
@@ -154,6 +156,8 @@ int build_plans(pisp_handle* h, int precision) {
   h->h_big.clear();
   h->h_all.clear();
   h->h_bigF.clear();
+  h->h_dag.clear();
+  h->dag_max_flags = 0;
   for (int l = 0; l < S.n_levels; ++l) {
     pisp::LevelPlan& lp = h->plans[l];
     std::vector<int32_t> lst(S.level_sn.begin() + S.level_off[l],
@@ -217,6 +221,18 @@ int build_plans(pisp_handle* h, int precision) {
         lp.big_maxns = std::max(lp.big_maxns, S.sn[s].ns());
       }
     }
+    // big fronts as one tile-DAG launch per level (policy 2), when a panel
+    // fits in shared memory
+    if (lp.big_count > 0 && h->factor_policy == 2 && lp.big_maxF <= pisp::max_dag_front(precision)) {
+      std::vector<pisp::DagTask> tk;
+      int32_t nfl = 0;
+      pisp::build_dag_tasks(h->h_bigF.data() + lp.big_off, lp.big_count, h->K_hint, tk, nfl);
+      lp.dag_task_off = (int64_t)h->h_dag.size();
+      lp.dag_tasks = (int32_t)tk.size();
+      lp.dag_flags = nfl;
+      h->h_dag.insert(h->h_dag.end(), tk.begin(), tk.end());
+      h->dag_max_flags = std::max(h->dag_max_flags, nfl);
+    }
     lo = 0;
     for (int c = 0; c < 6; ++c) {
       pisp::LevelPlan::Group G{(int64_t)h->h_all.size(), 0, 0, 0};
@@ -256,6 +272,9 @@ int build_plans(pisp_handle* h, int precision) {
   TRY(upload(h, h->d_small, h->h_small));
   TRY(upload(h, h->d_big, h->h_big));
   TRY(upload(h, h->d_all, h->h_all));
+  TRY(upload(h, h->d_dag, h->h_dag));
+  if (!h->dag_ticket.ensure(sizeof(int)) || !h->dag_flags.ensure((size_t)h->dag_max_flags * sizeof(int)))
+    return fail(h, PISP_ERR_OOM, "device allocation failed (factor schedule)");
   h->plan_precision = precision;
   h->units_K = h->units_R = 0;
   return PISP_OK;
@@ -673,9 +692,19 @@ int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
     prof_end(h, pb, PISP_PROF_FACTOR_SMALL, K * lp.bytes_fsmall, n);
     if (lp.big_count == 0) continue;
     pb = prof_begin(h);
-    n = pisp::launch_factor_big(precision, h->sd, lp, h->d_big.as<int32_t>(), h->h_bigF.data(),
-                                h->vals.as<double>(), h->D.as<double>(), sh, h->fronts.p,
-                                h->status.as<int32_t>(), h->badcol.as<int32_t>(), h->stream);
+    if (lp.dag_tasks > 0) {
+      CK(cudaMemsetAsync(h->dag_ticket.p, 0, sizeof(int), h->stream));
+      CK(cudaMemsetAsync(h->dag_flags.p, 0, (size_t)lp.dag_flags * sizeof(int), h->stream));
+      n = pisp::launch_factor_big_dag(precision, h->sd, lp, h->d_big.as<int32_t>(),
+                                      h->d_dag.as<pisp::DagTask>(), h->dag_ticket.as<int>(),
+                                      h->dag_flags.as<int>(), h->serr.as<int>(), h->vals.as<double>(),
+                                      h->D.as<double>(), sh, h->fronts.p, h->status.as<int32_t>(),
+                                      h->badcol.as<int32_t>(), h->stream);
+    } else {
+      n = pisp::launch_factor_big(precision, h->sd, lp, h->d_big.as<int32_t>(), h->h_bigF.data(),
+                                  h->vals.as<double>(), h->D.as<double>(), sh, h->fronts.p,
+                                  h->status.as<int32_t>(), h->badcol.as<int32_t>(), h->stream);
+    }
     TRY(count(h, n));
     prof_end(h, pb, PISP_PROF_FACTOR_BIG, K * lp.bytes_fbig, n);
   }

@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <vector>
 
 #include "pisp_internal.h"
 
@@ -78,6 +79,32 @@ __device__ __forceinline__ void panel_factor_rows(T* P, int ld, int F, int p0, i
   __syncthreads();
 }
 
+// Pivot-free elimination of a panel in shared memory: rows 0..Mr-1, nb <= 32
+// columns, P[i + c*ld] (ld odd).  Per pivot: scale the column by one
+// reciprocal, then lane j of each warp updates column j of the warp's rows;
+// the loops carry no integer division.
+template <typename T>
+__device__ __forceinline__ void panel_eliminate(T* P, int ld, int Mr, int nb, const SymDev& sd,
+                                                int s, int k, int K, int colbase, int32_t* status,
+                                                int32_t* badcol) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int c = 0; c < nb; ++c) {
+    const T piv = P[c + c * ld];
+    if (tid == 0) check_pivot(piv, sd, s, k, K, colbase + c, status, badcol);
+    const T rp = T(1) / piv;
+    for (int i = c + 1 + tid; i < Mr; i += nt) P[i + c * ld] *= rp;
+    __syncthreads();
+    if (lane > c && lane < nb) {
+      const T u = P[c + lane * ld];
+      T* col = P + lane * ld;
+      const T* lc = P + c * ld;
+      for (int i = c + 1 + wid; i < Mr; i += nw) col[i] -= lc[i] * u;
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Small fronts: whole front in shared memory, one CTA per (front, k).
 // ---------------------------------------------------------------------------
@@ -110,10 +137,13 @@ __global__ void k_front_small(SymDev sd, const int32_t* __restrict__ list,
     const int cns = sd.ns[c], cms = sd.ms[c], cF = cns + cms;
     const T* cf = fronts + (int64_t)K * sd.front_off[c] + (int64_t)k * cF * cF;
     const int32_t* em = sd.emap + sd.row_off[c];
-    const int n2 = cms * cms;
-    for (int q = tid; q < n2; q += nt) {
-      const int a = q % cms, b = q / cms;
-      f[em[a] + em[b] * F] += cf[(cns + a) + (int64_t)(cns + b) * cF];
+    {
+      const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+      for (int b = wid; b < cms; b += nw) {
+        T* dcol = f + em[b] * F;
+        const T* scol = cf + (int64_t)(cns + b) * cF + cns;
+        for (int a = lane; a < cms; a += 32) dcol[em[a]] += scol[a];
+      }
     }
     __syncthreads();
   }
@@ -122,12 +152,18 @@ __global__ void k_front_small(SymDev sd, const int32_t* __restrict__ list,
     const T piv = f[p * (F + 1)];
     if (tid == 0) check_pivot(piv, sd, s, k, K, c0 + p, status, badcol);
     const int m = F - p - 1;
-    for (int i = tid; i < m; i += nt) f[(p + 1 + i) + p * F] /= piv;
+    const T rp = T(1) / piv;
+    for (int i = tid; i < m; i += nt) f[(p + 1 + i) + p * F] *= rp;
     __syncthreads();
-    const int m2 = m * m;
-    for (int q = tid; q < m2; q += nt) {
-      const int i = p + 1 + q % m, j = p + 1 + q / m;
-      f[i + j * F] -= f[i + p * F] * f[p + j * F];
+    {
+      // lanes run down a column (consecutive i), warps take columns
+      const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+      const T* lc = f + p * F;
+      for (int j = p + 1 + wid; j < F; j += nw) {
+        const T u = f[p + j * F];
+        T* col = f + j * F;
+        for (int i = p + 1 + lane; i < F; i += 32) col[i] -= lc[i] * u;
+      }
     }
     __syncthreads();
   }
@@ -192,10 +228,11 @@ __global__ void __launch_bounds__(256) k_assemble_big(SymDev sd, const int32_t* 
     const int b1 = lower_bound_i(em, cms, j1);
     if (b1 > b0) {
       const T* cf = fronts + (int64_t)K * sd.front_off[c] + (int64_t)k * cF * cF;
-      const int n2 = (b1 - b0) * cms;
-      for (int q = tid; q < n2; q += nt) {
-        const int a = q % cms, b = b0 + q / cms;
-        f[em[a] + (int64_t)em[b] * F] += cf[(cns + a) + (int64_t)(cns + b) * cF];
+      const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+      for (int b = b0 + wid; b < b1; b += nw) {
+        T* dcol = f + (int64_t)em[b] * F;
+        const T* scol = cf + (int64_t)(cns + b) * cF + cns;
+        for (int a = lane; a < cms; a += 32) dcol[em[a]] += scol[a];
       }
     }
     __syncthreads();
@@ -222,31 +259,13 @@ __global__ void __launch_bounds__(512) k_panel_big(SymDev sd, const int32_t* __r
   const int ld = Mr | 1;
   const int tid = threadIdx.x, nt = blockDim.x;
   T* f = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * F * F;
-  const int np = Mr * nbe;
-  for (int q = tid; q < np; q += nt) {
-    const int i = q % Mr, c = q / Mr;
-    P[i + c * ld] = f[(p0 + i) + (int64_t)(p0 + c) * F];
-  }
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int c = wid; c < nbe; c += nw)
+    for (int i = lane; i < Mr; i += 32) P[i + c * ld] = f[(p0 + i) + (int64_t)(p0 + c) * F];
   __syncthreads();
-  const int c0 = sd.c0[s];
-  for (int c = 0; c < nbe; ++c) {
-    const T piv = P[c + c * ld];
-    if (tid == 0) check_pivot(piv, sd, s, k, K, c0 + p0 + c, status, badcol);
-    const T rp = T(1) / piv;
-    for (int i = c + 1 + tid; i < Mr; i += nt) P[i + c * ld] *= rp;
-    __syncthreads();
-    const int h = Mr - c - 1, w = nbe - c - 1;
-    const int n2 = h * w;
-    for (int q = tid; q < n2; q += nt) {
-      const int i = c + 1 + q % h, cc = c + 1 + q / h;
-      P[i + cc * ld] -= P[i + c * ld] * P[c + cc * ld];
-    }
-    __syncthreads();
-  }
-  for (int q = tid; q < np; q += nt) {
-    const int i = q % Mr, c = q / Mr;
-    f[(p0 + i) + (int64_t)(p0 + c) * F] = P[i + c * ld];
-  }
+  panel_eliminate<T>(P, ld, Mr, nbe, sd, s, k, K, sd.c0[s] + p0, status, badcol);
+  for (int c = wid; c < nbe; c += nw)
+    for (int i = lane; i < Mr; i += 32) f[(p0 + i) + (int64_t)(p0 + c) * F] = P[i + c * ld];
   // row block of U: columns j >= p0 + nbe
   for (int j = p0 + nbe + tid; j < F; j += nt) {
     T* col = f + (int64_t)j * F + p0;
@@ -392,10 +411,11 @@ __global__ void __launch_bounds__(256) k_front_cluster(SymDev sd, const int32_t*
     const int b1 = lower_bound_i(em, cms, j1);
     if (b1 > b0) {
       const T* cf = fronts + (int64_t)K * sd.front_off[c] + (int64_t)k * cF * cF;
-      const int n2 = (b1 - b0) * cms;
-      for (int q = tid; q < n2; q += nt) {
-        const int a = q % cms, b = b0 + q / cms;
-        M[em[a] + (em[b] - j0) * F] += cf[(cns + a) + (int64_t)(cns + b) * cF];
+      const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+      for (int b = b0 + wid; b < b1; b += nw) {
+        T* dcol = M + (size_t)(em[b] - j0) * F;
+        const T* scol = cf + (int64_t)(cns + b) * cF + cns;
+        for (int a = lane; a < cms; a += 32) dcol[em[a]] += scol[a];
       }
     }
     __syncthreads();
@@ -488,6 +508,198 @@ __global__ void __launch_bounds__(256) k_front_cluster(SymDev sd, const int32_t*
   cl.sync();
   T* out = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * F * F + (int64_t)j0 * F;
   for (int e = tid; e < F * nc; e += nt) out[e] = M[e];
+}
+
+// ---------------------------------------------------------------------------
+// Big fronts as a tile DAG, one persistent launch per level.  Column blocks
+// are 32 wide.  Tasks: ASM(j) assembles block j; PANEL(p) factors the panel
+// of pivots [32p, 32p+32) in shared memory; UPDATE(p, j) applies panel p to
+// block j (unit-lower solve of its 32 U rows, then the trailing update of all
+// rows below).  PANEL(p+1) waits only for UPDATE(p, p+1), so the next panel
+// starts while the rest of step p is still updating (look-ahead).  CTAs take
+// tasks in ticket order and wait only for tasks with smaller tickets; every
+// wait is bounded and sets *err when it gives up.
+// ---------------------------------------------------------------------------
+constexpr int64_t kDagWaitPolls = 1 << 22;
+
+__device__ __forceinline__ int dag_ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void dag_st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void dag_wait(const int* f, int need, int* err) {
+  if (dag_ld_acquire(f) >= need) return;
+  for (int64_t i = 0; i < kDagWaitPolls; ++i) {
+    __nanosleep(64);
+    if (dag_ld_acquire(f) >= need) return;
+  }
+  atomicExch(err, 1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_big_dag(SymDev sd, const int32_t* __restrict__ big,
+                                                 const DagTask* __restrict__ tasks, int ntasks,
+                                                 int* ticket, int* flags, int* err,
+                                                 const double* __restrict__ vals,
+                                                 const double* __restrict__ D, Shifts sh,
+                                                 T* __restrict__ fronts, int32_t* status,
+                                                 int32_t* badcol) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_t;
+  const int K = sh.K;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  for (;;) {
+    if (tid == 0) s_t = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int u = s_t;
+    __syncthreads();
+    if (u >= ntasks) return;
+    const DagTask t = tasks[u];
+    const int s = big[t.b];
+    const int k = t.k;
+    const int ns = sd.ns[s], F = ns + sd.ms[s];
+    const int J = (F + 31) / 32;
+    int* stepdone = flags + t.flags;
+    int* paneldone = stepdone + J;
+    T* f = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * F * F;
+    int publish_at = -1, publish_val = 0;
+    if (t.kind == kDagAsm) {
+      const int j0 = 32 * t.j, j1 = min(F, j0 + 32);
+      const int64_t nz = (int64_t)F * (j1 - j0);
+      for (int64_t q = tid; q < nz; q += nt) f[(int64_t)j0 * F + q] = T(0);
+      __syncthreads();
+      const int64_t a0 = sd.amap_off[s], a1 = sd.amap_off[s + 1];
+      const int64_t lo = lower_bound_col(sd.amap_dst, a0, a1, F, j0);
+      const int64_t hi = lower_bound_col(sd.amap_dst, lo, a1, F, j1);
+      for (int64_t q = lo + tid; q < hi; q += nt) atomicAdd(&f[sd.amap_dst[q]], (T)vals[sd.amap_src[q]]);
+      const double tk = sh.t[k];
+      const int c0 = sd.c0[s];
+      for (int c = j0 + tid; c < min(j1, ns); c += nt)
+        atomicAdd(&f[(int64_t)c * (F + 1)], (T)(tk * D[sd.perm[c0 + c]]));
+      __syncthreads();
+      for (int ci = sd.child_off[s]; ci < sd.child_off[s + 1]; ++ci) {
+        const int c = sd.child[ci];
+        const int cns = sd.ns[c], cms = sd.ms[c], cF = cns + cms;
+        const int32_t* em = sd.emap + sd.row_off[c];
+        const int b0 = lower_bound_i(em, cms, j0);
+        const int b1 = lower_bound_i(em, cms, j1);
+        if (b1 > b0) {
+          const T* cf = fronts + (int64_t)K * sd.front_off[c] + (int64_t)k * cF * cF;
+          for (int b = b0 + wid; b < b1; b += (nt >> 5)) {
+            T* dcol = f + (int64_t)em[b] * F;
+            const T* scol = cf + (int64_t)(cns + b) * cF + cns;
+            for (int a = lane; a < cms; a += 32) dcol[em[a]] += scol[a];
+          }
+        }
+        __syncthreads();
+      }
+      publish_at = t.j;
+      publish_val = 1;
+    } else if (t.kind == kDagPanel) {
+      if (tid == 0) dag_wait(&stepdone[t.p], t.p + 1, err);
+      __syncthreads();
+      T* P = reinterpret_cast<T*>(smraw);
+      const int r0 = 32 * t.p;
+      const int nb = min(32, ns - r0);
+      const int Mr = F - r0;
+      const int ld = Mr | 1;
+      for (int c = wid; c < nb; c += (nt >> 5))
+        for (int i = lane; i < Mr; i += 32) P[i + c * ld] = __ldcg(f + (r0 + i) + (int64_t)(r0 + c) * F);
+      __syncthreads();
+      panel_eliminate<T>(P, ld, Mr, nb, sd, s, k, K, sd.c0[s] + r0, status, badcol);
+      for (int c = wid; c < nb; c += (nt >> 5))
+        for (int i = lane; i < Mr; i += 32) f[(r0 + i) + (int64_t)(r0 + c) * F] = P[i + c * ld];
+      publish_at = J + t.p;
+      publish_val = 1;
+    } else {
+      const int p = t.p, j = t.j;
+      const int r0 = 32 * p;
+      const int nb = min(32, ns - r0);
+      const int jc0 = max(32 * j, r0 + nb), jc1 = min(32 * j + 32, F);
+      const int w = jc1 - jc0;
+      if (tid == 0) {
+        dag_wait(&paneldone[p], 1, err);
+        dag_wait(&stepdone[j], p + 1, err);
+      }
+      __syncthreads();
+      T* Ls = reinterpret_cast<T*>(smraw);       // 32 x 33: unit-lower L11 of panel p
+      T* Us = Ls + 32 * 33;                       // 32 x 33: U rows of this block
+      for (int e = tid; e < 32 * 32; e += nt) {
+        const int r = e & 31, c = e >> 5;
+        Ls[r * 33 + c] = (r < nb && c < r) ? __ldcg(f + (r0 + r) + (int64_t)(r0 + c) * F) : T(0);
+        Us[r * 33 + c] = (r < nb && c < w) ? __ldcg(f + (r0 + r) + (int64_t)(jc0 + c) * F) : T(0);
+      }
+      __syncthreads();
+      if (wid == 0) {
+        T uu[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) uu[r] = Us[r * 33 + lane];
+#pragma unroll
+        for (int r = 1; r < 32; ++r) {
+          T a = uu[r];
+#pragma unroll
+          for (int c = 0; c < 31; ++c)
+            if (c < r) a -= Ls[r * 33 + c] * uu[c];
+          uu[r] = a;
+        }
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+          Us[r * 33 + lane] = uu[r];
+          if (r < nb && lane < w) f[(r0 + r) + (int64_t)(jc0 + lane) * F] = uu[r];
+        }
+      }
+      __syncthreads();
+      for (int i = r0 + nb + tid; i < F; i += nt) {
+        T l[32], cv[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) l[c] = (c < nb) ? __ldcg(f + i + (int64_t)(r0 + c) * F) : T(0);
+#pragma unroll
+        for (int col = 0; col < 32; ++col) cv[col] = (col < w) ? __ldcg(f + i + (int64_t)(jc0 + col) * F) : T(0);
+#pragma unroll
+        for (int col = 0; col < 32; ++col) {
+          T a = T(0);
+#pragma unroll
+          for (int c = 0; c < 32; ++c) a += l[c] * Us[c * 33 + col];
+          cv[col] -= a;
+        }
+#pragma unroll
+        for (int col = 0; col < 32; ++col)
+          if (col < w) f[i + (int64_t)(jc0 + col) * F] = cv[col];
+      }
+      publish_at = j;
+      publish_val = p + 2;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0 && publish_at >= 0) dag_st_release(&stepdone[publish_at], publish_val);
+  }
+}
+
+template <typename T>
+int big_dag_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_big, const DagTask* tasks,
+                 int* ticket, int* flags, int* err, const double* vals, const double* D,
+                 const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol, cudaStream_t st) {
+  if (lp.dag_tasks == 0) return 0;
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_big_dag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  }
+  const size_t smem = std::max((size_t)(lp.big_maxF + 1) * 32, (size_t)2 * 32 * 33) * sizeof(T);
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_big_dag<T>, 256, smem);
+  const int grid = std::max(1, std::min(lp.dag_tasks, std::max(1, occ) * std::max(nsm, 1)));
+  k_big_dag<T><<<grid, 256, smem, st>>>(sd, d_big + lp.big_off, tasks + lp.dag_task_off, lp.dag_tasks,
+                                        ticket, flags, err, vals, D, sh, (T*)fronts, status, badcol);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 template <typename T>
@@ -629,6 +841,55 @@ int launch_factor_small(int precision, const SymDev& sd, const LevelPlan& lp,
   if (precision == PISP_FP32)
     return factor_small_impl<float>(sd, lp, d_small, vals, D, sh, fronts, status, badcol, st);
   return factor_small_impl<double>(sd, lp, d_small, vals, D, sh, fronts, status, badcol, st);
+}
+
+int max_dag_front(int precision) { return kSmemCap / (32 * (precision == PISP_FP32 ? 4 : 8)) - 1; }
+
+void build_dag_tasks(const BigFrontHost* big, int32_t nbig, int32_t K, std::vector<DagTask>& out,
+                     int32_t& nflags) {
+  out.clear();
+  std::vector<int32_t> foff((size_t)nbig * K);
+  nflags = 0;
+  int maxP = 0;
+  for (int b = 0; b < nbig; ++b) {
+    const int J = (big[b].F + 31) / 32, P = (big[b].ns + 31) / 32;
+    maxP = std::max(maxP, P);
+    for (int k = 0; k < K; ++k) {
+      foff[(size_t)b * K + k] = nflags;
+      nflags += J + P;
+    }
+  }
+  for (int b = 0; b < nbig; ++b)
+    for (int k = 0; k < K; ++k)
+      for (int j = 0; j < (big[b].F + 31) / 32; ++j)
+        out.push_back({kDagAsm, b, k, 0, j, foff[(size_t)b * K + k]});
+  for (int p = 0; p < maxP; ++p) {
+    for (int b = 0; b < nbig; ++b) {
+      const int F = big[b].F, ns = big[b].ns;
+      const int J = (F + 31) / 32, P = (ns + 31) / 32;
+      if (p >= P) continue;
+      const int nb = std::min(32, ns - 32 * p);
+      for (int k = 0; k < K; ++k) {
+        const int fo = foff[(size_t)b * K + k];
+        if (p == 0) out.push_back({kDagPanel, b, k, 0, 0, fo});
+        if (p + 1 < J) out.push_back({kDagUpdate, b, k, p, p + 1, fo});
+        if (p + 1 < P) out.push_back({kDagPanel, b, k, p + 1, 0, fo});
+        if (32 * p + nb < std::min(32 * p + 32, F)) out.push_back({kDagUpdate, b, k, p, p, fo});
+        for (int j = p + 2; j < J; ++j) out.push_back({kDagUpdate, b, k, p, j, fo});
+      }
+    }
+  }
+}
+
+int launch_factor_big_dag(int precision, const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,
+                          const DagTask* tasks, int* ticket, int* flags, int* err,
+                          const double* vals, const double* D, const Shifts& sh, void* fronts,
+                          int32_t* status, int32_t* badcol, cudaStream_t st) {
+  if (precision == PISP_FP32)
+    return big_dag_impl<float>(sd, lp, d_big, tasks, ticket, flags, err, vals, D, sh, fronts, status,
+                               badcol, st);
+  return big_dag_impl<double>(sd, lp, d_big, tasks, ticket, flags, err, vals, D, sh, fronts, status,
+                              badcol, st);
 }
 
 int launch_factor_big(int precision, const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "../../include/pisp.h"
 
@@ -60,6 +61,11 @@ struct LevelPlan {
   int32_t big_count = 0;
   int32_t big_maxF = 0;
   int32_t big_maxns = 0;
+  // tile-DAG schedule of the big fronts (see launch_factor_big_dag)
+  int64_t dag_task_off = 0;   // offset into the device task list
+  int32_t dag_tasks = 0;
+  int64_t dag_flag_off = 0;   // offset into the device flag area (per level)
+  int32_t dag_flags = 0;
   // every front of the level for the solves, grouped by size class
   Group sgroups[8];
   int32_t n_sgroups = 0;
@@ -74,6 +80,21 @@ struct BigFrontHost {
   int32_t F, ns;
 };
 
+// One task of the tile-DAG factorisation of a level's big fronts.  Column
+// blocks are 32 wide; kind 0 assembles block j, kind 1 factors the panel of
+// pivots [32p, 32p+32), kind 2 applies panel p to block j (triangular solve
+// of its U rows, then the trailing update of the rows below).  flags points
+// at the (front, k) pair's counters: J "updates applied" per column block,
+// then P "panel done" flags.
+enum DagKind { kDagAsm = 0, kDagPanel = 1, kDagUpdate = 2 };
+struct DagTask {
+  int32_t kind, b, k, p, j, flags;
+};
+
+// Builds the task list of one level (b indexes the level's big-front list).
+void build_dag_tasks(const BigFrontHost* big, int32_t nbig, int32_t K, std::vector<DagTask>& out,
+                     int32_t& nflags);
+
 // ---- factor (factor.cu) ----
 // Each launcher returns the number of kernels launched (>= 0) or -1 on a
 // launch error.  Small fronts of one level (shared-memory path):
@@ -86,6 +107,15 @@ int launch_factor_big(int precision, const SymDev& sd, const LevelPlan& lp, cons
                       const BigFrontHost* big_host, const double* vals, const double* D,
                       const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol,
                       cudaStream_t st);
+// Big fronts of one level as one persistent tile-DAG launch; ticket (1 int)
+// and flags (lp.dag_flags ints) must be zero; err is set if a bounded
+// dependency wait gave up.
+int launch_factor_big_dag(int precision, const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,
+                          const DagTask* tasks, int* ticket, int* flags, int* err,
+                          const double* vals, const double* D, const Shifts& sh, void* fronts,
+                          int32_t* status, int32_t* badcol, cudaStream_t st);
+// largest front the tile-DAG path takes (its panel must fit in shared memory)
+int max_dag_front(int precision);
 // largest front (in elements of the given precision) the shared-memory path takes
 int small_front_limit(int precision);
 // CTAs per cluster for a front of size F factored in distributed shared

@@ -20,7 +20,7 @@ import os
 import numpy as np
 
 RELAX = [(8, 0.05), (4, 0.0), (16, 0.10), (32, 0.20)]
-POLICIES = [0, 1]
+POLICIES = [0, 1, 2]
 SCHEDULES = [0, 1]
 
 

@@ -118,7 +118,7 @@ def test_factor_entries_match_pivot_free_lu(pisp):
 @pytest.mark.parametrize("n,density,prec,policy", [
     (220, 0.03, "fp64", 0), (300, 0.03, "fp64", 0), (300, 0.03, "fp32", 0), (700, 0.012, "fp32", 0),
     (220, 0.03, "fp64", 1), (300, 0.03, "fp64", 1), (300, 0.03, "fp32", 1), (420, 0.02, "fp32", 1),
-    (700, 0.012, "fp32", 1)])
+    (700, 0.012, "fp32", 1), (300, 0.03, "fp64", 2), (700, 0.012, "fp32", 2)])
 def test_factor_entries_large_fronts(pisp, n, density, prec, policy):
     """Fronts factored in shared memory, by CTA clusters or by the blocked global path
     equal dense Doolittle's."""
@@ -146,13 +146,13 @@ def test_factor_entries_large_fronts(pisp, n, density, prec, policy):
                                        atol=tol * scale)
 
 
-@pytest.mark.parametrize("schedule", [0, 1])
-def test_precision_config_fp64_big_fronts(pisp, schedule):
+@pytest.mark.parametrize("schedule,policy", [(0, 0), (1, 0), (0, 2)])
+def test_precision_config_fp64_big_fronts(pisp, schedule, policy):
     """2000-bus grid: its top fronts exceed the shared-memory path (blocked path)."""
     inst = pfgen.make_instance("precision")
     t = pfgen.symmetric_shifts(6)
     b = pfgen.rhs(inst.n, 3, 2)
-    s, val, D = _solver(pisp, [inst], solve_schedule=schedule)
+    s, val, D = _solver(pisp, [inst], solve_schedule=schedule, factor_policy=policy)
     assert s.stats()["max_front"] > 160
     s.factor(_dev(val), _dev(D), t, "fp64")
     x = s.solve(_dev(b)).cpu().numpy()
