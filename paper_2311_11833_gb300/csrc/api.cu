@@ -55,7 +55,8 @@ struct pisp_handle {
   double analyze_ms = 0.0;
   // device symbolic
   Buf c0, ns, ms, inst, front_off, vec_off, row_off, child_off, child, amap_off, amap_src,
-      amap_dst, rows, emap, perm, iperm, row_inst, row_ptr, col, parent, inv_off, inv_child, inv_a;
+      amap_dst, rows, emap, perm, iperm, row_inst, row_ptr, col, parent, inv_off, inv_child, inv_a, inv_vbase,
+      inv_cF, inv_col;
   // persistent solve schedule (depends on K and R)
   int32_t schedule = 0;
   int32_t factor_policy = 0;
@@ -596,6 +597,9 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   TRY(upload(h, h->inv_off, S.inv_off));
   TRY(upload(h, h->inv_child, S.inv_child));
   TRY(upload(h, h->inv_a, S.inv_a));
+  TRY(upload(h, h->inv_vbase, S.inv_vbase));
+  TRY(upload(h, h->inv_cF, S.inv_cF));
+  TRY(upload(h, h->inv_col, S.inv_col));
   pisp::SymDev& sd = h->sd;
   sd.c0 = h->c0.as<int32_t>();
   sd.ns = h->ns.as<int32_t>();
@@ -620,6 +624,9 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   sd.inv_off = h->inv_off.as<int64_t>();
   sd.inv_child = h->inv_child.as<int32_t>();
   sd.inv_a = h->inv_a.as<int32_t>();
+  sd.inv_vbase = h->inv_vbase.as<int64_t>();
+  sd.inv_cF = h->inv_cF.as<int32_t>();
+  sd.inv_col = h->inv_col.as<int32_t>();
   sd.N = S.N;
   sd.S = nS;
   h->analyzed = true;

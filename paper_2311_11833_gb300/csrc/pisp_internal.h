@@ -29,6 +29,9 @@ struct SymDev {
   const int64_t* inv_off;    // [sum F + 1] contributions to position vec_off[s] + j
   const int32_t* inv_child;  //   contributing child
   const int32_t* inv_a;      //   its update-row index
+  const int64_t* inv_vbase;  //   the child's vec_off
+  const int32_t* inv_cF;     //   the child's front size
+  const int32_t* inv_col;    //   position in the child's front
   const int32_t* perm;       // [N] perm[new] = old
   const int32_t* iperm;      // [N] iperm[old] = new
   const int32_t* row_inst;   // [N] instance of each original row

@@ -219,9 +219,8 @@ __device__ __forceinline__ T gather_position(const SymDev& sd, int s, int j, int
   T a = (j < ns) ? (T)load_rhs(sd, rhs, rhs_mode, c0 + j, k, K, R, r) : T(0);
   const int64_t e1 = sd.inv_off[sd.vec_off[s] + j + 1];
   for (int64_t e = sd.inv_off[sd.vec_off[s] + j]; e < e1; ++e) {
-    const int c = sd.inv_child[e];
-    const int cns = sd.ns[c], cF = cns + sd.ms[c];
-    a += __ldcg(V + (int64_t)K * R * sd.vec_off[c] + ((int64_t)k * R + r) * cF + cns + sd.inv_a[e]);
+    const int cF = sd.inv_cF[e];
+    a += __ldcg(V + (int64_t)K * R * sd.inv_vbase[e] + ((int64_t)k * R + r) * cF + sd.inv_col[e]);
   }
   return a;
 }
@@ -300,9 +299,11 @@ __device__ __forceinline__ void seg_forward(const SymDev& sd, const SegTask& t, 
   for (int r = 0; r < kRW; ++r)
     if (r < nr && sl < F) Vs[(int64_t)r * F + sl] = vv[r];
   if (sy.done) {
-    __threadfence();
     __syncwarp();
-    if (t.active && sl == 0) sy.add(t.s, k, K);
+    if (t.active && sl == 0) {
+      __threadfence();
+      sy.add(t.s, k, K);
+    }
   }
 }
 
@@ -368,9 +369,11 @@ __device__ __forceinline__ void seg_backward(const SymDev& sd, const SegTask& t,
     }
   }
   if (sy.done) {
-    __threadfence();
     __syncwarp();
-    if (t.active && sl == 0) sy.publish_children(sd, t.s, k, K);
+    if (t.active && sl == 0) {
+      __threadfence();
+      sy.publish_children(sd, t.s, k, K);
+    }
   }
 }
 
@@ -452,9 +455,11 @@ __device__ __forceinline__ void blk_forward(const SymDev& sd, int s, int k, int 
   T* outv = V + (int64_t)K * R * sd.vec_off[s] + ((int64_t)k * R + r0) * F;
   for (int q = tid; q < nr * F; q += nt) outv[q] = v[q];
   if (sy.done) {
-    __threadfence();
     __syncthreads();
-    if (tid == 0) sy.add(s, k, K);
+    if (tid == 0) {
+      __threadfence();
+      sy.add(s, k, K);
+    }
   }
 }
 
@@ -552,9 +557,11 @@ __device__ __forceinline__ void blk_backward(const SymDev& sd, int s, int k, int
     if (acc) acc[o] += (double)z[q];
   }
   if (sy.done) {
-    __threadfence();
     __syncthreads();
-    if (tid == 0) sy.publish_children(sd, s, k, K);
+    if (tid == 0) {
+      __threadfence();
+      sy.publish_children(sd, s, k, K);
+    }
   }
 }
 
@@ -654,9 +661,11 @@ __device__ __forceinline__ void blk_forward_staged(const SymDev& sd, int s, int 
   T* outv = V + (int64_t)K * R * sd.vec_off[s] + ((int64_t)k * R + r0) * F;
   for (int q = tid; q < nr * F; q += nt) outv[q] = v[q];
   if (sy.done) {
-    __threadfence();
     __syncthreads();
-    if (tid == 0) sy.add(s, k, K);
+    if (tid == 0) {
+      __threadfence();
+      sy.add(s, k, K);
+    }
   }
 }
 
@@ -759,9 +768,11 @@ __device__ __forceinline__ void blk_backward_staged(const SymDev& sd, int s, int
     if (acc) acc[o] += (double)z[q];
   }
   if (sy.done) {
-    __threadfence();
     __syncthreads();
-    if (tid == 0) sy.publish_children(sd, s, k, K);
+    if (tid == 0) {
+      __threadfence();
+      sy.publish_children(sd, s, k, K);
+    }
   }
 }
 

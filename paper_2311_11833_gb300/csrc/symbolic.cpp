@@ -363,6 +363,15 @@ std::string analyze(int32_t G, const int32_t* n, const int64_t* row_ptr,
         S.inv_a[q] = a;
       }
     }
+    S.inv_vbase.resize(S.inv_child.size());
+    S.inv_cF.resize(S.inv_child.size());
+    S.inv_col.resize(S.inv_child.size());
+    for (size_t q = 0; q < S.inv_child.size(); ++q) {
+      const Supernode& c = S.sn[S.inv_child[q]];
+      S.inv_vbase[q] = S.vec_off[S.inv_child[q]];
+      S.inv_cF[q] = c.F();
+      S.inv_col[q] = c.ns() + S.inv_a[q];
+    }
   }
   for (int32_t s = 0; s < nS; ++s) S.child_off[s + 1] += S.child_off[s];
   S.child.assign(S.child_off[nS], 0);

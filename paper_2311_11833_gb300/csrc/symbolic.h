@@ -60,6 +60,9 @@ struct Symbolic {
   std::vector<int64_t> inv_off;        // [sum F + 1]
   std::vector<int32_t> inv_child;      // child supernode
   std::vector<int32_t> inv_a;          // row index in the child's update part
+  std::vector<int64_t> inv_vbase;      // vec_off of the child (its front-vector block)
+  std::vector<int32_t> inv_cF;         // the child's front size
+  std::vector<int32_t> inv_col;        // ns(child) + inv_a: position in the child's front
   // children lists
   std::vector<int64_t> child_off;      // [S+1]
   std::vector<int32_t> child;          // children ids, ascending
