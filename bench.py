@@ -66,9 +66,9 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=None)
     ap.add_argument("--eps", type=float, default=1e-2)
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of a CUDA graph")
-    ap.add_argument("--factor-policy", type=int, default=0, choices=[0, 1, 2],
-                    help="fronts wider than 64: 0 single CTA / per-panel launches (default), "
-                         "1 CTA clusters, 2 single CTA / tile DAG")
+    ap.add_argument("--factor-policy", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="fronts wider than 64: 0 single CTA / column-block owners (default), "
+                         "1 CTA clusters, 2 single CTA / tile DAG, 3 single CTA / per-panel launches")
     ap.add_argument("--schedule", type=int, default=0, choices=[0, 1],
                     help="solve schedule: 0 persistent (default), 1 one launch per level")
     ap.add_argument("--autotune", action="store_true",
@@ -355,7 +355,7 @@ def run_pisp(args, rank, world, local_rank):
                    "K": K, "R": R, "shifts": "symmetric +-eps*alpha", "eps": args.eps,
                    "factor_precision": precision, "combine_precision": "fp64", "sweeps": sweeps,
                    "graph": use_graph, "solve_schedule": ["persistent", "per-level"][args.schedule],
-                   "factor_policy": ["single-CTA/per-panel", "clusters", "single-CTA/tile-DAG"][args.factor_policy], "l2": "flushed between steps (256 MB write outside the events)",
+                   "factor_policy": ["single-CTA/column-block-owners", "clusters", "single-CTA/tile-DAG", "single-CTA/per-panel"][args.factor_policy], "l2": "flushed between steps (256 MB write outside the events)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "families": families,

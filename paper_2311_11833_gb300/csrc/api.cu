@@ -55,7 +55,7 @@ struct pisp_handle {
   double analyze_ms = 0.0;
   // device symbolic
   Buf c0, ns, ms, inst, front_off, vec_off, row_off, child_off, child, amap_off, amap_src,
-      amap_dst, rows, emap, perm, iperm, row_inst, row_ptr, col, parent, inv_off, inv_child, inv_a, inv_vbase,
+      amap_dst, amap_coff, rows, emap, perm, iperm, row_inst, row_ptr, col, parent, inv_off, inv_child, inv_a, inv_vbase,
       inv_cF, inv_col;
   // persistent solve schedule (depends on K and R)
   int32_t schedule = 0;
@@ -222,12 +222,20 @@ int build_plans(pisp_handle* h, int precision) {
         lp.big_maxns = std::max(lp.big_maxns, S.sn[s].ns());
       }
     }
-    // big fronts as one tile-DAG launch per level (policy 2), when a panel
-    // fits in shared memory
-    if (lp.big_count > 0 && h->factor_policy == 2 && lp.big_maxF <= pisp::max_dag_front(precision)) {
+    // big fronts as one persistent launch per level: column-block owners
+    // (policy 0) or the tile DAG (policy 2), when their blocks fit in shared
+    // memory; else (and under policies 1 and 3) one panel launch and one
+    // update launch per 32 pivots
+    const bool owner = h->factor_policy == 0 && lp.big_maxF <= pisp::max_owner_front(precision);
+    const bool dag = h->factor_policy == 2 && lp.big_maxF <= pisp::max_dag_front(precision);
+    if (lp.big_count > 0 && (owner || dag)) {
       std::vector<pisp::DagTask> tk;
       int32_t nfl = 0;
-      pisp::build_dag_tasks(h->h_bigF.data() + lp.big_off, lp.big_count, h->K_hint, tk, nfl);
+      if (owner)
+        pisp::build_owner_tasks(h->h_bigF.data() + lp.big_off, lp.big_count, h->K_hint, tk, nfl);
+      else
+        pisp::build_dag_tasks(h->h_bigF.data() + lp.big_off, lp.big_count, h->K_hint, tk, nfl);
+      lp.dag_owner = owner ? 1 : 0;
       lp.dag_task_off = (int64_t)h->h_dag.size();
       lp.dag_tasks = (int32_t)tk.size();
       lp.dag_flags = nfl;
@@ -586,6 +594,7 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   TRY(upload(h, h->amap_off, S.amap_off));
   TRY(upload(h, h->amap_src, S.amap_src));
   TRY(upload(h, h->amap_dst, S.amap_dst));
+  TRY(upload(h, h->amap_coff, S.amap_coff));
   TRY(upload(h, h->rows, S.rows));
   TRY(upload(h, h->emap, S.emap));
   TRY(upload(h, h->perm, S.perm));
@@ -613,6 +622,7 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   sd.amap_off = h->amap_off.as<int64_t>();
   sd.amap_src = h->amap_src.as<int32_t>();
   sd.amap_dst = h->amap_dst.as<int32_t>();
+  sd.amap_coff = h->amap_coff.as<int64_t>();
   sd.rows = h->rows.as<int32_t>();
   sd.emap = h->emap.as<int32_t>();
   sd.perm = h->perm.as<int32_t>();

@@ -702,6 +702,298 @@ int big_dag_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_big, co
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
+// ---------------------------------------------------------------------------
+// Big fronts, column-block owners: one persistent launch per level.  A task
+// is the 32-column block j of one (front, k); the CTA that takes it keeps the
+// block, all F rows of it, in shared memory from assembly to its final value:
+//   1. assembly of the block's columns: the original entries (per-column
+//      ranges of the assembly map), t_k D on the diagonal, and the children's
+//      update columns through the inverse extend-add map.  Each destination
+//      column belongs to one warp, which adds its contributions in child
+//      order, so the sums are deterministic with no barrier between children;
+//   2. every earlier panel p, in pivot order: wait until its owner released
+//      it, solve the block's U rows with L11(p) and subtract L21(p) U(p, j)
+//      from the rows below (left-looking form of the static-pivot
+//      elimination of Sec. II-C);
+//   3. if the block holds pivots: factor its diagonal block in shared memory
+//      (one barrier per pivot), eliminate the rows below one thread per row
+//      with the reciprocal pivots, write the block to the front storage and
+//      release it; otherwise write the block (part of the Schur complement).
+// Every phase runs on all 8 warps with short loop bodies: straight-line code
+// run by a single warp is fetched cold and stalls on instruction fetch.
+// The same per-element sequence of multiply-adds as panel_eliminate is used
+// for the panel, so the pivot block and L21 match the per-panel path.
+// Tasks are taken in ticket order from a list sorted by j: every wait is on a
+// task with a smaller ticket, already held by a running CTA, so the schedule
+// cannot deadlock whatever the residency, and every wait is bounded.
+// ---------------------------------------------------------------------------
+constexpr int kOwnThreads = 256;
+constexpr unsigned kOwnFull = 0xffffffffu;
+
+// U rows r0..r0+nb-1 of the block, solved with the unit lower L11 in Ls
+// (row-major, ld 33): warp g takes columns [4g, 4g+4), lane r holds row r and
+// receives row q's final values by shuffle.  The loop body is small so one
+// warp's instruction stream stays cached.  Us gets the U rows row-major (32
+// per row, zero beyond w and nb) for the update.  Needs 8 warps.
+template <typename T>
+__device__ __forceinline__ void own_trsm(T* Bk, int ld, int r0, int nb, int w, const T* Ls, T* Us) {
+  const int lane = threadIdx.x & 31, cb = (threadIdx.x >> 5) * 4;
+  T x[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x[i] = (lane < nb && cb + i < w) ? Bk[r0 + lane + (cb + i) * ld] : T(0);
+  for (int q = 0; q + 1 < nb; ++q) {
+    T u[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) u[i] = __shfl_sync(kOwnFull, x[i], q);
+    if (lane > q) {
+      const T l = Ls[lane * 33 + q];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) x[i] -= l * u[i];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const bool in = lane < nb && cb + i < w;
+    if (in) Bk[r0 + lane + (cb + i) * ld] = x[i];
+    Us[lane * 32 + cb + i] = in ? x[i] : T(0);
+  }
+}
+
+// rows [i0, F) of the block: x(i, :) -= L(i, r0..r0+nb-1) U, L read from the
+// front storage (written by the panel's owner before its release), U from Us;
+// one work item is one row and CW columns.
+template <typename T, int CW>
+__device__ __forceinline__ void own_update_rows(T* Bk, int ld, const T* f, int F, int r0, int nb,
+                                                const T* Us, int i0, int w) {
+  constexpr int G = 32 / CW;
+  const int m = F - i0;
+  for (int q = threadIdx.x; q < m * G; q += blockDim.x) {
+    const int g = q / m;
+    const int i = i0 + (q - g * m);
+    const int cb = g * CW;
+    T l[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) l[c] = (c < nb) ? __ldcg(f + i + (int64_t)(r0 + c) * F) : T(0);
+    T x[CW];
+#pragma unroll
+    for (int col = 0; col < CW; ++col) x[col] = (cb + col < w) ? Bk[i + (cb + col) * ld] : T(0);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      const T* ur = Us + c * 32 + cb;
+#pragma unroll
+      for (int col = 0; col < CW; ++col) x[col] -= l[c] * ur[col];
+    }
+#pragma unroll
+    for (int col = 0; col < CW; ++col)
+      if (cb + col < w) Bk[i + (cb + col) * ld] = x[col];
+  }
+}
+
+// pivot-free LU of the np x w diagonal block D (rows = the block's pivots) in
+// shared memory, one barrier per pivot: lane = column, warp g = rows g,
+// g + 8, g + 16, g + 24.  Column c keeps its unscaled values during the
+// elimination (every thread forms the multiplier itself, as the same product
+// the per-panel path stores) and is scaled once at the end.  Writes the
+// reciprocal pivots to rinv and the U rows, row-major, to Us.
+template <typename T>
+__device__ __forceinline__ void own_factor_diag(T* D, int ld, int np, int w, T* Us, T* rinv,
+                                                const SymDev& sd, int s, int k, int K, int colbase,
+                                                int32_t* status, int32_t* badcol) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int c = 0; c < np; ++c) {
+    const T piv = D[c + c * ld];
+    const T rp = T(1) / piv;
+    if (threadIdx.x == 0) {
+      check_pivot(piv, sd, s, k, K, colbase + c, status, badcol);
+      rinv[c] = rp;
+    }
+    if (lane > c && lane < w) {
+      const T u = D[c + lane * ld];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = wid + 8 * i;
+        if (r > c && r < np) D[r + lane * ld] -= (D[r + c * ld] * rp) * u;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = wid + 8 * i;
+    T v = T(0);
+    if (r < np && lane < w) {
+      v = D[r + lane * ld];
+      if (lane < r) D[r + lane * ld] = v * rinv[lane];
+    }
+    Us[r * 32 + lane] = (r < np && lane < w && lane >= r) ? v : T(0);
+  }
+}
+
+// rows [r0+np, F) of the block after its diagonal block is factored: one
+// thread per row scales by the reciprocal pivots and eliminates in pivot
+// order (the remaining columns of a block that straddles the end of the
+// pivots are updated too).
+template <typename T>
+__device__ __forceinline__ void own_eliminate_rows(T* Bk, int ld, int F, int r0, int np, int w,
+                                                   const T* Us, const T* rinv) {
+  for (int i = r0 + np + threadIdx.x; i < F; i += blockDim.x) {
+    T x[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) x[c] = (c < w) ? Bk[i + c * ld] : T(0);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      if (c < np) {
+        const T l = x[c] * rinv[c];
+        x[c] = l;
+#pragma unroll
+        for (int cc = c + 1; cc < 32; ++cc) x[cc] -= l * Us[c * 32 + cc];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      if (c < w) Bk[i + c * ld] = x[c];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kOwnThreads) k_front_owner(SymDev sd, const int32_t* __restrict__ big,
+                                                             const DagTask* __restrict__ tasks, int ntasks,
+                                                             int* ticket, int* flags, int* err,
+                                                             const double* __restrict__ vals,
+                                                             const double* __restrict__ D, Shifts sh,
+                                                             T* __restrict__ fronts, int32_t* status,
+                                                             int32_t* badcol) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_t;
+  __shared__ T rinv[32];
+  T* Us = reinterpret_cast<T*>(smraw);  // 32 x 32 row-major: U rows of the current panel
+  T* Ls = Us + 32 * 32;                 // 32 x 33 row-major: unit-lower L11 of the current panel
+  T* Bk = Ls + 32 * 33;                 // ld x 32 column-major: the owned block
+  const int K = sh.K;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (;;) {
+    __syncthreads();  // the previous task is done with shared memory and s_t
+    if (tid == 0) s_t = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int u = s_t;
+    if (u >= ntasks) return;
+    const DagTask t = tasks[u];
+    const int s = big[t.b], k = t.k, j = t.j;
+    const int ns = sd.ns[s], F = ns + sd.ms[s];
+    const int P = (ns + 31) >> 5;
+    const int j0 = j << 5, w = min(32, F - j0);
+    const int ld = F | 1;
+    int* pflag = flags + t.flags;
+    T* f = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * F * F;
+    const int64_t vo = sd.vec_off[s];
+
+    // 1. assembly of columns [j0, j0 + w)
+    for (int q = tid; q < ld * w; q += nt) Bk[q] = T(0);
+    __syncthreads();
+    {
+      const int64_t a0 = sd.amap_coff[vo + j0], a1 = sd.amap_coff[vo + j0 + w];
+      for (int64_t q = a0 + tid; q < a1; q += nt) {
+        const int d = sd.amap_dst[q];
+        const int c = d / F;
+        atomicAdd(&Bk[(d - c * F) + (c - j0) * ld], (T)vals[sd.amap_src[q]]);
+      }
+      const double tk = sh.t[k];
+      const int c0 = sd.c0[s];
+      for (int c = j0 + tid; c < min(j0 + w, ns); c += nt)
+        atomicAdd(&Bk[c + (c - j0) * ld], (T)(tk * D[sd.perm[c0 + c]]));
+    }
+    __syncthreads();
+    for (int dc = wid; dc < w; dc += nw) {
+      const int64_t e0 = sd.inv_off[vo + j0 + dc], e1 = sd.inv_off[vo + j0 + dc + 1];
+      T* dcol = Bk + dc * ld;
+      for (int64_t eb = e0; eb < e1; eb += 32) {
+        const int ne = (int)min((int64_t)32, e1 - eb);
+        int ca = 0, cF = 1, ccol = 0;
+        int64_t cfo = 0, cro = 0;
+        if (lane < ne) {
+          const int ch = sd.inv_child[eb + lane];
+          ca = sd.inv_a[eb + lane];
+          cF = sd.inv_cF[eb + lane];
+          ccol = sd.inv_col[eb + lane];
+          cfo = sd.front_off[ch];
+          cro = sd.row_off[ch];
+        }
+        for (int e = 0; e < ne; ++e) {
+          const int eF = __shfl_sync(kOwnFull, cF, e);
+          const int ecol = __shfl_sync(kOwnFull, ccol, e);
+          const int cns = ecol - __shfl_sync(kOwnFull, ca, e);
+          const int cms = eF - cns;
+          const int32_t* em = sd.emap + __shfl_sync(kOwnFull, cro, e);
+          const T* scol = fronts + (int64_t)K * __shfl_sync(kOwnFull, cfo, e) + (int64_t)k * eF * eF +
+                          (int64_t)ecol * eF + cns;
+          for (int a = lane; a < cms; a += 32) dcol[em[a]] += scol[a];
+          __syncwarp();
+        }
+      }
+    }
+    __syncthreads();
+
+    // 2. the updates of every earlier panel, in pivot order
+    const int pe = min(j, P);
+    for (int p = 0; p < pe; ++p) {
+      const int r0 = p << 5, nb = min(32, ns - r0);
+      if (tid == 0) dag_wait(pflag + p, 1, err);
+      __syncthreads();
+      for (int e = tid; e < 32 * 32; e += nt) {
+        const int r = e & 31, c = e >> 5;
+        Ls[r * 33 + c] = (r < nb && c < r) ? __ldcg(f + (r0 + r) + (int64_t)(r0 + c) * F) : T(0);
+      }
+      __syncthreads();
+      own_trsm<T>(Bk, ld, r0, nb, w, Ls, Us);
+      __syncthreads();
+      own_update_rows<T, 8>(Bk, ld, f, F, r0, nb, Us, r0 + nb, w);
+      __syncthreads();
+    }
+
+    // 3. the block's own pivots
+    if (j < P) {
+      const int np = min(32, ns - j0);
+      own_factor_diag<T>(Bk + j0, ld, np, w, Us, rinv, sd, s, k, K, sd.c0[s] + j0, status, badcol);
+      __syncthreads();
+      own_eliminate_rows<T>(Bk, ld, F, j0, np, w, Us, rinv);
+      __syncthreads();
+    }
+    for (int c = wid; c < w; c += nw) {
+      T* dst = f + (int64_t)(j0 + c) * F;
+      const T* src = Bk + c * ld;
+      for (int i = lane; i < F; i += 32) dst[i] = src[i];
+    }
+    if (j < P) {
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) dag_st_release(pflag + j, 1);
+    }
+  }
+}
+
+template <typename T>
+int owner_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_big, const DagTask* tasks,
+               int* ticket, int* flags, int* err, const double* vals, const double* D,
+               const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol, cudaStream_t st) {
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_front_owner<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  }
+  const size_t smem = ((size_t)(lp.big_maxF | 1) * 32 + 32 * 32 + 32 * 33) * sizeof(T);
+  if (smem > (size_t)kSmemCap) return -1;
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_front_owner<T>, kOwnThreads, smem);
+  const int grid = std::max(1, std::min(lp.dag_tasks, std::max(1, occ) * std::max(nsm, 1)));
+  k_front_owner<T><<<grid, kOwnThreads, smem, st>>>(sd, d_big + lp.big_off, tasks + lp.dag_task_off,
+                                                    lp.dag_tasks, ticket, flags, err, vals, D, sh,
+                                                    (T*)fronts, status, badcol);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
 template <typename T>
 int small_threads(int maxF) {
   if (maxF <= 16) return 64;
@@ -845,6 +1137,32 @@ int launch_factor_small(int precision, const SymDev& sd, const LevelPlan& lp,
 
 int max_dag_front(int precision) { return kSmemCap / (32 * (precision == PISP_FP32 ? 4 : 8)) - 1; }
 
+int max_owner_front(int precision) {
+  // (F | 1) * 32 + 32 * 32 + 32 * 33 elements must fit in kSmemCap bytes
+  const int L = kSmemCap / (precision == PISP_FP32 ? 4 : 8) / 32 - 65;
+  return (L & 1) ? L : L - 1;
+}
+
+void build_owner_tasks(const BigFrontHost* big, int32_t nbig, int32_t K, std::vector<DagTask>& out,
+                       int32_t& nflags) {
+  out.clear();
+  std::vector<int32_t> foff((size_t)nbig * K);
+  nflags = 0;
+  int maxJ = 0;
+  for (int b = 0; b < nbig; ++b) {
+    maxJ = std::max(maxJ, (big[b].F + 31) / 32);
+    for (int k = 0; k < K; ++k) {
+      foff[(size_t)b * K + k] = nflags;
+      nflags += (big[b].ns + 31) / 32;
+    }
+  }
+  for (int j = 0; j < maxJ; ++j)
+    for (int b = 0; b < nbig; ++b) {
+      if (j >= (big[b].F + 31) / 32) continue;
+      for (int k = 0; k < K; ++k) out.push_back({kDagOwner, b, k, 0, j, foff[(size_t)b * K + k]});
+    }
+}
+
 void build_dag_tasks(const BigFrontHost* big, int32_t nbig, int32_t K, std::vector<DagTask>& out,
                      int32_t& nflags) {
   out.clear();
@@ -885,6 +1203,13 @@ int launch_factor_big_dag(int precision, const SymDev& sd, const LevelPlan& lp, 
                           const DagTask* tasks, int* ticket, int* flags, int* err,
                           const double* vals, const double* D, const Shifts& sh, void* fronts,
                           int32_t* status, int32_t* badcol, cudaStream_t st) {
+  if (lp.dag_owner) {
+    if (precision == PISP_FP32)
+      return owner_impl<float>(sd, lp, d_big, tasks, ticket, flags, err, vals, D, sh, fronts, status,
+                               badcol, st);
+    return owner_impl<double>(sd, lp, d_big, tasks, ticket, flags, err, vals, D, sh, fronts, status,
+                              badcol, st);
+  }
   if (precision == PISP_FP32)
     return big_dag_impl<float>(sd, lp, d_big, tasks, ticket, flags, err, vals, D, sh, fronts, status,
                                badcol, st);

@@ -23,6 +23,7 @@ struct SymDev {
   const int64_t* amap_off;   // [S+1]
   const int32_t* amap_src;   // A value index
   const int32_t* amap_dst;   // position i + j*F in the front
+  const int64_t* amap_coff;  // [sum F + 1] first entry of column j of front s at vec_off[s] + j
   const int32_t* rows;       // update rows (permuted global index)
   const int32_t* emap;       // position of each update row in the parent front
   const int32_t* parent;     // [S] parent supernode or -1
@@ -69,6 +70,7 @@ struct LevelPlan {
   int32_t dag_tasks = 0;
   int64_t dag_flag_off = 0;   // offset into the device flag area (per level)
   int32_t dag_flags = 0;
+  int32_t dag_owner = 0;      // 1: the tasks are column-block owner tasks
   // every front of the level for the solves, grouped by size class
   Group sgroups[8];
   int32_t n_sgroups = 0;
@@ -89,7 +91,11 @@ struct BigFrontHost {
 // of its U rows, then the trailing update of the rows below).  flags points
 // at the (front, k) pair's counters: J "updates applied" per column block,
 // then P "panel done" flags.
-enum DagKind { kDagAsm = 0, kDagPanel = 1, kDagUpdate = 2 };
+//
+// The column-block owner schedule (kind 3) uses the same record: one task per
+// (front b, perturbation k, 32-column block j), flags pointing at the pair's
+// P "panel released" flags.
+enum DagKind { kDagAsm = 0, kDagPanel = 1, kDagUpdate = 2, kDagOwner = 3 };
 struct DagTask {
   int32_t kind, b, k, p, j, flags;
 };
@@ -97,6 +103,10 @@ struct DagTask {
 // Builds the task list of one level (b indexes the level's big-front list).
 void build_dag_tasks(const BigFrontHost* big, int32_t nbig, int32_t K, std::vector<DagTask>& out,
                      int32_t& nflags);
+// Column-block owner tasks of one level, sorted by block index j so that a
+// task only waits on tasks with smaller tickets.
+void build_owner_tasks(const BigFrontHost* big, int32_t nbig, int32_t K, std::vector<DagTask>& out,
+                       int32_t& nflags);
 
 // ---- factor (factor.cu) ----
 // Each launcher returns the number of kernels launched (>= 0) or -1 on a
@@ -110,7 +120,8 @@ int launch_factor_big(int precision, const SymDev& sd, const LevelPlan& lp, cons
                       const BigFrontHost* big_host, const double* vals, const double* D,
                       const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol,
                       cudaStream_t st);
-// Big fronts of one level as one persistent tile-DAG launch; ticket (1 int)
+// Big fronts of one level as one persistent launch over the level's task
+// list (tile DAG, or column-block owners when lp.dag_owner); ticket (1 int)
 // and flags (lp.dag_flags ints) must be zero; err is set if a bounded
 // dependency wait gave up.
 int launch_factor_big_dag(int precision, const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,
@@ -119,6 +130,9 @@ int launch_factor_big_dag(int precision, const SymDev& sd, const LevelPlan& lp, 
                           int32_t* status, int32_t* badcol, cudaStream_t st);
 // largest front the tile-DAG path takes (its panel must fit in shared memory)
 int max_dag_front(int precision);
+// largest front the column-block owner path takes (a 32-column block of all
+// F rows must fit in shared memory)
+int max_owner_front(int precision);
 // largest front (in elements of the given precision) the shared-memory path takes
 int small_front_limit(int precision);
 // CTAs per cluster for a front of size F factored in distributed shared

@@ -440,6 +440,19 @@ std::string analyze(int32_t G, const int32_t* n, const int64_t* row_ptr,
       }
     }
   }
+  // first entry of every front column: column c of front s starts at
+  // amap_coff[vec_off[s] + c]; the entry after a front's last column is the
+  // next front's first, so consecutive fronts share it
+  S.amap_coff.assign(S.vec_off[nS] + 1, 0);
+  for (int32_t s = 0; s < nS; ++s) {
+    const int32_t F = S.sn[s].F();
+    int64_t q = S.amap_off[s];
+    for (int32_t c = 0; c <= F; ++c) {
+      while (q < S.amap_off[s + 1] && S.amap_dst[q] / F < c) ++q;
+      S.amap_coff[S.vec_off[s] + c] = q;
+    }
+  }
+  S.amap_coff[S.vec_off[nS]] = S.amap_off[nS];
   return std::string();
 }
 

@@ -53,6 +53,8 @@ struct Symbolic {
   std::vector<int64_t> amap_off;       // [S+1]
   std::vector<int32_t> amap_src;       // index into values
   std::vector<int32_t> amap_dst;       // i + j*F within the front
+  std::vector<int64_t> amap_coff;      // [sum F + 1] first entry of column j of front s
+                                       // at vec_off[s] + j
   // extend-add map: for supernode s, ms positions of its rows in the parent front
   std::vector<int32_t> emap;           // aligned with rows[]
   // inverse extend-add map: for position j of front p (index vec_off[p] + j)

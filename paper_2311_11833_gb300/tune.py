@@ -2,8 +2,8 @@
 
 The options that change performance but not the result are the supernode
 amalgamation (relax_small, relax_zeros: front sizes and tree height), the
-factor policy of wide fronts (single CTA / blocked global path, or CTA
-clusters) and the solve schedule (persistent or one launch per level).  For
+factor policy of wide fronts (column-block owners, CTA clusters, tile DAG or
+per-panel launches) and the solve schedule (persistent or one launch per level).  For
 one sparsity pattern, shift count, RHS count and precision, `autotune` times
 every candidate on the GPU with CUDA events (factor + solve, a few
 repetitions after a warm-up) and returns the fastest.  Results are cached in
@@ -20,7 +20,7 @@ import os
 import numpy as np
 
 RELAX = [(8, 0.05), (4, 0.0), (16, 0.10), (32, 0.20)]
-POLICIES = [0, 1, 2]
+POLICIES = [0, 1, 2, 3]
 SCHEDULES = [0, 1]
 
 

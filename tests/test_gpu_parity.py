@@ -118,10 +118,11 @@ def test_factor_entries_match_pivot_free_lu(pisp):
 @pytest.mark.parametrize("n,density,prec,policy", [
     (220, 0.03, "fp64", 0), (300, 0.03, "fp64", 0), (300, 0.03, "fp32", 0), (700, 0.012, "fp32", 0),
     (220, 0.03, "fp64", 1), (300, 0.03, "fp64", 1), (300, 0.03, "fp32", 1), (420, 0.02, "fp32", 1),
-    (700, 0.012, "fp32", 1), (300, 0.03, "fp64", 2), (700, 0.012, "fp32", 2)])
+    (700, 0.012, "fp32", 1), (300, 0.03, "fp64", 2), (700, 0.012, "fp32", 2),
+    (1200, 0.006, "fp32", 0), (220, 0.03, "fp64", 3), (700, 0.012, "fp32", 3)])
 def test_factor_entries_large_fronts(pisp, n, density, prec, policy):
-    """Fronts factored in shared memory, by CTA clusters or by the blocked global path
-    equal dense Doolittle's."""
+    """Fronts factored in shared memory, by CTA clusters, by column-block owners, as a
+    tile DAG or by per-panel launches equal dense Doolittle's."""
     inst = pfgen.random_sparse(n, density, seed=n)
     t = pfgen.symmetric_shifts(2)
     s, val, D = _solver(pisp, [inst], factor_policy=policy)
@@ -146,7 +147,7 @@ def test_factor_entries_large_fronts(pisp, n, density, prec, policy):
                                        atol=tol * scale)
 
 
-@pytest.mark.parametrize("schedule,policy", [(0, 0), (1, 0), (0, 2)])
+@pytest.mark.parametrize("schedule,policy", [(0, 0), (1, 0), (0, 2), (0, 3)])
 def test_precision_config_fp64_big_fronts(pisp, schedule, policy):
     """2000-bus grid: its top fronts exceed the shared-memory path (blocked path)."""
     inst = pfgen.make_instance("precision")
