@@ -760,60 +760,113 @@ __device__ __forceinline__ void own_trsm(T* Bk, int ld, int r0, int nb, int w, c
 }
 
 // rows [i0, F) of the block: x(i, :) -= L(i, r0..r0+nb-1) U, L read from the
-// front storage (written by the panel's owner before its release), U from Us;
-// one work item is one row and CW columns.
-template <typename T, int CW>
+// front storage (written by the panel's owner before its release) straight
+// into registers, U from Us; a work item is one row and 16 columns.
+template <typename T>
 __device__ __forceinline__ void own_update_rows(T* Bk, int ld, const T* f, int F, int r0, int nb,
                                                 const T* Us, int i0, int w) {
-  constexpr int G = 32 / CW;
   const int m = F - i0;
-  for (int q = threadIdx.x; q < m * G; q += blockDim.x) {
-    const int g = q / m;
-    const int i = i0 + (q - g * m);
-    const int cb = g * CW;
+  for (int q = threadIdx.x; q < 2 * m; q += blockDim.x) {
+    const int g = q >= m ? 1 : 0;
+    const int i = i0 + q - g * m;
+    const int cb = 16 * g;
+    if (cb >= w) continue;
     T l[32];
 #pragma unroll
     for (int c = 0; c < 32; ++c) l[c] = (c < nb) ? __ldcg(f + i + (int64_t)(r0 + c) * F) : T(0);
-    T x[CW];
+    T x[16];
 #pragma unroll
-    for (int col = 0; col < CW; ++col) x[col] = (cb + col < w) ? Bk[i + (cb + col) * ld] : T(0);
+    for (int col = 0; col < 16; ++col) x[col] = Bk[i + (cb + col) * ld];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      const T* ur = Us + c * 32 + cb;
+    for (int cg = 0; cg < 32; cg += 8) {
+      if (cg < nb) {
 #pragma unroll
-      for (int col = 0; col < CW; ++col) x[col] -= l[c] * ur[col];
+        for (int c = cg; c < cg + 8; ++c) {
+          const T* ur = Us + c * 32 + cb;
+#pragma unroll
+          for (int col = 0; col < 16; ++col) x[col] -= l[c] * ur[col];
+        }
+      }
     }
 #pragma unroll
-    for (int col = 0; col < CW; ++col)
+    for (int col = 0; col < 16; ++col)
       if (cb + col < w) Bk[i + (cb + col) * ld] = x[col];
   }
 }
 
 // pivot-free LU of the np x w diagonal block D (rows = the block's pivots) in
-// shared memory, one barrier per pivot: lane = column, warp g = rows g,
-// g + 8, g + 16, g + 24.  Column c keeps its unscaled values during the
-// elimination (every thread forms the multiplier itself, as the same product
-// the per-panel path stores) and is scaled once at the end.  Writes the
-// reciprocal pivots to rinv and the U rows, row-major, to Us.
+// shared memory: lane = column, warp g = rows g, g + 8, g + 16, g + 24, and
+// two pivots per barrier.  Columns keep their unscaled values during the
+// elimination and are scaled once at the end; every thread forms the
+// multipliers, the second pivot and the second pivot's row and column entries
+// after the first elimination itself, as the same expressions in the same
+// order as the one-pivot-at-a-time elimination (so every thread holds the
+// values the owners of those entries store).  Writes the reciprocal pivots to
+// rinv and the U rows, row-major, to Us.
 template <typename T>
 __device__ __forceinline__ void own_factor_diag(T* D, int ld, int np, int w, T* Us, T* rinv,
                                                 const SymDev& sd, int s, int k, int K, int colbase,
                                                 int32_t* status, int32_t* badcol) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int c = 0; c < np; ++c) {
-    const T piv = D[c + c * ld];
-    const T rp = T(1) / piv;
+  int c = 0;
+  for (; c + 1 < np; c += 2) {
+    const T p0 = D[c + c * ld], b = D[(c + 1) + c * ld], e = D[c + (c + 1) * ld];
+    const T p1raw = D[(c + 1) + (c + 1) * ld];
+    const T rp0 = T(1) / p0;
+    const T l1 = b * rp0;
+    const T p1 = p1raw - l1 * e;
+    const T rp1 = T(1) / p1;
     if (threadIdx.x == 0) {
-      check_pivot(piv, sd, s, k, K, colbase + c, status, badcol);
-      rinv[c] = rp;
+      check_pivot(p0, sd, s, k, K, colbase + c, status, badcol);
+      check_pivot(p1, sd, s, k, K, colbase + c + 1, status, badcol);
+      rinv[c] = rp0;
+      rinv[c + 1] = rp1;
     }
+    // row c + 1 and column c + 1 are read unmodified by every thread in this
+    // step, so their new values are stored only after the barrier (nothing
+    // reads them again before the step after next)
+    T held[4];
+    int hmask = 0;
     if (lane > c && lane < w) {
-      const T u = D[c + lane * ld];
+      const T u0 = D[c + lane * ld];
+      const T u1 = D[(c + 1) + lane * ld] - l1 * u0;
+      T a0[4], a1[4], d[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int r = wid + 8 * i;
-        if (r > c && r < np) D[r + lane * ld] -= (D[r + c * ld] * rp) * u;
+        a0[i] = r < np ? D[r + c * ld] : T(0);
+        a1[i] = r < np ? D[r + (c + 1) * ld] : T(0);
+        d[i] = r < np ? D[r + lane * ld] : T(0);
       }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = wid + 8 * i;
+        held[i] = T(0);
+        if (r > c && r < np) {
+          const T m0 = a0[i] * rp0;
+          T v = d[i] - m0 * u0;
+          if (r > c + 1 && lane > c + 1) {
+            const T m1 = (a1[i] - m0 * e) * rp1;
+            v = v - m1 * u1;
+            D[r + lane * ld] = v;
+          } else {
+            held[i] = v;
+            hmask |= 1 << i;
+          }
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (hmask & (1 << i)) D[(wid + 8 * i) + lane * ld] = held[i];
+  }
+  __syncthreads();
+  if (c < np) {  // odd count: the last pivot updates nothing below it
+    if (threadIdx.x == 0) {
+      const T piv = D[c + c * ld];
+      check_pivot(piv, sd, s, k, K, colbase + c, status, badcol);
+      rinv[c] = T(1) / piv;
     }
     __syncthreads();
   }
@@ -927,7 +980,20 @@ __global__ void __launch_bounds__(kOwnThreads) k_front_owner(SymDev sd, const in
           const int32_t* em = sd.emap + __shfl_sync(kOwnFull, cro, e);
           const T* scol = fronts + (int64_t)K * __shfl_sync(kOwnFull, cfo, e) + (int64_t)k * eF * eF +
                           (int64_t)ecol * eF + cns;
-          for (int a = lane; a < cms; a += 32) dcol[em[a]] += scol[a];
+          // all loads of a group of 8 x 32 rows first, then the adds
+          for (int a0 = 0; a0 < cms; a0 += 256) {
+            int r[8];
+            T v[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              const int a = a0 + lane + 32 * t;
+              r[t] = a < cms ? em[a] : -1;
+              v[t] = a < cms ? scol[a] : T(0);
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+              if (r[t] >= 0) dcol[r[t]] += v[t];
+          }
           __syncwarp();
         }
       }
@@ -947,7 +1013,7 @@ __global__ void __launch_bounds__(kOwnThreads) k_front_owner(SymDev sd, const in
       __syncthreads();
       own_trsm<T>(Bk, ld, r0, nb, w, Ls, Us);
       __syncthreads();
-      own_update_rows<T, 8>(Bk, ld, f, F, r0, nb, Us, r0 + nb, w);
+      own_update_rows<T>(Bk, ld, f, F, r0, nb, Us, r0 + nb, w);
       __syncthreads();
     }
 
@@ -959,15 +1025,23 @@ __global__ void __launch_bounds__(kOwnThreads) k_front_owner(SymDev sd, const in
       own_eliminate_rows<T>(Bk, ld, F, j0, np, w, Us, rinv);
       __syncthreads();
     }
+    // rows from the block's first pivot down are what later panels read:
+    // write them, release the block, then write the U rows above
+    const int rs = j < P ? j0 : 0;
     for (int c = wid; c < w; c += nw) {
       T* dst = f + (int64_t)(j0 + c) * F;
       const T* src = Bk + c * ld;
-      for (int i = lane; i < F; i += 32) dst[i] = src[i];
+      for (int i = rs + lane; i < F; i += 32) dst[i] = src[i];
     }
     if (j < P) {
       __threadfence();
       __syncthreads();
       if (tid == 0) dag_st_release(pflag + j, 1);
+      for (int c = wid; c < w; c += nw) {
+        T* dst = f + (int64_t)(j0 + c) * F;
+        const T* src = Bk + c * ld;
+        for (int i = lane; i < rs; i += 32) dst[i] = src[i];
+      }
     }
   }
 }
