@@ -181,6 +181,12 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // done[s*K + k] counts the finished RHS chunks of (front s, perturbation k).
 // Forward solve: a front waits until the counter of each child reaches
 // nch[child].  Backward solve: a front waits until its parent's counter
@@ -200,27 +206,55 @@ struct Sync {
   __device__ void add(int s, int k, int K) const {
     asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(done + (int64_t)s * K + k) : "memory");
   }
-  // forward: wait for child c of this front
-  __device__ void wait_child(int c, int k, int K) const { wait_ge(done + (int64_t)c * K + k, nch[c]); }
   // backward: front s waits for its parent p (which publishes to itself)
   __device__ void wait_parent(int s, int p, int k, int K) const {
     wait_ge(done + (int64_t)p * K + k, nch[p]);
   }
   __device__ void publish_children(const SymDev& sd, int s, int k, int K) const { add(s, k, K); }
+  // forward: the n threads (index 0..n-1) of a CTA or a lane group poll the
+  // children's counters in parallel with relaxed loads and then each issues
+  // an acquire fence, so a front with many children pays one round trip
+  // instead of one per child; the caller's barrier orders the group's later
+  // reads after the fences
+  __device__ void wait_children(const SymDev& sd, int s, int k, int K, int idx, int n) const {
+    const int cb = sd.child_off[s], ce = sd.child_off[s + 1];
+    for (int ci = cb + idx; ci < ce; ci += n) {
+      const int c = sd.child[ci];
+      const int* f = done + (int64_t)c * K + k;
+      const int need = nch[c];
+      if (ld_relaxed(f) >= need) continue;
+      int64_t i = 0;
+      for (; i < kWaitPolls; ++i) {
+        __nanosleep(64);
+        if (ld_relaxed(f) >= need) break;
+      }
+      if (i == kWaitPolls) atomicExch(err, 1);
+    }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  }
 };
 
 // Right-hand side of front s (rows of its pivot part) plus the children's
 // contributions to position j, summed in child order: the same order as an
 // extend-add that visits children one by one, without a barrier per child.
-template <typename T>
+// NB contributions' loads are in flight at a time; they are added in child
+// order whatever NB is.
+template <typename T, int NB = 4>
 __device__ __forceinline__ T gather_position(const SymDev& sd, int s, int j, int ns, int c0,
                                              const double* rhs, int rhs_mode, const T* V, int k, int K,
                                              int R, int r) {
   T a = (j < ns) ? (T)load_rhs(sd, rhs, rhs_mode, c0 + j, k, K, R, r) : T(0);
   const int64_t e1 = sd.inv_off[sd.vec_off[s] + j + 1];
-  for (int64_t e = sd.inv_off[sd.vec_off[s] + j]; e < e1; ++e) {
-    const int cF = sd.inv_cF[e];
-    a += __ldcg(V + (int64_t)K * R * sd.inv_vbase[e] + ((int64_t)k * R + r) * cF + sd.inv_col[e]);
+  const int64_t kr = (int64_t)k * R + r, kR = (int64_t)K * R;
+  for (int64_t e = sd.inv_off[sd.vec_off[s] + j]; e < e1; e += NB) {
+    const int n = (int)min((int64_t)NB, e1 - e);
+    T v[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+      v[q] = q < n ? __ldcg(V + kR * sd.inv_vbase[e + q] + kr * sd.inv_cF[e + q] + sd.inv_col[e + q]) : T(0);
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+      if (q < n) a += v[q];
   }
   return a;
 }
@@ -261,22 +295,19 @@ __device__ __forceinline__ void seg_forward(const SymDev& sd, const SegTask& t, 
                                             T (*bw)[SEG + 1], const T* __restrict__ fronts,
                                             const double* __restrict__ rhs, int rhs_mode,
                                             T* __restrict__ V, int R, int K, const Sync& sy) {
-  int ns = 0, ms = 0, F = 0, c0 = 0, ch0 = 0, nchn = 0;
+  int ns = 0, ms = 0, F = 0, c0 = 0;
   if (t.active) {
     ns = sd.ns[t.s];
     ms = sd.ms[t.s];
     F = ns + ms;
     c0 = sd.c0[t.s];
-    ch0 = sd.child_off[t.s];
-    nchn = sd.child_off[t.s + 1] - ch0;
   }
   const int k = t.k, r0 = t.r0, nr = t.nr;
   const T* f = fronts + (t.active ? (int64_t)K * sd.front_off[t.s] + (int64_t)k * F * F : 0);
   T Lr[SEG];
 #pragma unroll
   for (int c = 0; c < SEG; ++c) Lr[c] = (c < ns && sl > c && sl < F) ? f[sl + c * F] : T(0);
-  if (sy.done && sl == 0)
-    for (int ci = 0; ci < nchn; ++ci) sy.wait_child(sd.child[ch0 + ci], k, K);
+  if (sy.done && t.active) sy.wait_children(sd, t.s, k, K, sl, SEG);
   __syncwarp();
   T vv[kRW];
 #pragma unroll
@@ -379,13 +410,103 @@ __device__ __forceinline__ void seg_backward(const SymDev& sd, const SegTask& t,
 
 // ---------------------------------------------------------------------------
 // Fronts with F > 32: a whole CTA per (front, k, RHS chunk), blocked by 32
-// pivots.  The 32x32 diagonal block of step b+1 is staged in shared memory
-// while step b updates the rows below it, so each step costs one global
-// latency: warps solve the diagonal block with shuffles (one warp per
-// right-hand side), then every thread updates its rows with the 32 solved
-// values, reading the factor panel with coalesced column loads.
+// pivots.  Warps solve the staged 32x32 diagonal block with shuffles (one
+// warp per right-hand side), then every thread updates its rows with the 32
+// solved values, reading the factor panel with coalesced column loads.  None
+// of the factor entries a step reads depend on the solution, so each step
+// issues its first rows' panel loads and the next diagonal block's loads into
+// registers before the diagonal solve: the step's memory latency overlaps
+// the solve instead of following it.
 // ---------------------------------------------------------------------------
 constexpr int kBS = 33;  // padded row stride of a staged 32x32 block
+
+// rows prefetched per thread before the diagonal solve: more would push the
+// persistent kernel past its 128-register budget (two CTAs per SM) and spill
+template <typename T> struct BlkPF { static constexpr int N = 1; };
+
+// L[c] = f[i + (p0 + c) * F] for c < nb (zero elsewhere or when !ok)
+template <typename T>
+__device__ __forceinline__ void load_prow(T (&L)[32], const T* f, int F, int i, int p0, int nb, bool ok) {
+#pragma unroll
+  for (int c = 0; c < 32; ++c) L[c] = (ok && c < nb) ? f[i + (int64_t)(p0 + c) * F] : T(0);
+}
+
+// this thread's 4 elements of a 32x32 diagonal block (q = tid + 256 t,
+// row q & 31, column q >> 5), kept as stage_block would write them
+template <typename T>
+__device__ __forceinline__ void load_block_regs(T (&nx)[4], const T* f, int F, int p0, int nb, bool lower,
+                                                bool ok, int tid) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int q = tid + 256 * t, i = q & 31, c = q >> 5;
+    const bool keep = ok && (i < nb && c < nb) && (lower ? (i > c) : (i <= c));
+    nx[t] = keep ? f[(p0 + i) + (int64_t)(p0 + c) * F] : T(0);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_block_regs(T* dst, const T (&nx)[4], int tid) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int q = tid + 256 * t;
+    dst[(q & 31) * kBS + (q >> 5)] = nx[t];
+  }
+}
+
+// One warp, one right-hand side: vi (lane = row of the block) becomes
+// L11^{-1} v for the unit lower triangle staged in B (strictly lower part,
+// zeros elsewhere).  Two pivots per step: every lane forms the second solved
+// value itself, as the same operations its owner lane performs, so the
+// dependent shuffle chain is half as long and the result is unchanged.
+template <typename T>
+__device__ __forceinline__ void fwd_block_solve(const T* B, T& vi, int nb, int lane) {
+  for (int c = 0; c < nb; c += 2) {
+    const T y0 = __shfl_sync(kFull, vi, c);
+    const T v1 = __shfl_sync(kFull, vi, (c + 1) & 31);
+    vi -= B[lane * kBS + c] * y0;
+    if (c + 1 < nb) {
+      const T y1 = v1 - B[(c + 1) * kBS + c] * y0;
+      vi -= B[lane * kBS + c + 1] * y1;
+    }
+  }
+}
+
+// One warp, one right-hand side: zi becomes U11^{-1} z for the upper triangle
+// (with its diagonal) staged in B, two pivots per step from the bottom, with
+// the same per-lane operations as one pivot at a time.
+template <typename T>
+__device__ __forceinline__ void bwd_block_solve(const T* B, T& zi, int nb, int lane) {
+  const T rd = (lane < nb) ? T(1) / B[lane * kBS + lane] : T(0);
+  int c = nb - 1;
+  for (; c >= 1; c -= 2) {
+    const T zc = __shfl_sync(kFull, zi, c), zc1 = __shfl_sync(kFull, zi, c - 1);
+    const T rc = __shfl_sync(kFull, rd, c), rc1 = __shfl_sync(kFull, rd, c - 1);
+    const T xc = zc * rc;
+    const T xc1 = (zc1 - B[(c - 1) * kBS + c] * xc) * rc1;
+    if (lane == c) zi = xc;
+    else if (lane == c - 1) zi = xc1;
+    else if (lane < c - 1) zi = (zi - B[lane * kBS + c] * xc) - B[lane * kBS + c - 1] * xc1;
+  }
+  if (c == 0) {
+    const T x0 = __shfl_sync(kFull, zi, 0) * __shfl_sync(kFull, rd, 0);
+    if (lane == 0) zi = x0;
+  }
+}
+
+// vec[r * ld + i] -= sum_{c < nb} L[c] vec[r * ld + p0 + c] for r < nr
+template <typename T>
+__device__ __forceinline__ void apply_prow(const T (&L)[32], T* vec, int ld, int i, int p0, int nb, int nr) {
+  for (int r = 0; r < nr; ++r) {
+    const T* yb = vec + r * ld + p0;
+    T a = T(0);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      if (c >= nb) break;
+      a += L[c] * yb[c];
+    }
+    vec[r * ld + i] -= a;
+  }
+}
 
 template <typename T>
 __device__ __forceinline__ void stage_block(T* dst, const T* f, int F, int p0, int nb, bool lower,
@@ -410,45 +531,42 @@ __device__ __forceinline__ void blk_forward(const SymDev& sd, int s, int k, int 
   T* v = blk + 2 * 32 * kBS;                      // nr x F
   const T* f = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * F * F;
   stage_block(blk, f, F, 0, min(32, ns), true, tid, nt);
-  const int cb = sd.child_off[s], ce = sd.child_off[s + 1];
-  if (sy.done && tid == 0)
-    for (int ci = cb; ci < ce; ++ci) sy.wait_child(sd.child[ci], k, K);
+  if (sy.done) sy.wait_children(sd, s, k, K, tid, nt);
   __syncthreads();
   for (int q = tid; q < nr * F; q += nt) {
     const int j = q % F, r = q / F;
-    v[r * F + j] = gather_position<T>(sd, s, j, ns, c0, rhs, rhs_mode, V, k, K, R, r0 + r);
+    v[r * F + j] = gather_position<T, 8>(sd, s, j, ns, c0, rhs, rhs_mode, V, k, K, R, r0 + r);
   }
   __syncthreads();
+  constexpr int PF = BlkPF<T>::N;
   int cur = 0;
   for (int p0 = 0; p0 < ns; p0 += 32) {
     const int nb = min(32, ns - p0);
+    const int ib = p0 + nb;
+    const bool more = p0 + 32 < ns;
+    T Lp[PF][32], nx[4];
+#pragma unroll
+    for (int g = 0; g < PF; ++g) load_prow(Lp[g], f, F, ib + g * nt + tid, p0, nb, ib + g * nt + tid < F);
+    load_block_regs(nx, f, F, p0 + 32, more ? min(32, ns - p0 - 32) : 0, true, more, tid);
     const T* B = blk + cur * 32 * kBS;
     for (int r = wid; r < nr; r += nw) {
       T vi = (lane < nb) ? v[r * F + p0 + lane] : T(0);
-#pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        if (c >= nb) break;
-        vi -= B[lane * kBS + c] * __shfl_sync(kFull, vi, c);
-      }
+      fwd_block_solve(B, vi, nb, lane);
       if (lane < nb) v[r * F + p0 + lane] = vi;
     }
     __syncthreads();
-    if (p0 + 32 < ns) stage_block(blk + (cur ^ 1) * 32 * kBS, f, F, p0 + 32, min(32, ns - p0 - 32), true, tid, nt);
-    for (int i = p0 + nb + tid; i < F; i += nt) {
-      T Lc[32];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) Lc[c] = (c < nb) ? f[i + (int64_t)(p0 + c) * F] : T(0);
-      for (int r = 0; r < nr; ++r) {
-        const T* yb = v + r * F + p0;
-        T a = T(0);
+    for (int g = 0; g < PF; ++g)
+      if (ib + g * nt + tid < F) apply_prow(Lp[g], v, F, ib + g * nt + tid, p0, nb, nr);
+    // rows beyond the prefetched ones: PF rows per round, loads first
+    for (int i0 = ib + PF * nt + tid; i0 < F; i0 += PF * nt) {
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          if (c >= nb) break;
-          a += Lc[c] * yb[c];
-        }
-        v[r * F + i] -= a;
-      }
+      for (int g = 0; g < PF; ++g) load_prow(Lp[g], f, F, i0 + g * nt, p0, nb, i0 + g * nt < F);
+#pragma unroll
+      for (int g = 0; g < PF; ++g)
+        if (i0 + g * nt < F) apply_prow(Lp[g], v, F, i0 + g * nt, p0, nb, nr);
     }
+    if (more) store_block_regs(blk + (cur ^ 1) * 32 * kBS, nx, tid);
     __syncthreads();
     cur ^= 1;
   }
@@ -514,39 +632,32 @@ __device__ __forceinline__ void blk_backward(const SymDev& sd, int s, int k, int
     }
     __syncthreads();
   }
+  constexpr int PF = BlkPF<T>::N;
   int cur = 0;
   for (int p0 = last0; p0 >= 0; p0 -= 32) {
     const int nb = min(32, ns - p0);
+    T Up[PF][32], nx[4];
+#pragma unroll
+    for (int g = 0; g < PF; ++g) load_prow(Up[g], f, F, g * nt + tid, p0, nb, g * nt + tid < p0);
+    load_block_regs(nx, f, F, p0 - 32, 32, false, p0 > 0, tid);
     const T* B = blk + cur * 32 * kBS;
     for (int r = wid; r < nr; r += nw) {
       T zi = (lane < nb) ? z[r * ns + p0 + lane] : T(0);
-      const T rd = (lane < nb) ? T(1) / B[lane * kBS + lane] : T(0);
-#pragma unroll
-      for (int c = 31; c >= 0; --c) {
-        if (c >= nb) continue;
-        if (lane == c) zi *= rd;
-        const T xc = __shfl_sync(kFull, zi, c);
-        if (lane < c) zi -= B[lane * kBS + c] * xc;
-      }
+      bwd_block_solve(B, zi, nb, lane);
       if (lane < nb) z[r * ns + p0 + lane] = zi;
     }
     __syncthreads();
-    if (p0 > 0) stage_block(blk + (cur ^ 1) * 32 * kBS, f, F, p0 - 32, 32, false, tid, nt);
-    for (int i = tid; i < p0; i += nt) {
-      T Uc[32];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) Uc[c] = (c < nb) ? f[i + (int64_t)(p0 + c) * F] : T(0);
-      for (int r = 0; r < nr; ++r) {
-        const T* xb = z + r * ns + p0;
-        T a = T(0);
+    for (int g = 0; g < PF; ++g)
+      if (g * nt + tid < p0) apply_prow(Up[g], z, ns, g * nt + tid, p0, nb, nr);
+    for (int i0 = PF * nt + tid; i0 < p0; i0 += PF * nt) {
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          if (c >= nb) break;
-          a += Uc[c] * xb[c];
-        }
-        z[r * ns + i] -= a;
-      }
+      for (int g = 0; g < PF; ++g) load_prow(Up[g], f, F, i0 + g * nt, p0, nb, i0 + g * nt < p0);
+#pragma unroll
+      for (int g = 0; g < PF; ++g)
+        if (i0 + g * nt < p0) apply_prow(Up[g], z, ns, i0 + g * nt, p0, nb, nr);
     }
+    if (p0 > 0) store_block_regs(blk + (cur ^ 1) * 32 * kBS, nx, tid);
     __syncthreads();
     cur ^= 1;
   }
@@ -610,13 +721,11 @@ __device__ __forceinline__ void blk_forward_staged(const SymDev& sd, int s, int 
   const T* f = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * F * F;
   stage_panel(pb, F, f, F, 0, min(32, ns), 0, F, tid, nt);
   cp_async_commit();
-  const int cb = sd.child_off[s], ce = sd.child_off[s + 1];
-  if (sy.done && tid == 0)
-    for (int ci = cb; ci < ce; ++ci) sy.wait_child(sd.child[ci], k, K);
+  if (sy.done) sy.wait_children(sd, s, k, K, tid, nt);
   __syncthreads();
   for (int q = tid; q < nr * F; q += nt) {
     const int j = q % F, r = q / F;
-    v[r * F + j] = gather_position<T>(sd, s, j, ns, c0, rhs, rhs_mode, V, k, K, R, r0 + r);
+    v[r * F + j] = gather_position<T, 8>(sd, s, j, ns, c0, rhs, rhs_mode, V, k, K, R, r0 + r);
   }
   cp_async_wait_all();
   __syncthreads();
