@@ -42,8 +42,8 @@ L2_BYTES = 129 * 1024 * 1024
 # on a workload, from the ncu captures summarised under profiles/; an entry is
 # removed when its kernel changes.
 TRAFFIC_PER_LAUNCH = {
-    ("precision", "forward"): 6.33e6,     # profiles/k_solve_persistent_precision_2000bus_K6_R16.md
-    ("precision", "backward"): 12.89e6,
+    ("precision", "forward"): 6.557e6,    # profiles/k_solve_persistent_precision_2000bus_K6_R16.md
+    ("precision", "backward"): 12.291e6,
 }
 
 BENCH = {
