@@ -130,7 +130,7 @@ const char* pisp_last_error(const pisp_handle* h);
 int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row_ptr,
                  const int32_t* col_idx, const pisp_options* opt);
 
-/* Alg. 1 steps 1-2 (factor part): forms P (A + t_k D) P^T for every shift in
+/* Alg. 1, factor part (Eq. xap / xam): forms P (A + t_k D) P^T for every shift in
  * the fixed pivot order and factors all K perturbations pivot-free, level by
  * level of the assembly forest, all K (and all instances) in the same launches.
  *   values    device FP64 [nnz], CSR order of the analysed pattern
@@ -144,7 +144,7 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
 int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
                           const double* t, int32_t K, int32_t precision);
 
-/* Alg. 1 steps 2-4 (solve part): for every perturbation k and RHS r solves
+/* Alg. 1, solve and combine part (Eq. x_star): for every perturbation k and RHS r solves
  * (A + t_k D) x_k = b with the pivot-free factors, then writes
  *     x[i][r] = sum_k w_k x_k[i][r]       (FP64 accumulation)
  *   b        device FP64 [N][R]
@@ -166,7 +166,7 @@ int pisp_solve(pisp_handle* h, const double* b, int32_t R, const double* w, doub
  *   w  host FP64 [K] or NULL for pisp_weights(t);   x device FP64 [N][R]. */
 int pisp_combine(pisp_handle* h, const double* w, double* x);
 
-/* Alg. 1 step 5 turned into a correction: `iters` times
+/* The optional residual check of Alg. 1 turned into a correction: `iters` times
  *     r = b - A x (FP64, original values);  x += sum_k beta_k (A + t_k D)^{-1} r
  * with each inner perturbed solve done with `sweeps` residual corrections.
  * Converges to A^{-1} b when the Neumann series converges (eps * max|alpha| *

@@ -22,8 +22,8 @@ What it computes, by the plain definitions of the paper:
   perturbed solve is done with partial pivoting (the pivot-free LU is only
   the fast route to the same vectors).
 * ``refine`` - the FP64 residual r = B - A x and one correction
-  x + sum_k beta_k (A + t_k D)^{-1} r (the optional error test of Alg. 1,
-  step 5, turned into a correction).
+  x + sum_k beta_k (A + t_k D)^{-1} r (the optional residual check of
+  Alg. 1 turned into a correction).
 * ``adjoint`` - lambda_k = (A + t_k D)^{-T} W, dL/db = sum_k beta_k lambda_k,
   dL/dA_ij = -sum_k beta_k sum_r lambda_k[i,r] x_k[j,r] on A's pattern.
 * ``pivot_free_lu`` - dense Doolittle LU without pivoting of a given

@@ -163,8 +163,8 @@ def x_star(A, B) -> np.ndarray:
 def refine(A, D, t, B, x, iters: int = 1, beta=None) -> np.ndarray:
     """x <- x + sum_k beta_k (A + t_k D)^{-1} (B - A x), `iters` times (FP64).
 
-    The residual is the error test of Alg. 1, step 5; using the same combined
-    perturbed operator on it gives one correction step.
+    The residual is the optional error check of Alg. 1; using the same
+    combined perturbed operator on it gives one correction step.
     """
     if beta is None:
         beta = weights_float(t)

@@ -1,4 +1,4 @@
-// Pivot-free multifrontal LU of all K perturbed matrices (Alg. 1, steps 1-2).
+// Pivot-free multifrontal LU of all K perturbed matrices (Alg. 1, Eq. xap / xam).
 //
 // Each supernode s owns a dense front of size F = ns + ms per perturbation k:
 //   1. assembly: P (A + t_k D) P^T entries that belong to s, plus the
