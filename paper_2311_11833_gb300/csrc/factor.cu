@@ -105,6 +105,60 @@ __device__ __forceinline__ void panel_eliminate(T* P, int ld, int Mr, int nb, co
   }
 }
 
+// Children's update columns added into the destination columns [d0, d0 + w)
+// of front s, stored at dst[row + (col - d0) * ld].  Each destination column
+// belongs to one warp (col - d0 = warp, warp + warps, ...), which walks the
+// column's inverse extend-add list in child order: every element receives its
+// contributions in child order, with no barrier between children, and a
+// group of 8 x 32 child rows is loaded before any of them is added.
+template <typename T>
+__device__ __forceinline__ void extend_add_columns(const SymDev& sd, int s, int k, int K,
+                                                   const T* __restrict__ fronts, T* dst, int ld,
+                                                   int d0, int w) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t vo = sd.vec_off[s];
+  for (int dc = wid; dc < w; dc += nw) {
+    const int64_t e0 = sd.inv_off[vo + d0 + dc], e1 = sd.inv_off[vo + d0 + dc + 1];
+    T* dcol = dst + (int64_t)dc * ld;
+    for (int64_t eb = e0; eb < e1; eb += 32) {
+      const int ne = (int)min((int64_t)32, e1 - eb);
+      int ca = 0, cF = 1, ccol = 0;
+      int64_t cfo = 0, cro = 0;
+      if (lane < ne) {
+        const int ch = sd.inv_child[eb + lane];
+        ca = sd.inv_a[eb + lane];
+        cF = sd.inv_cF[eb + lane];
+        ccol = sd.inv_col[eb + lane];
+        cfo = sd.front_off[ch];
+        cro = sd.row_off[ch];
+      }
+      for (int e = 0; e < ne; ++e) {
+        const int eF = __shfl_sync(0xffffffffu, cF, e);
+        const int ecol = __shfl_sync(0xffffffffu, ccol, e);
+        const int cns = ecol - __shfl_sync(0xffffffffu, ca, e);
+        const int cms = eF - cns;
+        const int32_t* em = sd.emap + __shfl_sync(0xffffffffu, cro, e);
+        const T* scol = fronts + (int64_t)K * __shfl_sync(0xffffffffu, cfo, e) + (int64_t)k * eF * eF +
+                        (int64_t)ecol * eF + cns;
+        for (int a0 = 0; a0 < cms; a0 += 256) {
+          int r[8];
+          T v[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const int a = a0 + lane + 32 * t;
+            r[t] = a < cms ? em[a] : -1;
+            v[t] = a < cms ? scol[a] : T(0);
+          }
+#pragma unroll
+          for (int t = 0; t < 8; ++t)
+            if (r[t] >= 0) dcol[r[t]] += v[t];
+        }
+        __syncwarp();
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Small fronts: whole front in shared memory, one CTA per (front, k).
 // ---------------------------------------------------------------------------
@@ -131,22 +185,9 @@ __global__ void k_front_small(SymDev sd, const int32_t* __restrict__ list,
   const int c0 = sd.c0[s];
   for (int c = tid; c < ns; c += nt) atomicAdd(&f[c * (F + 1)], (T)(tk * D[sd.perm[c0 + c]]));
   __syncthreads();
-  // 1c. extend-add of the children's Schur complements, one child at a time
-  for (int ci = sd.child_off[s]; ci < sd.child_off[s + 1]; ++ci) {
-    const int c = sd.child[ci];
-    const int cns = sd.ns[c], cms = sd.ms[c], cF = cns + cms;
-    const T* cf = fronts + (int64_t)K * sd.front_off[c] + (int64_t)k * cF * cF;
-    const int32_t* em = sd.emap + sd.row_off[c];
-    {
-      const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-      for (int b = wid; b < cms; b += nw) {
-        T* dcol = f + em[b] * F;
-        const T* scol = cf + (int64_t)(cns + b) * cF + cns;
-        for (int a = lane; a < cms; a += 32) dcol[em[a]] += scol[a];
-      }
-    }
-    __syncthreads();
-  }
+  // 1c. extend-add of the children's Schur complements (child order per element)
+  extend_add_columns<T>(sd, s, k, K, fronts, f, F, 0, F);
+  __syncthreads();
   // 2. ns steps of pivot-free elimination
   for (int p = 0; p < ns; ++p) {
     const T piv = f[p * (F + 1)];
@@ -957,47 +998,7 @@ __global__ void __launch_bounds__(kOwnThreads) k_front_owner(SymDev sd, const in
         atomicAdd(&Bk[c + (c - j0) * ld], (T)(tk * D[sd.perm[c0 + c]]));
     }
     __syncthreads();
-    for (int dc = wid; dc < w; dc += nw) {
-      const int64_t e0 = sd.inv_off[vo + j0 + dc], e1 = sd.inv_off[vo + j0 + dc + 1];
-      T* dcol = Bk + dc * ld;
-      for (int64_t eb = e0; eb < e1; eb += 32) {
-        const int ne = (int)min((int64_t)32, e1 - eb);
-        int ca = 0, cF = 1, ccol = 0;
-        int64_t cfo = 0, cro = 0;
-        if (lane < ne) {
-          const int ch = sd.inv_child[eb + lane];
-          ca = sd.inv_a[eb + lane];
-          cF = sd.inv_cF[eb + lane];
-          ccol = sd.inv_col[eb + lane];
-          cfo = sd.front_off[ch];
-          cro = sd.row_off[ch];
-        }
-        for (int e = 0; e < ne; ++e) {
-          const int eF = __shfl_sync(kOwnFull, cF, e);
-          const int ecol = __shfl_sync(kOwnFull, ccol, e);
-          const int cns = ecol - __shfl_sync(kOwnFull, ca, e);
-          const int cms = eF - cns;
-          const int32_t* em = sd.emap + __shfl_sync(kOwnFull, cro, e);
-          const T* scol = fronts + (int64_t)K * __shfl_sync(kOwnFull, cfo, e) + (int64_t)k * eF * eF +
-                          (int64_t)ecol * eF + cns;
-          // all loads of a group of 8 x 32 rows first, then the adds
-          for (int a0 = 0; a0 < cms; a0 += 256) {
-            int r[8];
-            T v[8];
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-              const int a = a0 + lane + 32 * t;
-              r[t] = a < cms ? em[a] : -1;
-              v[t] = a < cms ? scol[a] : T(0);
-            }
-#pragma unroll
-            for (int t = 0; t < 8; ++t)
-              if (r[t] >= 0) dcol[r[t]] += v[t];
-          }
-          __syncwarp();
-        }
-      }
-    }
+    extend_add_columns<T>(sd, s, k, K, fronts, Bk, ld, j0, w);
     __syncthreads();
 
     // 2. the updates of every earlier panel, in pivot order
