@@ -20,7 +20,6 @@ namespace {
 
 constexpr int kSolveThreads = 256;
 constexpr int kSolveSmem = 96 * 1024;
-constexpr int kStagedSmemMax = 0;  // panel staging of the persistent solve (off: measured slower)
 
 // Forward substitution with L (unit lower, TRANS = false) or with U^T
 // (TRANS = true, used by the adjoint), front by front.
@@ -676,215 +675,6 @@ __device__ __forceinline__ void blk_backward(const SymDev& sd, int s, int k, int
   }
 }
 
-// ---------------------------------------------------------------------------
-// Staged variants for fronts whose 32-column panels fit twice in shared
-// memory: the panel of block b+1 (all rows it touches, 32 columns) is copied
-// with cp.async while block b is solved, so each block waits on at most one
-// in-flight copy instead of a chain of dependent global loads.  The factor
-// does not depend on the solve, so the copies can always be issued ahead.
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  if (sizeof(T) == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// buf[c*ld + (i - r0)] = f[i + (col0 + c)*F] for i in [r0, r1), c < nb
-template <typename T>
-__device__ __forceinline__ void stage_panel(T* buf, int ld, const T* f, int F, int col0, int nb, int r0,
-                                            int r1, int tid, int nt) {
-  const int h = r1 - r0;
-  if (h <= 0) return;
-  const int n = h * nb;
-  for (int q = tid; q < n; q += nt) {
-    const int c = q / h, i = q - c * h;
-    cp_async_elem(buf + c * ld + i, f + (r0 + i) + (int64_t)(col0 + c) * F);
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void blk_forward_staged(const SymDev& sd, int s, int k, int r0, int nr, int ch,
-                                                   unsigned char* smraw, const T* __restrict__ fronts,
-                                                   const double* __restrict__ rhs, int rhs_mode,
-                                                   T* __restrict__ V, int R, int K, const Sync& sy) {
-  const int ns = sd.ns[s], ms = sd.ms[s], F = ns + ms;
-  const int c0 = sd.c0[s];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-  T* pb = reinterpret_cast<T*>(smraw);            // 2 panels, 32 x F each: pb[c*F + (i - p0)]
-  T* v = pb + 2 * 32 * F;                          // nr x F
-  const T* f = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * F * F;
-  stage_panel(pb, F, f, F, 0, min(32, ns), 0, F, tid, nt);
-  cp_async_commit();
-  if (sy.done) sy.wait_children(sd, s, k, K, tid, nt);
-  __syncthreads();
-  for (int q = tid; q < nr * F; q += nt) {
-    const int j = q % F, r = q / F;
-    v[r * F + j] = gather_position<T, 8>(sd, s, j, ns, c0, rhs, rhs_mode, V, k, K, R, r0 + r);
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  int cur = 0;
-  for (int p0 = 0; p0 < ns; p0 += 32) {
-    const int nb = min(32, ns - p0);
-    const T* P = pb + cur * 32 * F;                // P[c*F + (i - p0)] = L(i, p0 + c)
-    if (p0 + 32 < ns) {
-      stage_panel(pb + (cur ^ 1) * 32 * F, F, f, F, p0 + 32, min(32, ns - p0 - 32), p0 + 32, F, tid, nt);
-      cp_async_commit();
-    }
-    for (int r = wid; r < nr; r += nw) {
-      T vi = (lane < nb) ? v[r * F + p0 + lane] : T(0);
-#pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        if (c >= nb) break;
-        const T l = (lane > c && lane < nb) ? P[c * F + lane] : T(0);
-        vi -= l * __shfl_sync(kFull, vi, c);
-      }
-      if (lane < nb) v[r * F + p0 + lane] = vi;
-    }
-    __syncthreads();
-    for (int i = p0 + nb + tid; i < F; i += nt) {
-      T Lc[32];
-#pragma unroll
-      for (int c = 0; c < 32; ++c) Lc[c] = (c < nb) ? P[c * F + (i - p0)] : T(0);
-      for (int r = 0; r < nr; ++r) {
-        const T* yb = v + r * F + p0;
-        T a = T(0);
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          if (c >= nb) break;
-          a += Lc[c] * yb[c];
-        }
-        v[r * F + i] -= a;
-      }
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    cur ^= 1;
-  }
-  T* outv = V + (int64_t)K * R * sd.vec_off[s] + ((int64_t)k * R + r0) * F;
-  for (int q = tid; q < nr * F; q += nt) outv[q] = v[q];
-  if (sy.done) {
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      sy.add(s, k, K);
-    }
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void blk_backward_staged(const SymDev& sd, int s, int k, int r0, int nr, int ch,
-                                                    unsigned char* smraw, const T* __restrict__ fronts,
-                                                    const T* __restrict__ V, double* out, double* acc,
-                                                    int R, int K, const Sync& sy) {
-  const int ns = sd.ns[s], ms = sd.ms[s], F = ns + ms;
-  const int c0 = sd.c0[s];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-  T* pb = reinterpret_cast<T*>(smraw);            // 2 panels: pb[c*F + i] = U(i, p0 + c), i < p0 + nb
-  T* xr = pb + 2 * 32 * F;
-  T* z = xr + nr * ms;
-  const T* f = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * F * F;
-  const int32_t* rows = sd.rows + sd.row_off[s];
-  const int last0 = ((ns - 1) / 32) * 32;
-  stage_panel(pb, F, f, F, last0, ns - last0, 0, ns, tid, nt);
-  cp_async_commit();
-  const T* y = V + (int64_t)K * R * sd.vec_off[s] + ((int64_t)k * R + r0) * F;
-  for (int q = tid; q < nr * ns; q += nt) {
-    const int p = q % ns, r = q / ns;
-    z[q] = y[(int64_t)r * F + p];
-  }
-  if (sy.done && tid == 0 && ms > 0) sy.wait_parent(s, sd.parent[s], k, K);
-  __syncthreads();
-  for (int q = tid; q < nr * ms; q += nt) {
-    const int j = q % ms, r = q / ms;
-    xr[q] = (T)__ldcg(out + ((int64_t)rows[j] * K + k) * R + r0 + r);
-  }
-  __syncthreads();
-  if (ms > 0) {
-    const int JG = max(1, min(32, nt / ns));
-    for (int q = tid; q < ns * JG; q += nt) {
-      const int p = q % ns, jj = q / ns;
-      for (int rr = 0; rr < nr; rr += 4) {
-        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        for (int j = jj; j < ms; j += JG) {
-          const T u = f[p + (int64_t)(ns + j) * F];
-          const T* x0 = xr + rr * ms + j;
-          a0 += u * x0[0];
-          if (rr + 1 < nr) a1 += u * x0[ms];
-          if (rr + 2 < nr) a2 += u * x0[2 * ms];
-          if (rr + 3 < nr) a3 += u * x0[3 * ms];
-        }
-        atomicAdd(&z[rr * ns + p], -a0);
-        if (rr + 1 < nr) atomicAdd(&z[(rr + 1) * ns + p], -a1);
-        if (rr + 2 < nr) atomicAdd(&z[(rr + 2) * ns + p], -a2);
-        if (rr + 3 < nr) atomicAdd(&z[(rr + 3) * ns + p], -a3);
-      }
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  int cur = 0;
-  for (int p0 = last0; p0 >= 0; p0 -= 32) {
-    const int nb = min(32, ns - p0);
-    const T* P = pb + cur * 32 * F;                // P[c*F + i] = U(i, p0 + c), i < p0 + nb
-    if (p0 > 0) {
-      stage_panel(pb + (cur ^ 1) * 32 * F, F, f, F, p0 - 32, 32, 0, p0, tid, nt);
-      cp_async_commit();
-    }
-    for (int r = wid; r < nr; r += nw) {
-      T zi = (lane < nb) ? z[r * ns + p0 + lane] : T(0);
-      const T rd = (lane < nb) ? T(1) / P[lane * F + p0 + lane] : T(0);
-#pragma unroll
-      for (int c = 31; c >= 0; --c) {
-        if (c >= nb) continue;
-        if (lane == c) zi *= rd;
-        const T xc = __shfl_sync(kFull, zi, c);
-        if (lane < c) zi -= P[c * F + p0 + lane] * xc;
-      }
-      if (lane < nb) z[r * ns + p0 + lane] = zi;
-    }
-    __syncthreads();
-    for (int i = tid; i < p0; i += nt) {
-      T Uc[32];
-#pragma unroll
-      for (int c = 0; c < 32; ++c) Uc[c] = (c < nb) ? P[c * F + i] : T(0);
-      for (int r = 0; r < nr; ++r) {
-        const T* xb = z + r * ns + p0;
-        T a = T(0);
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          if (c >= nb) break;
-          a += Uc[c] * xb[c];
-        }
-        z[r * ns + i] -= a;
-      }
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    cur ^= 1;
-  }
-  for (int q = tid; q < nr * ns; q += nt) {
-    const int p = q % ns, r = q / ns;
-    const int64_t o = ((int64_t)(c0 + p) * K + k) * R + r0 + r;
-    out[o] = (double)z[q];
-    if (acc) acc[o] += (double)z[q];
-  }
-  if (sy.done) {
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      sy.publish_children(sd, s, k, K);
-    }
-  }
-}
-
 // ---- level-synchronous kernels (one launch per level and size class) ----
 template <typename T, int SEG>
 __global__ void __launch_bounds__(256, 2) k_forward_seg(SymDev sd, const int32_t* __restrict__ list,
@@ -943,7 +733,7 @@ __global__ void __launch_bounds__(kSolveThreads, 2)
 k_solve_persistent(SymDev sd, const SolveUnit* __restrict__ units, int nunits, int* ticket,
                    int* done, int* err, const int* __restrict__ nch, const int32_t* __restrict__ all,
                    const T* __restrict__ fronts, const double* __restrict__ rhs, int rhs_mode,
-                   T* __restrict__ V, double* out, double* acc, int R, int K, int staged) {
+                   T* __restrict__ V, double* out, double* acc, int R, int K) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_unit;
   const Sync sy{done, err, nch};
@@ -957,17 +747,10 @@ k_solve_persistent(SymDev sd, const SolveUnit* __restrict__ units, int nunits, i
     const SolveUnit U = units[u];
     if (U.kind == kUnitBlk) {
       const int r0 = U.c * U.d;
-      if (FWD) {
-        if (staged)
-          blk_forward_staged<T>(sd, U.a, U.b, r0, min(U.d, R - r0), U.c, smraw, fronts, rhs, rhs_mode, V, R, K, sy);
-        else
-          blk_forward<T>(sd, U.a, U.b, r0, min(U.d, R - r0), U.c, smraw, fronts, rhs, rhs_mode, V, R, K, sy);
-      } else {
-        if (staged)
-          blk_backward_staged<T>(sd, U.a, U.b, r0, min(U.d, R - r0), U.c, smraw, fronts, V, out, acc, R, K, sy);
-        else
-          blk_backward<T>(sd, U.a, U.b, r0, min(U.d, R - r0), U.c, smraw, fronts, V, out, acc, R, K, sy);
-      }
+      if (FWD)
+        blk_forward<T>(sd, U.a, U.b, r0, min(U.d, R - r0), U.c, smraw, fronts, rhs, rhs_mode, V, R, K, sy);
+      else
+        blk_backward<T>(sd, U.a, U.b, r0, min(U.d, R - r0), U.c, smraw, fronts, V, out, acc, R, K, sy);
     } else {
       const int SEG = U.kind == kUnitSeg8 ? 8 : (U.kind == kUnitSeg16 ? 16 : 32);
       const int64_t sg = (int64_t)U.b + tid / SEG;
@@ -1216,10 +999,7 @@ int persistent_impl(bool forward, const SymDev& sd, const SolveUnit* units, int 
   static int smem_set = 0, nsm = 0, occ_f = 0, occ_b = 0;
   const size_t seg_smem = (size_t)(256 / 8) * kRW * 9 * sizeof(T);
   const size_t mF = (size_t)std::max(max_blk_F, 1);
-  // stage whole 32-column panels when two of them fit next to the RHS block
-  const size_t staged_smem = (2 * 32 * mF + kSolveChunk * mF) * sizeof(T);
-  const int staged = staged_smem <= (size_t)kStagedSmemMax ? 1 : 0;
-  const size_t blk_smem = staged ? staged_smem : (size_t)(2 * 32 * kBS + kSolveChunk * mF) * sizeof(T);
+  const size_t blk_smem = (size_t)(2 * 32 * kBS + kSolveChunk * mF) * sizeof(T);
   const size_t smem = std::max(seg_smem, blk_smem);
   if (!smem_set) {
     cudaFuncSetAttribute(k_solve_persistent<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -1236,12 +1016,10 @@ int persistent_impl(bool forward, const SymDev& sd, const SolveUnit* units, int 
   const int grid = std::max(1, std::min(nunits, occ * std::max(nsm, 1)));
   if (forward)
     k_solve_persistent<T, true><<<grid, kSolveThreads, smem, st>>>(
-        sd, units, nunits, ticket, done, err, nch, d_all, (const T*)fronts, rhs, rhs_mode, (T*)V, out, acc, R, K,
-        staged);
+        sd, units, nunits, ticket, done, err, nch, d_all, (const T*)fronts, rhs, rhs_mode, (T*)V, out, acc, R, K);
   else
     k_solve_persistent<T, false><<<grid, kSolveThreads, smem, st>>>(
-        sd, units, nunits, ticket, done, err, nch, d_all, (const T*)fronts, rhs, rhs_mode, (T*)V, out, acc, R, K,
-        staged);
+        sd, units, nunits, ticket, done, err, nch, d_all, (const T*)fronts, rhs, rhs_mode, (T*)V, out, acc, R, K);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
