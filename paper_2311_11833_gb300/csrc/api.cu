@@ -226,13 +226,15 @@ int build_plans(pisp_handle* h, int precision) {
     // (policy 0) or the tile DAG (policy 2), when their blocks fit in shared
     // memory; else (and under policies 1 and 3) one panel launch and one
     // update launch per 32 pivots
-    const bool owner = h->factor_policy == 0 && lp.big_maxF <= pisp::max_owner_front(precision);
+    const bool owner = h->factor_policy == 0;
     const bool dag = h->factor_policy == 2 && lp.big_maxF <= pisp::max_dag_front(precision);
     if (lp.big_count > 0 && (owner || dag)) {
       std::vector<pisp::DagTask> tk;
       int32_t nfl = 0;
-      if (owner)
-        pisp::build_owner_tasks(h->h_bigF.data() + lp.big_off, lp.big_count, h->K_hint, tk, nfl);
+      if (owner) {
+        lp.own_ch = pisp::owner_chunk_rows(precision, lp.big_maxF);
+        pisp::build_owner_tasks(h->h_bigF.data() + lp.big_off, lp.big_count, h->K_hint, lp.own_ch, tk, nfl);
+      }
       else
         pisp::build_dag_tasks(h->h_bigF.data() + lp.big_off, lp.big_count, h->K_hint, tk, nfl);
       lp.dag_owner = owner ? 1 : 0;

@@ -106,7 +106,7 @@ __device__ __forceinline__ void panel_eliminate(T* P, int ld, int Mr, int nb, co
 }
 
 // Children's update columns added into the destination columns [d0, d0 + w)
-// of front s, stored at dst[row + (col - d0) * ld].  Each destination column
+// and rows [R0, R1) of front s, stored at dst[(row - R0) + (col - d0) * ld].  Each destination column
 // belongs to one warp (col - d0 = warp, warp + warps, ...), which walks the
 // column's inverse extend-add list in child order: every element receives its
 // contributions in child order, with no barrier between children, and a
@@ -114,7 +114,7 @@ __device__ __forceinline__ void panel_eliminate(T* P, int ld, int Mr, int nb, co
 template <typename T>
 __device__ __forceinline__ void extend_add_columns(const SymDev& sd, int s, int k, int K,
                                                    const T* __restrict__ fronts, T* dst, int ld,
-                                                   int d0, int w) {
+                                                   int d0, int w, int R0, int R1) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t vo = sd.vec_off[s];
   for (int dc = wid; dc < w; dc += nw) {
@@ -151,7 +151,7 @@ __device__ __forceinline__ void extend_add_columns(const SymDev& sd, int s, int 
           }
 #pragma unroll
           for (int t = 0; t < 8; ++t)
-            if (r[t] >= 0) dcol[r[t]] += v[t];
+            if (r[t] >= R0 && r[t] < R1) dcol[r[t] - R0] += v[t];
         }
         __syncwarp();
       }
@@ -186,7 +186,7 @@ __global__ void k_front_small(SymDev sd, const int32_t* __restrict__ list,
   for (int c = tid; c < ns; c += nt) atomicAdd(&f[c * (F + 1)], (T)(tk * D[sd.perm[c0 + c]]));
   __syncthreads();
   // 1c. extend-add of the children's Schur complements (child order per element)
-  extend_add_columns<T>(sd, s, k, K, fronts, f, F, 0, F);
+  extend_add_columns<T>(sd, s, k, K, fronts, f, F, 0, F, 0, F);
   __syncthreads();
   // 2. ns steps of pivot-free elimination
   for (int p = 0; p < ns; ++p) {
@@ -800,13 +800,13 @@ __device__ __forceinline__ void own_trsm(T* Bk, int ld, int r0, int nb, int w, c
   }
 }
 
-// rows [i0, F) of the block: x(i, :) -= L(i, r0..r0+nb-1) U, L read from the
-// front storage (written by the panel's owner before its release) straight
-// into registers, U from Us; a work item is one row and 16 columns.
+// rows [i0, i1) of the tile (stored from row R0): x(i, :) -= L(i, r0..r0+nb-1) U,
+// L read from the front storage (written before its release) straight into
+// registers, U from Us; a work item is one row and 16 columns.
 template <typename T>
-__device__ __forceinline__ void own_update_rows(T* Bk, int ld, const T* f, int F, int r0, int nb,
-                                                const T* Us, int i0, int w) {
-  const int m = F - i0;
+__device__ __forceinline__ void own_update_rows(T* Bt, int ld, int R0, const T* f, int F, int r0, int nb,
+                                                const T* Us, int i0, int i1, int w) {
+  const int m = i1 - i0;
   for (int q = threadIdx.x; q < 2 * m; q += blockDim.x) {
     const int g = q >= m ? 1 : 0;
     const int i = i0 + q - g * m;
@@ -815,9 +815,10 @@ __device__ __forceinline__ void own_update_rows(T* Bk, int ld, const T* f, int F
     T l[32];
 #pragma unroll
     for (int c = 0; c < 32; ++c) l[c] = (c < nb) ? __ldcg(f + i + (int64_t)(r0 + c) * F) : T(0);
+    T* row = Bt + (i - R0);
     T x[16];
 #pragma unroll
-    for (int col = 0; col < 16; ++col) x[col] = Bk[i + (cb + col) * ld];
+    for (int col = 0; col < 16; ++col) x[col] = row[(cb + col) * ld];
 #pragma unroll
     for (int cg = 0; cg < 32; cg += 8) {
       if (cg < nb) {
@@ -831,7 +832,7 @@ __device__ __forceinline__ void own_update_rows(T* Bk, int ld, const T* f, int F
     }
 #pragma unroll
     for (int col = 0; col < 16; ++col)
-      if (cb + col < w) Bk[i + (cb + col) * ld] = x[col];
+      if (cb + col < w) row[(cb + col) * ld] = x[col];
   }
 }
 
@@ -923,17 +924,18 @@ __device__ __forceinline__ void own_factor_diag(T* D, int ld, int np, int w, T* 
   }
 }
 
-// rows [r0+np, F) of the block after its diagonal block is factored: one
-// thread per row scales by the reciprocal pivots and eliminates in pivot
-// order (the remaining columns of a block that straddles the end of the
-// pivots are updated too).
+// rows [i0, i1) of the tile (stored from row R0), all below the factored
+// diagonal block: one thread per row scales by the reciprocal pivots and
+// eliminates in pivot order (the remaining columns of a block that straddles
+// the end of the pivots are updated too).
 template <typename T>
-__device__ __forceinline__ void own_eliminate_rows(T* Bk, int ld, int F, int r0, int np, int w,
+__device__ __forceinline__ void own_eliminate_rows(T* Bt, int ld, int R0, int i0, int i1, int np, int w,
                                                    const T* Us, const T* rinv) {
-  for (int i = r0 + np + threadIdx.x; i < F; i += blockDim.x) {
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    T* row = Bt + (i - R0);
     T x[32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) x[c] = (c < w) ? Bk[i + c * ld] : T(0);
+    for (int c = 0; c < 32; ++c) x[c] = (c < w) ? row[c * ld] : T(0);
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
       if (c < np) {
@@ -945,7 +947,7 @@ __device__ __forceinline__ void own_eliminate_rows(T* Bk, int ld, int F, int r0,
     }
 #pragma unroll
     for (int c = 0; c < 32; ++c)
-      if (c < w) Bk[i + c * ld] = x[c];
+      if (c < w) row[c * ld] = x[c];
   }
 }
 
@@ -956,16 +958,17 @@ __global__ void __launch_bounds__(kOwnThreads) k_front_owner(SymDev sd, const in
                                                              const double* __restrict__ vals,
                                                              const double* __restrict__ D, Shifts sh,
                                                              T* __restrict__ fronts, int32_t* status,
-                                                             int32_t* badcol) {
+                                                             int32_t* badcol, int CH) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_t;
   __shared__ T rinv[32];
   T* Us = reinterpret_cast<T*>(smraw);  // 32 x 32 row-major: U rows of the current panel
   T* Ls = Us + 32 * 32;                 // 32 x 33 row-major: unit-lower L11 of the current panel
-  T* Bk = Ls + 32 * 33;                 // ld x 32 column-major: the owned block
+  T* Bt = Ls + 32 * 33;                 // (CH + 1) x 32 column-major: the owned tile
   const int K = sh.K;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int ld = CH + 1;
   for (;;) {
     __syncthreads();  // the previous task is done with shared memory and s_t
     if (tid == 0) s_t = atomicAdd(ticket, 1);
@@ -973,76 +976,123 @@ __global__ void __launch_bounds__(kOwnThreads) k_front_owner(SymDev sd, const in
     const int u = s_t;
     if (u >= ntasks) return;
     const DagTask t = tasks[u];
-    const int s = big[t.b], k = t.k, j = t.j;
+    const int s = big[t.b], k = t.k, j = t.j, q = t.p;
     const int ns = sd.ns[s], F = ns + sd.ms[s];
-    const int P = (ns + 31) >> 5;
+    const int P = (ns + 31) >> 5, J = (F + 31) >> 5, Q = (F + CH - 1) / CH;
     const int j0 = j << 5, w = min(32, F - j0);
-    const int ld = F | 1;
-    int* pflag = flags + t.flags;
+    const int R0 = q * CH, R1 = min(F, R0 + CH);
+    int* Lf = flags + t.flags;  // [P][Q]: rows of chunk q of panel block p final
+    int* Uf = Lf + P * Q;       // [P][J]: U rows of panel p in block j final
     T* f = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * F * F;
     const int64_t vo = sd.vec_off[s];
 
-    // 1. assembly of columns [j0, j0 + w)
-    for (int q = tid; q < ld * w; q += nt) Bk[q] = T(0);
+    // 1. assembly of the tile: rows [R0, R1) of columns [j0, j0 + w)
+    for (int e = tid; e < ld * w; e += nt) Bt[e] = T(0);
     __syncthreads();
     {
       const int64_t a0 = sd.amap_coff[vo + j0], a1 = sd.amap_coff[vo + j0 + w];
-      for (int64_t q = a0 + tid; q < a1; q += nt) {
-        const int d = sd.amap_dst[q];
-        const int c = d / F;
-        atomicAdd(&Bk[(d - c * F) + (c - j0) * ld], (T)vals[sd.amap_src[q]]);
+      for (int64_t e = a0 + tid; e < a1; e += nt) {
+        const int d = sd.amap_dst[e];
+        const int c = d / F, i = d - c * F;
+        if (i >= R0 && i < R1) atomicAdd(&Bt[(i - R0) + (c - j0) * ld], (T)vals[sd.amap_src[e]]);
       }
       const double tk = sh.t[k];
       const int c0 = sd.c0[s];
-      for (int c = j0 + tid; c < min(j0 + w, ns); c += nt)
-        atomicAdd(&Bk[c + (c - j0) * ld], (T)(tk * D[sd.perm[c0 + c]]));
+      for (int c = max(j0, R0) + tid; c < min(min(j0 + w, ns), R1); c += nt)
+        atomicAdd(&Bt[(c - R0) + (c - j0) * ld], (T)(tk * D[sd.perm[c0 + c]]));
     }
     __syncthreads();
-    extend_add_columns<T>(sd, s, k, K, fronts, Bk, ld, j0, w);
+    extend_add_columns<T>(sd, s, k, K, fronts, Bt, ld, j0, w, R0, R1);
     __syncthreads();
 
-    // 2. the updates of every earlier panel, in pivot order
+    // 2. the updates of every earlier panel, in pivot order; panels whose
+    //    pivot rows lie below the tile do not touch it
     const int pe = min(j, P);
     for (int p = 0; p < pe; ++p) {
-      const int r0 = p << 5, nb = min(32, ns - r0);
-      if (tid == 0) dag_wait(pflag + p, 1, err);
-      __syncthreads();
-      for (int e = tid; e < 32 * 32; e += nt) {
-        const int r = e & 31, c = e >> 5;
-        Ls[r * 33 + c] = (r < nb && c < r) ? __ldcg(f + (r0 + r) + (int64_t)(r0 + c) * F) : T(0);
+      const int r0 = p << 5, nb = min(32, ns - r0), qp = r0 / CH;
+      if (q < qp) break;
+      if (q == qp) {
+        // the tile holds panel p's pivot rows: solve this block's U rows
+        if (tid == 0) dag_wait(Lf + p * Q + qp, 1, err);
+        __syncthreads();
+        for (int e = tid; e < 32 * 32; e += nt) {
+          const int r = e & 31, c = e >> 5;
+          Ls[r * 33 + c] = (r < nb && c < r) ? __ldcg(f + (r0 + r) + (int64_t)(r0 + c) * F) : T(0);
+        }
+        __syncthreads();
+        own_trsm<T>(Bt + (r0 - R0), ld, 0, nb, w, Ls, Us);
+        __syncthreads();
+        if (qp + 1 < Q) {  // chunks below read these U rows
+          for (int c = wid; c < w; c += nw)
+            for (int r = lane; r < nb; r += 32) f[(r0 + r) + (int64_t)(j0 + c) * F] = Bt[(r0 - R0 + r) + c * ld];
+          __threadfence();
+          __syncthreads();
+          if (tid == 0) dag_st_release(Uf + p * J + j, 1);
+        }
+        own_update_rows<T>(Bt, ld, R0, f, F, r0, nb, Us, r0 + nb, R1, w);
+        __syncthreads();
+      } else {
+        // a chunk below panel p: its U rows of this block come from the
+        // chunk holding the pivot rows, its L rows from this chunk's tile of
+        // panel p
+        if (tid == 0) {
+          dag_wait(Uf + p * J + j, 1, err);
+          dag_wait(Lf + p * Q + q, 1, err);
+        }
+        __syncthreads();
+        for (int e = tid; e < 32 * 32; e += nt) {
+          const int r = e >> 5, c = e & 31;
+          Us[e] = (r < nb && c < w) ? __ldcg(f + (r0 + r) + (int64_t)(j0 + c) * F) : T(0);
+        }
+        __syncthreads();
+        own_update_rows<T>(Bt, ld, R0, f, F, r0, nb, Us, R0, R1, w);
+        __syncthreads();
       }
-      __syncthreads();
-      own_trsm<T>(Bk, ld, r0, nb, w, Ls, Us);
-      __syncthreads();
-      own_update_rows<T>(Bk, ld, f, F, r0, nb, Us, r0 + nb, w);
-      __syncthreads();
     }
 
     // 3. the block's own pivots
+    const int qj = j0 / CH;
     if (j < P) {
       const int np = min(32, ns - j0);
-      own_factor_diag<T>(Bk + j0, ld, np, w, Us, rinv, sd, s, k, K, sd.c0[s] + j0, status, badcol);
-      __syncthreads();
-      own_eliminate_rows<T>(Bk, ld, F, j0, np, w, Us, rinv);
-      __syncthreads();
+      if (q == qj) {
+        own_factor_diag<T>(Bt + (j0 - R0), ld, np, w, Us, rinv, sd, s, k, K, sd.c0[s] + j0, status, badcol);
+        __syncthreads();
+        own_eliminate_rows<T>(Bt, ld, R0, j0 + np, R1, np, w, Us, rinv);
+        __syncthreads();
+      } else if (q > qj) {
+        // rows below the diagonal block's chunk: its factored rows come from
+        // the front storage once that tile has released them
+        if (tid == 0) dag_wait(Lf + j * Q + qj, 1, err);
+        __syncthreads();
+        for (int e = tid; e < 32 * 32; e += nt) {
+          const int r = e >> 5, c = e & 31;
+          Us[e] = (r < np && c < w && c >= r) ? __ldcg(f + (j0 + r) + (int64_t)(j0 + c) * F) : T(0);
+        }
+        if (tid < np) rinv[tid] = T(1) / __ldcg(f + (int64_t)(j0 + tid) * (F + 1));
+        __syncthreads();
+        own_eliminate_rows<T>(Bt, ld, R0, R0, R1, np, w, Us, rinv);
+        __syncthreads();
+      }
     }
-    // rows from the block's first pivot down are what later panels read:
-    // write them, release the block, then write the U rows above
-    const int rs = j < P ? j0 : 0;
+
+    // 4. write the tile; tiles holding L rows of this block release them
+    //    (rows from the first pivot down first, then the U rows above)
+    const bool rel = j < P && q >= qj;
+    const int rs = (rel && q == qj) ? j0 : R0;
     for (int c = wid; c < w; c += nw) {
       T* dst = f + (int64_t)(j0 + c) * F;
-      const T* src = Bk + c * ld;
-      for (int i = rs + lane; i < F; i += 32) dst[i] = src[i];
+      const T* src = Bt + c * ld;
+      for (int i = rs + lane; i < R1; i += 32) dst[i] = src[i - R0];
     }
-    if (j < P) {
+    if (rel) {
       __threadfence();
       __syncthreads();
-      if (tid == 0) dag_st_release(pflag + j, 1);
-      for (int c = wid; c < w; c += nw) {
-        T* dst = f + (int64_t)(j0 + c) * F;
-        const T* src = Bk + c * ld;
-        for (int i = lane; i < rs; i += 32) dst[i] = src[i];
-      }
+      if (tid == 0) dag_st_release(Lf + j * Q + q, 1);
+    }
+    for (int c = wid; c < w; c += nw) {
+      T* dst = f + (int64_t)(j0 + c) * F;
+      const T* src = Bt + c * ld;
+      for (int i = R0 + lane; i < rs; i += 32) dst[i] = src[i - R0];
     }
   }
 }
@@ -1058,14 +1108,14 @@ int owner_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_big, cons
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(k_front_owner<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
   }
-  const size_t smem = ((size_t)(lp.big_maxF | 1) * 32 + 32 * 32 + 32 * 33) * sizeof(T);
-  if (smem > (size_t)kSmemCap) return -1;
+  const size_t smem = ((size_t)(lp.own_ch + 1) * 32 + 32 * 32 + 32 * 33) * sizeof(T);
+  if (lp.own_ch < 32 || lp.own_ch % 32 || smem > (size_t)kSmemCap) return -1;
   int occ = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_front_owner<T>, kOwnThreads, smem);
   const int grid = std::max(1, std::min(lp.dag_tasks, std::max(1, occ) * std::max(nsm, 1)));
   k_front_owner<T><<<grid, kOwnThreads, smem, st>>>(sd, d_big + lp.big_off, tasks + lp.dag_task_off,
                                                     lp.dag_tasks, ticket, flags, err, vals, D, sh,
-                                                    (T*)fronts, status, badcol);
+                                                    (T*)fronts, status, badcol, lp.own_ch);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
@@ -1212,30 +1262,42 @@ int launch_factor_small(int precision, const SymDev& sd, const LevelPlan& lp,
 
 int max_dag_front(int precision) { return kSmemCap / (32 * (precision == PISP_FP32 ? 4 : 8)) - 1; }
 
-int max_owner_front(int precision) {
-  // (F | 1) * 32 + 32 * 32 + 32 * 33 elements must fit in kSmemCap bytes
-  const int L = kSmemCap / (precision == PISP_FP32 ? 4 : 8) / 32 - 65;
-  return (L & 1) ? L : L - 1;
+int owner_chunk_rows(int precision, int maxF) {
+  // Rows per tile.  FP64 elimination runs at a small fraction of the FP32
+  // rate on this part, so one SM per 32-column block is the bottleneck of a
+  // panel step: 32-row tiles spread a block's update and elimination over
+  // its chunks (1354-bus root: 0.66 ms against 0.82 with whole columns).  In
+  // FP32 the extra hand-offs and reloads of row chunks cost more than they
+  // save (10000-bus: 3.2-5.1 ms with 256- to 96-row tiles against 3.0), so a
+  // tile is a whole column block while it fits in shared memory.
+  const int full = (maxF + 31) / 32 * 32;
+  if (precision != PISP_FP32) return std::min(32, full);
+  const int fit = ((kSmemCap / 4 - 32 * 32 - 32 * 33) / 32 - 1) / 32 * 32;  // (CH + 1) * 32 + 2080 floats
+  return std::min(full, fit);
 }
 
-void build_owner_tasks(const BigFrontHost* big, int32_t nbig, int32_t K, std::vector<DagTask>& out,
-                       int32_t& nflags) {
+void build_owner_tasks(const BigFrontHost* big, int32_t nbig, int32_t K, int32_t CH,
+                       std::vector<DagTask>& out, int32_t& nflags) {
   out.clear();
   std::vector<int32_t> foff((size_t)nbig * K);
   nflags = 0;
-  int maxJ = 0;
+  int maxJ = 0, maxQ = 0;
   for (int b = 0; b < nbig; ++b) {
-    maxJ = std::max(maxJ, (big[b].F + 31) / 32);
+    const int P = (big[b].ns + 31) / 32, J = (big[b].F + 31) / 32, Q = (big[b].F + CH - 1) / CH;
+    maxJ = std::max(maxJ, J);
+    maxQ = std::max(maxQ, Q);
     for (int k = 0; k < K; ++k) {
       foff[(size_t)b * K + k] = nflags;
-      nflags += (big[b].ns + 31) / 32;
+      nflags += P * (Q + J);
     }
   }
+  // (block, chunk) order: every wait of a tile is on a tile earlier in it
   for (int j = 0; j < maxJ; ++j)
-    for (int b = 0; b < nbig; ++b) {
-      if (j >= (big[b].F + 31) / 32) continue;
-      for (int k = 0; k < K; ++k) out.push_back({kDagOwner, b, k, 0, j, foff[(size_t)b * K + k]});
-    }
+    for (int q = 0; q < maxQ; ++q)
+      for (int b = 0; b < nbig; ++b) {
+        if (j >= (big[b].F + 31) / 32 || q >= (big[b].F + CH - 1) / CH) continue;
+        for (int k = 0; k < K; ++k) out.push_back({kDagOwner, b, k, q, j, foff[(size_t)b * K + k]});
+      }
 }
 
 void build_dag_tasks(const BigFrontHost* big, int32_t nbig, int32_t K, std::vector<DagTask>& out,

@@ -71,6 +71,7 @@ struct LevelPlan {
   int64_t dag_flag_off = 0;   // offset into the device flag area (per level)
   int32_t dag_flags = 0;
   int32_t dag_owner = 0;      // 1: the tasks are column-block owner tasks
+  int32_t own_ch = 0;         //    rows per owner tile (a multiple of 32)
   // every front of the level for the solves, grouped by size class
   Group sgroups[8];
   int32_t n_sgroups = 0;
@@ -92,9 +93,9 @@ struct BigFrontHost {
 // at the (front, k) pair's counters: J "updates applied" per column block,
 // then P "panel done" flags.
 //
-// The column-block owner schedule (kind 3) uses the same record: one task per
-// (front b, perturbation k, 32-column block j), flags pointing at the pair's
-// P "panel released" flags.
+// The owner schedule (kind 3) uses the same record: one task per (front b,
+// perturbation k, 32-column block j, row chunk q in p), flags pointing at the
+// pair's P x Q "rows released" and P x J "U rows released" flags.
 enum DagKind { kDagAsm = 0, kDagPanel = 1, kDagUpdate = 2, kDagOwner = 3 };
 struct DagTask {
   int32_t kind, b, k, p, j, flags;
@@ -103,10 +104,11 @@ struct DagTask {
 // Builds the task list of one level (b indexes the level's big-front list).
 void build_dag_tasks(const BigFrontHost* big, int32_t nbig, int32_t K, std::vector<DagTask>& out,
                      int32_t& nflags);
-// Column-block owner tasks of one level, sorted by block index j so that a
-// task only waits on tasks with smaller tickets.
-void build_owner_tasks(const BigFrontHost* big, int32_t nbig, int32_t K, std::vector<DagTask>& out,
-                       int32_t& nflags);
+// Owner tiles (32-column block j, chunk q of CH rows) of one level, sorted by
+// (j, q) so that a tile only waits on tiles with smaller tickets; the record
+// carries q in its p field.
+void build_owner_tasks(const BigFrontHost* big, int32_t nbig, int32_t K, int32_t CH,
+                       std::vector<DagTask>& out, int32_t& nflags);
 
 // ---- factor (factor.cu) ----
 // Each launcher returns the number of kernels launched (>= 0) or -1 on a
@@ -130,9 +132,8 @@ int launch_factor_big_dag(int precision, const SymDev& sd, const LevelPlan& lp, 
                           int32_t* status, int32_t* badcol, cudaStream_t st);
 // largest front the tile-DAG path takes (its panel must fit in shared memory)
 int max_dag_front(int precision);
-// largest front the column-block owner path takes (a 32-column block of all
-// F rows must fit in shared memory)
-int max_owner_front(int precision);
+// rows per owner tile for a level whose widest front is maxF
+int owner_chunk_rows(int precision, int maxF);
 // largest front (in elements of the given precision) the shared-memory path takes
 int small_front_limit(int precision);
 // CTAs per cluster for a front of size F factored in distributed shared

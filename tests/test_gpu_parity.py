@@ -355,6 +355,21 @@ def test_full_precision_config_fp32_sweeps_all_rhs(pisp):
     assert err.shape == (c["R"],) and np.all(err <= TOL64)
 
 
+def test_fp32_front_taller_than_a_shared_memory_column(pisp):
+    """A front of 1774 rows: one 32-column FP32 block no longer fits in shared memory, so
+    the owner tiles split its columns into row chunks; FP32 factors plus sweeps still
+    reach the FP64 definition of x_hat."""
+    inst = pfgen.random_sparse(2200, 0.008, seed=2200)
+    t = pfgen.symmetric_shifts(2)
+    s, val, D = _solver(pisp, [inst])
+    assert s.stats()["max_front"] > 1728
+    s.factor(_dev(val), _dev(D), t, "fp32")
+    assert s.status()[0] == 0
+    b = pfgen.rhs(inst.n, 2, 9)
+    x = s.solve(_dev(b), sweeps=4).cpu().numpy()
+    assert _maxrel(x, _oracle_xhat(inst, t, b)) <= TOL64
+
+
 def test_full_scale_config_fp32_sweeps(pisp):
     """10000-bus grid: 23 fronts wider than the shared-memory limit, several per level,
     up to the dense F = 1594 root (column-block owners); FP32 factors plus sweeps reach
