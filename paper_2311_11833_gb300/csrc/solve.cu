@@ -471,24 +471,18 @@ __device__ __forceinline__ void fwd_block_solve(const T* B, T& vi, int nb, int l
 }
 
 // One warp, one right-hand side: zi becomes U11^{-1} z for the upper triangle
-// (with its diagonal) staged in B, two pivots per step from the bottom, with
-// the same per-lane operations as one pivot at a time.
+// (with its diagonal) staged in B, one pivot per step from the bottom (unlike
+// the forward solve, pairing pivots here costs more shuffles and selects
+// than it saves).
 template <typename T>
 __device__ __forceinline__ void bwd_block_solve(const T* B, T& zi, int nb, int lane) {
   const T rd = (lane < nb) ? T(1) / B[lane * kBS + lane] : T(0);
-  int c = nb - 1;
-  for (; c >= 1; c -= 2) {
-    const T zc = __shfl_sync(kFull, zi, c), zc1 = __shfl_sync(kFull, zi, c - 1);
-    const T rc = __shfl_sync(kFull, rd, c), rc1 = __shfl_sync(kFull, rd, c - 1);
-    const T xc = zc * rc;
-    const T xc1 = (zc1 - B[(c - 1) * kBS + c] * xc) * rc1;
-    if (lane == c) zi = xc;
-    else if (lane == c - 1) zi = xc1;
-    else if (lane < c - 1) zi = (zi - B[lane * kBS + c] * xc) - B[lane * kBS + c - 1] * xc1;
-  }
-  if (c == 0) {
-    const T x0 = __shfl_sync(kFull, zi, 0) * __shfl_sync(kFull, rd, 0);
-    if (lane == 0) zi = x0;
+#pragma unroll
+  for (int c = 31; c >= 0; --c) {
+    if (c >= nb) continue;
+    if (lane == c) zi *= rd;
+    const T xc = __shfl_sync(kFull, zi, c);
+    if (lane < c) zi -= B[lane * kBS + c] * xc;
   }
 }
 
