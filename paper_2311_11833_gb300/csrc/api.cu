@@ -93,8 +93,19 @@ struct pisp_handle {
   std::vector<Bracket> prof_br;
   double prof_ms[PISP_PROF_FAMILIES] = {}, prof_bytes[PISP_PROF_FAMILIES] = {};
   int64_t prof_launches[PISP_PROF_FAMILIES] = {};
+  // side streams for the independent size classes of a level, forked from
+  // and joined back into `stream` with events (parallel branches when the
+  // caller captures the work into a CUDA graph)
+  static constexpr int kSide = 3;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
   ~pisp_handle() {
     for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
+    for (int i = 0; i < kSide; ++i) {
+      if (side[i]) cudaStreamDestroy(side[i]);
+      if (join_ev[i]) cudaEventDestroy(join_ev[i]);
+    }
+    if (fork_ev) cudaEventDestroy(fork_ev);
   }
 };
 
@@ -544,7 +555,16 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   int64_t N = 0;
   for (int g = 0; g < G; ++g) N += n[g] < 0 ? 0 : n[g];
   if (row_ptr[N] > 0 && !col_idx) return fail(h, PISP_ERR_INVALID_ARG, "null col_idx");
-  if (h->device >= 0) TRY(set_device(h));
+  if (h->device >= 0) {
+    TRY(set_device(h));
+    if (!h->fork_ev) {  // side streams of the factorisation (created outside any capture)
+      CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+      for (int i = 0; i < pisp_handle::kSide; ++i) {
+        CK(cudaStreamCreateWithFlags(&h->side[i], cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->join_ev[i], cudaEventDisableTiming));
+      }
+    }
+  }
   pisp::SymbolicOptions so;
   h->schedule = opt ? opt->solve_schedule : 0;
   h->factor_policy = opt ? opt->factor_policy : 0;
@@ -704,9 +724,30 @@ int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
   for (int l = 0; l < S.n_levels; ++l) {
     const pisp::LevelPlan& lp = h->plans[l];
     int pb = prof_begin(h);
-    int n = pisp::launch_factor_small(precision, h->sd, lp, h->d_small.as<int32_t>(),
-                                      h->vals.as<double>(), h->D.as<double>(), sh, h->fronts.p,
-                                      h->status.as<int32_t>(), h->badcol.as<int32_t>(), h->stream);
+    int n = 0;
+    if (lp.n_groups <= 1) {
+      n = pisp::launch_factor_small(precision, h->sd, lp, h->d_small.as<int32_t>(),
+                                    h->vals.as<double>(), h->D.as<double>(), sh, h->fronts.p,
+                                    h->status.as<int32_t>(), h->badcol.as<int32_t>(), h->stream);
+    } else {
+      // the size classes of a level are independent: fork them onto side
+      // streams after the work queued so far, join before the next level
+      CK(cudaEventRecord(h->fork_ev, h->stream));
+      const int used = std::min(lp.n_groups - 1, pisp_handle::kSide);
+      for (int i = 0; i < used; ++i) CK(cudaStreamWaitEvent(h->side[i], h->fork_ev, 0));
+      for (int g = 0; g < lp.n_groups && n >= 0; ++g) {
+        const cudaStream_t st = g == 0 ? h->stream : h->side[(g - 1) % pisp_handle::kSide];
+        const int m = pisp::launch_factor_small_group(precision, h->sd, lp, g, h->d_small.as<int32_t>(),
+                                                      h->vals.as<double>(), h->D.as<double>(), sh,
+                                                      h->fronts.p, h->status.as<int32_t>(),
+                                                      h->badcol.as<int32_t>(), st);
+        n = m < 0 ? -1 : n + m;
+      }
+      for (int i = 0; i < used; ++i) {
+        CK(cudaEventRecord(h->join_ev[i], h->side[i]));
+        CK(cudaStreamWaitEvent(h->stream, h->join_ev[i], 0));
+      }
+    }
     TRY(count(h, n));
     prof_end(h, pb, PISP_PROF_FACTOR_SMALL, K * lp.bytes_fsmall, n);
     if (lp.big_count == 0) continue;

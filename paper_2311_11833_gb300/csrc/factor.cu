@@ -1166,16 +1166,16 @@ int run_panels(const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,
 }
 
 template <typename T>
-int factor_small_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_small,
-                      const double* vals, const double* D, const Shifts& sh, void* fronts,
-                      int32_t* status, int32_t* badcol, cudaStream_t st) {
+int factor_small_group(const SymDev& sd, const LevelPlan& lp, int g, const int32_t* d_small,
+                       const double* vals, const double* D, const Shifts& sh, void* fronts,
+                       int32_t* status, int32_t* badcol, cudaStream_t st) {
   set_smem_attrs<T>();
   T* fr = reinterpret_cast<T*>(fronts);
   const int K = sh.K;
   int launches = 0;
-  for (int g = 0; g < lp.n_groups; ++g) {
+  {
     const auto& G = lp.groups[g];
-    if (G.count == 0) continue;
+    if (G.count == 0) return 0;
     if (G.cluster == 0) {
       const size_t smem = (size_t)G.maxF * G.maxF * sizeof(T);
       k_front_small<T><<<dim3(G.count, K), small_threads<T>(G.maxF), smem, st>>>(
@@ -1202,6 +1202,19 @@ int factor_small_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_sm
     ++launches;
   }
   if (cudaGetLastError() != cudaSuccess) return -1;
+  return launches;
+}
+
+template <typename T>
+int factor_small_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_small,
+                      const double* vals, const double* D, const Shifts& sh, void* fronts,
+                      int32_t* status, int32_t* badcol, cudaStream_t st) {
+  int launches = 0;
+  for (int g = 0; g < lp.n_groups; ++g) {
+    const int n = factor_small_group<T>(sd, lp, g, d_small, vals, D, sh, fronts, status, badcol, st);
+    if (n < 0) return -1;
+    launches += n;
+  }
   return launches;
 }
 
@@ -1258,6 +1271,15 @@ int launch_factor_small(int precision, const SymDev& sd, const LevelPlan& lp,
   if (precision == PISP_FP32)
     return factor_small_impl<float>(sd, lp, d_small, vals, D, sh, fronts, status, badcol, st);
   return factor_small_impl<double>(sd, lp, d_small, vals, D, sh, fronts, status, badcol, st);
+}
+
+int launch_factor_small_group(int precision, const SymDev& sd, const LevelPlan& lp, int g,
+                              const int32_t* d_small, const double* vals, const double* D,
+                              const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol,
+                              cudaStream_t st) {
+  if (precision == PISP_FP32)
+    return factor_small_group<float>(sd, lp, g, d_small, vals, D, sh, fronts, status, badcol, st);
+  return factor_small_group<double>(sd, lp, g, d_small, vals, D, sh, fronts, status, badcol, st);
 }
 
 int max_dag_front(int precision) { return kSmemCap / (32 * (precision == PISP_FP32 ? 4 : 8)) - 1; }

@@ -117,6 +117,11 @@ int launch_factor_small(int precision, const SymDev& sd, const LevelPlan& lp,
                         const int32_t* d_small, const double* vals, const double* D,
                         const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol,
                         cudaStream_t st);
+// One size-class group of a level (the groups of a level are independent):
+int launch_factor_small_group(int precision, const SymDev& sd, const LevelPlan& lp, int g,
+                              const int32_t* d_small, const double* vals, const double* D,
+                              const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol,
+                              cudaStream_t st);
 // Big fronts of one level (blocked path):
 int launch_factor_big(int precision, const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,
                       const BigFrontHost* big_host, const double* vals, const double* D,
