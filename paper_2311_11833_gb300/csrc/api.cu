@@ -97,14 +97,16 @@ struct pisp_handle {
   // and joined back into `stream` with events (parallel branches when the
   // caller captures the work into a CUDA graph)
   static constexpr int kSide = 3;
-  cudaStream_t side[kSide] = {};
-  cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
+  cudaStream_t side[kSide] = {}, big_side = nullptr;  // big_side: the level's wide fronts
+  cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {}, big_join = nullptr;
   ~pisp_handle() {
     for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
     for (int i = 0; i < kSide; ++i) {
       if (side[i]) cudaStreamDestroy(side[i]);
       if (join_ev[i]) cudaEventDestroy(join_ev[i]);
     }
+    if (big_side) cudaStreamDestroy(big_side);
+    if (big_join) cudaEventDestroy(big_join);
     if (fork_ev) cudaEventDestroy(fork_ev);
   }
 };
@@ -385,16 +387,16 @@ const char* kFamilyNames[PISP_PROF_FAMILIES] = {"factor_small", "factor_big", "f
 
 // Event record that also works inside a stream capture: there it must become
 // an event-record node of the graph (external record) to be timed on replay.
-void record_event(pisp_handle* h, cudaEvent_t e) {
+void record_event(pisp_handle* h, cudaEvent_t e, cudaStream_t st) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  cudaStreamIsCapturing(h->stream, &cs);
-  cudaEventRecordWithFlags(e, h->stream,
+  cudaStreamIsCapturing(st, &cs);
+  cudaEventRecordWithFlags(e, st,
                            cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
                                                                : cudaEventRecordDefault);
 }
 
 // Records a start event of a profiling bracket; returns its index or -1.
-int prof_begin(pisp_handle* h) {
+int prof_begin(pisp_handle* h, cudaStream_t st = nullptr) {
   if (!h->prof_on) return -1;
   if (h->prof_next + 2 > (int)h->prof_ev.size()) {
     for (int q = 0; q < 64; ++q) {
@@ -405,13 +407,14 @@ int prof_begin(pisp_handle* h) {
   }
   const int i = h->prof_next;
   h->prof_next += 2;
-  record_event(h, h->prof_ev[i]);
+  record_event(h, h->prof_ev[i], st ? st : h->stream);
   return i;
 }
 
-void prof_end(pisp_handle* h, int i, int fam, double bytes, int launches) {
+// Closes the bracket on the stream it was opened on (default: the handle's).
+void prof_end(pisp_handle* h, int i, int fam, double bytes, int launches, cudaStream_t st = nullptr) {
   if (i < 0 || launches <= 0) return;
-  record_event(h, h->prof_ev[i + 1]);
+  record_event(h, h->prof_ev[i + 1], st ? st : h->stream);
   h->prof_br.push_back({fam, i, i + 1, launches, bytes});
 }
 
@@ -563,6 +566,8 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
         CK(cudaStreamCreateWithFlags(&h->side[i], cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&h->join_ev[i], cudaEventDisableTiming));
       }
+      CK(cudaStreamCreateWithFlags(&h->big_side, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&h->big_join, cudaEventDisableTiming));
     }
   }
   pisp::SymbolicOptions so;
@@ -722,19 +727,39 @@ int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
   h->launches = 0;
   const pisp::Shifts sh = make_shifts(h, h->beta);
   for (int l = 0; l < S.n_levels; ++l) {
+    // The fronts of a level are independent: its wide fronts (owner kernel)
+    // and each size class of its narrow ones go to their own streams, forked
+    // from the work queued so far and joined before the next level (parallel
+    // branches when the caller captures the work into a CUDA graph).
     const pisp::LevelPlan& lp = h->plans[l];
-    int pb = prof_begin(h);
-    int n = 0;
-    if (lp.n_groups <= 1) {
-      n = pisp::launch_factor_small(precision, h->sd, lp, h->d_small.as<int32_t>(),
+    const bool mixed = lp.big_count > 0 && lp.n_groups > 0;
+    const int used = lp.n_groups > 1 ? std::min(lp.n_groups - 1, pisp_handle::kSide) : 0;
+    if (used > 0 || mixed) CK(cudaEventRecord(h->fork_ev, h->stream));
+    for (int i = 0; i < used; ++i) CK(cudaStreamWaitEvent(h->side[i], h->fork_ev, 0));
+    const cudaStream_t bst = mixed ? h->big_side : h->stream;
+    if (mixed) CK(cudaStreamWaitEvent(bst, h->fork_ev, 0));
+    if (lp.big_count > 0) {
+      const int pb = prof_begin(h, bst);
+      int n = 0;
+      if (lp.dag_tasks > 0) {
+        CK(cudaMemsetAsync(h->dag_ticket.p, 0, sizeof(int), bst));
+        CK(cudaMemsetAsync(h->dag_flags.p, 0, (size_t)lp.dag_flags * sizeof(int), bst));
+        n = pisp::launch_factor_big_dag(precision, h->sd, lp, h->d_big.as<int32_t>(),
+                                        h->d_dag.as<pisp::DagTask>(), h->dag_ticket.as<int>(),
+                                        h->dag_flags.as<int>(), h->serr.as<int>(), h->vals.as<double>(),
+                                        h->D.as<double>(), sh, h->fronts.p, h->status.as<int32_t>(),
+                                        h->badcol.as<int32_t>(), bst);
+      } else {
+        n = pisp::launch_factor_big(precision, h->sd, lp, h->d_big.as<int32_t>(), h->h_bigF.data(),
                                     h->vals.as<double>(), h->D.as<double>(), sh, h->fronts.p,
-                                    h->status.as<int32_t>(), h->badcol.as<int32_t>(), h->stream);
-    } else {
-      // the size classes of a level are independent: fork them onto side
-      // streams after the work queued so far, join before the next level
-      CK(cudaEventRecord(h->fork_ev, h->stream));
-      const int used = std::min(lp.n_groups - 1, pisp_handle::kSide);
-      for (int i = 0; i < used; ++i) CK(cudaStreamWaitEvent(h->side[i], h->fork_ev, 0));
+                                    h->status.as<int32_t>(), h->badcol.as<int32_t>(), bst);
+      }
+      TRY(count(h, n));
+      prof_end(h, pb, PISP_PROF_FACTOR_BIG, K * lp.bytes_fbig, n, bst);
+    }
+    if (lp.n_groups > 0) {
+      const int pb = prof_begin(h);
+      int n = 0;
       for (int g = 0; g < lp.n_groups && n >= 0; ++g) {
         const cudaStream_t st = g == 0 ? h->stream : h->side[(g - 1) % pisp_handle::kSide];
         const int m = pisp::launch_factor_small_group(precision, h->sd, lp, g, h->d_small.as<int32_t>(),
@@ -747,26 +772,13 @@ int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
         CK(cudaEventRecord(h->join_ev[i], h->side[i]));
         CK(cudaStreamWaitEvent(h->stream, h->join_ev[i], 0));
       }
+      TRY(count(h, n));
+      prof_end(h, pb, PISP_PROF_FACTOR_SMALL, K * lp.bytes_fsmall, n);
     }
-    TRY(count(h, n));
-    prof_end(h, pb, PISP_PROF_FACTOR_SMALL, K * lp.bytes_fsmall, n);
-    if (lp.big_count == 0) continue;
-    pb = prof_begin(h);
-    if (lp.dag_tasks > 0) {
-      CK(cudaMemsetAsync(h->dag_ticket.p, 0, sizeof(int), h->stream));
-      CK(cudaMemsetAsync(h->dag_flags.p, 0, (size_t)lp.dag_flags * sizeof(int), h->stream));
-      n = pisp::launch_factor_big_dag(precision, h->sd, lp, h->d_big.as<int32_t>(),
-                                      h->d_dag.as<pisp::DagTask>(), h->dag_ticket.as<int>(),
-                                      h->dag_flags.as<int>(), h->serr.as<int>(), h->vals.as<double>(),
-                                      h->D.as<double>(), sh, h->fronts.p, h->status.as<int32_t>(),
-                                      h->badcol.as<int32_t>(), h->stream);
-    } else {
-      n = pisp::launch_factor_big(precision, h->sd, lp, h->d_big.as<int32_t>(), h->h_bigF.data(),
-                                  h->vals.as<double>(), h->D.as<double>(), sh, h->fronts.p,
-                                  h->status.as<int32_t>(), h->badcol.as<int32_t>(), h->stream);
+    if (mixed) {
+      CK(cudaEventRecord(h->big_join, bst));
+      CK(cudaStreamWaitEvent(h->stream, h->big_join, 0));
     }
-    TRY(count(h, n));
-    prof_end(h, pb, PISP_PROF_FACTOR_BIG, K * lp.bytes_fbig, n);
   }
   h->factored = true;
   return PISP_OK;
