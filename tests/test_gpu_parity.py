@@ -381,7 +381,7 @@ def test_full_scale_config_fp32_sweeps(pisp):
     assert s.stats()["max_front"] > 1000
     s.factor(_dev(val), _dev(D), t, "fp32")
     b = pfgen.rhs(inst.n, 4, 11)
-    x = s.solve(_dev(b), sweeps=3).cpu().numpy()
+    x = s.solve(_dev(b), sweeps=2).cpu().numpy()
     assert _maxrel(x, _oracle_xhat(inst, t, b)) <= TOL64
 
 
