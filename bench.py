@@ -39,11 +39,11 @@ UNIT = "solves/s"
 TOL = 1e-10
 L2_BYTES = 129 * 1024 * 1024
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel family
-# on a workload, from the ncu captures summarised under profiles/; an entry is
-# removed when its kernel changes.
+# on a workload, from an ncu capture of that kernel on that workload; an entry
+# is removed when its kernel changes.
 TRAFFIC_PER_LAUNCH = {
-    ("precision", "forward"): 6.557e6,    # profiles/k_solve_persistent_precision_2000bus_K6_R16.md
-    ("precision", "backward"): 12.291e6,
+    ("precision", "forward"): 7.163e6,
+    ("precision", "backward"): 12.894e6,
 }
 
 BENCH = {
