@@ -794,6 +794,31 @@ __global__ void k_residual_per_k(SymDev sd, const double* __restrict__ vals,
   const int64_t pi = sd.iperm[i];
   const int64_t e0 = sd.row_ptr[i], e1 = sd.row_ptr[i + 1];
   const double di = D[i];
+  if (e1 - e0 <= 32) {
+    // the row's entries and permuted columns are loaded once, one per lane,
+    // and broadcast: the (k, r) columns of the row do not repeat the chain
+    // of dependent index loads; the sum keeps the entry order
+    const int nz = (int)(e1 - e0);
+    double v = 0.0;
+    int64_t pc = 0;
+    if (lane < nz) {
+      v = vals[e0 + lane];
+      pc = sd.iperm[sd.col[e0 + lane]];
+    }
+    for (int q0 = 0; q0 < KR; q0 += 32) {  // warp-uniform: every lane reaches the shuffles
+      const int q = q0 + lane;
+      const bool act = q < KR;
+      const int k = act ? q / R : 0, r = act ? q - k * R : 0;
+      double a = act ? b[i * R + r] - sh.t[k] * di * X[(pi * K + k) * R + r] : 0.0;
+      for (int e = 0; e < nz; ++e) {
+        const double ve = __shfl_sync(kFull, v, e);
+        const int64_t pe = __shfl_sync(kFull, pc, e);
+        if (act) a -= ve * X[(pe * K + k) * R + r];
+      }
+      if (act) Rk[(pi * K + k) * R + r] = a;
+    }
+    return;
+  }
   for (int q = lane; q < KR; q += 32) {
     const int k = q / R, r = q % R;
     double a = b[i * R + r] - sh.t[k] * di * X[(pi * K + k) * R + r];
@@ -832,16 +857,22 @@ __global__ void k_grad_values(SymDev sd, const double* __restrict__ Lam,
   const int K = sh.K;
   const int KR = K * R;
   const int64_t pi = sd.iperm[i];
-  for (int64_t e = sd.row_ptr[i]; e < sd.row_ptr[i + 1]; ++e) {
-    const int64_t pj = sd.iperm[sd.col[e]];
-    double a = 0.0;
-    for (int q = lane; q < KR; q += 32) {
-      const int k = q / R;
-      a += sh.w[k] * Lam[pi * KR + q] * X[pj * KR + q];
-    }
+  const int64_t e0 = sd.row_ptr[i], e1 = sd.row_ptr[i + 1];
+  for (int64_t eb = e0; eb < e1; eb += 32) {
+    // permuted columns of up to 32 entries loaded at once, one per lane
+    const int ne = (int)min((int64_t)32, e1 - eb);
+    const int64_t pjl = lane < ne ? (int64_t)sd.iperm[sd.col[eb + lane]] : 0;
+    for (int e = 0; e < ne; ++e) {
+      const int64_t pj = __shfl_sync(0xffffffffu, pjl, e);
+      double a = 0.0;
+      for (int q = lane; q < KR; q += 32) {
+        const int k = q / R;
+        a += sh.w[k] * Lam[pi * KR + q] * X[pj * KR + q];
+      }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) grad[e] = -a;
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) grad[eb + e] = -a;
+    }
   }
 }
 
