@@ -66,11 +66,12 @@ typedef struct pisp_options {
                              and wait (boundedly) for their dependencies;
                              1 = one launch per level and front-size class */
   int32_t factor_policy;  /* fronts wider than 64: 0 (default) = one CTA each while
-                             the front fits in shared memory; larger fronts in one
-                             persistent launch per level where each CTA owns a
-                             32-column block of a (front, k) in shared memory,
-                             assembles it and applies the earlier panels as their
-                             owners release them (fronts too large for that: as 3);
+                             the front fits in shared memory; larger fronts, of
+                             any size, in one persistent launch per level where
+                             each CTA owns a tile (a 32-column block of a (front,
+                             k), all its rows in FP32 while they fit, 32-row
+                             chunks in FP64) in shared memory, assembles it and
+                             applies the earlier panels as they are released;
                              1 = thread-block clusters of up to 8 CTAs holding the
                              front in distributed shared memory wherever it fits;
                              2 = as 0 but larger fronts as a tile DAG (column-block

@@ -698,7 +698,10 @@ int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
     return fail(h, PISP_ERR_INVALID_ARG, "precision must be PISP_FP32 or PISP_FP64");
   const pisp::Symbolic& S = h->sym;
   if ((S.nnzA > 0 && !values) || (S.N > 0 && !D)) return fail(h, PISP_ERR_INVALID_ARG, "null values or D");
-  if (S.max_front > pisp::max_solve_front(precision) || S.max_front > pisp::max_big_front(precision))
+  // the owner tiles (policy 0) take fronts of any size; the per-panel path,
+  // which the other policies fall back to, needs a panel in shared memory
+  if (S.max_front > pisp::max_solve_front(precision) ||
+      (h->factor_policy != 0 && S.max_front > pisp::max_big_front(precision)))
     return fail(h, PISP_ERR_UNSUPPORTED, "front too large for this precision");
   double beta[PISP_K_MAX];
   if (pisp_weights(t, K, beta) != PISP_OK) return fail(h, PISP_ERR_INVALID_ARG, g_last_error);
