@@ -727,13 +727,13 @@ int big_dag_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_big, co
                  int* ticket, int* flags, int* err, const double* vals, const double* D,
                  const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol, cudaStream_t st) {
   if (lp.dag_tasks == 0) return 0;
-  static int nsm = 0;
-  if (!nsm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  static int nsm_dev[kMaxDevices] = {};
+  const int dev = current_device();
+  if (!nsm_dev[dev]) {
     cudaFuncSetAttribute(k_big_dag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    cudaDeviceGetAttribute(&nsm_dev[dev], cudaDevAttrMultiProcessorCount, dev);
   }
+  const int nsm = nsm_dev[dev];
   const size_t smem = std::max((size_t)(lp.big_maxF + 1) * 32, (size_t)2 * 32 * 33) * sizeof(T);
   int occ = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_big_dag<T>, 256, smem);
@@ -1101,13 +1101,13 @@ template <typename T>
 int owner_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_big, const DagTask* tasks,
                int* ticket, int* flags, int* err, const double* vals, const double* D,
                const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol, cudaStream_t st) {
-  static int nsm = 0;
-  if (!nsm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  static int nsm_dev[kMaxDevices] = {};
+  const int dev = current_device();
+  if (!nsm_dev[dev]) {
     cudaFuncSetAttribute(k_front_owner<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    cudaDeviceGetAttribute(&nsm_dev[dev], cudaDevAttrMultiProcessorCount, dev);
   }
+  const int nsm = nsm_dev[dev];
   const size_t smem = ((size_t)(lp.own_ch + 1) * 32 + 32 * 32 + 32 * 33) * sizeof(T);
   if (lp.own_ch < 32 || lp.own_ch % 32 || smem > (size_t)kSmemCap) return -1;
   int occ = 1;
@@ -1129,15 +1129,16 @@ int small_threads(int maxF) {
 
 template <typename T>
 void set_smem_attrs() {
-  static bool done = false;
-  if (done) return;
+  static bool done_dev[kMaxDevices] = {};
+  const int dev = current_device();
+  if (done_dev[dev]) return;
   cudaFuncSetAttribute(k_front_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
   cudaFuncSetAttribute(k_front_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
   cudaFuncSetAttribute(k_panel_big<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
   cudaFuncSetAttribute(k_panel_big<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
   cudaFuncSetAttribute(k_panel_big<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
   cudaFuncSetAttribute(k_panel_big<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
-  done = true;
+  done_dev[dev] = true;
 }
 
 template <typename T, int NB>

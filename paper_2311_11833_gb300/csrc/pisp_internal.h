@@ -9,6 +9,16 @@
 
 namespace pisp {
 
+// Launchers set kernel attributes (shared-memory limits) and read the SM
+// count once per device: these are per-device properties, so the flags are
+// indexed by the current device.
+constexpr int kMaxDevices = 64;
+inline int current_device() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return 0;
+  return d;
+}
+
 // Device view of the symbolic structure (all arrays live on the device).
 struct SymDev {
   const int32_t* c0;         // [S] first permuted column of each supernode
