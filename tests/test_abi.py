@@ -206,3 +206,32 @@ def test_empty_instances_analyze(lib):
     hs = HostSymbolic(lib, sizes, rp, col)
     assert hs.rc == 0 and hs.stats["N"] == 3 and hs.stats["n_supernodes"] >= 1
     hs.close()
+
+
+@pytest.mark.parametrize("wl,n,S,levels,max_front,n_wide", [
+    ("plain", 539, 114, 7, 50, 0),
+    ("precision", 3599, 802, 8, 307, 2),
+    ("differentiation", 2436, 564, 8, 225, 1),
+    ("scale", 17999, 4033, 11, 1594, 23),
+])
+def test_workload_structures_are_stable(lib, wl, n, S, levels, max_front, n_wide):
+    """The symbolic phase is deterministic on the benchmark patterns: supernodes, levels,
+    widest front and the number of fronts wider than the shared-memory path (which decide
+    the kernels the factorisation uses) are reproduced exactly, and a second analysis gives
+    the same permutation."""
+    inst = pfgen.make_instance(wl)
+    assert inst.n == n
+    a = HostSymbolic(lib, [inst.n], inst.row_ptr, inst.col)
+    b = HostSymbolic(lib, [inst.n], inst.row_ptr, inst.col)
+    try:
+        assert a.rc == 0 and b.rc == 0
+        F = (a.c1 - a.c0) + a.ms
+        assert len(F) == S == a.stats["n_supernodes"]
+        assert a.stats["n_levels"] == levels
+        assert a.stats["max_front"] == max_front == F.max()
+        assert int((F > 224).sum()) == n_wide
+        assert np.array_equal(a.perm, b.perm)
+        assert np.array_equal(a.ms, b.ms) and np.array_equal(a.rows, b.rows)
+    finally:
+        a.close()
+        b.close()
