@@ -235,9 +235,9 @@ int build_plans(pisp_handle* h, int precision) {
         lp.big_maxns = std::max(lp.big_maxns, S.sn[s].ns());
       }
     }
-    // big fronts as one persistent launch per level: column-block owners
-    // (policy 0) or the tile DAG (policy 2), when their blocks fit in shared
-    // memory; else (and under policies 1 and 3) one panel launch and one
+    // big fronts as one persistent launch per level: owner tiles (policy 0,
+    // any front size) or the tile DAG (policy 2, while a panel fits in shared
+    // memory); else (and under policies 1 and 3) one panel launch and one
     // update launch per 32 pivots
     const bool owner = h->factor_policy == 0;
     const bool dag = h->factor_policy == 2 && lp.big_maxF <= pisp::max_dag_front(precision);

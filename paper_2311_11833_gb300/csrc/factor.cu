@@ -744,29 +744,35 @@ int big_dag_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_big, co
 }
 
 // ---------------------------------------------------------------------------
-// Big fronts, column-block owners: one persistent launch per level.  A task
-// is the 32-column block j of one (front, k); the CTA that takes it keeps the
-// block, all F rows of it, in shared memory from assembly to its final value:
-//   1. assembly of the block's columns: the original entries (per-column
-//      ranges of the assembly map), t_k D on the diagonal, and the children's
-//      update columns through the inverse extend-add map.  Each destination
-//      column belongs to one warp, which adds its contributions in child
-//      order, so the sums are deterministic with no barrier between children;
-//   2. every earlier panel p, in pivot order: wait until its owner released
-//      it, solve the block's U rows with L11(p) and subtract L21(p) U(p, j)
-//      from the rows below (left-looking form of the static-pivot
-//      elimination of Sec. II-C);
-//   3. if the block holds pivots: factor its diagonal block in shared memory
-//      (one barrier per pivot), eliminate the rows below one thread per row
-//      with the reciprocal pivots, write the block to the front storage and
-//      release it; otherwise write the block (part of the Schur complement).
+// Big fronts, owner tiles: one persistent launch per level.  A task is a
+// tile: the 32-column block j of one (front, k) restricted to a chunk of CH
+// rows (CH a multiple of 32; a whole column when CH >= F).  The CTA that takes
+// it keeps the tile in shared memory from assembly to its final value:
+//   1. assembly of the tile: the original entries (per-column ranges of the
+//      assembly map), t_k D on the diagonal, and the children's update
+//      columns through the inverse extend-add map.  Each destination column
+//      belongs to one warp, which adds its contributions in child order, so
+//      the sums are deterministic with no barrier between children;
+//   2. every earlier panel p, in pivot order (left-looking form of the
+//      static-pivot elimination of Sec. II-C): the tile holding panel p's
+//      pivot rows waits for L11(p), solves the block's U rows and releases
+//      them for the chunks below; every tile below the pivot rows waits for
+//      those U rows and for its own chunk's rows of L21(p), then subtracts
+//      L21(p) U(p, j) from its rows;
+//   3. if the block holds pivots: the tile holding the diagonal block factors
+//      it in shared memory (two pivots per barrier), eliminates its rows below
+//      it and releases them; the tiles of the chunks below wait for that,
+//      then eliminate their rows with the released U rows and reciprocal
+//      pivots.  Tiles are written to the front storage before their release
+//      flags (st.release.gpu) are set.
 // Every phase runs on all 8 warps with short loop bodies: straight-line code
 // run by a single warp is fetched cold and stalls on instruction fetch.
 // The same per-element sequence of multiply-adds as panel_eliminate is used
 // for the panel, so the pivot block and L21 match the per-panel path.
-// Tasks are taken in ticket order from a list sorted by j: every wait is on a
-// task with a smaller ticket, already held by a running CTA, so the schedule
-// cannot deadlock whatever the residency, and every wait is bounded.
+// Tasks are taken in ticket order from a list sorted by (block, chunk):
+// every wait is on a tile earlier in that order, already held by a running
+// CTA, so the schedule cannot deadlock whatever the residency, and every wait
+// is bounded.
 // ---------------------------------------------------------------------------
 constexpr int kOwnThreads = 256;
 constexpr unsigned kOwnFull = 0xffffffffu;

@@ -80,7 +80,7 @@ struct LevelPlan {
   int32_t dag_tasks = 0;
   int64_t dag_flag_off = 0;   // offset into the device flag area (per level)
   int32_t dag_flags = 0;
-  int32_t dag_owner = 0;      // 1: the tasks are column-block owner tasks
+  int32_t dag_owner = 0;      // 1: the tasks are owner tiles
   int32_t own_ch = 0;         //    rows per owner tile (a multiple of 32)
   // every front of the level for the solves, grouped by size class
   Group sgroups[8];
@@ -138,7 +138,7 @@ int launch_factor_big(int precision, const SymDev& sd, const LevelPlan& lp, cons
                       const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol,
                       cudaStream_t st);
 // Big fronts of one level as one persistent launch over the level's task
-// list (tile DAG, or column-block owners when lp.dag_owner); ticket (1 int)
+// list (tile DAG, or owner tiles when lp.dag_owner); ticket (1 int)
 // and flags (lp.dag_flags ints) must be zero; err is set if a bounded
 // dependency wait gave up.
 int launch_factor_big_dag(int precision, const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,
