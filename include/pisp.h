@@ -194,6 +194,21 @@ int pisp_adjoint(pisp_handle* h, const double* g, const double* w, double* grad_
  * solution of sum_k beta_k t_k^j = [j == 0], j = 0..K-1. */
 int pisp_weights(const double* t, int32_t K, double* beta);
 
+/* Structural row matching (Sec. IV: the paper applied Hopcroft-Karp as a
+ * comparison, to move nonzeros onto the diagonal before a pivot-free solve).
+ * Host only, no handle: finds a maximum matching of the rows of the n x n
+ * pattern to its columns and writes row_perm[c] = the row matched to column
+ * c, so that the matrix whose row c is row row_perm[c] of A has a
+ * structurally nonzero diagonal.  Permuting the rows of A and of b this way
+ * before pisp_analyze leaves the solution unchanged.
+ *   n        unknowns (>= 0)
+ *   row_ptr  host int64 [n + 1], CSR row pointer, nondecreasing from 0
+ *   col_idx  host int32 [row_ptr[n]], column indices in [0, n)
+ *   row_perm host int32 [n] output
+ * Returns PISP_ERR_INVALID_ARG for a bad pattern or a structurally singular
+ * one (no matching covers every column; pisp_last_error(NULL) says which). */
+int pisp_match_rows(int32_t n, const int64_t* row_ptr, const int32_t* col_idx, int32_t* row_perm);
+
 /* Synchronises the stream and copies host [G*K] status codes of the last
  * factorisation: 0 ok, PISP_ERR_ZERO_PIVOT or PISP_ERR_NONFINITE.  If
  * first_bad_col is not NULL it receives host [G*K] the first failing

@@ -55,6 +55,7 @@ _SIGS = {
     "pisp_refine": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32]),
     "pisp_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pisp_weights": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "pisp_match_rows": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p]),
     "pisp_get_status": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "pisp_get_stats": (c_int32, [c_void_p, P(PispStats)]),
     "pisp_get_perm": (c_int32, [c_void_p, c_void_p]),

@@ -670,6 +670,22 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   return PISP_OK;
 }
 
+int pisp_match_rows(int32_t n, const int64_t* row_ptr, const int32_t* col_idx, int32_t* row_perm) {
+  if (n < 0 || (n > 0 && (!row_ptr || !row_perm))) return fail(nullptr, PISP_ERR_INVALID_ARG, "bad arguments");
+  if (n == 0) return PISP_OK;
+  if (row_ptr[0] != 0) return fail(nullptr, PISP_ERR_INVALID_ARG, "row_ptr[0] must be 0");
+  for (int32_t i = 0; i < n; ++i)
+    if (row_ptr[i + 1] < row_ptr[i]) return fail(nullptr, PISP_ERR_INVALID_ARG, "row_ptr must be nondecreasing");
+  if (row_ptr[n] > 0 && !col_idx) return fail(nullptr, PISP_ERR_INVALID_ARG, "null col_idx");
+  for (int64_t e = 0; e < row_ptr[n]; ++e)
+    if (col_idx[e] < 0 || col_idx[e] >= n) return fail(nullptr, PISP_ERR_INVALID_ARG, "column index out of range");
+  std::vector<int32_t> row_of_col;
+  const std::string err = pisp::match_rows(n, row_ptr, col_idx, row_of_col);
+  if (!err.empty()) return fail(nullptr, PISP_ERR_INVALID_ARG, err);
+  std::copy(row_of_col.begin(), row_of_col.end(), row_perm);
+  return PISP_OK;
+}
+
 int pisp_weights(const double* t, int32_t K, double* beta) {
   if (!t || !beta || K < 1 || K > PISP_K_MAX)
     return fail(nullptr, PISP_ERR_INVALID_ARG, "pisp_weights: bad arguments");

@@ -8,6 +8,7 @@
 #include "symbolic.h"
 
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 #include <numeric>
 #include <set>
@@ -116,6 +117,96 @@ int32_t pos_in_front(const Supernode& s, const int32_t* rows, int32_t x) {
 }
 
 }  // namespace
+
+// Maximum matching of rows to columns in the bipartite graph of the pattern
+// (Hopcroft-Karp: breadth-first layering from the free rows, then
+// vertex-disjoint shortest augmenting paths by depth-first search along the
+// layers, repeated until no augmenting path is left).  The depth-first search
+// keeps an explicit stack, so path length is not bounded by the call stack.
+std::string match_rows(int32_t n, const int64_t* row_ptr, const int32_t* col,
+                       std::vector<int32_t>& row_of_col) {
+  const int32_t kNil = -1, kInf = INT32_MAX;
+  std::vector<int32_t> col_of_row(n, kNil), dist(n), queue(n), stack;
+  std::vector<int64_t> it(n);
+  row_of_col.assign(n, kNil);
+  for (int32_t r = 0; r < n; ++r)  // greedy start
+    for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e)
+      if (row_of_col[col[e]] == kNil) {
+        row_of_col[col[e]] = r;
+        col_of_row[r] = col[e];
+        break;
+      }
+  for (;;) {
+    int32_t qh = 0, qt = 0;
+    bool reach_free = false;
+    for (int32_t r = 0; r < n; ++r) {
+      if (col_of_row[r] == kNil) {
+        dist[r] = 0;
+        queue[qt++] = r;
+      } else {
+        dist[r] = kInf;
+      }
+    }
+    while (qh < qt) {
+      const int32_t r = queue[qh++];
+      for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+        const int32_t r2 = row_of_col[col[e]];
+        if (r2 == kNil) {
+          reach_free = true;
+        } else if (dist[r2] == kInf) {
+          dist[r2] = dist[r] + 1;
+          queue[qt++] = r2;
+        }
+      }
+    }
+    if (!reach_free) break;
+    for (int32_t r = 0; r < n; ++r) it[r] = row_ptr[r];
+    int32_t augmented = 0;
+    for (int32_t r0 = 0; r0 < n; ++r0) {
+      if (col_of_row[r0] != kNil || dist[r0] != 0) continue;
+      stack.assign(1, r0);
+      while (!stack.empty()) {
+        const int32_t r = stack.back();
+        int32_t next = kNil;
+        bool free_col = false;
+        for (; it[r] < row_ptr[r + 1]; ++it[r]) {
+          const int32_t r2 = row_of_col[col[it[r]]];
+          if (r2 == kNil) {
+            free_col = true;
+            break;
+          }
+          if (dist[r2] == dist[r] + 1) {
+            next = r2;
+            break;
+          }
+        }
+        if (free_col) {
+          // each row on the stack takes the column it points at; the column
+          // of a row was held by the row above it on the stack
+          for (size_t i = 0; i < stack.size(); ++i) {
+            const int32_t rr = stack[i], cc = col[it[rr]];
+            col_of_row[rr] = cc;
+            row_of_col[cc] = rr;
+            dist[rr] = kInf;  // off the layered graph for the rest of the phase
+          }
+          ++augmented;
+          break;
+        }
+        if (next != kNil) {
+          stack.push_back(next);
+        } else {
+          dist[r] = kInf;  // dead end for this phase
+          stack.pop_back();
+          if (!stack.empty()) ++it[stack.back()];
+        }
+      }
+    }
+    if (augmented == 0) break;
+  }
+  for (int32_t c = 0; c < n; ++c)
+    if (row_of_col[c] == kNil) return "structurally singular: no matching covers every column";
+  return std::string();
+}
 
 std::string analyze(int32_t G, const int32_t* n, const int64_t* row_ptr,
                     const int32_t* col, const SymbolicOptions& opt, Symbolic& S) {

@@ -90,6 +90,12 @@ struct Symbolic {
 std::string analyze(int32_t G, const int32_t* n, const int64_t* row_ptr,
                     const int32_t* col, const SymbolicOptions& opt, Symbolic& out);
 
+// Maximum matching of the rows of an n x n pattern (CSR row_ptr[n + 1], col)
+// to its columns: row_of_col[c] is the row matched to column c.  Returns an
+// empty string, or an error when no matching covers every column.
+std::string match_rows(int32_t n, const int64_t* row_ptr, const int32_t* col,
+                       std::vector<int32_t>& row_of_col);
+
 // Minimum-degree ordering of a symmetric graph given by adjacency lists
 // (no self loops).  Returns perm[new] = old.
 std::vector<int32_t> minimum_degree(int32_t n, const std::vector<int32_t>& xadj,

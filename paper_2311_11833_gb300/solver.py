@@ -45,6 +45,27 @@ def weights(t: Sequence[float]) -> np.ndarray:
     return out
 
 
+def match_rows(n: int, row_ptr, col) -> np.ndarray:
+    """pisp_match_rows: row_perm with row_perm[c] the row matched to column c."""
+    lib = _lib.load()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    out = np.zeros(int(n), dtype=np.int32)
+    check(lib.pisp_match_rows(int(n), rp.ctypes.data_as(ctypes.c_void_p), cl.ctypes.data_as(ctypes.c_void_p),
+                              out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def permute_rows(row_ptr, col, val, row_perm):
+    """CSR of the matrix whose row c is row row_perm[c] of (row_ptr, col, val)."""
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    lens = np.diff(row_ptr)[row_perm]
+    new_ptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    idx = np.concatenate([np.arange(row_ptr[r], row_ptr[r + 1]) for r in row_perm]) if len(row_perm) else \
+        np.zeros(0, dtype=np.int64)
+    return new_ptr, np.asarray(col)[idx], np.asarray(val)[idx]
+
+
 class Solver:
     """One analysed sparsity pattern (G instances, block diagonal) on one device.
 
