@@ -42,4 +42,4 @@ from .core import (  # noqa: F401
     x_hat, x_star, refine, adjoint, true_gradient, residual_norm, rel_err,
     pivot_free_lu, spectral_radius, to_dense, to_scipy, error_identity,
 )
-from . import exact  # noqa: F401
+from . import exact, newton  # noqa: F401

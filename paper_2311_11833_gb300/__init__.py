@@ -7,6 +7,7 @@ sm_103a); this package is its thin Python binding.
 """
 from ._lib import FP32, FP64, K_MAX, PispError, header_functions, load  # noqa: F401
 from .solver import Solver, match_rows, permute_rows, solve, weights  # noqa: F401
+from .newton import NewtonResult, newton  # noqa: F401
 
-__all__ = ["Solver", "solve", "weights", "match_rows", "permute_rows", "load", "PispError", "FP32",
+__all__ = ["Solver", "solve", "weights", "match_rows", "permute_rows", "newton", "NewtonResult", "load", "PispError", "FP32",
            "FP64", "K_MAX", "header_functions"]

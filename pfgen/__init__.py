@@ -39,7 +39,7 @@ import numpy as np
 __all__ = [
     "Instance", "grid_jacobian", "perturbation_diag", "symmetric_shifts",
     "one_sided_shifts", "rhs", "CONFIGS", "make_instance", "batch_sizes",
-    "random_sparse", "csr_to_dense",
+    "random_sparse", "csr_to_dense", "PowerFlowCase", "power_flow_case", "diag_rule",
 ]
 
 
@@ -104,13 +104,33 @@ def _grid(rng: np.random.Generator, N: int, n_pv: int):
     return fr, to, y, Vm, Va, pv, part
 
 
-def grid_jacobian(N: int, n_pv: int | None = None, seed: int = 0) -> Instance:
-    """Reduced distributed-slack polar power-flow Jacobian at a random point."""
-    if n_pv is None:
-        n_pv = int(round(0.2 * N))
-    rng = np.random.default_rng(seed)
-    fr, to, y, Vm, Va, pv, part = _grid(rng, N, n_pv)
-    # bus admittance matrix (dense per row is wasteful; build as dict-of-rows)
+class _Layout:
+    """Unknown and equation indices of the reduced distributed-slack formulation.
+
+    Unknowns [theta_i (i != slack); |V|_i (PQ); lambda], equations
+    [P_i (i != slack); Q_i (PQ); P_slack]; -1 marks an entry that does not exist.
+    """
+
+    def __init__(self, N: int, pv: np.ndarray):
+        is_pv = np.zeros(N, dtype=bool)
+        is_pv[pv] = True
+        self.N = N
+        self.pq = np.array([i for i in range(1, N) if not is_pv[i]], dtype=np.int64)
+        self.th_idx = -np.ones(N, dtype=np.int64)
+        self.th_idx[1:] = np.arange(N - 1)
+        self.vm_idx = -np.ones(N, dtype=np.int64)
+        self.vm_idx[self.pq] = (N - 1) + np.arange(len(self.pq))
+        self.lam_idx = N - 1 + len(self.pq)
+        self.n = self.lam_idx + 1
+        self.p_row = -np.ones(N, dtype=np.int64)
+        self.p_row[1:] = np.arange(N - 1)
+        self.p_row[0] = self.n - 1
+        self.q_row = -np.ones(N, dtype=np.int64)
+        self.q_row[self.pq] = (N - 1) + np.arange(len(self.pq))
+
+
+def _admittance(N: int, fr, to, y):
+    """Diagonal of the bus admittance matrix and the off-diagonal entries per bus."""
     Ydiag = np.zeros(N, dtype=np.complex128)
     np.add.at(Ydiag, fr, y)
     np.add.at(Ydiag, to, y)
@@ -118,38 +138,34 @@ def grid_jacobian(N: int, n_pv: int | None = None, seed: int = 0) -> Instance:
     for a, b, yy in zip(fr.tolist(), to.tolist(), y.tolist()):
         nbr[a].append((b, -yy))
         nbr[b].append((a, -yy))
+    return Ydiag, nbr
+
+
+def _injections(Ydiag, nbr, Vm, Va):
+    """Complex power injections S_i = V_i * conj(sum_j Y_ij V_j); returns (P, Q)."""
     V = Vm * np.exp(1j * Va)
-    # complex power injections S_i = V_i * conj(sum_j Y_ij V_j)
     I = Ydiag * V
-    for i in range(N):
+    for i in range(len(Vm)):
         for j, yij in nbr[i]:
             I[i] += yij * V[j]
     S = V * np.conj(I)
-    P, Q = S.real, S.imag
-    is_pv = np.zeros(N, dtype=bool)
-    is_pv[pv] = True
-    pq = np.array([i for i in range(1, N) if not is_pv[i]], dtype=np.int64)
-    # unknown indices
-    th_idx = -np.ones(N, dtype=np.int64)
-    th_idx[1:] = np.arange(N - 1)
-    vm_idx = -np.ones(N, dtype=np.int64)
-    vm_idx[pq] = (N - 1) + np.arange(len(pq))
-    lam_idx = N - 1 + len(pq)
-    n = lam_idx + 1
-    # equation indices: P_i (i != slack) rows 0..N-2, Q_i (PQ) next, P_slack last
-    p_row = -np.ones(N, dtype=np.int64)
-    p_row[1:] = np.arange(N - 1)
-    p_row[0] = n - 1
-    q_row = -np.ones(N, dtype=np.int64)
-    q_row[pq] = (N - 1) + np.arange(len(pq))
+    return S.real, S.imag
+
+
+def _jacobian_csr(lay: _Layout, Ydiag, nbr, part, Vm, Va):
+    """Polar power-flow Jacobian at (Vm, Va) as CSR (row_ptr, col, val).
+
+    The pattern depends on the topology only, never on the values.
+    """
+    N, n = lay.N, lay.n
+    P, Q = _injections(Ydiag, nbr, Vm, Va)
+    p_row, q_row, th_idx, vm_idx = lay.p_row, lay.q_row, lay.th_idx, lay.vm_idx
     rows = [dict() for _ in range(n)]
 
     def put(r, c, v):
         if r >= 0 and c >= 0:
             rows[r][c] = rows[r].get(c, 0.0) + v
 
-    G = lambda z: z.real
-    B = lambda z: z.imag
     for i in range(N):
         Gii, Bii = Ydiag[i].real, Ydiag[i].imag
         # diagonal blocks
@@ -160,7 +176,7 @@ def grid_jacobian(N: int, n_pv: int | None = None, seed: int = 0) -> Instance:
         for j, yij in nbr[i]:
             th = Va[i] - Va[j]
             c, s = math.cos(th), math.sin(th)
-            g, b = G(yij), B(yij)
+            g, b = yij.real, yij.imag
             t1 = g * s - b * c
             t2 = g * c + b * s
             put(p_row[i], th_idx[j], Vm[i] * Vm[j] * t1)
@@ -168,7 +184,7 @@ def grid_jacobian(N: int, n_pv: int | None = None, seed: int = 0) -> Instance:
             put(q_row[i], th_idx[j], -Vm[i] * Vm[j] * t2)
             put(q_row[i], vm_idx[j], Vm[i] * t1)
         if part[i] != 0.0:
-            put(p_row[i], lam_idx, -part[i])
+            put(p_row[i], lay.lam_idx, -part[i])
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     cols, vals = [], []
     for r in range(n):
@@ -176,12 +192,115 @@ def grid_jacobian(N: int, n_pv: int | None = None, seed: int = 0) -> Instance:
         row_ptr[r + 1] = row_ptr[r] + len(items)
         cols.extend(c for c, _ in items)
         vals.extend(v for _, v in items)
-    col = np.asarray(cols, dtype=np.int32)
-    val = np.asarray(vals, dtype=np.float64)
-    inst = Instance(n=n, row_ptr=row_ptr, col=col, val=val, D=None,
-                    meta=dict(N=N, n_pv=n_pv, n_pq=len(pq), seed=seed, n_lines=len(fr)))
+    return row_ptr, np.asarray(cols, dtype=np.int32), np.asarray(vals, dtype=np.float64)
+
+
+def grid_jacobian(N: int, n_pv: int | None = None, seed: int = 0) -> Instance:
+    """Reduced distributed-slack polar power-flow Jacobian at a random point."""
+    if n_pv is None:
+        n_pv = int(round(0.2 * N))
+    rng = np.random.default_rng(seed)
+    fr, to, y, Vm, Va, pv, part = _grid(rng, N, n_pv)
+    lay = _Layout(N, pv)
+    Ydiag, nbr = _admittance(N, fr, to, y)
+    row_ptr, col, val = _jacobian_csr(lay, Ydiag, nbr, part, Vm, Va)
+    inst = Instance(n=lay.n, row_ptr=row_ptr, col=col, val=val, D=None,
+                    meta=dict(N=N, n_pv=n_pv, n_pq=len(lay.pq), seed=seed, n_lines=len(fr)))
     inst.D = perturbation_diag(inst)
     return inst
+
+
+@dataclasses.dataclass
+class PowerFlowCase:
+    """A solvable distributed-slack power flow with a planted solution.
+
+    The specified injections are those of a random operating point (Vm*, Va*)
+    with slack share lambda*: P_spec_i = P_i(V*) - p_i lambda*, Q_spec_i =
+    Q_i(V*), so F(x_star) = 0.  The unknowns and equations are ordered as in
+    `grid_jacobian`; the Jacobian pattern (row_ptr, col) is fixed by the
+    topology, so one symbolic analysis serves every Newton iteration.
+    """
+    N: int
+    n: int
+    row_ptr: np.ndarray
+    col: np.ndarray
+    x_star: np.ndarray
+    P_spec: np.ndarray
+    Q_spec: np.ndarray
+    Vm_fixed: np.ndarray      # |V| of the slack and PV buses (PQ entries unused)
+    part: np.ndarray
+    meta: dict
+    _lay: _Layout = dataclasses.field(repr=False)
+    _Ydiag: np.ndarray = dataclasses.field(repr=False)
+    _nbr: list = dataclasses.field(repr=False)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def state(self, x):
+        """(Vm, Va, lambda) of the unknown vector x."""
+        lay = self._lay
+        Va = np.zeros(self.N)
+        Va[1:] = x[lay.th_idx[1:]]
+        Vm = self.Vm_fixed.copy()
+        Vm[lay.pq] = x[lay.vm_idx[lay.pq]]
+        return Vm, Va, float(x[lay.lam_idx])
+
+    def mismatch(self, x) -> np.ndarray:
+        """F(x): P_i - P_spec_i - p_i lambda (every bus), Q_i - Q_spec_i (PQ buses)."""
+        lay = self._lay
+        Vm, Va, lam = self.state(np.asarray(x, dtype=np.float64))
+        P, Q = _injections(self._Ydiag, self._nbr, Vm, Va)
+        F = np.zeros(self.n)
+        F[lay.p_row] = P - self.P_spec - self.part * lam
+        F[lay.q_row[lay.pq]] = Q[lay.pq] - self.Q_spec[lay.pq]
+        return F
+
+    def jacobian(self, x) -> np.ndarray:
+        """dF/dx at x: the values on the fixed pattern (row_ptr, col)."""
+        Vm, Va, _ = self.state(np.asarray(x, dtype=np.float64))
+        rp, col, val = _jacobian_csr(self._lay, self._Ydiag, self._nbr, self.part, Vm, Va)
+        assert np.array_equal(rp, self.row_ptr) and np.array_equal(col, self.col)
+        return val
+
+    def flat_start(self) -> np.ndarray:
+        """theta = 0, |V| = 1 on PQ buses, lambda = 0."""
+        x = np.zeros(self.n)
+        x[self._lay.vm_idx[self._lay.pq]] = 1.0
+        return x
+
+
+def power_flow_case(N: int, n_pv: int | None = None, seed: int = 0,
+                    angle_scale: float = 1.0) -> PowerFlowCase:
+    """Grid as in `grid_jacobian` (same draws); the drawn point, with its angles
+    scaled by `angle_scale` (heavier loading for larger values) and lambda* ~
+    U[-1, 1] pu, is the planted solution."""
+    if n_pv is None:
+        n_pv = int(round(0.2 * N))
+    rng = np.random.default_rng(seed)
+    fr, to, y, Vm, Va, pv, part = _grid(rng, N, n_pv)
+    lam = float(rng.uniform(-1.0, 1.0))
+    Va = Va * angle_scale
+    lay = _Layout(N, pv)
+    Ydiag, nbr = _admittance(N, fr, to, y)
+    P, Q = _injections(Ydiag, nbr, Vm, Va)
+    x_star = np.zeros(lay.n)
+    x_star[lay.th_idx[1:]] = Va[1:]
+    x_star[lay.vm_idx[lay.pq]] = Vm[lay.pq]
+    x_star[lay.lam_idx] = lam
+    row_ptr, col, _ = _jacobian_csr(lay, Ydiag, nbr, part, Vm, Va)
+    return PowerFlowCase(N=N, n=lay.n, row_ptr=row_ptr, col=col, x_star=x_star,
+                         P_spec=P - part * lam, Q_spec=Q, Vm_fixed=Vm.copy(), part=part,
+                         meta=dict(N=N, n_pv=n_pv, n_pq=len(lay.pq), seed=seed,
+                                   angle_scale=angle_scale, n_lines=len(fr)),
+                         _lay=lay, _Ydiag=Ydiag, _nbr=nbr)
+
+
+def diag_rule(n: int, row_ptr, col, val) -> np.ndarray:
+    """The perturbation diagonal of `perturbation_diag` for raw CSR arrays."""
+    return perturbation_diag(Instance(n=n, row_ptr=np.asarray(row_ptr), col=np.asarray(col),
+                                      val=np.asarray(val, dtype=np.float64), D=None, meta={}))
 
 
 def perturbation_diag(inst: Instance) -> np.ndarray:
