@@ -8,7 +8,7 @@ Two zero-diagonal cases are built from the 300-bus Jacobian:
   diagonal entries are structurally zero.  In the solver's fill-reducing order one of
   them reaches its pivot untouched (an exact zero pivot); the perturbed systems are
   pivot-free factorable with element growth O(1/eps), and their combination converges
-  to A^{-1} b as eps^m.
+  to A^{-1} b as eps^K (the product of the shifts in the error identity).
 * lambda-first: the slack-participation unknown lambda is ordered first, which moves
   every diagonal entry but a few off the diagonal.  Perturbation does not rescue this
   one (the perturbed pivot-free factors grow past 1e12); the row matching does.
@@ -92,7 +92,8 @@ def test_swapped_rows_meet_a_zero_pivot_in_the_solver_order(lib):
 
 def test_perturbation_rescues_the_swapped_rows(lib):
     """Each perturbed system is pivot-free factorable in the solver order with growth
-    O(1/eps), and x_hat approaches A^{-1} b as eps^m (Eq. 5 with m = 4)."""
+    O(1/eps), and x_hat approaches A^{-1} b as eps^K, K = 4 (the error identity of
+    the Neumann expansion carries the product of the shifts)."""
     M = _swapped()
     n = M.shape[0]
     perm = _solver_order(lib, M)
@@ -155,6 +156,30 @@ def test_match_rows_size_matches_scipy(pisp, seed):
     else:
         with pytest.raises(pisp.PispError):
             pisp.match_rows(n, M.indptr, M.indices)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_match_rows_on_planted_matchings(pisp, seed):
+    """Larger patterns: a random permutation (a perfect matching that the diagonal
+    does not show) plus random entries, and the same with one column emptied
+    (structurally singular); the result is checked against scipy's matching size."""
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(200, 3000))
+    perm = rng.permutation(n)
+    extra = sp.random(n, n, density=3.0 / n, random_state=rng, format="csr")
+    M = (sp.csr_matrix((np.ones(n), (perm, np.arange(n))), shape=(n, n)) + extra).tocsr()
+    M.sort_indices()
+    rp = pisp.match_rows(n, M.indptr, M.indices)
+    assert sorted(rp.tolist()) == list(range(n))
+    assert np.all(np.asarray(M[rp, :].todense()).diagonal() != 0)
+    M = M.tolil()
+    M[:, int(rng.integers(n))] = 0
+    M = M.tocsr()
+    M.eliminate_zeros()
+    M.sort_indices()
+    assert np.any(maximum_bipartite_matching(M, perm_type="row") < 0)
+    with pytest.raises(pisp.PispError):
+        pisp.match_rows(n, M.indptr, M.indices)
 
 
 def test_match_rows_rejects_bad_patterns(pisp):
