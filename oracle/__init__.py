@@ -29,6 +29,9 @@ What it computes, by the plain definitions of the paper:
 * ``pivot_free_lu`` - dense Doolittle LU without pivoting of a given
   symmetric permutation of A + t D (unique when it exists), for factor-level
   comparisons on small systems.
+* diagnostics: ``spectral_radius`` rho(A^{-1} D), ``cond1`` kappa_1(A),
+  ``pivot_stats`` (growth factor and pivot spread of the pivot-free LU),
+  ``rel_err`` and ``residual_norm`` (the forward error and the residual of Fig. 1).
 * ``exact`` - brute force in rational arithmetic for tiny systems.
 
 Every function cites the passage of the paper it follows.  Parity of each
@@ -40,6 +43,6 @@ brute force.
 from .core import (  # noqa: F401
     weights_gamma, weights, weights_float, pistol, perturbed_solutions, combine,
     x_hat, x_star, refine, adjoint, true_gradient, residual_norm, rel_err,
-    pivot_free_lu, spectral_radius, to_dense, to_scipy, error_identity,
+    pivot_free_lu, spectral_radius, to_dense, to_scipy, error_identity, cond1, pivot_stats,
 )
 from . import exact, newton  # noqa: F401

@@ -250,6 +250,28 @@ def spectral_radius(A, D) -> float:
     return float(lam)
 
 
+def cond1(A) -> float:
+    """kappa_1(A) = ||A||_1 ||A^{-1}||_1, by the dense inverse (diagnostic of the
+    conditioning that static pivoting leaves unguarded, Sec. I)."""
+    Ad = A.toarray() if sp.issparse(A) else np.asarray(A, dtype=np.float64)
+    Ainv = np.linalg.solve(Ad, np.eye(Ad.shape[0]))
+    return float(np.abs(Ad).sum(axis=0).max() * np.abs(Ainv).sum(axis=0).max())
+
+
+def pivot_stats(A, D, t: float, perm=None):
+    """Growth and pivot spread of the pivot-free LU of P (A + t D) P^T.
+
+    Returns (growth, pivot_ratio): growth = max|U_ij| / max|(A + t D)_ij| and
+    pivot_ratio = min|u_jj| / max|u_jj|.  A static pivot order controls
+    neither (Sec. I); these are the quantities to watch.
+    """
+    _, U = pivot_free_lu(A, D, t, perm)
+    Ad = A.toarray() if sp.issparse(A) else np.asarray(A, dtype=np.float64)
+    M = Ad + float(t) * np.diag(np.asarray(D, dtype=np.float64))
+    d = np.abs(np.diag(U))
+    return float(np.abs(U).max() / np.abs(M).max()), float(d.min() / d.max())
+
+
 def error_identity(A, D, t, B, beta=None) -> np.ndarray:
     """Closed form of x_hat - x* from the Neumann series (Sec. II-B).
 

@@ -314,6 +314,34 @@ def test_pivot_free_lu_permuted_reconstructs():
     assert np.allclose(np.tril(L, -1) + np.eye(11), L) and np.allclose(np.triu(U), U)
 
 
+@pytest.mark.parametrize("delta", [0.3, 1e-2, 1e-5])
+def test_cond1_and_pivot_stats_closed_forms(delta):
+    """A = [[d, 1], [1, 1]]: kappa_1 = 4 / (1 - d); unpivoted U = [[d, 1], [0, 1 - 1/d]],
+    so growth = max(d, 1, 1/d - 1) and pivot ratio = min(d, 1/d - 1) / max(d, 1/d - 1);
+    in the swapped order U = [[1, 1], [0, d - 1]]: growth 1, ratio 1 - d."""
+    A = np.array([[delta, 1.0], [1.0, 1.0]])
+    assert oracle.cond1(A) == pytest.approx(4.0 / (1.0 - delta), rel=1e-12)
+    u22 = 1.0 / delta - 1.0
+    g, r = oracle.pivot_stats(A, np.zeros(2), 0.0)
+    assert g == pytest.approx(max(1.0, u22), rel=1e-12)
+    assert r == pytest.approx(min(delta, u22) / max(delta, u22), rel=1e-12)
+    g, r = oracle.pivot_stats(A, np.zeros(2), 0.0, perm=[1, 0])
+    assert g == pytest.approx(1.0, rel=1e-12) and r == pytest.approx(1.0 - delta, rel=1e-12)
+    # a shift on the diagonal: A + t I = [[d + t, 1], [1, 1 + t]]
+    t = 0.25
+    u22 = (1.0 + t) - 1.0 / (delta + t)
+    g, r = oracle.pivot_stats(A, np.ones(2), t)
+    assert g == pytest.approx(max(delta + t, 1.0, abs(u22)) / (1.0 + t), rel=1e-12)
+    assert r == pytest.approx(min(delta + t, abs(u22)) / max(delta + t, abs(u22)), rel=1e-12)
+
+
+def test_cond1_and_pivot_stats_of_a_diagonal_matrix():
+    d = np.array([3.0, -0.5, 8.0, 2.0])
+    assert oracle.cond1(np.diag(d)) == pytest.approx(16.0, rel=1e-14)
+    g, r = oracle.pivot_stats(np.diag(d), np.ones(4), 0.25)
+    assert g == pytest.approx(1.0) and r == pytest.approx(0.25 / 8.25, rel=1e-14)   # |d + 0.25|
+
+
 def test_pivot_free_zero_pivot_raises():
     A = np.array([[0.0, 1.0], [1.0, 0.0]])
     with pytest.raises(ZeroDivisionError):
