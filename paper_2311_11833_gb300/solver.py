@@ -50,6 +50,10 @@ def match_rows(n: int, row_ptr, col) -> np.ndarray:
     lib = _lib.load()
     rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
     cl = np.ascontiguousarray(col, dtype=np.int32)
+    if int(n) < 0 or rp.shape != (int(n) + 1,):
+        raise ValueError("row_ptr must have n + 1 entries")
+    if cl.size < (int(rp[-1]) if rp.size else 0):
+        raise ValueError("col is shorter than row_ptr[n]")
     out = np.zeros(int(n), dtype=np.int32)
     check(lib.pisp_match_rows(int(n), rp.ctypes.data_as(ctypes.c_void_p), cl.ctypes.data_as(ctypes.c_void_p),
                               out.ctypes.data_as(ctypes.c_void_p)))

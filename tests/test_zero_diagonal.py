@@ -188,6 +188,10 @@ def test_match_rows_rejects_bad_patterns(pisp):
     with pytest.raises(pisp.PispError):
         pisp.match_rows(2, [0, 1, 2], [0, 5])         # column out of range
     assert len(pisp.match_rows(0, [0], [])) == 0
+    with pytest.raises(ValueError):
+        pisp.match_rows(3, [0, 1, 2], [0, 1])         # row_ptr too short for n
+    with pytest.raises(ValueError):
+        pisp.match_rows(2, [0, 1, 3], [0, 1])         # col shorter than row_ptr[n]
 
 
 @pytest.mark.gpu
