@@ -36,6 +36,14 @@ def _dev_f64(t: torch.Tensor, name: str, shape=None) -> torch.Tensor:
     return t.contiguous()
 
 
+def _host_out(a, name: str, size: int) -> np.ndarray:
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise TypeError(f"{name} must be a C-contiguous float64 numpy array")
+    if a.size != size:
+        raise ValueError(f"{name} has {a.size} entries, expected {size}")
+    return a
+
+
 def weights(t: Sequence[float]) -> np.ndarray:
     """pisp_weights: per-solve weights prod_{l != k} t_l / (t_l - t_k)."""
     lib = _lib.load()
@@ -92,6 +100,8 @@ class Solver:
         cl = np.ascontiguousarray(np.asarray(col, dtype=np.int32))
         if rp.shape != (self.N + 1,):
             raise ValueError("row_ptr must have N + 1 entries")
+        if cl.size < int(rp[-1]):
+            raise ValueError("col is shorter than row_ptr[N]")
         self.nnz = int(rp[-1])
         self._row_ptr, self._col = rp, cl
         h = ctypes.c_void_p()
@@ -107,6 +117,20 @@ class Solver:
         self.R = 0
 
     # ------------------------------------------------------------- plumbing --
+    def _dev(self, t, name: str, shape=None) -> torch.Tensor:
+        """A float64 CUDA tensor on this solver's device (every pointer the
+        library reads or writes is sized from the analysed pattern)."""
+        t = _dev_f64(t, name, shape)
+        if t.device.index != self.device:
+            raise ValueError(f"{name} is on {t.device}, the solver on cuda:{self.device}")
+        return t
+
+    def _dev_out(self, t, name: str, numel: int) -> torch.Tensor:
+        t2 = self._dev(t, name)
+        if t2.data_ptr() != t.data_ptr() or t.numel() != numel:
+            raise ValueError(f"{name} must be contiguous with {numel} entries")
+        return t
+
     def _sync_stream(self):
         s = torch.cuda.current_stream(self.device).cuda_stream
         check(self._lib.pisp_set_stream(self._h, ctypes.c_void_p(s)), self._h)
@@ -125,8 +149,8 @@ class Solver:
     # ------------------------------------------------------------------ ABI --
     def factor(self, values: torch.Tensor, D: torch.Tensor, t: Sequence[float], precision="fp64"):
         """pisp_factor_perturbed: pivot-free LU of P (A + t_k D) P^T for all k."""
-        values = _dev_f64(values, "values", (self.nnz,))
-        D = _dev_f64(D, "D", (self.N,))
+        values = self._dev(values, "values", (self.nnz,))
+        D = self._dev(D, "D", (self.N,))
         tt = _host_f64(t)
         prec = _PREC[precision]
         self._sync_stream()
@@ -138,9 +162,9 @@ class Solver:
     def solve(self, b: torch.Tensor, weights=None, sweeps: int = 0, out: torch.Tensor | None = None):
         """pisp_solve: x = sum_k w_k (A + t_k D)^{-1} b; b is [N] or [N, R]."""
         vec = b.dim() == 1
-        b2 = _dev_f64(b, "b").reshape(self.N, -1)
+        b2 = self._dev(b, "b").reshape(self.N, -1)
         R = b2.shape[1]
-        x = out if out is not None else torch.empty_like(b2)
+        x = self._dev_out(out, "out", self.N * R) if out is not None else torch.empty_like(b2)
         w = None if weights is None else _host_f64(weights)
         self._sync_stream()
         check(self._lib.pisp_solve(self._h, _ptr(b2), R,
@@ -151,8 +175,8 @@ class Solver:
 
     def combine(self, weights=None, out: torch.Tensor | None = None):
         """pisp_combine: re-weights the kept per-perturbation solutions."""
-        x = out if out is not None else torch.empty((self.N, self.R), dtype=torch.float64,
-                                                    device=f"cuda:{self.device}")
+        x = self._dev_out(out, "out", self.N * self.R) if out is not None else \
+            torch.empty((self.N, self.R), dtype=torch.float64, device=f"cuda:{self.device}")
         w = None if weights is None else _host_f64(weights)
         self._sync_stream()
         check(self._lib.pisp_combine(self._h, None if w is None else w.ctypes.data_as(ctypes.c_void_p),
@@ -162,10 +186,8 @@ class Solver:
     def refine(self, b: torch.Tensor, x: torch.Tensor, iters: int = 1, sweeps: int = 0):
         """pisp_refine: x += sum_k beta_k (A + t_k D)^{-1} (b - A x), in place."""
         vec = b.dim() == 1
-        b2 = _dev_f64(b, "b").reshape(self.N, -1)
-        if not x.is_contiguous():
-            raise ValueError("x must be contiguous")
-        x2 = x.reshape(self.N, -1)
+        b2 = self._dev(b, "b").reshape(self.N, -1)
+        x2 = self._dev_out(x, "x", b2.numel()).reshape(self.N, -1)
         self._sync_stream()
         check(self._lib.pisp_refine(self._h, _ptr(b2), _ptr(x2), b2.shape[1], int(iters), int(sweeps)),
               self._h)
@@ -173,7 +195,9 @@ class Solver:
 
     def adjoint(self, g: torch.Tensor, weights=None, need_b=True, need_values=True):
         """pisp_adjoint: (dL/db, dL/dvalues) for dL/dx = g of the last solve."""
-        g2 = _dev_f64(g, "g").reshape(self.N, -1)
+        g2 = self._dev(g, "g").reshape(self.N, -1)
+        if g2.shape[1] != self.R:
+            raise ValueError(f"g has {g2.shape[1]} columns, the last solve had R = {self.R}")
         gb = torch.empty_like(g2) if need_b else None
         gv = torch.empty(self.nnz, dtype=torch.float64, device=g2.device) if need_values else None
         w = None if weights is None else _host_f64(weights)
@@ -233,8 +257,10 @@ class Solver:
         vals = _host_f64(values)
         DD = _host_f64(D)
         tt = _host_f64(t)
+        if vals.size != self.nnz or DD.size != self.N:
+            raise ValueError(f"values needs {self.nnz} entries and D {self.N}")
         bb = _host_f64(b).reshape(self.N, -1)
-        x = out if out is not None else np.empty_like(bb)
+        x = _host_out(out, "out", bb.size) if out is not None else np.empty_like(bb)
         self._sync_stream()
         check(self._lib.pisp_solve_host(self._h, vals.ctypes.data_as(ctypes.c_void_p),
                                         DD.ctypes.data_as(ctypes.c_void_p),
