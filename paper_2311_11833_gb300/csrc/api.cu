@@ -585,6 +585,8 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   std::string msg = pisp::analyze(G, n, row_ptr, col_idx, so, h->sym);
   h->analyze_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (!msg.empty()) return fail(h, PISP_ERR_INVALID_ARG, msg);
+  msg = pisp::validate(h->sym);
+  if (!msg.empty()) return fail(h, PISP_ERR_BOUNDS, msg);
   const pisp::Symbolic& S = h->sym;
   if (S.max_front > 46340) return fail(h, PISP_ERR_UNSUPPORTED, "front larger than 46340");
   if (h->device < 0) {  // host-only handle: symbolic structure for inspection only

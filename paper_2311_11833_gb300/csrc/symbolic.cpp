@@ -547,4 +547,108 @@ std::string analyze(int32_t G, const int32_t* n, const int64_t* row_ptr,
   return std::string();
 }
 
+// Every index the kernels follow, checked against the sizes they assume.
+std::string validate(const Symbolic& S) {
+  const int64_t N = S.N, nS = (int64_t)S.sn.size();
+  auto bad = [](const char* what) { return std::string("structure check failed: ") + what; };
+  auto prefix_ok = [](const std::vector<int64_t>& off, size_t len, int64_t last) {
+    if (off.size() != len || off[0] != 0 || off.back() != last) return false;
+    for (size_t i = 1; i < off.size(); ++i)
+      if (off[i] < off[i - 1]) return false;
+    return true;
+  };
+  if (S.G < 1 || !prefix_ok(S.inst_off, (size_t)S.G + 1, N) ||
+      !prefix_ok(S.inst_nnz_off, (size_t)S.G + 1, S.nnzA))
+    return bad("instance offsets");
+  if ((int64_t)S.perm.size() != N || (int64_t)S.iperm.size() != N || (int64_t)S.col_sn.size() != N)
+    return bad("permutation sizes");
+  for (int64_t i = 0; i < N; ++i)
+    if (S.perm[i] < 0 || S.perm[i] >= N || S.iperm[S.perm[i]] != i) return bad("permutation");
+  if (!prefix_ok(S.front_off, nS + 1, S.front_elems) || !prefix_ok(S.vec_off, nS + 1, S.vec_off.back()))
+    return bad("front offsets");
+  int32_t maxF = 0;
+  int64_t next_col = 0;
+  for (int64_t s = 0; s < nS; ++s) {
+    const Supernode& sn = S.sn[s];
+    const int64_t F = sn.F();
+    if (sn.c0 != next_col || sn.c1 <= sn.c0 || sn.ms < 0) return bad("supernode column ranges");
+    next_col = sn.c1;
+    if (sn.instance < 0 || sn.instance >= S.G || sn.c0 < S.inst_off[sn.instance] ||
+        sn.c1 > S.inst_off[sn.instance + 1])
+      return bad("supernode instance");
+    if (sn.parent != -1 && (sn.parent <= s || sn.parent >= nS)) return bad("parent");
+    if (sn.row_off < 0 || sn.row_off + sn.ms > (int64_t)S.rows.size()) return bad("row list range");
+    for (int32_t a = 0; a < sn.ms; ++a) {
+      const int32_t r = S.rows[sn.row_off + a];
+      if (r < sn.c1 || r >= S.inst_off[sn.instance + 1] || (a > 0 && r <= S.rows[sn.row_off + a - 1]))
+        return bad("update rows");
+    }
+    for (int32_t c = sn.c0; c < sn.c1; ++c)
+      if (S.col_sn[c] != s) return bad("column owner");
+    if (S.front_off[s + 1] - S.front_off[s] != F * F || S.vec_off[s + 1] - S.vec_off[s] != F)
+      return bad("front sizes");
+    maxF = std::max<int32_t>(maxF, (int32_t)F);
+    if (sn.parent >= 0) {  // extend-add positions: the row's place in the parent's index list
+      const Supernode& P = S.sn[sn.parent];
+      if (S.sn[sn.parent].level <= sn.level) return bad("levels");
+      for (int32_t a = 0; a < sn.ms; ++a) {
+        const int32_t pos = S.emap[sn.row_off + a], r = S.rows[sn.row_off + a];
+        if (pos < 0 || pos >= P.F()) return bad("extend-add map range");
+        const int32_t at = pos < P.ns() ? P.c0 + pos : S.rows[P.row_off + pos - P.ns()];
+        if (at != r) return bad("extend-add map target");
+      }
+    }
+  }
+  if (next_col != N || maxF != S.max_front || S.emap.size() != S.rows.size()) return bad("supernode cover");
+  const int64_t V = S.vec_off[nS];
+  // assembly map
+  if (!prefix_ok(S.amap_off, nS + 1, S.nnzA) || (int64_t)S.amap_src.size() != S.nnzA ||
+      (int64_t)S.amap_dst.size() != S.nnzA || (int64_t)S.amap_coff.size() != V + 1 ||
+      S.amap_coff[V] != S.nnzA)
+    return bad("assembly map sizes");
+  for (int64_t s = 0; s < nS; ++s) {
+    const int64_t F = S.sn[s].F();
+    if (S.amap_coff[S.vec_off[s]] != S.amap_off[s]) return bad("assembly column offsets");
+    for (int64_t c = 0; c < F; ++c) {
+      const int64_t q0 = S.amap_coff[S.vec_off[s] + c], q1 = S.amap_coff[S.vec_off[s] + c + 1];
+      if (q0 > q1 || q1 > S.amap_off[s + 1]) return bad("assembly column offsets");
+      for (int64_t q = q0; q < q1; ++q)
+        if (S.amap_src[q] < 0 || S.amap_src[q] >= S.nnzA || S.amap_dst[q] < 0 || S.amap_dst[q] >= F * F ||
+            S.amap_dst[q] / F != c)
+          return bad("assembly map entries");
+    }
+  }
+  // inverse extend-add map
+  if (!prefix_ok(S.inv_off, (size_t)V + 1, (int64_t)S.inv_child.size())) return bad("inverse map offsets");
+  const size_t nI = S.inv_child.size();
+  if (S.inv_a.size() != nI || S.inv_vbase.size() != nI || S.inv_cF.size() != nI || S.inv_col.size() != nI)
+    return bad("inverse map sizes");
+  for (int64_t p = 0; p < nS; ++p)
+    for (int64_t j = 0; j < S.sn[p].F(); ++j)
+      for (int64_t q = S.inv_off[S.vec_off[p] + j]; q < S.inv_off[S.vec_off[p] + j + 1]; ++q) {
+        const int32_t c = S.inv_child[q];
+        if (c < 0 || c >= nS || S.sn[c].parent != p || S.inv_a[q] < 0 || S.inv_a[q] >= S.sn[c].ms ||
+            S.emap[S.sn[c].row_off + S.inv_a[q]] != j || S.inv_vbase[q] != S.vec_off[c] ||
+            S.inv_cF[q] != S.sn[c].F() || S.inv_col[q] != S.sn[c].ns() + S.inv_a[q])
+          return bad("inverse map entries");
+      }
+  // children and levels
+  if (!prefix_ok(S.child_off, nS + 1, (int64_t)S.child.size())) return bad("child offsets");
+  for (int64_t s = 0; s < nS; ++s)
+    for (int64_t q = S.child_off[s]; q < S.child_off[s + 1]; ++q)
+      if (S.child[q] < 0 || S.child[q] >= nS || S.sn[S.child[q]].parent != s ||
+          (q > S.child_off[s] && S.child[q] <= S.child[q - 1]))
+        return bad("children");
+  if (!prefix_ok(S.level_off, (size_t)S.n_levels + 1, nS) || (int64_t)S.level_sn.size() != nS)
+    return bad("level offsets");
+  std::vector<char> seen(nS, 0);
+  for (int32_t l = 0; l < S.n_levels; ++l)
+    for (int64_t q = S.level_off[l]; q < S.level_off[l + 1]; ++q) {
+      const int32_t s = S.level_sn[q];
+      if (s < 0 || s >= nS || seen[s] || S.sn[s].level != l) return bad("level schedule");
+      seen[s] = 1;
+    }
+  return std::string();
+}
+
 }  // namespace pisp

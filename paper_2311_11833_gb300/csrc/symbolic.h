@@ -90,6 +90,12 @@ struct Symbolic {
 std::string analyze(int32_t G, const int32_t* n, const int64_t* row_ptr,
                     const int32_t* col, const SymbolicOptions& opt, Symbolic& out);
 
+// Checks every index of S against the sizes the kernels assume (offsets are
+// prefix sums of the front sizes, maps land inside their fronts and
+// arrays, children precede parents and sit on lower levels).  Returns an
+// empty string, or a message naming the first inconsistency.
+std::string validate(const Symbolic& S);
+
 // Maximum matching of the rows of an n x n pattern (CSR row_ptr[n + 1], col)
 // to its columns: row_of_col[c] is the row matched to column c.  Returns an
 // empty string, or an error when no matching covers every column.

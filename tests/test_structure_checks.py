@@ -1,0 +1,107 @@
+"""The symbolic structure passes its index checks on every pattern the library is run on.
+
+pisp_analyze ends with a check of every index array the kernels follow (assembly
+and extend-add maps inside their fronts, offsets equal to prefix sums of the front
+sizes, children before parents on lower levels); a failure returns
+PISP_ERR_BOUNDS instead of handing the kernels a bad map.  These tests run the
+analysis on host-only handles for the benchmark workloads, the patterns of the GPU
+tests and random patterns, under every amalgamation setting the autotuner tries and
+both orderings, and require every one to pass.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import pfgen
+from test_abi import HostSymbolic
+
+RELAX = [(8, 0.05), (4, 0.0), (16, 0.10), (32, 0.20)]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2311_11833_gb300._lib as L
+    return L.load()
+
+
+def _concat(insts):
+    sizes = [I.n for I in insts]
+    rps, cols, off, nz = [np.zeros(1, np.int64)], [], 0, 0
+    for I in insts:
+        rps.append(I.row_ptr[1:] + nz)
+        cols.append(I.col + off)
+        off += I.n
+        nz += I.nnz
+    return sizes, np.concatenate(rps), np.concatenate(cols).astype(np.int32)
+
+
+def _check(lib, insts, **opt):
+    sizes, rp, col = _concat(insts)
+    hs = HostSymbolic(lib, sizes, rp, col, **opt)
+    try:
+        assert hs.rc == 0, lib.pisp_last_error(hs.h)
+    finally:
+        hs.close()
+
+
+def _csr(M):
+    M = M.tocsr()
+    M.sort_indices()
+    return pfgen.Instance(n=M.shape[0], row_ptr=M.indptr.astype(np.int64), col=M.indices.astype(np.int32),
+                          val=M.data.astype(np.float64), D=np.ones(M.shape[0]), meta={})
+
+
+@pytest.mark.parametrize("rs,rz", RELAX)
+@pytest.mark.parametrize("wl", ["plain", "precision", "differentiation", "scale"])
+def test_workloads(lib, wl, rs, rz):
+    _check(lib, [pfgen.make_instance(wl)], relax_small=rs, relax_zeros=rz)
+
+
+@pytest.fixture(scope="module")
+def batch():
+    return [pfgen.make_instance("batching", g) for g in range(pfgen.CONFIGS["batching"]["G"])]
+
+
+@pytest.mark.parametrize("rs,rz", RELAX[:2])
+def test_full_batch(lib, batch, rs, rz):
+    _check(lib, batch, relax_small=rs, relax_zeros=rz)
+
+
+GPU_TEST_PATTERNS = [(1, 1.0, 11), (2, 1.0, 12), (7, 0.4, 17), (33, 0.15, 43), (100, 0.05, 110),
+                     (257, 0.02, 267), (64, 0.1, 74), (220, 0.03, 220), (300, 0.03, 300),
+                     (700, 0.012, 700), (420, 0.02, 420), (1200, 0.006, 1200), (1200, 0.012, 1200),
+                     (2200, 0.008, 2200), (40, 0.1, 8), (30, 0.15, 12), (9, 0.3, 4), (12, 0.3, 5),
+                     (5, 0.5, 1), (96, 0.08, 11), (128, 0.08, 12)]
+
+
+@pytest.mark.parametrize("ordering", [0, 1])
+@pytest.mark.parametrize("rs,rz", RELAX)
+def test_random_patterns(lib, ordering, rs, rz):
+    for n, d, seed in GPU_TEST_PATTERNS:
+        _check(lib, [pfgen.random_sparse(n, d, seed=seed)], ordering=ordering, relax_small=rs, relax_zeros=rz)
+    rng = np.random.default_rng(rs)
+    for _ in range(20):
+        n = int(rng.integers(1, 400))
+        _check(lib, [pfgen.random_sparse(n, float(rng.uniform(0.0, 0.2)), seed=int(rng.integers(1 << 30)))],
+               ordering=ordering, relax_small=rs, relax_zeros=rz)
+
+
+def test_uneven_batches_and_a_diagonal_instance(lib):
+    n = 6
+    diag = pfgen.Instance(n=n, row_ptr=np.arange(n + 1, dtype=np.int64), col=np.arange(n, dtype=np.int32),
+                          val=np.ones(n), D=np.ones(n), meta={})
+    _check(lib, [diag, pfgen.random_sparse(9, 0.3, seed=4)])
+    insts = [pfgen.make_instance("batching", g) for g in (1, 3, 5, 9, 13)]
+    _check(lib, insts + [pfgen.random_sparse(5, 0.5, seed=3)])
+
+
+def test_zero_diagonal_and_power_flow_patterns(lib):
+    import test_zero_diagonal as zd
+    import paper_2311_11833_gb300 as pisp
+    for M in (zd._swapped(), zd._lambda_first()):
+        _check(lib, [_csr(M)])
+        rp = pisp.match_rows(M.shape[0], M.indptr, M.indices)
+        _check(lib, [_csr(M[rp, :])])
+    for N, npv, seed, a in [(300, 60, 7, 1.0), (300, 60, 12, 1.5)]:
+        c = pfgen.power_flow_case(N, npv, seed=seed, angle_scale=a)
+        _check(lib, [_csr(sp.csr_matrix((c.jacobian(c.x_star), c.col, c.row_ptr), shape=(c.n, c.n)))])
