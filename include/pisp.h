@@ -127,7 +127,11 @@ const char* pisp_last_error(const pisp_handle* h);
  *   col_idx  host [nnz] global column indices; each row's columns must lie in
  *            its own instance's block; duplicates are summed
  *   opt      host, may be NULL for defaults
- * The pattern is copied; the host arrays may be freed afterwards. */
+ * The pattern is copied; the host arrays may be freed afterwards.  Returns
+ * PISP_ERR_INVALID_ARG for a malformed pattern, PISP_ERR_UNSUPPORTED for a
+ * front wider than 46340, and PISP_ERR_BOUNDS if the computed structure fails
+ * its index checks (every map the kernels follow lands inside its front and
+ * arrays); the kernels are never given an unchecked structure. */
 int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row_ptr,
                  const int32_t* col_idx, const pisp_options* opt);
 
