@@ -241,6 +241,17 @@ int pisp_get_supernodes(const pisp_handle* h, int32_t* c0, int32_t* c1, int32_t*
  * to *F_out.  Synchronises the stream.  For factor-level tests. */
 int pisp_get_front(pisp_handle* h, int32_t supernode, int32_t k, double* out, int32_t* F_out);
 
+/* Pivot spread of the last factorisation: for every instance g and
+ * perturbation k, the smallest and largest |u_jj| over the pivots of g's
+ * factor of A + t_k D (the quantities a static pivot order leaves unguarded,
+ * Sec. I; a zero-diagonal entry rescued by a small perturbation shows as a
+ * small minimum).  A non-finite pivot gives NaN for both.
+ *   min_abs, max_abs  host FP64 [G*K] outputs, index g*K + k
+ * Reads only the pivots (one strided device-to-host copy per front and k).
+ * Synchronises the stream.  Returns PISP_ERR_NOT_FACTORED before a
+ * factorisation. */
+int pisp_get_pivot_range(pisp_handle* h, double* min_abs, double* max_abs);
+
 /* End-to-end convenience: host buffers, copies inside.  Factor + solve +
  * combine of `values`, `D`, `b` given in host memory; x written to host.
  * Synchronises the stream. */

@@ -61,6 +61,7 @@ _SIGS = {
     "pisp_get_perm": (c_int32, [c_void_p, c_void_p]),
     "pisp_get_supernodes": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pisp_get_front": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, P(c_int32)]),
+    "pisp_get_pivot_range": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "pisp_solve_host": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
                                   c_void_p, c_int32, c_void_p, c_int32]),
     "pisp_dense_solve_static": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32,

@@ -975,6 +975,53 @@ int pisp_get_front(pisp_handle* h, int32_t s, int32_t k, double* out, int32_t* F
   return PISP_OK;
 }
 
+int pisp_get_pivot_range(pisp_handle* h, double* min_abs, double* max_abs) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  if (!h->factored) return fail(h, PISP_ERR_NOT_FACTORED, "no factorisation");
+  if (!min_abs || !max_abs) return fail(h, PISP_ERR_INVALID_ARG, "null output");
+  TRY(set_device(h));
+  const pisp::Symbolic& S = h->sym;
+  const int K = h->K;
+  const size_t es = esize(h->precision);
+  const size_t GK = (size_t)S.G * K;
+  std::vector<double> lo(GK, HUGE_VAL), hi(GK, 0.0);
+  std::vector<char> bad(GK, 0);
+  // pivots of perturbation k, permuted column c, at buf[k * N + c]
+  std::vector<unsigned char> buf((size_t)S.N * K * es);
+  for (size_t s = 0; s < S.sn.size(); ++s) {
+    const pisp::Supernode& sn = S.sn[s];
+    const int64_t F = sn.F(), ns = sn.ns();
+    for (int k = 0; k < K; ++k) {
+      // u_jj of the front's pivot block sits at j + j*F of the column-major
+      // F x F front of (s, k): every (F + 1)-th element, ns of them
+      const char* src = (const char*)h->fronts.p + ((size_t)K * S.front_off[s] + (size_t)k * F * F) * es;
+      CK(cudaMemcpy2DAsync(buf.data() + ((size_t)k * S.N + sn.c0) * es, es, src, (size_t)(F + 1) * es, es,
+                           (size_t)ns, cudaMemcpyDeviceToHost, h->stream));
+    }
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  for (size_t s = 0; s < S.sn.size(); ++s) {
+    const pisp::Supernode& sn = S.sn[s];
+    for (int k = 0; k < K; ++k) {
+      const size_t q = (size_t)sn.instance * K + k;
+      for (int32_t c = sn.c0; c < sn.c1; ++c) {
+        const size_t e = (size_t)k * S.N + c;
+        const double u = std::fabs(es == 4 ? (double)reinterpret_cast<const float*>(buf.data())[e]
+                                           : reinterpret_cast<const double*>(buf.data())[e]);
+        if (!std::isfinite(u)) bad[q] = 1;
+        lo[q] = std::min(lo[q], u);
+        hi[q] = std::max(hi[q], u);
+      }
+    }
+  }
+  for (size_t q = 0; q < GK; ++q) {
+    const bool empty = lo[q] == HUGE_VAL;  // an instance with no unknowns
+    min_abs[q] = bad[q] || empty ? NAN : lo[q];
+    max_abs[q] = bad[q] || empty ? NAN : hi[q];
+  }
+  return PISP_OK;
+}
+
 int pisp_solve_host(pisp_handle* h, const double* values_host, const double* D_host,
                     const double* t, int32_t K, int32_t precision, const double* b_host,
                     int32_t R, double* x_host, int32_t sweeps) {

@@ -251,6 +251,15 @@ class Solver:
               self._h)
         return out.reshape(F.value, F.value, order="F")
 
+    def pivot_range(self):
+        """pisp_get_pivot_range: (min |u_jj|, max |u_jj|), each [G, K], of the last factorisation."""
+        lo = np.zeros(self.G * self.K)
+        hi = np.zeros(self.G * self.K)
+        self._sync_stream()
+        check(self._lib.pisp_get_pivot_range(self._h, lo.ctypes.data_as(ctypes.c_void_p),
+                                             hi.ctypes.data_as(ctypes.c_void_p)), self._h)
+        return lo.reshape(self.G, self.K), hi.reshape(self.G, self.K)
+
     def solve_host(self, values: np.ndarray, D: np.ndarray, t, b: np.ndarray, precision="fp64",
                    sweeps: int = 0, out: np.ndarray | None = None) -> np.ndarray:
         """pisp_solve_host: end to end from host buffers (copies included)."""

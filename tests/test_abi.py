@@ -196,6 +196,10 @@ def test_analyze_rejects_bad_patterns(lib):
     # numeric calls on a host-only handle fail cleanly
     t = np.array([0.01])
     assert lib.pisp_factor_perturbed(h, None, None, t.ctypes.data_as(ctypes.c_void_p), 1, 64) != 0
+    lo, hi = np.zeros(2), np.zeros(2)
+    assert lib.pisp_get_pivot_range(h, lo.ctypes.data_as(ctypes.c_void_p),
+                                    hi.ctypes.data_as(ctypes.c_void_p)) == 3      # NOT_FACTORED
+    assert lib.pisp_get_pivot_range(None, None, None) == 1
     lib.pisp_destroy(h)
 
 

@@ -115,6 +115,29 @@ def test_factor_entries_match_pivot_free_lu(pisp):
                                        atol=1e-12 * scale)
 
 
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-10), ("fp32", 1e-3)])
+def test_pivot_range_matches_pivot_free_lu(pisp, prec, rtol):
+    """Smallest and largest |u_jj| per (instance, k) equal those of dense Doolittle in
+    the solver's order (FP32 factors: within single-precision rounding, which a
+    float32 Doolittle in this order puts below 1e-5)."""
+    insts = [pfgen.make_instance("plain"), pfgen.random_sparse(40, 0.1, seed=8)]
+    t = pfgen.symmetric_shifts(4)
+    s, val, D = _solver(pisp, insts)
+    s.factor(_dev(val), _dev(D), t, prec)
+    lo, hi = s.pivot_range()
+    assert lo.shape == (2, 4) and hi.shape == (2, 4)
+    perm = s.perm()
+    off = 0
+    for g, inst in enumerate(insts):
+        p = perm[off:off + inst.n] - off            # each instance keeps its own block
+        A = oracle.to_dense(inst)
+        for k in range(4):
+            _, U = oracle.pivot_free_lu(A, inst.D, t[k], p)
+            d = np.abs(np.diag(U))
+            np.testing.assert_allclose([lo[g, k], hi[g, k]], [d.min(), d.max()], rtol=rtol)
+        off += inst.n
+
+
 @pytest.mark.parametrize("n,density,prec,policy", [
     (220, 0.03, "fp64", 0), (300, 0.03, "fp64", 0), (300, 0.03, "fp32", 0), (700, 0.012, "fp32", 0),
     (220, 0.03, "fp64", 1), (300, 0.03, "fp64", 1), (300, 0.03, "fp32", 1), (420, 0.02, "fp32", 1),
