@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pisp.h"
 #include "pisp_internal.h"
 #include "symbolic.h"
@@ -114,6 +116,15 @@ struct pisp_handle {
 namespace {
 
 size_t esize(int precision) { return precision == PISP_FP32 ? 4 : 8; }
+
+// NVTX range over one ABI call, so that profilers can scope a capture to a
+// phase (factor, solve, ...); without an attached tool it costs a pointer test.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 int fail(pisp_handle* h, int code, const std::string& msg) {
   if (h) h->err = msg; else g_last_error = msg;
@@ -554,6 +565,7 @@ int pisp_set_stream(pisp_handle* h, void* stream) {
 int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row_ptr,
                  const int32_t* col_idx, const pisp_options* opt) {
   if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  NvtxRange nvtx_("pisp_analyze");
   if (G < 1 || !n || !row_ptr) return fail(h, PISP_ERR_INVALID_ARG, "bad instance description");
   int64_t N = 0;
   for (int g = 0; g < G; ++g) N += n[g] < 0 ? 0 : n[g];
@@ -710,6 +722,7 @@ int pisp_weights(const double* t, int32_t K, double* beta) {
 int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
                           const double* t, int32_t K, int32_t precision) {
   if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  NvtxRange nvtx_("pisp_factor_perturbed");
   if (!h->analyzed) return fail(h, PISP_ERR_NOT_ANALYZED, "pisp_analyze has not succeeded");
   if (K < 1 || K > PISP_K_MAX || !t) return fail(h, PISP_ERR_INVALID_ARG, "K must be in 1..16");
   if (precision != PISP_FP32 && precision != PISP_FP64)
@@ -808,6 +821,7 @@ int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
 int pisp_solve(pisp_handle* h, const double* b, int32_t R, const double* w, double* x,
                int32_t sweeps) {
   if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  NvtxRange nvtx_("pisp_solve");
   if (!h->factored) return fail(h, PISP_ERR_NOT_FACTORED, "no factorisation");
   if (R < 1 || sweeps < 0) return fail(h, PISP_ERR_INVALID_ARG, "R must be >= 1, sweeps >= 0");
   if (h->sym.N > 0 && (!b || !x)) return fail(h, PISP_ERR_INVALID_ARG, "null b or x");
@@ -829,6 +843,7 @@ int pisp_solve(pisp_handle* h, const double* b, int32_t R, const double* w, doub
 
 int pisp_combine(pisp_handle* h, const double* w, double* x) {
   if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  NvtxRange nvtx_("pisp_combine");
   if (!h->solved) return fail(h, PISP_ERR_NOT_FACTORED, "pisp_solve has not run");
   if (h->sym.N > 0 && !x) return fail(h, PISP_ERR_INVALID_ARG, "null x");
   TRY(set_device(h));
@@ -843,6 +858,7 @@ int pisp_combine(pisp_handle* h, const double* w, double* x) {
 int pisp_refine(pisp_handle* h, const double* b, double* x, int32_t R, int32_t iters,
                 int32_t sweeps) {
   if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  NvtxRange nvtx_("pisp_refine");
   if (!h->factored) return fail(h, PISP_ERR_NOT_FACTORED, "no factorisation");
   if (R < 1 || iters < 0 || sweeps < 0) return fail(h, PISP_ERR_INVALID_ARG, "bad R/iters/sweeps");
   if (h->sym.N > 0 && (!b || !x)) return fail(h, PISP_ERR_INVALID_ARG, "null b or x");
@@ -866,6 +882,7 @@ int pisp_refine(pisp_handle* h, const double* b, double* x, int32_t R, int32_t i
 int pisp_adjoint(pisp_handle* h, const double* g, const double* w, double* grad_b,
                  double* grad_values) {
   if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  NvtxRange nvtx_("pisp_adjoint");
   if (!h->solved) return fail(h, PISP_ERR_NOT_FACTORED, "pisp_solve has not run");
   if (h->sym.N > 0 && !g) return fail(h, PISP_ERR_INVALID_ARG, "null g");
   TRY(set_device(h));
@@ -1026,6 +1043,7 @@ int pisp_solve_host(pisp_handle* h, const double* values_host, const double* D_h
                     const double* t, int32_t K, int32_t precision, const double* b_host,
                     int32_t R, double* x_host, int32_t sweeps) {
   if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  NvtxRange nvtx_("pisp_solve_host");
   if (!h->analyzed) return fail(h, PISP_ERR_NOT_ANALYZED, "pisp_analyze has not succeeded");
   if (R < 1) return fail(h, PISP_ERR_INVALID_ARG, "R must be >= 1");
   const pisp::Symbolic& S = h->sym;
