@@ -62,7 +62,7 @@ def batch():
     return [pfgen.make_instance("batching", g) for g in range(pfgen.CONFIGS["batching"]["G"])]
 
 
-@pytest.mark.parametrize("rs,rz", RELAX[:2])
+@pytest.mark.parametrize("rs,rz", RELAX)
 def test_full_batch(lib, batch, rs, rz):
     _check(lib, batch, relax_small=rs, relax_zeros=rz)
 
