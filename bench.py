@@ -187,12 +187,7 @@ class Arm:
         s.factor(self.vals, self.D, self.t, self.precision)
         s.solve(self.b, sweeps=self.sweeps, out=self.x)
         if self.adjoint:
-            self.s._sync_stream()
-            import ctypes
-            from paper_2311_11833_gb300._lib import check
-            check(s._lib.pisp_adjoint(s._h, ctypes.c_void_p(self.g.data_ptr()), None,
-                                      ctypes.c_void_p(self.gb.data_ptr()),
-                                      ctypes.c_void_p(self.gv.data_ptr())), s._h)
+            s.adjoint(self.g, out_b=self.gb, out_values=self.gv)
 
     def capture(self, profile: bool):
         torch = self.torch

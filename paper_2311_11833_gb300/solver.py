@@ -193,18 +193,28 @@ class Solver:
               self._h)
         return x.reshape(-1) if vec else x
 
-    def adjoint(self, g: torch.Tensor, weights=None, need_b=True, need_values=True):
-        """pisp_adjoint: (dL/db, dL/dvalues) for dL/dx = g of the last solve."""
+    def adjoint(self, g: torch.Tensor, weights=None, need_b=True, need_values=True,
+                out_b: torch.Tensor | None = None, out_values: torch.Tensor | None = None):
+        """pisp_adjoint: (dL/db, dL/dvalues) for dL/dx = g of the last solve.
+
+        out_b / out_values: preallocated outputs (e.g. inside a CUDA graph);
+        without them the outputs that are needed are allocated."""
         g2 = self._dev(g, "g").reshape(self.N, -1)
         if g2.shape[1] != self.R:
             raise ValueError(f"g has {g2.shape[1]} columns, the last solve had R = {self.R}")
-        gb = torch.empty_like(g2) if need_b else None
-        gv = torch.empty(self.nnz, dtype=torch.float64, device=g2.device) if need_values else None
+        if out_b is not None:
+            gb = self._dev_out(out_b, "out_b", g2.numel())
+        else:
+            gb = torch.empty_like(g2) if need_b else None
+        if out_values is not None:
+            gv = self._dev_out(out_values, "out_values", self.nnz)
+        else:
+            gv = torch.empty(self.nnz, dtype=torch.float64, device=g2.device) if need_values else None
         w = None if weights is None else _host_f64(weights)
         self._sync_stream()
         check(self._lib.pisp_adjoint(self._h, _ptr(g2), None if w is None else w.ctypes.data_as(ctypes.c_void_p),
                                      _ptr(gb), _ptr(gv)), self._h)
-        if gb is not None and g.dim() == 1:
+        if gb is not None and out_b is None and g.dim() == 1:
             gb = gb.reshape(-1)
         return gb, gv
 
