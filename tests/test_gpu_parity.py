@@ -283,6 +283,13 @@ def test_adjoint_matches_oracle(pisp):
     rb, rv = oracle.adjoint(oracle.to_scipy(inst), inst.D, t, b, W)
     assert _maxrel(gb.cpu().numpy(), rb) <= TOL64
     assert np.linalg.norm(gv.cpu().numpy() - rv) <= TOL64 * np.linalg.norm(rv)
+    # preallocated outputs (the form a captured graph uses) give the same result
+    import torch
+    ob, ov = torch.full_like(gb, float("nan")), torch.full_like(gv, float("nan"))
+    rb2, rv2 = s.adjoint(_dev(W), out_b=ob, out_values=ov)
+    assert rb2 is ob and rv2 is ov
+    assert _maxrel(ob.cpu().numpy(), gb.cpu().numpy()) <= 1e-13
+    assert np.linalg.norm(ov.cpu().numpy() - gv.cpu().numpy()) <= 1e-13 * np.linalg.norm(gv.cpu().numpy())
 
 
 def test_autograd_finite_differences(pisp):
