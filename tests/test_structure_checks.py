@@ -105,3 +105,30 @@ def test_zero_diagonal_and_power_flow_patterns(lib):
     for N, npv, seed, a in [(300, 60, 7, 1.0), (300, 60, 12, 1.5)]:
         c = pfgen.power_flow_case(N, npv, seed=seed, angle_scale=a)
         _check(lib, [_csr(sp.csr_matrix((c.jacobian(c.x_star), c.col, c.row_ptr), shape=(c.n, c.n)))])
+
+
+@pytest.mark.parametrize("wl,fronts,blocks", [("plain", 7, 8), ("precision", 8, 17),
+                                               ("differentiation", 8, 15), ("scale", 11, 60)])
+def test_critical_chain_of_the_solve(lib, wl, fronts, blocks):
+    """Longest leaf-to-root chain of the assembly tree, in fronts and in 32-pivot
+    diagonal blocks: the dependency bound of a solve pass."""
+    inst = pfgen.make_instance(wl)
+    hs = HostSymbolic(lib, [inst.n], inst.row_ptr, inst.col)
+    try:
+        c0, c1, ms, rows = hs.c0, hs.c1, hs.ms, hs.rows
+    finally:
+        hs.close()
+    S = len(c0)
+    owner = np.zeros(inst.n, np.int64)
+    for s in range(S):
+        owner[c0[s]:c1[s]] = s
+    roff = np.concatenate([[0], np.cumsum(ms)])
+    depth_f, depth_b = np.zeros(S, np.int64), np.zeros(S, np.int64)
+    for s in range(S):                       # children before parents
+        depth_f[s] += 1
+        depth_b[s] += (c1[s] - c0[s] + 31) // 32
+        if ms[s] > 0:
+            p = owner[rows[roff[s]]]         # the parent owns the first update row
+            depth_f[p] = max(depth_f[p], depth_f[s])
+            depth_b[p] = max(depth_b[p], depth_b[s])
+    assert (int(depth_f.max()), int(depth_b.max())) == (fronts, blocks)
