@@ -1,0 +1,51 @@
+"""Host side of the autotuner: the candidate set, the cache key and the cache file.
+(Timing the candidates needs a GPU and is covered by the GPU tests.)"""
+import json
+
+import numpy as np
+import torch
+
+import pfgen
+from paper_2311_11833_gb300 import tune
+
+
+def test_candidates_cover_every_option_once():
+    c = list(tune.candidates())
+    assert len(c) == len(tune.RELAX) * len(tune.POLICIES) * len(tune.SCHEDULES) == 32
+    assert len({tuple(sorted(d.items())) for d in c}) == 32
+    assert {d["factor_policy"] for d in c} == {0, 1, 2, 3} and {d["solve_schedule"] for d in c} == {0, 1}
+
+
+def test_key_depends_on_pattern_and_call_shape():
+    inst = pfgen.make_instance("plain")
+    k = tune._key([inst.n], inst.row_ptr, inst.col, 4, 2, "fp32", 2)
+    assert k == tune._key([inst.n], inst.row_ptr.copy(), inst.col.copy(), 4, 2, "fp32", 2)
+    col = inst.col.copy()
+    col[[0, 1]] = col[[1, 0]]
+    others = {tune._key([inst.n], inst.row_ptr, col, 4, 2, "fp32", 2),
+              tune._key([inst.n], inst.row_ptr, inst.col, 6, 2, "fp32", 2),
+              tune._key([inst.n], inst.row_ptr, inst.col, 4, 3, "fp32", 2),
+              tune._key([inst.n], inst.row_ptr, inst.col, 4, 2, "fp64", 2),
+              tune._key([inst.n], inst.row_ptr, inst.col, 4, 2, "fp32", 1)}
+    assert k not in others and len(others) == 5
+
+
+def test_cache_hit_returns_without_timing(tmp_path):
+    inst = pfgen.make_instance("plain")
+    t = pfgen.symmetric_shifts(4)
+    b = torch.zeros(inst.n, 2, dtype=torch.float64)
+    key = tune._key([inst.n], inst.row_ptr, inst.col, len(t), 2, "fp32", 2)
+    hit = {"options": {"relax_small": 16, "relax_zeros": 0.1, "factor_policy": 0, "solve_schedule": 0},
+           "ms": 0.5, "all": []}
+    path = tmp_path / "tune.json"
+    path.write_text(json.dumps({key: hit}))
+    # values and D are not touched on a hit (no device needed)
+    got = tune.autotune([inst.n], inst.row_ptr, inst.col, None, None, t, b, "fp32", 2, cache=str(path))
+    assert got == hit
+
+
+def test_unreadable_cache_is_empty(tmp_path):
+    assert tune._load(str(tmp_path / "missing.json")) == {}
+    bad = tmp_path / "bad.json"
+    bad.write_text("{not json")
+    assert tune._load(str(bad)) == {}
