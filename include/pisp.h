@@ -21,6 +21,8 @@
  *  - Work is enqueued on the stream given to pisp_create and is ordered on
  *    it; only pisp_get_status and pisp_solve_host synchronise the stream.
  *  - A handle is not thread-safe; use one handle per host thread.
+ *  - A call makes the handle's device current while it runs and restores
+ *    the caller's current device before it returns.
  *  - Instances: the matrix is the block diagonal of G independent instances
  *    of sizes n[0..G-1]; N = sum n[g].  All vectors are row-major [N][R]
  *    FP64 (R right-hand sides per instance row), values are the CSR values

@@ -138,12 +138,29 @@ int fail(pisp_handle* h, int code, const std::string& msg) {
       return fail(h, PISP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-int set_device(pisp_handle* h) {
+// The handle's device is made current for one ABI call and the caller's
+// current device is restored when the call returns, so the library never
+// leaves a different device current behind (streams and buffers stay bound to
+// the handle's device).
+struct DeviceScope {
+  int prev = -1;
+  DeviceScope() = default;
+  DeviceScope(const DeviceScope&) = delete;
+  DeviceScope& operator=(const DeviceScope&) = delete;
+  ~DeviceScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+int set_device(pisp_handle* h, DeviceScope& scope) {
   if (h->device < 0)
     return fail(h, PISP_ERR_INVALID_ARG, "host-only handle (device -1): numeric calls need a device");
   int cur = -1;
   CK(cudaGetDevice(&cur));
-  if (cur != h->device) CK(cudaSetDevice(h->device));
+  if (cur != h->device) {
+    CK(cudaSetDevice(h->device));
+    if (scope.prev < 0) scope.prev = cur;
+  }
   return PISP_OK;
 }
 
@@ -566,12 +583,13 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
                  const int32_t* col_idx, const pisp_options* opt) {
   if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
   NvtxRange nvtx_("pisp_analyze");
+  DeviceScope dev_scope_;
   if (G < 1 || !n || !row_ptr) return fail(h, PISP_ERR_INVALID_ARG, "bad instance description");
   int64_t N = 0;
   for (int g = 0; g < G; ++g) N += n[g] < 0 ? 0 : n[g];
   if (row_ptr[N] > 0 && !col_idx) return fail(h, PISP_ERR_INVALID_ARG, "null col_idx");
   if (h->device >= 0) {
-    TRY(set_device(h));
+    TRY(set_device(h, dev_scope_));
     if (!h->fork_ev) {  // side streams of the factorisation (created outside any capture)
       CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
       for (int i = 0; i < pisp_handle::kSide; ++i) {
@@ -736,7 +754,8 @@ int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
     return fail(h, PISP_ERR_UNSUPPORTED, "front too large for this precision");
   double beta[PISP_K_MAX];
   if (pisp_weights(t, K, beta) != PISP_OK) return fail(h, PISP_ERR_INVALID_ARG, g_last_error);
-  TRY(set_device(h));
+  DeviceScope dev_scope_;
+  TRY(set_device(h, dev_scope_));
   h->factored = h->solved = false;
   h->K_hint = K;
   if (h->plan_precision != precision || h->plan_K != K) TRY(build_plans(h, precision));
@@ -826,7 +845,8 @@ int pisp_solve(pisp_handle* h, const double* b, int32_t R, const double* w, doub
   if (R < 1 || sweeps < 0) return fail(h, PISP_ERR_INVALID_ARG, "R must be >= 1, sweeps >= 0");
   if (h->sym.N > 0 && (!b || !x)) return fail(h, PISP_ERR_INVALID_ARG, "null b or x");
   if (b == x && b) return fail(h, PISP_ERR_INVALID_ARG, "x may not alias b");
-  TRY(set_device(h));
+  DeviceScope dev_scope_;
+  TRY(set_device(h, dev_scope_));
   TRY(set_weights(h, w, h->w_last));
   TRY(ensure_solve_buffers(h, R));
   const pisp::Shifts sh = make_shifts(h, h->w_last);
@@ -846,7 +866,8 @@ int pisp_combine(pisp_handle* h, const double* w, double* x) {
   NvtxRange nvtx_("pisp_combine");
   if (!h->solved) return fail(h, PISP_ERR_NOT_FACTORED, "pisp_solve has not run");
   if (h->sym.N > 0 && !x) return fail(h, PISP_ERR_INVALID_ARG, "null x");
-  TRY(set_device(h));
+  DeviceScope dev_scope_;
+  TRY(set_device(h, dev_scope_));
   double ww[PISP_K_MAX];
   TRY(set_weights(h, w, ww));
   const pisp::Shifts sh = make_shifts(h, ww);
@@ -862,7 +883,8 @@ int pisp_refine(pisp_handle* h, const double* b, double* x, int32_t R, int32_t i
   if (!h->factored) return fail(h, PISP_ERR_NOT_FACTORED, "no factorisation");
   if (R < 1 || iters < 0 || sweeps < 0) return fail(h, PISP_ERR_INVALID_ARG, "bad R/iters/sweeps");
   if (h->sym.N > 0 && (!b || !x)) return fail(h, PISP_ERR_INVALID_ARG, "null b or x");
-  TRY(set_device(h));
+  DeviceScope dev_scope_;
+  TRY(set_device(h, dev_scope_));
   TRY(ensure_solve_buffers(h, R));
   const size_t nkr = (size_t)h->sym.N * h->K * R * sizeof(double);
   const size_t nr = (size_t)h->sym.N * R * sizeof(double);
@@ -885,7 +907,8 @@ int pisp_adjoint(pisp_handle* h, const double* g, const double* w, double* grad_
   NvtxRange nvtx_("pisp_adjoint");
   if (!h->solved) return fail(h, PISP_ERR_NOT_FACTORED, "pisp_solve has not run");
   if (h->sym.N > 0 && !g) return fail(h, PISP_ERR_INVALID_ARG, "null g");
-  TRY(set_device(h));
+  DeviceScope dev_scope_;
+  TRY(set_device(h, dev_scope_));
   double ww[PISP_K_MAX];
   TRY(set_weights(h, w, ww));
   const int32_t R = h->R;
@@ -903,7 +926,8 @@ int pisp_adjoint(pisp_handle* h, const double* g, const double* w, double* grad_
 int pisp_get_status(pisp_handle* h, int32_t* per_instance_k, int32_t* first_bad_col) {
   if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
   if (!h->factored) return fail(h, PISP_ERR_NOT_FACTORED, "no factorisation");
-  TRY(set_device(h));
+  DeviceScope dev_scope_;
+  TRY(set_device(h, dev_scope_));
   const size_t n = (size_t)h->sym.G * h->K;
   std::vector<int32_t> st(n), bc(n);
   CK(cudaMemcpyAsync(st.data(), h->status.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
@@ -977,7 +1001,8 @@ int pisp_get_front(pisp_handle* h, int32_t s, int32_t k, double* out, int32_t* F
   if (!h->factored) return fail(h, PISP_ERR_NOT_FACTORED, "no factorisation");
   if (s < 0 || s >= (int32_t)h->sym.sn.size() || k < 0 || k >= h->K)
     return fail(h, PISP_ERR_INVALID_ARG, "supernode or k out of range");
-  TRY(set_device(h));
+  DeviceScope dev_scope_;
+  TRY(set_device(h, dev_scope_));
   const int64_t F = h->sym.sn[s].F();
   if (F_out) *F_out = (int32_t)F;
   if (!out) return PISP_OK;
@@ -996,7 +1021,8 @@ int pisp_get_pivot_range(pisp_handle* h, double* min_abs, double* max_abs) {
   if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
   if (!h->factored) return fail(h, PISP_ERR_NOT_FACTORED, "no factorisation");
   if (!min_abs || !max_abs) return fail(h, PISP_ERR_INVALID_ARG, "null output");
-  TRY(set_device(h));
+  DeviceScope dev_scope_;
+  TRY(set_device(h, dev_scope_));
   const pisp::Symbolic& S = h->sym;
   const int K = h->K;
   const size_t es = esize(h->precision);
@@ -1049,7 +1075,8 @@ int pisp_solve_host(pisp_handle* h, const double* values_host, const double* D_h
   const pisp::Symbolic& S = h->sym;
   if ((S.nnzA && !values_host) || (S.N && (!D_host || !b_host || !x_host)))
     return fail(h, PISP_ERR_INVALID_ARG, "null host buffer");
-  TRY(set_device(h));
+  DeviceScope dev_scope_;
+  TRY(set_device(h, dev_scope_));
   const size_t nv = S.nnzA * sizeof(double), nd = S.N * sizeof(double);
   const size_t nb = (size_t)S.N * R * sizeof(double);
   if (!h->in_vals.ensure(nv) || !h->in_D.ensure(nd) || !h->in_b.ensure(nb) || !h->out_x.ensure(nb))
@@ -1067,7 +1094,8 @@ int pisp_solve_host(pisp_handle* h, const double* values_host, const double* D_h
 int pisp_profile(pisp_handle* h, int32_t on) {
   if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
   if (on) {
-    TRY(set_device(h));
+    DeviceScope dev_scope_;
+    TRY(set_device(h, dev_scope_));
     while (h->prof_ev.size() < 2048) {  // events exist before any stream capture
       cudaEvent_t e;
       CK(cudaEventCreate(&e));
@@ -1084,7 +1112,8 @@ int pisp_profile(pisp_handle* h, int32_t on) {
 
 int pisp_profile_collect(pisp_handle* h) {
   if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
-  TRY(set_device(h));
+  DeviceScope dev_scope_;
+  TRY(set_device(h, dev_scope_));
   CK(cudaStreamSynchronize(h->stream));
   for (const auto& b : h->prof_br) {
     float ms = 0.f;
