@@ -14,6 +14,7 @@
 // Storage: front s of perturbation k occupies F*F contiguous elements
 // (column-major) at K*front_off[s] + k*F*F.  After factorisation it holds
 // L11\U11, L21, U12 and the Schur complement F22 that the parent reads.
+#include <atomic>
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -727,13 +728,14 @@ int big_dag_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_big, co
                  int* ticket, int* flags, int* err, const double* vals, const double* D,
                  const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol, cudaStream_t st) {
   if (lp.dag_tasks == 0) return 0;
-  static int nsm_dev[kMaxDevices] = {};
+  static std::atomic<int> nsm_dev[kMaxDevices];
   const int dev = current_device();
-  if (!nsm_dev[dev]) {
+  int nsm = nsm_dev[dev].load(std::memory_order_acquire);
+  if (!nsm) {
     cudaFuncSetAttribute(k_big_dag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
-    cudaDeviceGetAttribute(&nsm_dev[dev], cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    nsm_dev[dev].store(nsm, std::memory_order_release);
   }
-  const int nsm = nsm_dev[dev];
   const size_t smem = std::max((size_t)(lp.big_maxF + 1) * 32, (size_t)2 * 32 * 33) * sizeof(T);
   int occ = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_big_dag<T>, 256, smem);
@@ -1107,13 +1109,14 @@ template <typename T>
 int owner_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_big, const DagTask* tasks,
                int* ticket, int* flags, int* err, const double* vals, const double* D,
                const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol, cudaStream_t st) {
-  static int nsm_dev[kMaxDevices] = {};
+  static std::atomic<int> nsm_dev[kMaxDevices];
   const int dev = current_device();
-  if (!nsm_dev[dev]) {
+  int nsm = nsm_dev[dev].load(std::memory_order_acquire);
+  if (!nsm) {
     cudaFuncSetAttribute(k_front_owner<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
-    cudaDeviceGetAttribute(&nsm_dev[dev], cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    nsm_dev[dev].store(nsm, std::memory_order_release);
   }
-  const int nsm = nsm_dev[dev];
   const size_t smem = ((size_t)(lp.own_ch + 1) * 32 + 32 * 32 + 32 * 33) * sizeof(T);
   if (lp.own_ch < 32 || lp.own_ch % 32 || smem > (size_t)kSmemCap) return -1;
   int occ = 1;
@@ -1135,16 +1138,16 @@ int small_threads(int maxF) {
 
 template <typename T>
 void set_smem_attrs() {
-  static bool done_dev[kMaxDevices] = {};
+  static std::atomic<bool> done_dev[kMaxDevices];
   const int dev = current_device();
-  if (done_dev[dev]) return;
+  if (done_dev[dev].load(std::memory_order_acquire)) return;
   cudaFuncSetAttribute(k_front_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
   cudaFuncSetAttribute(k_front_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
   cudaFuncSetAttribute(k_panel_big<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
   cudaFuncSetAttribute(k_panel_big<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
   cudaFuncSetAttribute(k_panel_big<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
   cudaFuncSetAttribute(k_panel_big<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
-  done_dev[dev] = true;
+  done_dev[dev].store(true, std::memory_order_release);
 }
 
 template <typename T, int NB>

@@ -9,6 +9,7 @@
 //                            update part = contribution to the parent)
 // Forward solves run the assembly forest bottom-up, backward solves top-down;
 // one CTA handles one (front, perturbation, RHS chunk).
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -888,9 +889,9 @@ __global__ void k_fill_nan_failed(SymDev sd, const int32_t* __restrict__ status,
 
 template <typename T>
 void set_solve_attrs() {
-  static bool done_dev[kMaxDevices] = {};
+  static std::atomic<bool> done_dev[kMaxDevices];
   const int dev = current_device();
-  if (done_dev[dev]) return;
+  if (done_dev[dev].load(std::memory_order_acquire)) return;
   cudaFuncSetAttribute(k_forward<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSolveSmem);
   cudaFuncSetAttribute(k_forward<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSolveSmem);
   cudaFuncSetAttribute(k_backward<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSolveSmem);
@@ -899,7 +900,7 @@ void set_solve_attrs() {
                        kSolveSmem + 2 * 32 * kBS * (int)sizeof(T));
   cudaFuncSetAttribute(k_backward_blk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        kSolveSmem + 2 * 32 * kBS * (int)sizeof(T));
-  done_dev[dev] = true;
+  done_dev[dev].store(true, std::memory_order_release);
 }
 
 // RHS chunk: enough CTAs to fill the GPU, within the shared-memory budget.
@@ -1022,19 +1023,20 @@ int persistent_impl(bool forward, const SymDev& sd, const SolveUnit* units, int 
                     int rhs_mode, void* V, double* out, double* acc, int R, int K, int max_blk_F,
                     cudaStream_t st) {
   if (nunits == 0) return 0;
-  static int nsm_dev[kMaxDevices] = {};
+  static std::atomic<int> nsm_dev[kMaxDevices];
   int occ_f = 0, occ_b = 0;
   const size_t seg_smem = (size_t)(256 / 8) * kRW * 9 * sizeof(T);
   const size_t mF = (size_t)std::max(max_blk_F, 1);
   const size_t blk_smem = (size_t)(2 * 32 * kBS + kSolveChunk * mF) * sizeof(T);
   const size_t smem = std::max(seg_smem, blk_smem);
   const int dev = current_device();
-  if (!nsm_dev[dev]) {
+  int nsm = nsm_dev[dev].load(std::memory_order_acquire);
+  if (!nsm) {
     cudaFuncSetAttribute(k_solve_persistent<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_solve_persistent<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaDeviceGetAttribute(&nsm_dev[dev], cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    nsm_dev[dev].store(nsm, std::memory_order_release);
   }
-  const int nsm = nsm_dev[dev];
   if (smem > 200 * 1024) return -1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_solve_persistent<T, true>, kSolveThreads, smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_solve_persistent<T, false>, kSolveThreads, smem);
