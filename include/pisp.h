@@ -116,7 +116,8 @@ int pisp_destroy(pisp_handle* h);
 /* Rebinds the handle to another stream of the same device. */
 int pisp_set_stream(pisp_handle* h, void* stream);
 
-/* Message for the last failing call on h (or for a NULL handle). */
+/* Message for the last failing call on h; for a NULL handle, for the last
+ * failing call without a handle made by the calling host thread. */
 const char* pisp_last_error(const pisp_handle* h);
 
 /* Symbolic phase (host).  Static pivot order of Sec. II-C: a fill-reducing

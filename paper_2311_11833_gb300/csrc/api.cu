@@ -44,7 +44,7 @@ struct Buf {
   T* as() const { return reinterpret_cast<T*>(p); }
 };
 
-std::string g_last_error;  // for calls without a valid handle
+thread_local std::string g_last_error;  // for calls without a valid handle, per host thread
 
 }  // namespace
 
