@@ -22,3 +22,16 @@ def test_reference_arm_prints_one_json_line():
     assert d["impl"] == "reference" and d["steps"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["config"]["workload"] == "plain"
+
+
+def test_product_arm_fails_loudly_without_a_gpu():
+    """No CPU fallback: without a CUDA device the product arm exits non-zero and
+    prints no result line."""
+    import pytest
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    r = subprocess.run([sys.executable, "bench.py", "--steps", "1", "--warmup", "1"], cwd=ROOT,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0
+    assert not any(l.strip().startswith("{") for l in r.stdout.splitlines())
