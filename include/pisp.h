@@ -165,22 +165,33 @@ int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
  *            factors this makes every x_k (and so x) agree with the FP64
  *            definition to working accuracy.
  * The per-perturbation solutions are kept in the handle for pisp_combine and
- * pisp_adjoint. */
+ * pisp_adjoint.  Returns PISP_ERR_NOT_FACTORED before a factorisation,
+ * PISP_ERR_INVALID_ARG for R < 1, sweeps < 0, NULL or aliased b / x; a
+ * failed (instance, k) of the factorisation leaves that instance's rows of x
+ * NaN and the call still returns PISP_OK (pisp_get_status reports it). */
 int pisp_solve(pisp_handle* h, const double* b, int32_t R, const double* w, double* x,
                int32_t sweeps);
 
 /* Re-combines the kept per-perturbation solutions of the last pisp_solve with
  * other weights (Eq. x_star):  x = sum_k w_k x_k.
- *   w  host FP64 [K] or NULL for pisp_weights(t);   x device FP64 [N][R]. */
+ *   w  host FP64 [K] or NULL for pisp_weights(t);   x device FP64 [N][R],
+ *   R of the last pisp_solve.
+ * Returns PISP_ERR_NOT_FACTORED when no kept solutions exist. */
 int pisp_combine(pisp_handle* h, const double* w, double* x);
 
 /* The optional residual check of Alg. 1 turned into a correction: `iters` times
- *     r = b - A x (FP64, original values);  x += sum_k beta_k (A + t_k D)^{-1} r
+ *     r = b - A x (FP64, the values of the last factorisation);
+ *     x += sum_k beta_k (A + t_k D)^{-1} r
  * with each inner perturbed solve done with `sweeps` residual corrections.
  * Converges to A^{-1} b when the Neumann series converges (eps * max|alpha| *
  * rho(A^{-1} D) < 1, Sec. II-B).
- *   values device FP64 [nnz]; b device FP64 [N][R]; x device FP64 [N][R] in/out;
- *   R must equal the R of the last pisp_solve. */
+ *   b device FP64 [N][R]; x device FP64 [N][R] in/out; R >= 1, iters >= 0.
+ * The kept solutions of the last pisp_solve survive a refine with at most as
+ * many right-hand sides; a larger R releases them (pisp_combine and
+ * pisp_adjoint then return PISP_ERR_NOT_FACTORED until the next pisp_solve).
+ * Returns PISP_ERR_NOT_FACTORED before a factorisation, PISP_ERR_INVALID_ARG
+ * for bad sizes or NULL buffers, PISP_ERR_OOM if its workspace cannot be
+ * allocated. */
 int pisp_refine(pisp_handle* h, const double* b, double* x, int32_t R, int32_t iters,
                 int32_t sweeps);
 
@@ -192,7 +203,10 @@ int pisp_refine(pisp_handle* h, const double* b, double* x, int32_t R, int32_t i
  *   grad_b      device FP64 [N][R] output, or NULL
  *   grad_values device FP64 [nnz] output, or NULL
  *   w           host FP64 [K] or NULL (pisp_weights(t)): the combination used
- *               in the forward pass. */
+ *               in the forward pass.
+ * R is that of the last pisp_solve.  Returns PISP_ERR_NOT_FACTORED when no
+ * kept solutions exist, PISP_ERR_INVALID_ARG for a NULL g, PISP_ERR_OOM if its
+ * workspace cannot be allocated. */
 int pisp_adjoint(pisp_handle* h, const double* g, const double* w, double* grad_b,
                  double* grad_values);
 

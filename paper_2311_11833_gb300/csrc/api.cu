@@ -885,6 +885,10 @@ int pisp_refine(pisp_handle* h, const double* b, double* x, int32_t R, int32_t i
   if (h->sym.N > 0 && (!b || !x)) return fail(h, PISP_ERR_INVALID_ARG, "null b or x");
   DeviceScope dev_scope_;
   TRY(set_device(h, dev_scope_));
+  // more right-hand sides than the last solve may reallocate the store of the
+  // kept per-perturbation solutions: they are then gone, and pisp_combine /
+  // pisp_adjoint refuse until the next pisp_solve
+  if (h->solved && R > h->R) h->solved = false;
   TRY(ensure_solve_buffers(h, R));
   const size_t nkr = (size_t)h->sym.N * h->K * R * sizeof(double);
   const size_t nr = (size_t)h->sym.N * R * sizeof(double);

@@ -74,4 +74,10 @@ def test_device_buffers_are_sized_from_the_pattern():
         s.combine(out=torch.empty(9, dtype=torch.float64, device=dev))
     gb, gv = s.adjoint(torch.zeros((9, 2), dtype=torch.float64, device=dev))
     assert gb.shape == (9, 2) and gv.shape == (inst.nnz,)
+    # a refine with more right-hand sides than the last solve may reallocate the
+    # kept per-perturbation solutions: combine then refuses instead of reading them
+    b3 = torch.tensor(pfgen.rhs(9, 3, 2), device=dev)
+    s.refine(b3, torch.zeros((9, 3), dtype=torch.float64, device=dev))
+    with pytest.raises(pisp.PispError):
+        s.combine()
     s.close()
