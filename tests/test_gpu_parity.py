@@ -415,6 +415,25 @@ def test_full_scale_config_fp32_sweeps(pisp):
     assert _maxrel(x, _oracle_xhat(inst, t, b)) <= TOL64
 
 
+def test_full_differentiation_config(pisp):
+    """The 1354-bus workload at its full size (K = 4, R = 64, FP64, the bench's
+    seeds): x_hat, dL/db and dL/dvalues of L = sum(W * x_hat) against the oracle."""
+    c = pfgen.CONFIGS["differentiation"]
+    inst = pfgen.make_instance("differentiation")
+    t = pfgen.symmetric_shifts(c["K"])
+    b = pfgen.rhs(inst.n, c["R"], 1)
+    W = pfgen.rhs(inst.n, c["R"], 2)
+    s, val, D = _solver(pisp, [inst])
+    s.factor(_dev(val), _dev(D), t, "fp64")
+    x = s.solve(_dev(b)).cpu().numpy()
+    gb, gv = s.adjoint(_dev(W))
+    A = oracle.to_scipy(inst)
+    assert _maxrel(x, oracle.x_hat(A, inst.D, t, b)) <= TOL64
+    rb, rv = oracle.adjoint(A, inst.D, t, b, W)
+    assert _maxrel(gb.cpu().numpy(), rb) <= TOL64
+    assert np.linalg.norm(gv.cpu().numpy() - rv) <= TOL64 * np.linalg.norm(rv)
+
+
 def test_full_batching_config_sampled(pisp):
     """All 256 grids in one factor/solve; sampled instances checked against the oracle."""
     c = pfgen.CONFIGS["batching"]
