@@ -52,10 +52,9 @@ def _lambda_first():
 
 
 def _zero_diag_rule(M):
-    """D: |A_ii| where the diagonal is nonzero, else the largest magnitude of row i."""
-    d = np.abs(M.diagonal()).astype(float)
-    rowmax = np.asarray(abs(M).max(axis=1).todense()).ravel()
-    return np.where(d > 1e-12 * abs(M).max(), d, rowmax)
+    """D: |A_ii| where the diagonal is nonzero, else the largest magnitude of row i
+    (the generator's rule, applied to a sorted CSR matrix)."""
+    return pfgen.diag_rule(M.shape[0], M.indptr, M.indices, M.data)
 
 
 def _solver_order(lib, M):
