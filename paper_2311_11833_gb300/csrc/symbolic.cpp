@@ -11,7 +11,7 @@
 #include <climits>
 #include <cstdio>
 #include <numeric>
-#include <set>
+#include <queue>
 #include <utility>
 
 namespace pisp {
@@ -30,20 +30,25 @@ std::vector<int32_t> minimum_degree(int32_t n, const std::vector<int32_t>& xadj,
   std::vector<std::vector<int32_t>> vadj(n), eadj(n), le(n);
   std::vector<char> state(n, 0);  // 0 variable, 1 live element, 2 absorbed
   std::vector<int32_t> deg(n), mark(n, -1), w(n, 0), wstamp(n, -1);
-  std::set<std::pair<int32_t, int32_t>> pq;
+  // (degree, index) min-heap with lazy deletion: every variable has an entry
+  // with its current degree; entries left behind by a degree update, or by
+  // an elimination, are skipped when they reach the top.  The next pivot is
+  // the lowest index among the smallest degrees.
+  using Entry = std::pair<int32_t, int32_t>;
+  std::priority_queue<Entry, std::vector<Entry>, std::greater<Entry>> pq;
   for (int32_t i = 0; i < n; ++i) {
     vadj[i].assign(adj.begin() + xadj[i], adj.begin() + xadj[i + 1]);
     deg[i] = (int32_t)vadj[i].size();
-    pq.insert({deg[i], i});
+    pq.push({deg[i], i});
   }
   std::vector<int32_t> perm;
   perm.reserve(n);
   int32_t live = n;
   std::vector<int32_t> Lp, nv, ne;
   for (int32_t step = 0; step < n; ++step) {
-    auto it = pq.begin();
-    const int32_t p = it->second;
-    pq.erase(it);
+    while (state[pq.top().second] != 0 || deg[pq.top().second] != pq.top().first) pq.pop();
+    const int32_t p = pq.top().second;
+    pq.pop();
     perm.push_back(p);
     --live;
     Lp.clear();
@@ -90,9 +95,10 @@ std::vector<int32_t> minimum_degree(int32_t n, const std::vector<int32_t>& xadj,
       ne.push_back(p);
       eadj[i].swap(ne);
       if (d > live - 1) d = live - 1;
-      pq.erase({deg[i], i});
-      deg[i] = (int32_t)d;
-      pq.insert({deg[i], i});
+      if (deg[i] != (int32_t)d) {
+        deg[i] = (int32_t)d;
+        pq.push({deg[i], i});
+      }
     }
   }
   return perm;
