@@ -3,7 +3,7 @@
 Sec. IV takes its systems from Newton-Raphson on a distributed-slack AC power
 flow: every iteration solves J(x_i) dx = F(x_i) with the same sparsity
 pattern, so the symbolic analysis (ordering, supernodes, levels) is done once
-and every iteration only refactors.  This driver does exactly that through an
+and every iteration only refactors.  This loop does exactly that through an
 analysed `Solver`: per iteration it uploads the Jacobian values and the
 perturbation diagonal, runs pisp_factor_perturbed for the shifts t, and takes
 dx = sum_k beta_k (J + t_k D)^{-1} F from pisp_solve (with `sweeps` FP64

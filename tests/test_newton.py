@@ -6,8 +6,8 @@ random operating point), so convergence is checked against a known answer.
 
 CPU tests pin the mismatch F and Jacobian J (central differences, F(x_star) = 0),
 the exact Newton loop of the oracle (quadratic convergence to x_star), the
-iteration counts with the perturbed step, and the library's driver with a
-stand-in solver; the GPU test runs the driver on libpisp and compares it with
+iteration counts with the perturbed step, and the library's Newton loop with a
+stand-in solver; the GPU test runs that loop on libpisp and compares it with
 the oracle's loop.
 """
 import numpy as np
@@ -110,7 +110,7 @@ def test_perturbed_newton_stalls_at_the_edge_of_the_region():
 
 class _OracleSolver:
     """Stand-in with the Solver's calls, computing with the oracle on the CPU, to
-    test the driver's host logic without a GPU."""
+    test the Newton loop's host logic without a GPU."""
 
     device = torch.device("cpu")
 
@@ -130,7 +130,7 @@ class _OracleSolver:
         return torch.from_numpy(oracle.x_hat(self.J, self.D, self.t, b.numpy()))
 
 
-def test_driver_follows_the_oracle_loop_on_the_cpu():
+def test_library_loop_follows_the_oracle_loop_on_the_cpu():
     import paper_2311_11833_gb300 as pisp
     c = _case("heavy")
     t = pfgen.symmetric_shifts(4, 1e-3)
@@ -146,7 +146,7 @@ def test_driver_follows_the_oracle_loop_on_the_cpu():
     assert not res.converged and res.iterations == 2 and len(res.mismatch) == 3
 
 
-def test_driver_raises_on_a_failed_factorisation():
+def test_library_loop_raises_on_a_failed_factorisation():
     import paper_2311_11833_gb300 as pisp
     c = _case("light")
 
@@ -163,7 +163,7 @@ def test_driver_raises_on_a_failed_factorisation():
 @pytest.mark.parametrize("name,precision,sweeps", [("light", "fp64", 0), ("heavy", "fp64", 0),
                                                     ("heavy", "fp32", 2)])
 def test_newton_on_the_gpu(name, precision, sweeps):
-    """The driver on libpisp: one analysis, a refactorisation per iteration; the
+    """The Newton loop on libpisp: one analysis, a refactorisation per iteration; the
     iteration count is the oracle loop's (within one step: the two solves differ
     by rounding) and the limit is the planted solution."""
     import paper_2311_11833_gb300 as pisp
