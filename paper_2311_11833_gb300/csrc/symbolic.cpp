@@ -8,6 +8,9 @@
 #include "symbolic.h"
 
 #include <algorithm>
+#include <thread>
+#include <functional>
+#include <atomic>
 #include <climits>
 #include <cstdio>
 #include <numeric>
@@ -214,6 +217,199 @@ std::string match_rows(int32_t n, const int64_t* row_ptr, const int32_t* col,
   return std::string();
 }
 
+namespace {
+
+// Ordering, elimination tree, column structures and relaxed supernodes of one
+// instance (local indices).  Instances are independent, so they can be
+// analysed concurrently; `analyze` merges them in instance order.
+struct InstanceResult {
+  std::string err;
+  std::vector<int32_t> pf;         // [ng] local permutation, new -> old
+  std::vector<LocalSn> merged;     // supernodes, children before parents
+  std::vector<int32_t> sn_parent;  // local parent supernode, or -1
+  std::vector<int32_t> lsn;        // [ng] local supernode of each permuted column
+  int64_t nnzL = 0;
+  int32_t height = 0;              // elimination-tree height
+};
+
+std::string analyze_instance(int32_t ng, int64_t off, const int64_t* row_ptr, const int32_t* col,
+                             const SymbolicOptions& opt, InstanceResult& R) {
+  // symmetric adjacency of A + A^T without the diagonal (local indices)
+  std::vector<int32_t> cnt(ng + 1, 0);
+  for (int32_t i = 0; i < ng; ++i)
+    for (int64_t e = row_ptr[off + i]; e < row_ptr[off + i + 1]; ++e) {
+      const int64_t j = (int64_t)col[e] - off;
+      if (j < 0 || j >= ng) return "column index outside its instance block";
+      if (j != i) { ++cnt[i + 1]; ++cnt[j + 1]; }
+    }
+  std::vector<int32_t> xadj(ng + 1, 0);
+  for (int32_t i = 0; i < ng; ++i) xadj[i + 1] = xadj[i] + cnt[i + 1];
+  std::vector<int32_t> adj(xadj[ng]);
+  std::vector<int32_t> fill(xadj.begin(), xadj.end() - 1);
+  for (int32_t i = 0; i < ng; ++i)
+    for (int64_t e = row_ptr[off + i]; e < row_ptr[off + i + 1]; ++e) {
+      const int32_t j = (int32_t)(col[e] - off);
+      if (j != i) { adj[fill[i]++] = j; adj[fill[j]++] = i; }
+    }
+  // sort + unique each list
+  {
+    std::vector<int32_t> x2(ng + 1, 0), a2;
+    a2.reserve(adj.size());
+    for (int32_t i = 0; i < ng; ++i) {
+      auto b = adj.begin() + xadj[i], e = adj.begin() + xadj[i + 1];
+      std::sort(b, e);
+      auto u = std::unique(b, e);
+      a2.insert(a2.end(), b, u);
+      x2[i + 1] = (int32_t)a2.size();
+    }
+    xadj.swap(x2);
+    adj.swap(a2);
+  }
+  std::vector<int32_t> pl;
+  if (opt.ordering == 0) {
+    pl = minimum_degree(ng, xadj, adj);
+  } else {
+    pl.resize(ng);
+    std::iota(pl.begin(), pl.end(), 0);
+  }
+  std::vector<int32_t> ipl(ng);
+  for (int32_t i = 0; i < ng; ++i) ipl[pl[i]] = i;
+  // elimination tree of the permuted pattern
+  std::vector<int32_t> parent(ng, -1), anc(ng, -1);
+  for (int32_t j = 0; j < ng; ++j) {
+    const int32_t o = pl[j];
+    for (int32_t q = xadj[o]; q < xadj[o + 1]; ++q) {
+      int32_t r = ipl[adj[q]];
+      if (r >= j) continue;
+      while (anc[r] != -1 && anc[r] != j) { const int32_t t = anc[r]; anc[r] = j; r = t; }
+      if (anc[r] == -1) { anc[r] = j; parent[r] = j; }
+    }
+  }
+  // postorder (children visited in ascending order)
+  std::vector<int32_t> head(ng, -1), next(ng, -1);
+  for (int32_t j = ng - 1; j >= 0; --j)
+    if (parent[j] >= 0) { next[j] = head[parent[j]]; head[parent[j]] = j; }
+  std::vector<int32_t> post;
+  post.reserve(ng);
+  std::vector<int32_t> stack;
+  for (int32_t r = 0; r < ng; ++r) {
+    if (parent[r] != -1) continue;
+    stack.push_back(r);
+    while (!stack.empty()) {
+      const int32_t v = stack.back();
+      if (head[v] >= 0) {
+        const int32_t c = head[v];
+        head[v] = next[c];
+        stack.push_back(c);
+      } else {
+        stack.pop_back();
+        post.push_back(v);
+      }
+    }
+  }
+  std::vector<int32_t> ipost(ng);
+  for (int32_t k = 0; k < ng; ++k) ipost[post[k]] = k;
+  std::vector<int32_t> pf(ng), ipf(ng), par(ng);
+  for (int32_t k = 0; k < ng; ++k) {
+    pf[k] = pl[post[k]];
+    par[k] = parent[post[k]] >= 0 ? ipost[parent[post[k]]] : -1;
+  }
+  for (int32_t k = 0; k < ng; ++k) ipf[pf[k]] = k;
+  // column structures of L (rows > j) by merging children
+  std::vector<std::vector<int32_t>> st(ng);
+  std::vector<int32_t> mk(ng, -1), height(ng, 0);
+  std::vector<std::vector<int32_t>> kids(ng);
+  for (int32_t j = 0; j < ng; ++j)
+    if (par[j] >= 0) kids[par[j]].push_back(j);
+  for (int32_t j = 0; j < ng; ++j) {
+    std::vector<int32_t>& s = st[j];
+    mk[j] = j;
+    const int32_t o = pf[j];
+    for (int32_t q = xadj[o]; q < xadj[o + 1]; ++q) {
+      const int32_t i = ipf[adj[q]];
+      if (i > j && mk[i] != j) { mk[i] = j; s.push_back(i); }
+    }
+    for (int32_t c : kids[j]) {
+      height[j] = std::max(height[j], height[c] + 1);
+      for (int32_t i : st[c])
+        if (i > j && mk[i] != j) { mk[i] = j; s.push_back(i); }
+    }
+    std::sort(s.begin(), s.end());
+    R.nnzL += (int64_t)s.size();
+    R.height = std::max(R.height, height[j] + 1);
+  }
+  // maximal supernodes: j-1 joins j when struct(j-1) = {j} u struct(j)
+  std::vector<LocalSn> fund;
+  for (int32_t j = 0; j < ng; ++j) {
+    const bool join = j > 0 && par[j - 1] == j && st[j - 1].size() == st[j].size() + 1;
+    if (join) {
+      fund.back().c1 = j + 1;
+    } else {
+      LocalSn s;
+      s.c0 = j;
+      s.c1 = j + 1;
+      fund.push_back(std::move(s));
+    }
+  }
+  for (auto& s : fund) s.rows = st[s.c1 - 1];
+  std::vector<std::vector<int32_t>>().swap(st);
+  // relaxed amalgamation of last-child chains
+  std::vector<LocalSn> merged;
+  for (auto& p : fund) {
+    LocalSn cur = std::move(p);
+    while (!merged.empty()) {
+      LocalSn& c = merged.back();
+      if (c.c1 != cur.c0) break;
+      const int32_t pc = par[c.c1 - 1];
+      if (pc < cur.c0 || pc >= cur.c1) break;
+      const int64_t nsc = c.c1 - c.c0, nsp = cur.c1 - cur.c0;
+      const int64_t msc = (int64_t)c.rows.size(), msp = (int64_t)cur.rows.size();
+      const int64_t z = c.zeros + cur.zeros + nsc * (nsp + msp - msc);
+      const int64_t ns = nsc + nsp;
+      const double E = (double)ns * (ns + 1) / 2.0 + (double)ns * msp;
+      if (!(ns <= opt.relax_small || (double)z <= opt.relax_zeros * E)) break;
+      cur.c0 = c.c0;
+      cur.zeros = z;
+      merged.pop_back();
+    }
+    merged.push_back(std::move(cur));
+  }
+  // supernode parents and levels (children precede parents)
+  std::vector<int32_t> lsn(ng, -1);
+  for (int32_t s = 0; s < (int32_t)merged.size(); ++s)
+    for (int32_t j = merged[s].c0; j < merged[s].c1; ++j) lsn[j] = s;
+  R.sn_parent.resize(merged.size());
+  for (size_t s = 0; s < merged.size(); ++s) {
+    const int32_t pc = par[merged[s].c1 - 1];
+    R.sn_parent[s] = pc >= 0 ? lsn[pc] : -1;
+  }
+  R.pf.swap(pf);
+  R.merged.swap(merged);
+  R.lsn.swap(lsn);
+  return std::string();
+}
+
+// Runs body(g) for g = 0..G-1, on up to 16 host threads when there are
+// several instances; each g is run exactly once.
+void for_each_instance(int32_t G, const std::function<void(int32_t)>& body) {
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int32_t T = (int32_t)std::min<unsigned>(std::min<unsigned>(hw, 16u), (unsigned)G);
+  if (T <= 1) {
+    for (int32_t g = 0; g < G; ++g) body(g);
+    return;
+  }
+  std::atomic<int32_t> next(0);
+  std::vector<std::thread> pool;
+  pool.reserve(T);
+  for (int32_t t = 0; t < T; ++t)
+    pool.emplace_back([&]() {
+      for (int32_t g = next.fetch_add(1); g < G; g = next.fetch_add(1)) body(g);
+    });
+  for (auto& th : pool) th.join();
+}
+
+}  // namespace
+
 std::string analyze(int32_t G, const int32_t* n, const int64_t* row_ptr,
                     const int32_t* col, const SymbolicOptions& opt, Symbolic& S) {
   S = Symbolic();
@@ -237,157 +433,22 @@ std::string analyze(int32_t G, const int32_t* n, const int64_t* row_ptr,
   S.iperm.assign(S.N, 0);
   S.col_sn.assign(S.N, -1);
 
+  std::vector<InstanceResult> res(G);
+  for_each_instance(G, [&](int32_t g) {
+    if (n[g] > 0) res[g].err = analyze_instance(n[g], S.inst_off[g], row_ptr, col, opt, res[g]);
+  });
+  for (int32_t g = 0; g < G; ++g)
+    if (!res[g].err.empty()) return res[g].err;
   for (int32_t g = 0; g < G; ++g) {
     const int32_t ng = n[g];
     const int64_t off = S.inst_off[g];
     if (ng == 0) continue;
-    // symmetric adjacency of A + A^T without the diagonal (local indices)
-    std::vector<int32_t> cnt(ng + 1, 0);
-    for (int32_t i = 0; i < ng; ++i)
-      for (int64_t e = row_ptr[off + i]; e < row_ptr[off + i + 1]; ++e) {
-        const int64_t j = (int64_t)col[e] - off;
-        if (j < 0 || j >= ng) return "column index outside its instance block";
-        if (j != i) { ++cnt[i + 1]; ++cnt[j + 1]; }
-      }
-    std::vector<int32_t> xadj(ng + 1, 0);
-    for (int32_t i = 0; i < ng; ++i) xadj[i + 1] = xadj[i] + cnt[i + 1];
-    std::vector<int32_t> adj(xadj[ng]);
-    std::vector<int32_t> fill(xadj.begin(), xadj.end() - 1);
-    for (int32_t i = 0; i < ng; ++i)
-      for (int64_t e = row_ptr[off + i]; e < row_ptr[off + i + 1]; ++e) {
-        const int32_t j = (int32_t)(col[e] - off);
-        if (j != i) { adj[fill[i]++] = j; adj[fill[j]++] = i; }
-      }
-    // sort + unique each list
-    {
-      std::vector<int32_t> x2(ng + 1, 0), a2;
-      a2.reserve(adj.size());
-      for (int32_t i = 0; i < ng; ++i) {
-        auto b = adj.begin() + xadj[i], e = adj.begin() + xadj[i + 1];
-        std::sort(b, e);
-        auto u = std::unique(b, e);
-        a2.insert(a2.end(), b, u);
-        x2[i + 1] = (int32_t)a2.size();
-      }
-      xadj.swap(x2);
-      adj.swap(a2);
-    }
-    std::vector<int32_t> pl;
-    if (opt.ordering == 0) {
-      pl = minimum_degree(ng, xadj, adj);
-    } else {
-      pl.resize(ng);
-      std::iota(pl.begin(), pl.end(), 0);
-    }
-    std::vector<int32_t> ipl(ng);
-    for (int32_t i = 0; i < ng; ++i) ipl[pl[i]] = i;
-    // elimination tree of the permuted pattern
-    std::vector<int32_t> parent(ng, -1), anc(ng, -1);
-    for (int32_t j = 0; j < ng; ++j) {
-      const int32_t o = pl[j];
-      for (int32_t q = xadj[o]; q < xadj[o + 1]; ++q) {
-        int32_t r = ipl[adj[q]];
-        if (r >= j) continue;
-        while (anc[r] != -1 && anc[r] != j) { const int32_t t = anc[r]; anc[r] = j; r = t; }
-        if (anc[r] == -1) { anc[r] = j; parent[r] = j; }
-      }
-    }
-    // postorder (children visited in ascending order)
-    std::vector<int32_t> head(ng, -1), next(ng, -1);
-    for (int32_t j = ng - 1; j >= 0; --j)
-      if (parent[j] >= 0) { next[j] = head[parent[j]]; head[parent[j]] = j; }
-    std::vector<int32_t> post;
-    post.reserve(ng);
-    std::vector<int32_t> stack;
-    for (int32_t r = 0; r < ng; ++r) {
-      if (parent[r] != -1) continue;
-      stack.push_back(r);
-      while (!stack.empty()) {
-        const int32_t v = stack.back();
-        if (head[v] >= 0) {
-          const int32_t c = head[v];
-          head[v] = next[c];
-          stack.push_back(c);
-        } else {
-          stack.pop_back();
-          post.push_back(v);
-        }
-      }
-    }
-    std::vector<int32_t> ipost(ng);
-    for (int32_t k = 0; k < ng; ++k) ipost[post[k]] = k;
-    std::vector<int32_t> pf(ng), ipf(ng), par(ng);
-    for (int32_t k = 0; k < ng; ++k) {
-      pf[k] = pl[post[k]];
-      par[k] = parent[post[k]] >= 0 ? ipost[parent[post[k]]] : -1;
-    }
-    for (int32_t k = 0; k < ng; ++k) ipf[pf[k]] = k;
-    // column structures of L (rows > j) by merging children
-    std::vector<std::vector<int32_t>> st(ng);
-    std::vector<int32_t> mk(ng, -1), height(ng, 0);
-    std::vector<std::vector<int32_t>> kids(ng);
-    for (int32_t j = 0; j < ng; ++j)
-      if (par[j] >= 0) kids[par[j]].push_back(j);
-    for (int32_t j = 0; j < ng; ++j) {
-      std::vector<int32_t>& s = st[j];
-      mk[j] = j;
-      const int32_t o = pf[j];
-      for (int32_t q = xadj[o]; q < xadj[o + 1]; ++q) {
-        const int32_t i = ipf[adj[q]];
-        if (i > j && mk[i] != j) { mk[i] = j; s.push_back(i); }
-      }
-      for (int32_t c : kids[j]) {
-        height[j] = std::max(height[j], height[c] + 1);
-        for (int32_t i : st[c])
-          if (i > j && mk[i] != j) { mk[i] = j; s.push_back(i); }
-      }
-      std::sort(s.begin(), s.end());
-      S.nnzL += (int64_t)s.size();
-      S.etree_height = std::max(S.etree_height, height[j] + 1);
-    }
-    // maximal supernodes: j-1 joins j when struct(j-1) = {j} u struct(j)
-    std::vector<LocalSn> fund;
-    for (int32_t j = 0; j < ng; ++j) {
-      const bool join = j > 0 && par[j - 1] == j && st[j - 1].size() == st[j].size() + 1;
-      if (join) {
-        fund.back().c1 = j + 1;
-      } else {
-        LocalSn s;
-        s.c0 = j;
-        s.c1 = j + 1;
-        fund.push_back(std::move(s));
-      }
-    }
-    for (auto& s : fund) s.rows = st[s.c1 - 1];
-    std::vector<std::vector<int32_t>>().swap(st);
-    // relaxed amalgamation of last-child chains
-    std::vector<LocalSn> merged;
-    for (auto& p : fund) {
-      LocalSn cur = std::move(p);
-      while (!merged.empty()) {
-        LocalSn& c = merged.back();
-        if (c.c1 != cur.c0) break;
-        const int32_t pc = par[c.c1 - 1];
-        if (pc < cur.c0 || pc >= cur.c1) break;
-        const int64_t nsc = c.c1 - c.c0, nsp = cur.c1 - cur.c0;
-        const int64_t msc = (int64_t)c.rows.size(), msp = (int64_t)cur.rows.size();
-        const int64_t z = c.zeros + cur.zeros + nsc * (nsp + msp - msc);
-        const int64_t ns = nsc + nsp;
-        const double E = (double)ns * (ns + 1) / 2.0 + (double)ns * msp;
-        if (!(ns <= opt.relax_small || (double)z <= opt.relax_zeros * E)) break;
-        cur.c0 = c.c0;
-        cur.zeros = z;
-        merged.pop_back();
-      }
-      merged.push_back(std::move(cur));
-    }
-    // supernode parents and levels (children precede parents)
-    std::vector<int32_t> lsn(ng, -1);
-    for (int32_t s = 0; s < (int32_t)merged.size(); ++s)
-      for (int32_t j = merged[s].c0; j < merged[s].c1; ++j) lsn[j] = s;
+    InstanceResult& R = res[g];
+    S.nnzL += R.nnzL;
+    S.etree_height = std::max(S.etree_height, R.height);
     const int32_t base = (int32_t)S.sn.size();
-    for (int32_t s = 0; s < (int32_t)merged.size(); ++s) {
-      const LocalSn& L = merged[s];
+    for (size_t s = 0; s < R.merged.size(); ++s) {
+      const LocalSn& L = R.merged[s];
       Supernode sn;
       sn.c0 = (int32_t)(L.c0 + off);
       sn.c1 = (int32_t)(L.c1 + off);
@@ -395,8 +456,7 @@ std::string analyze(int32_t G, const int32_t* n, const int64_t* row_ptr,
       sn.ms = (int32_t)L.rows.size();
       sn.row_off = (int64_t)S.rows.size();
       for (int32_t r : L.rows) S.rows.push_back((int32_t)(r + off));
-      const int32_t pc = par[L.c1 - 1];
-      sn.parent = pc >= 0 ? base + lsn[pc] : -1;
+      sn.parent = R.sn_parent[s] >= 0 ? base + R.sn_parent[s] : -1;
       S.sn.push_back(sn);
     }
     for (int32_t s = base; s < (int32_t)S.sn.size(); ++s) {
@@ -404,10 +464,11 @@ std::string analyze(int32_t G, const int32_t* n, const int64_t* row_ptr,
       if (p >= 0) S.sn[p].level = std::max(S.sn[p].level, S.sn[s].level + 1);
     }
     for (int32_t k = 0; k < ng; ++k) {
-      S.perm[off + k] = (int32_t)(pf[k] + off);
-      S.iperm[off + pf[k]] = (int32_t)(k + off);
-      S.col_sn[off + k] = base + lsn[k];
+      S.perm[off + k] = (int32_t)(R.pf[k] + off);
+      S.iperm[off + R.pf[k]] = (int32_t)(k + off);
+      S.col_sn[off + k] = base + R.lsn[k];
     }
+    R = InstanceResult();  // release this instance's buffers
   }
 
   const int32_t nS = (int32_t)S.sn.size();
