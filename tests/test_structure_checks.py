@@ -132,3 +132,33 @@ def test_critical_chain_of_the_solve(lib, wl, fronts, blocks):
             depth_f[p] = max(depth_f[p], depth_f[s])
             depth_b[p] = max(depth_b[p], depth_b[s])
     assert (int(depth_f.max()), int(depth_b.max())) == (fronts, blocks)
+
+
+def test_batch_analysis_equals_instance_by_instance(lib, batch):
+    """A batch is analysed on several host threads and merged in instance order:
+    every instance's permutation block and supernodes equal those of the same
+    instance analysed alone (shifted by its offsets)."""
+    insts = batch[:40]
+    sizes, rp, col = _concat(insts)
+    hb = HostSymbolic(lib, sizes, rp, col)
+    try:
+        assert hb.rc == 0
+        perm, c0, c1, ms, rows = hb.perm, hb.c0, hb.c1, hb.ms, hb.rows
+    finally:
+        hb.close()
+    roff = np.concatenate([[0], np.cumsum(ms)])
+    off, s0 = 0, 0
+    for inst in insts:
+        h1 = HostSymbolic(lib, [inst.n], inst.row_ptr, inst.col)
+        try:
+            S1 = len(h1.c0)
+            np.testing.assert_array_equal(perm[off:off + inst.n], h1.perm + off)
+            np.testing.assert_array_equal(c0[s0:s0 + S1], h1.c0 + off)
+            np.testing.assert_array_equal(c1[s0:s0 + S1], h1.c1 + off)
+            np.testing.assert_array_equal(ms[s0:s0 + S1], h1.ms)
+            np.testing.assert_array_equal(rows[roff[s0]:roff[s0 + S1]], h1.rows + off)
+        finally:
+            h1.close()
+        off += inst.n
+        s0 += S1
+    assert s0 == len(c0)
