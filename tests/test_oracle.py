@@ -222,6 +222,49 @@ def test_theorem1_error_order(m):
     assert np.log2(err[0] / err[1]) == pytest.approx(2 * m, abs=0.15)
 
 
+# ------------------------------------------------ spectral radius pins --
+# rho(A^{-1} D) decides where Theorem 1 applies (Sec. II-B) and gates
+# assertions elsewhere, so both of its branches (dense eigenvalues up to
+# n = 1500, Arnoldi above) are pinned to values fixed independently of it.
+@pytest.mark.parametrize("n", [7, 1600])
+def test_spectral_radius_diagonal_closed_form(n):
+    """Diagonal A and D: A^{-1} D = diag(d_i / a_i), so rho = max |d_i / a_i|."""
+    rng = np.random.default_rng(n)
+    a = rng.uniform(0.5, 2.0, n) * rng.choice([-1.0, 1.0], n)
+    d = rng.uniform(0.1, 1.0, n)
+    d[n // 3] = 3.0                        # one clearly dominant ratio
+    A = sp.diags(a).tocsr()
+    assert oracle.spectral_radius(A, d) == pytest.approx(float(np.max(np.abs(d / a))), rel=1e-9)
+
+
+def _complex_pair_system(n):
+    """A, D with A^{-1} D = blockdiag(C, 0.5 I), C = [[1, 4], [-1, 1]] placed on
+    rows/columns (p, q): C has the eigenvalues 1 +- 2i, so rho = sqrt(5), and
+    C is not normal, so a power iteration's norm ratio oscillates."""
+    C_inv = np.linalg.inv(np.array([[1.0, 4.0], [-1.0, 1.0]]))
+    A = np.eye(n) * 2.0                   # A^{-1} D = 0.5 I off the block (D = 1)
+    p, q = (n - 1) // 2, (n - 1) // 2 + 1
+    A[np.ix_([p, q], [p, q])] = C_inv
+    return A, np.ones(n)
+
+
+@pytest.mark.parametrize("n", [2, 1600])
+def test_spectral_radius_complex_dominant_pair(n):
+    A, D = _complex_pair_system(n)
+    assert oracle.spectral_radius(A, D) == pytest.approx(np.sqrt(5.0), rel=1e-9)
+
+
+def test_spectral_radius_arnoldi_branch_matches_dense_eigenvalues():
+    """Just above the branch point, the Arnoldi estimate equals the largest
+    |eigenvalue| of the dense A^{-1} D computed by LAPACK."""
+    inst = pfgen.random_sparse(1550, 0.004, seed=77, diag_boost=1.0)
+    A = oracle.to_dense(inst)
+    rng = np.random.default_rng(5)
+    D = rng.uniform(0.2, 2.0, inst.n)
+    ref = float(np.max(np.abs(np.linalg.eigvals(np.linalg.solve(A, np.diag(D))))))
+    assert oracle.spectral_radius(sp.csr_matrix(A), D) == pytest.approx(ref, rel=1e-8)
+
+
 def test_error_falls_with_order_inside_convergence_region():
     A, D, b = _well_posed()
     rho = oracle.spectral_radius(A, D)
