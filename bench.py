@@ -4,16 +4,19 @@
 A step is one pass of the whole hot path over one batch of synthetic
 power-flow Jacobians already resident in HBM: perturb + pivot-free factor of
 all K shifted matrices, forward/backward solves of R right-hand sides, FP64
-residual sweeps (FP32 factors) and the expansion-weighted FP64 combine.  The
+residual sweeps (FP32 factors) and the expansion-weighted FP64 combine, as
+one replay of the CUDA graph the library captured (pisp_graph_capture).  The
 metric counts combined solutions x_hat (instances x RHS) per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
   python bench.py --impl reference ...    # the CPU oracle on bounded samples
+  python bench.py --study dense|newton    # timing tables of next rows f4 / f2
 
-Workloads (pfgen.CONFIGS): precision (default: 2000-bus grid, K = 6, R = 16,
-FP32 factors + FP64 sweeps/combine), plain, batching, differentiation, scale.
-Under torchrun every rank solves its own independent replica of the workload
-(weak scaling, no collective on the data path); rank 0 prints one JSON line.
+Workloads (pfgen.CONFIGS): batching (default: 256 grids of 118-3000 buses,
+K = 4, R = 8, FP32 factors + FP64 sweeps/combine), plain, precision,
+differentiation, scale.  Under torchrun every rank solves its own independent
+replica of the workload (weak scaling, no collective on the data path); rank
+0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -39,11 +42,10 @@ UNIT = "solves/s"
 TOL = 1e-10
 L2_BYTES = 129 * 1024 * 1024
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel family
-# on a workload, from an ncu capture of that kernel on that workload; an entry
-# is removed when its kernel changes.
+# on a workload, from an ncu capture of that kernel on that workload (scaled
+# to the full workload where the capture ran a reduced batch); an entry is
+# removed when its kernel changes.
 TRAFFIC_PER_LAUNCH = {
-    ("precision", "forward"): 7.163e6,
-    ("precision", "backward"): 12.894e6,
 }
 
 BENCH = {
@@ -61,7 +63,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="pisp", choices=["pisp", "reference"])
-    ap.add_argument("--workload", default="precision", choices=list(pfgen.CONFIGS))
+    ap.add_argument("--workload", default="batching", choices=list(pfgen.CONFIGS))
+    ap.add_argument("--instances", type=int, default=None,
+                    help="batching only: the first G grids of the 256 (reduced batches for profiler captures)")
+    ap.add_argument("--study", default=None, choices=["dense", "newton"],
+                    help="timing study of next row f4 (dense batches vs n and G) or f2 (Newton loop)")
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
     ap.add_argument("--sweeps", type=int, default=None)
     ap.add_argument("--eps", type=float, default=1e-2)
@@ -79,12 +85,13 @@ def parse():
 
 
 # ----------------------------------------------------------------- inputs --
-def workload_instances(name: str, rank: int):
+def workload_instances(name: str, rank: int, G: int | None = None):
     c = pfgen.CONFIGS[name]
     if name == "batching":
         sizes = pfgen.batch_sizes(c["G"])
+        G = c["G"] if G is None else max(1, min(int(G), c["G"]))
         insts = [pfgen.grid_jacobian(int(sizes[g]), None, 1000 * c["index"] + g + 100_000 * rank)
-                 for g in range(c["G"])]
+                 for g in range(G)]
     else:
         insts = [pfgen.grid_jacobian(c["N"], c.get("n_pv"), 1000 * c["index"] + 100_000 * rank)]
     return insts
@@ -180,55 +187,65 @@ class Arm:
             self.g = torch.tensor(pfgen.rhs(self.N, R, 2), device=dev)
             self.gb = torch.empty_like(self.b)
             self.gv = torch.empty_like(self.vals)
-        self.graph = None
+        self.graph = False
 
     def step(self):
         s = self.s
         s.factor(self.vals, self.D, self.t, self.precision)
         s.solve(self.b, sweeps=self.sweeps, out=self.x)
         if self.adjoint:
-            s.adjoint(self.g, out_b=self.gb, out_values=self.gv)
+            s.adjoint(self.g, out_b=self.gb, out_values=self.gv, sweeps=self.sweeps)
 
     def capture(self, profile: bool):
-        torch = self.torch
-        self.step()                      # allocate workspaces before capture
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        st = torch.cuda.Stream()
-        st.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(st):
-            if profile:
-                self.s.profile(True)
-            with torch.cuda.graph(g, stream=st):
-                self.step()
-            if profile:
-                self.s.profile(False)
-        torch.cuda.current_stream().wait_stream(st)
-        torch.cuda.synchronize()
-        self.graph = g
+        """The whole step captured by the library (pisp_graph_capture); with
+        profile, the per-family event brackets are recorded into the graph."""
+        if profile:
+            self.s.profile(True)
+        kw = dict(g=self.g, out_b=self.gb, out_values=self.gv, adjoint_sweeps=self.sweeps) if self.adjoint else {}
+        self.s.graph_capture(self.vals, self.D, self.t, self.b, self.x, precision=self.precision,
+                             sweeps=self.sweeps, **kw)
+        if profile:
+            self.s.profile(False)
+        self.torch.cuda.synchronize()
+        self.graph = True
 
     def run(self):
-        if self.graph is not None:
-            self.graph.replay()
+        if self.graph:
+            self.s.graph_launch()
         else:
             self.step()
 
 
-def oracle_err(arm, sample_rhs=2, sample_inst=3):
-    """Max relative error of the last x against the CPU oracle on a sample."""
+def _entrywise(x, ref):
+    """Per right-hand side: max_i |x_ir - ref_ir| / max_i |ref_ir|."""
+    scale = np.abs(ref).max(axis=0)
+    scale = np.where(scale > 0, scale, 1.0)
+    return np.max(np.abs(x - ref), axis=0) / scale
+
+
+def oracle_check(arm, max_instances=12):
+    """Error of the last x against the CPU oracle for every right-hand side of a
+    sample of instances spread over the size range (smallest and largest
+    included): entry-wise (max |x - ref| / max |ref| per RHS) and normwise."""
     import oracle
     x = arm.x.cpu().numpy()
     offs = np.concatenate([[0], np.cumsum([I.n for I in arm.insts])])
     G = len(arm.insts)
-    pick = sorted(set([0, G // 2, G - 1][:sample_inst]))
-    cols = list(range(min(sample_rhs, arm.R)))
-    err = 0.0
+    order = np.argsort([I.n for I in arm.insts], kind="stable")
+    pick = sorted(set(int(order[i]) for i in np.linspace(0, G - 1, min(G, max_instances)).round().astype(int)))
+    per = []
     for g in pick:
         I = arm.insts[g]
         sl = slice(offs[g], offs[g + 1])
-        ref = oracle.x_hat(oracle.to_scipy(I), I.D, arm.t, arm.b_host[sl][:, cols])
-        err = max(err, float(np.max(oracle.rel_err(x[sl][:, cols], ref))))
-    return err
+        ref = oracle.x_hat(oracle.to_scipy(I), I.D, arm.t, arm.b_host[sl])
+        ew = _entrywise(x[sl], ref)
+        nw = oracle.rel_err(x[sl], ref)
+        per.append({"instance": g, "n": I.n, "entrywise": [float(f"{v:.3e}") for v in ew],
+                    "normwise": [float(f"{v:.3e}") for v in nw]})
+    mx = max(max(p["entrywise"]) for p in per)
+    return {"tol": TOL, "instances": len(pick), "results": sum(len(p["entrywise"]) for p in per),
+            "max_entrywise": mx, "max_normwise": max(max(p["normwise"]) for p in per),
+            "all_within_tol": bool(mx <= TOL), "per_instance": per}
 
 
 def cpu_baseline(insts, K, R, eps, budget_s=12.0):
@@ -252,6 +269,27 @@ def cpu_baseline(insts, K, R, eps, budget_s=12.0):
                       f"{elapsed:.1f} s of CPU work (numpy/LAPACK, BLAS threads = host cores)"}
 
 
+def min_bytes_per_launch(fam, st, K, R, p):
+    """Minimum data one launch of a kernel family must move (the algorithmic
+    bytes of the roofline): factor entries of the triangle it uses for all K
+    shifts, their int32 indices read ONCE for all K, the vectors in and out.
+    nnzU = (nnzF + N) / 2 entries of U (diagonal included), nnzL = (nnzF - N) / 2
+    entries strictly below it.  None for the factor families (several launches
+    per step, each over part of the fronts: the library's per-launch count is
+    used there)."""
+    N, nnzA, nnzF = float(st["N"]), float(st["nnzA"]), float(st["nnzF_stored"])
+    nnzU, nnzL = (nnzF + N) / 2, (nnzF - N) / 2
+    if fam == "backward":       # U factors, indices, y in (factor precision), x out (FP64)
+        return K * p * nnzU + 4 * nnzU + K * p * N * R + 8 * N * R
+    if fam == "forward":        # L factors, indices, b in (FP64), y out (factor precision)
+        return K * p * nnzL + 4 * nnzL + 8 * N * R + K * p * N * R
+    if fam == "residual":       # A values + columns, b, the K solutions in, K residuals out
+        return 12 * nnzA + 8 * N * R + 16 * N * K * R
+    if fam == "combine":        # K solutions in, x out
+        return 8 * N * K * R + 8 * N * R
+    return None
+
+
 def run_pisp(args, rank, world, local_rank):
     import torch
     import __graft_entry__
@@ -267,7 +305,7 @@ def run_pisp(args, rank, world, local_rank):
     if precision == "fp64" and args.sweeps is None:
         sweeps = 0
     K, R = c["K"], c["R"]
-    insts = workload_instances(args.workload, rank)
+    insts = workload_instances(args.workload, rank, args.instances)
     tuned = None
     if args.autotune:
         from paper_2311_11833_gb300 import tune
@@ -325,21 +363,32 @@ def run_pisp(args, rank, world, local_rank):
         arm.s.profile(False)
     if rank != 0:
         return None
-    # roofline of the dominant kernel family
+    # roofline of the dominant kernel family: minimum bytes per launch over the
+    # family's average launch time (CUDA events on the library's stream)
     peak, peak_kind = load_peaks()
     fam = max(prof, key=lambda f: prof[f]["ms"])
     pf = prof[fam]
-    achieved = pf["bytes"] / (pf["ms"] / 1e3) / 1e9 if pf["ms"] > 0 else 0.0
-    traffic = TRAFFIC_PER_LAUNCH.get((args.workload, fam))
+    p = 4 if precision == "fp32" else 8
+    launch_ms = pf["ms"] / max(1, pf["launches"])
+    lib_bytes = pf["bytes"] / max(1, pf["launches"])
+    mb = min_bytes_per_launch(fam, stats, K, R, p)
+    alg = mb if mb is not None else lib_bytes
+    achieved = alg / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else 0.0
+    traffic = TRAFFIC_PER_LAUNCH.get((args.workload, fam, G))
     roofline = {"bound": "hbm", "kernel": fam, "achieved": round(achieved, 2), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 5), "peak_source": peak_kind,
-                "traffic": traffic,
-                "algorithmic_bytes_per_launch": pf["bytes"] / max(1, pf["launches"]),
-                "avg_launch_us": 1e3 * pf["ms"] / max(1, pf["launches"]),
+                "traffic": traffic, "algorithmic_bytes_per_launch": alg,
+                "algorithmic_bytes_rule": "minimum (indices once for all K)" if mb is not None
+                else "library count",
+                "library_bytes_per_launch": lib_bytes,
+                "avg_launch_us": round(1e3 * launch_ms, 3),
                 "share_of_step": round(pf["ms"] / total_ms, 4) if world == 1 else None}
     families = {f: {"ms_per_step": round(v["ms"] / args.steps, 4),
-                    "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 2) if v["ms"] > 0 else 0.0,
-                    "launches_per_step": v["launches"] / args.steps} for f, v in prof.items()}
+                    "launches_per_step": v["launches"] / args.steps,
+                    "min_GBps": (round(min_bytes_per_launch(f, stats, K, R, p) / (v["ms"] / v["launches"] / 1e3) / 1e9, 2)
+                                 if v["ms"] > 0 and min_bytes_per_launch(f, stats, K, R, p) is not None else None),
+                    "library_GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 2) if v["ms"] > 0 else 0.0}
+                for f, v in prof.items() if v["launches"] > 0}
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
@@ -349,7 +398,8 @@ def run_pisp(args, rank, world, local_rank):
         "config": {"workload": args.workload, "instances": G, "N": arm.N, "nnzA": int(stats["nnzA"]),
                    "K": K, "R": R, "shifts": "symmetric +-eps*alpha", "eps": args.eps,
                    "factor_precision": precision, "combine_precision": "fp64", "sweeps": sweeps,
-                   "graph": use_graph, "solve_schedule": ["persistent", "per-level"][args.schedule],
+                   "graph": "library (pisp_graph_capture)" if use_graph else None,
+                   "solve_schedule": ["persistent", "per-level"][args.schedule],
                    "factor_policy": ["single-CTA/column-block-owners", "clusters", "single-CTA/tile-DAG", "single-CTA/per-panel"][args.factor_policy], "l2": "flushed between steps (256 MB write outside the events)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
@@ -368,13 +418,13 @@ def run_pisp(args, rank, world, local_rank):
     if clk:
         out["clocks"] = clk
     if not args.quick:
-        out["max_rel_err_vs_oracle"] = oracle_err(arm)
+        chk = oracle_check(arm)
+        out["oracle_check"] = chk
+        out["max_rel_err_vs_oracle"] = chk["max_entrywise"]
         # plain FP64 single-instance path: FP64 factors, no sweeps, instances
         # one after another, eager launches, no graph
         plain_ms = []
-        plain_err = 0.0
-        arms = [Arm(pisp, torch, [I], K, R, args.eps, "fp64", 0, args.workload, dev)
-                for I in (insts if G <= 8 else insts)]
+        arms = [Arm(pisp, torch, [I], K, R, args.eps, "fp64", 0, args.workload, dev) for I in insts]
         n_plain_steps = 5 if G > 1 else min(args.steps, 20)
         for a in arms:
             a.step()
@@ -388,13 +438,15 @@ def run_pisp(args, rank, world, local_rank):
             e1.record()
             e1.synchronize()
             plain_ms.append(e0.elapsed_time(e1))
-        plain_err = max(oracle_err(a) for a in arms[:1])
+        plain_err = oracle_check(arms[0], 1)["max_entrywise"]
         pv = units / (statistics.mean(plain_ms) / 1e3)
         out["plain_fp64_path"] = {"value": round(pv, 2), "ms_per_step": round(statistics.mean(plain_ms), 4),
                                   "steps": n_plain_steps, "max_rel_err_vs_oracle": plain_err,
                                   "speedup_of_value": round(value / world / pv, 3)}
         del arms
-        # end to end through the public API with host buffers (pinned), copies inside
+        # end to end through the public API with host buffers (pinned): the
+        # host-to-device copies of values, D and b, the factorisation, the
+        # solve and the device-to-host copy of x, L2 flushed before each step
         sizes, rp, col, val, D = concat(insts)
         hv = torch.tensor(val).pin_memory().numpy()
         hD = torch.tensor(D).pin_memory().numpy()
@@ -402,16 +454,115 @@ def run_pisp(args, rank, world, local_rank):
         hx = torch.empty(arm.b_host.shape, dtype=torch.float64).pin_memory().numpy()
         e2e_steps = min(args.steps, 20)
         arm.s.solve_host(hv, hD, arm.t, hb, precision, sweeps, out=hx)
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
+        e2e_total = 0.0
+        for i in range(e2e_steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             arm.s.solve_host(hv, hD, arm.t, hb, precision, sweeps, out=hx)
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
+            e2e_total += time.perf_counter() - t0
+        e2e_s = e2e_total / e2e_steps
         out["e2e"] = {"value": round(units * world / e2e_s, 2), "unit": UNIT,
                       "h2d_bytes_per_step": int(hv.nbytes + hD.nbytes + hb.nbytes),
                       "d2h_bytes_per_step": int(hx.nbytes), "ms_per_step": round(e2e_s * 1e3, 4),
-                      "path": "pisp_solve_host: pinned host buffers, H2D + factor + solve + D2H, eager"}
+                      "path": "pisp_solve_host: pinned host buffers, H2D + factor + solve + D2H, eager, "
+                              "L2 flushed before each step"}
         out["cpu_baseline"] = cpu_baseline(insts, K, R, args.eps)
     return out
+
+
+# ----------------------------------------------------------------- studies --
+def _dense_instance(n, seed):
+    return pfgen.random_sparse(n, 1.0, seed=seed, diag_boost=2.0 * math.sqrt(n))
+
+
+def study_dense(args):
+    """Next row f4: dense batches of G systems of size n, K = 10 shifts, one RHS,
+    FP64: time of one captured factor + solve step against n and G (the
+    flatness in the batch size the paper reports for its batched LU, Sec. IV)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2311_11833_gb300 as pisp
+    dev = torch.device("cuda", 0)
+    K, R = 10, 1
+    rows = []
+    clocks = ClockSampler(0)
+    for n in (64, 150, 300, 531):
+        for G in (1, 2, 4, 8, 16):
+            insts = [_dense_instance(n, 1000 * n + g) for g in range(G)]
+            arm = Arm(pisp, torch, insts, K, R, args.eps, "fp64", 0, "dense", dev)
+            arm.capture(profile=True)
+            for _ in range(3):
+                arm.run()
+            torch.cuda.synchronize()
+            arm.s.profile_reset()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 20
+            e0.record()
+            for _ in range(reps):
+                arm.run()
+                arm.s.profile_collect()
+            e1.record()
+            e1.synchronize()
+            prof = arm.s.profile_read()
+            fac = (prof["factor_small"]["ms"] + prof["factor_big"]["ms"]) / reps
+            sol = (prof["forward"]["ms"] + prof["backward"]["ms"]) / reps
+            rows.append({"n": n, "G": G, "ms_step": round(e0.elapsed_time(e1) / reps, 4),
+                         "ms_factor": round(fac, 4), "ms_solve": round(sol, 4)})
+            arm.s.close()
+    clk = clocks.stop()
+    return {"study": "dense batches (next row f4)", "K": K, "R": R, "precision": "fp64",
+            "shifts": "symmetric +-eps*alpha", "eps": args.eps,
+            "family": "Gaussian, diagonal +-2 sqrt(n) (dense)", "timing": "CUDA events over 20 graph replays",
+            "table": rows, "clocks": clk}
+
+
+def study_newton(args):
+    """Next row f2: the Newton-Raphson power-flow loop, analysed once and
+    refactored every iteration: per-iteration host Jacobian time, device
+    factor + solve time (CUDA events) and wall time, to max |F| <= 1e-10."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2311_11833_gb300 as pisp
+    dev = torch.device("cuda", 0)
+    cases = [("300-bus", 300, 60, 7, 1.0, 1e-3), ("2000-bus", 2000, 400, 2001, 1.0, 1e-3)]
+    out = []
+    clocks = ClockSampler(0)
+    for name, N, npv, seed, ang, eps in cases:
+        c = pfgen.power_flow_case(N, npv, seed=seed, angle_scale=ang)
+        for precision, sweeps in (("fp64", 0), ("fp32", 2)):
+            s = pisp.Solver(c.n, c.row_ptr, c.col, device=0)
+            t = pfgen.symmetric_shifts(4, eps)
+            x = c.flat_start()
+            its = []
+            for it in range(25):
+                w0 = time.perf_counter()
+                F = c.mismatch(x)
+                r = float(np.max(np.abs(F)))
+                if r <= 1e-10:
+                    break
+                h0 = time.perf_counter()
+                vals = c.jacobian(x)
+                D = pfgen.diag_rule(c.n, c.row_ptr, c.col, vals)
+                h1 = time.perf_counter()
+                vt, Dt, Ft = (torch.tensor(a, device=dev) for a in (vals, D, F))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                s.factor(vt, Dt, t, precision)
+                dx = s.solve(Ft, sweeps=sweeps)
+                e1.record()
+                dxh = dx.cpu().numpy()
+                x = x - dxh
+                its.append({"max_F": float(f"{r:.3e}"), "host_jacobian_ms": round(1e3 * (h1 - h0), 3),
+                            "device_factor_solve_ms": round(e0.elapsed_time(e1), 4),
+                            "wall_ms": round(1e3 * (time.perf_counter() - w0), 3)})
+            out.append({"case": name, "n": c.n, "nnz": c.nnz, "precision": precision, "sweeps": sweeps,
+                        "eps": eps, "K": 4, "iterations": len(its),
+                        "converged": bool(np.max(np.abs(c.mismatch(x))) <= 1e-10), "per_iteration": its})
+            s.close()
+    return {"study": "Newton-Raphson loop (next row f2)", "tol": 1e-10, "cases": out, "clocks": clocks.stop()}
 
 
 def run_reference(args, rank, world):
@@ -421,7 +572,7 @@ def run_reference(args, rank, world):
     import oracle
     c = pfgen.CONFIGS[args.workload]
     K, R = c["K"], c["R"]
-    insts = workload_instances(args.workload, 0)
+    insts = workload_instances(args.workload, 0, args.instances)
     t = pfgen.symmetric_shifts(K, args.eps)
     beta = oracle.weights_float(list(t))
     G = len(insts)
@@ -464,7 +615,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
+    if args.study:
+        out = (study_dense if args.study == "dense" else study_newton)(args) if rank == 0 else None
+    elif args.impl == "reference":
         out = run_reference(args, rank, world)
     else:
         if world > 1:

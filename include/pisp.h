@@ -82,6 +82,11 @@ typedef struct pisp_options {
                              3 = as 0 but larger fronts by a blocked factorisation
                              in global memory (one panel launch and one
                              tiled-update launch per 32 pivots) */
+  int32_t analyze_threads; /* host threads pisp_analyze may use for the instances
+                              of a batch: 0 = the hardware concurrency, at most
+                              16 (default); 1 = the calling thread only.  A
+                              caller that already analyses patterns from
+                              several threads should cap this. */
 } pisp_options;
 
 typedef struct pisp_stats {
@@ -195,7 +200,8 @@ int pisp_combine(pisp_handle* h, const double* w, double* x);
 int pisp_refine(pisp_handle* h, const double* b, double* x, int32_t R, int32_t iters,
                 int32_t sweeps);
 
-/* Reverse mode of x = sum_k beta_k (A + t_k D)^{-1} b for the last pisp_solve:
+/* Reverse mode of x = sum_k beta_k (A + t_k D)^{-1} b for the last pisp_solve
+ * (the derivative of Eq. x_star with respect to b and to A's entries):
  *   lambda_k = (A + t_k D)^{-T} g,  grad_b = sum_k beta_k lambda_k,
  *   grad_values[e] = - sum_k beta_k sum_r lambda_k[i_e][r] x_k[j_e][r]
  * on A's pattern (D held fixed), using the same factors transposed.
@@ -204,11 +210,16 @@ int pisp_refine(pisp_handle* h, const double* b, double* x, int32_t R, int32_t i
  *   grad_values device FP64 [nnz] output, or NULL
  *   w           host FP64 [K] or NULL (pisp_weights(t)): the combination used
  *               in the forward pass.
+ *   sweeps      FP64 residual corrections of every lambda_k on the transposed
+ *               system, lambda_k += (L_k U_k)^{-T} (g - (A + t_k D)^T lambda_k),
+ *               as pisp_solve's sweeps do for x_k; with FP32 factors they make
+ *               the gradients agree with the FP64 definition (0: one
+ *               transposed solve, FP32 accuracy with FP32 factors).
  * R is that of the last pisp_solve.  Returns PISP_ERR_NOT_FACTORED when no
- * kept solutions exist, PISP_ERR_INVALID_ARG for a NULL g, PISP_ERR_OOM if its
- * workspace cannot be allocated. */
+ * kept solutions exist, PISP_ERR_INVALID_ARG for a NULL g or sweeps < 0,
+ * PISP_ERR_OOM if its workspace cannot be allocated. */
 int pisp_adjoint(pisp_handle* h, const double* g, const double* w, double* grad_b,
-                 double* grad_values);
+                 double* grad_values, int32_t sweeps);
 
 /* Host helper: per-solve weights for distinct shifts t[K] (Remark 2 written
  * for arbitrary shifts): beta_k = prod_{l != k} t_l / (t_l - t_k), the unique
@@ -229,6 +240,48 @@ int pisp_weights(const double* t, int32_t K, double* beta);
  * Returns PISP_ERR_INVALID_ARG for a bad pattern or a structurally singular
  * one (no matching covers every column; pisp_last_error(NULL) says which). */
 int pisp_match_rows(int32_t n, const int64_t* row_ptr, const int32_t* col_idx, int32_t* row_perm);
+
+/* Batch solving under a CUDA graph (Sec. I, Alg. 1 run repeatedly on new
+ * values, as in the Newton-Raphson use of Sec. IV): captures one whole step
+ *   pisp_factor_perturbed(values, D, t, K, precision);
+ *   pisp_solve(b, R, w, x, sweeps);
+ *   and, if g != NULL, pisp_adjoint(g, w, grad_b, grad_values, adjoint_sweeps)
+ * into a CUDA graph owned by the handle.  The step runs once eagerly first
+ * (it checks the arguments, allocates every workspace and leaves its
+ * results), then is captured on a private stream ordered after the work
+ * already queued on the handle's stream.  pisp_graph_launch replays it on the
+ * handle's stream: each replay reads the CURRENT contents of values, D, b and
+ * g and writes x, grad_b and grad_values, so a caller updates those buffers
+ * in place (same pointers) and replays.  t, K, precision, R, w and the sweep
+ * counts are fixed at capture.  The buffers must stay allocated while the
+ * graph is used.  The graph stays valid until the next pisp_analyze,
+ * pisp_factor_perturbed, pisp_solve, pisp_refine, pisp_solve_host,
+ * pisp_set_wait_limit or pisp_graph_capture on the handle (those may
+ * rebuild the schedules or workspace the graph refers to); pisp_combine,
+ * pisp_adjoint and the queries keep it.  Returns the error of the eager step,
+ * or PISP_ERR_CUDA if the capture fails. */
+int pisp_graph_capture(pisp_handle* h, const double* values, const double* D, const double* t,
+                       int32_t K, int32_t precision, const double* b, int32_t R, const double* w,
+                       double* x, int32_t sweeps, const double* g, double* grad_b, double* grad_values,
+                       int32_t adjoint_sweeps);
+
+/* Replays the captured step on the handle's stream.  Returns
+ * PISP_ERR_INVALID_ARG when no valid captured step exists. */
+int pisp_graph_launch(pisp_handle* h);
+
+/* The bounded device waits (no counterpart in the paper).  Every dependency
+ * wait of the persistent solves polls a completion counter at most `polls`
+ * times (about 64 ns apart) and then gives up: it records the failure, the
+ * task goes on with whatever data is there, the launch ends normally, and
+ * pisp_get_status returns PISP_ERR_TIMEOUT until the next
+ * pisp_factor_perturbed clears the record.  polls = 0 restores the default
+ * (2^22 polls, a few tenths of a second per wait).  unreachable != 0 is a test
+ * hook: the next solves also wait on one completion target raised by one, which
+ * no task ever reaches, so that a wait runs out on purpose (results of those
+ * solves are not valid); unreachable = 0 restores the true targets.  Applies
+ * from the next pisp_solve / pisp_refine.  Returns PISP_ERR_INVALID_ARG for
+ * polls < 0. */
+int pisp_set_wait_limit(pisp_handle* h, int64_t polls, int32_t unreachable);
 
 /* Synchronises the stream and copies host [G*K] status codes of the last
  * factorisation: 0 ok, PISP_ERR_ZERO_PIVOT or PISP_ERR_NONFINITE.  If
@@ -307,7 +360,10 @@ int pisp_solve_host(pisp_handle* h, const double* values_host, const double* D_h
  * array, which keeps the last call's contents; each call overwrites the part
  * it reads, but calls that overlap on the GPU (other streams or host threads)
  * race on it, so order them on one stream.  A zero pivot is not reported:
- * it shows as Inf/NaN in x. */
+ * it shows as Inf/NaN in x.  If a CUDA error is already pending on the
+ * calling host thread, the call returns PISP_ERR_CUDA without launching and
+ * leaves that error for the caller (cudaGetLastError still returns it); a
+ * failed launch returns PISP_ERR_CUDA with nothing further enqueued. */
 int pisp_dense_solve_static(void* stream, int32_t n, const double* A, const double* D,
                             const double* t, int32_t K, const double* b, int32_t R, double* x);
 

@@ -27,7 +27,7 @@ K_MAX = 16
 
 class PispOptions(ctypes.Structure):
     _fields_ = [("ordering", c_int32), ("relax_small", c_int32), ("relax_zeros", c_double),
-                ("solve_schedule", c_int32), ("factor_policy", c_int32)]
+                ("solve_schedule", c_int32), ("factor_policy", c_int32), ("analyze_threads", c_int32)]
 
 
 class PispStats(ctypes.Structure):
@@ -53,7 +53,12 @@ _SIGS = {
     "pisp_solve": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_int32]),
     "pisp_combine": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "pisp_refine": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32]),
-    "pisp_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "pisp_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32]),
+    "pisp_graph_capture": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p,
+                                     c_int32, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p,
+                                     c_int32]),
+    "pisp_graph_launch": (c_int32, [c_void_p]),
+    "pisp_set_wait_limit": (c_int32, [c_void_p, c_int64, c_int32]),
     "pisp_weights": (c_int32, [c_void_p, c_int32, c_void_p]),
     "pisp_match_rows": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p]),
     "pisp_get_status": (c_int32, [c_void_p, c_void_p, c_void_p]),

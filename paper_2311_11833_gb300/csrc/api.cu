@@ -7,6 +7,8 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -58,13 +60,17 @@ struct pisp_handle {
   // device symbolic
   Buf c0, ns, ms, inst, front_off, vec_off, row_off, child_off, child, amap_off, amap_src,
       amap_dst, amap_coff, rows, emap, perm, iperm, row_inst, row_ptr, col, parent, inv_off, inv_child, inv_a, inv_vbase,
-      inv_cF, inv_col;
+      inv_cF, inv_col, at_ptr, at_row, at_src;
   // persistent solve schedule (depends on K and R)
   int32_t schedule = 0;
   int32_t factor_policy = 0;
   int32_t units_K = 0, units_R = 0;
   int32_t n_units_f = 0, n_units_b = 0, units_maxF = 0;
   Buf units_f, units_b, ticket, done, serr, nch;
+  // bounded waits of the persistent solves: polls before giving up (0 = the
+  // default), and the test hook that makes one dependency unreachable
+  int64_t wait_polls = 0;
+  int32_t wait_unreachable = 0;
   pisp::SymDev sd{};
   // level plans (depend on the factor precision)
   int plan_precision = 0;
@@ -84,6 +90,20 @@ struct pisp_handle {
   // host-buffer entry point staging
   Buf in_vals, in_D, in_b, out_x;
   int launches = 0;
+  // library-owned CUDA graph of one factor + solve step (pisp_graph_capture)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t cap_ev = nullptr;
+  bool graph_valid = false;
+  bool capturing = false;  // inside pisp_graph_capture's own factor + solve calls
+  void drop_graph() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (graph) cudaGraphDestroy(graph);
+    graph_exec = nullptr;
+    graph = nullptr;
+    graph_valid = false;
+  }
   // profiling: CUDA events bracketing each kernel family per level
   struct Bracket {
     int fam, e0, e1, launches;
@@ -102,6 +122,9 @@ struct pisp_handle {
   cudaStream_t side[kSide] = {}, big_side = nullptr;  // big_side: the level's wide fronts
   cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {}, big_join = nullptr;
   ~pisp_handle() {
+    drop_graph();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (cap_ev) cudaEventDestroy(cap_ev);
     for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
     for (int i = 0; i < kSide; ++i) {
       if (side[i]) cudaStreamDestroy(side[i]);
@@ -371,6 +394,16 @@ int build_units(pisp_handle* h, int32_t K, int32_t R) {
         U.push_back({kind, (int32_t)G.off, (int32_t)b, (int32_t)segs, 0});
     }
   }
+  if (h->wait_unreachable) {
+    // test hook: one front's completion target can never be reached, so the
+    // waits on it (its parent's in the forward pass, its children's in the
+    // backward pass) run out of polls
+    for (size_t q = 0; q < S.sn.size(); ++q)
+      if (S.sn[q].parent >= 0) {
+        nch[q] += 1;
+        break;
+      }
+  }
   std::vector<pisp::SolveUnit> f, b;
   for (int l = 0; l < S.n_levels; ++l) f.insert(f.end(), per_level[l].begin(), per_level[l].end());
   for (int l = S.n_levels - 1; l >= 0; --l) b.insert(b.end(), per_level[l].begin(), per_level[l].end());
@@ -476,7 +509,8 @@ int solve_pass(pisp_handle* h, bool trans, const double* rhs, int rhs_mode, doub
     int n = pisp::launch_solve_persistent(h->precision, true, h->sd, h->units_f.as<pisp::SolveUnit>(),
                                           h->n_units_f, h->ticket.as<int>(), h->done.as<int>(),
                                           h->serr.as<int>(), h->nch.as<int>(), h->d_all.as<int32_t>(), h->fronts.p, rhs,
-                                          rhs_mode, h->V.p, out, acc, R, h->K, h->units_maxF, h->stream);
+                                          rhs_mode, h->V.p, out, acc, R, h->K, h->units_maxF, h->wait_polls,
+                                          h->stream);
     TRY(count(h, n));
     prof_end(h, pb, PISP_PROF_FORWARD, bf, n);
     CK(cudaMemsetAsync(h->done.p, 0, nd, h->stream));
@@ -484,7 +518,8 @@ int solve_pass(pisp_handle* h, bool trans, const double* rhs, int rhs_mode, doub
     n = pisp::launch_solve_persistent(h->precision, false, h->sd, h->units_b.as<pisp::SolveUnit>(),
                                       h->n_units_b, h->ticket.as<int>() + 1, h->done.as<int>(),
                                       h->serr.as<int>(), h->nch.as<int>(), h->d_all.as<int32_t>(), h->fronts.p, rhs,
-                                      rhs_mode, h->V.p, out, acc, R, h->K, h->units_maxF, h->stream);
+                                      rhs_mode, h->V.p, out, acc, R, h->K, h->units_maxF, h->wait_polls,
+                                      h->stream);
     TRY(count(h, n));
     prof_end(h, pb, PISP_PROF_BACKWARD, bb, n);
     return PISP_OK;
@@ -579,10 +614,14 @@ int pisp_set_stream(pisp_handle* h, void* stream) {
   return PISP_OK;
 }
 
-int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row_ptr,
+}  // extern "C"
+
+namespace {
+
+int analyze_impl(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row_ptr,
                  const int32_t* col_idx, const pisp_options* opt) {
-  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
   NvtxRange nvtx_("pisp_analyze");
+  h->drop_graph();
   DeviceScope dev_scope_;
   if (G < 1 || !n || !row_ptr) return fail(h, PISP_ERR_INVALID_ARG, "bad instance description");
   int64_t N = 0;
@@ -608,6 +647,8 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
     so.ordering = opt->ordering;
     if (opt->relax_small >= 0) so.relax_small = opt->relax_small;
     if (opt->relax_zeros >= 0) so.relax_zeros = opt->relax_zeros;
+    if (opt->analyze_threads < 0) return fail(h, PISP_ERR_INVALID_ARG, "analyze_threads must be >= 0");
+    so.threads = opt->analyze_threads;
   }
   h->analyzed = h->factored = h->solved = false;
   h->plan_precision = 0;
@@ -668,6 +709,24 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   TRY(upload(h, h->inv_vbase, S.inv_vbase));
   TRY(upload(h, h->inv_cF, S.inv_cF));
   TRY(upload(h, h->inv_col, S.inv_col));
+  {
+    // columns of A (CSC by counting sort): row and CSR entry of every entry of
+    // column j, for the transposed residuals of the adjoint sweeps
+    std::vector<int64_t> atp(S.N + 1, 0);
+    for (int64_t e = 0; e < S.nnzA; ++e) ++atp[cl[e] + 1];
+    for (int64_t j = 0; j < S.N; ++j) atp[j + 1] += atp[j];
+    std::vector<int32_t> atr(S.nnzA), ats(S.nnzA);
+    std::vector<int64_t> fill(atp.begin(), atp.end() - 1);
+    for (int64_t i = 0; i < S.N; ++i)
+      for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+        const int64_t q = fill[cl[e]]++;
+        atr[q] = (int32_t)i;
+        ats[q] = (int32_t)e;
+      }
+    TRY(upload(h, h->at_ptr, atp));
+    TRY(upload(h, h->at_row, atr));
+    TRY(upload(h, h->at_src, ats));
+  }
   pisp::SymDev& sd = h->sd;
   sd.c0 = h->c0.as<int32_t>();
   sd.ns = h->ns.as<int32_t>();
@@ -696,10 +755,33 @@ int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   sd.inv_vbase = h->inv_vbase.as<int64_t>();
   sd.inv_cF = h->inv_cF.as<int32_t>();
   sd.inv_col = h->inv_col.as<int32_t>();
+  sd.at_ptr = h->at_ptr.as<int64_t>();
+  sd.at_row = h->at_row.as<int32_t>();
+  sd.at_src = h->at_src.as<int32_t>();
   sd.N = S.N;
   sd.S = nS;
   h->analyzed = true;
   return PISP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pisp_analyze(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row_ptr,
+                 const int32_t* col_idx, const pisp_options* opt) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  // no C++ exception may cross the C boundary: host allocation failures of
+  // the analysis (or of its staging vectors) become error codes
+  try {
+    return analyze_impl(h, G, n, row_ptr, col_idx, opt);
+  } catch (const std::bad_alloc&) {
+    h->analyzed = false;
+    return fail(h, PISP_ERR_OOM, "out of host memory in pisp_analyze");
+  } catch (const std::exception& e) {
+    h->analyzed = false;
+    return fail(h, PISP_ERR_INVALID_ARG, std::string("pisp_analyze failed: ") + e.what());
+  }
 }
 
 int pisp_match_rows(int32_t n, const int64_t* row_ptr, const int32_t* col_idx, int32_t* row_perm) {
@@ -740,6 +822,7 @@ int pisp_weights(const double* t, int32_t K, double* beta) {
 int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
                           const double* t, int32_t K, int32_t precision) {
   if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  if (!h->capturing) h->graph_valid = false;
   NvtxRange nvtx_("pisp_factor_perturbed");
   if (!h->analyzed) return fail(h, PISP_ERR_NOT_ANALYZED, "pisp_analyze has not succeeded");
   if (K < 1 || K > PISP_K_MAX || !t) return fail(h, PISP_ERR_INVALID_ARG, "K must be in 1..16");
@@ -840,6 +923,7 @@ int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
 int pisp_solve(pisp_handle* h, const double* b, int32_t R, const double* w, double* x,
                int32_t sweeps) {
   if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  if (!h->capturing) h->graph_valid = false;
   NvtxRange nvtx_("pisp_solve");
   if (!h->factored) return fail(h, PISP_ERR_NOT_FACTORED, "no factorisation");
   if (R < 1 || sweeps < 0) return fail(h, PISP_ERR_INVALID_ARG, "R must be >= 1, sweeps >= 0");
@@ -879,6 +963,7 @@ int pisp_combine(pisp_handle* h, const double* w, double* x) {
 int pisp_refine(pisp_handle* h, const double* b, double* x, int32_t R, int32_t iters,
                 int32_t sweeps) {
   if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  if (!h->capturing) h->graph_valid = false;
   NvtxRange nvtx_("pisp_refine");
   if (!h->factored) return fail(h, PISP_ERR_NOT_FACTORED, "no factorisation");
   if (R < 1 || iters < 0 || sweeps < 0) return fail(h, PISP_ERR_INVALID_ARG, "bad R/iters/sweeps");
@@ -906,11 +991,12 @@ int pisp_refine(pisp_handle* h, const double* b, double* x, int32_t R, int32_t i
 }
 
 int pisp_adjoint(pisp_handle* h, const double* g, const double* w, double* grad_b,
-                 double* grad_values) {
+                 double* grad_values, int32_t sweeps) {
   if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
   NvtxRange nvtx_("pisp_adjoint");
   if (!h->solved) return fail(h, PISP_ERR_NOT_FACTORED, "pisp_solve has not run");
   if (h->sym.N > 0 && !g) return fail(h, PISP_ERR_INVALID_ARG, "null g");
+  if (sweeps < 0) return fail(h, PISP_ERR_INVALID_ARG, "sweeps must be >= 0");
   DeviceScope dev_scope_;
   TRY(set_device(h, dev_scope_));
   double ww[PISP_K_MAX];
@@ -920,10 +1006,89 @@ int pisp_adjoint(pisp_handle* h, const double* g, const double* w, double* grad_
     return fail(h, PISP_ERR_OOM, "device allocation failed (adjoint workspace)");
   const pisp::Shifts sh = make_shifts(h, ww);
   TRY(solve_pass(h, true, g, pisp::RHS_BROADCAST, h->Lam.as<double>(), nullptr, R));
+  // FP64 residual sweeps of every lambda_k on the transposed systems, as the
+  // forward sweeps do for x_k: with FP32 factors the adjoint then reaches the
+  // FP64 definition too (Rk and Y are the solve's workspace, sized for R)
+  for (int it = 0; it < sweeps; ++it) {
+    TRY(count(h, pisp::launch_residual_T_per_k(h->sd, h->vals.as<double>(), h->D.as<double>(), sh, g,
+                                               h->Lam.as<double>(), R, h->Rk.as<double>(), h->stream)));
+    TRY(solve_pass(h, true, h->Rk.as<double>(), pisp::RHS_PER_K, h->Y.as<double>(), h->Lam.as<double>(), R));
+  }
   if (grad_b) TRY(count(h, pisp::launch_combine(h->sd, h->Lam.as<double>(), sh, R, grad_b, h->stream)));
   if (grad_values)
     TRY(count(h, pisp::launch_grad_values(h->sd, h->Lam.as<double>(), h->X.as<double>(), sh, R,
                                           grad_values, h->stream)));
+  return PISP_OK;
+}
+
+int pisp_graph_capture(pisp_handle* h, const double* values, const double* D, const double* t,
+                       int32_t K, int32_t precision, const double* b, int32_t R, const double* w,
+                       double* x, int32_t sweeps, const double* g, double* grad_b, double* grad_values,
+                       int32_t adjoint_sweeps) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  NvtxRange nvtx_("pisp_graph_capture");
+  if (!h->analyzed) return fail(h, PISP_ERR_NOT_ANALYZED, "pisp_analyze has not succeeded");
+  DeviceScope dev_scope_;
+  TRY(set_device(h, dev_scope_));
+  h->drop_graph();
+  // one eager step: checks the arguments, allocates every workspace the step
+  // needs (nothing may be allocated during the capture) and leaves its results
+  auto step = [&]() -> int {
+    TRY(pisp_factor_perturbed(h, values, D, t, K, precision));
+    TRY(pisp_solve(h, b, R, w, x, sweeps));
+    if (g) TRY(pisp_adjoint(h, g, w, grad_b, grad_values, adjoint_sweeps));
+    return PISP_OK;
+  };
+  TRY(step());
+  if (h->prof_on) {  // only the brackets recorded into the graph are replayed
+    h->prof_next = 0;
+    h->prof_br.clear();
+  }
+  if (!h->cap_stream) {
+    CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->cap_ev, cudaEventDisableTiming));
+  }
+  // capture on a private stream ordered after the work queued so far
+  CK(cudaEventRecord(h->cap_ev, h->stream));
+  CK(cudaStreamWaitEvent(h->cap_stream, h->cap_ev, 0));
+  const cudaStream_t user = h->stream;
+  h->stream = h->cap_stream;
+  h->capturing = true;
+  cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+  int rc = e == cudaSuccess ? step() : PISP_ERR_CUDA;
+  cudaGraph_t gr = nullptr;
+  const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(h->cap_stream, &gr) : e;
+  h->capturing = false;
+  h->stream = user;
+  if (rc) {
+    if (gr) cudaGraphDestroy(gr);
+    return rc;
+  }
+  if (e2 != cudaSuccess || !gr)
+    return fail(h, PISP_ERR_CUDA, std::string("stream capture failed: ") + cudaGetErrorString(e2));
+  h->graph = gr;
+  CK(cudaGraphInstantiate(&h->graph_exec, h->graph, 0));
+  h->graph_valid = true;
+  return PISP_OK;
+}
+
+int pisp_graph_launch(pisp_handle* h) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  if (!h->graph_valid || !h->graph_exec)
+    return fail(h, PISP_ERR_INVALID_ARG, "no valid captured step (pisp_graph_capture)");
+  DeviceScope dev_scope_;
+  TRY(set_device(h, dev_scope_));
+  CK(cudaGraphLaunch(h->graph_exec, h->stream));
+  return PISP_OK;
+}
+
+int pisp_set_wait_limit(pisp_handle* h, int64_t polls, int32_t unreachable) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  if (polls < 0) return fail(h, PISP_ERR_INVALID_ARG, "polls must be >= 0");
+  h->wait_polls = polls;
+  h->wait_unreachable = unreachable ? 1 : 0;
+  h->units_K = h->units_R = 0;  // the next persistent solve rebuilds its targets
+  h->graph_valid = false;
   return PISP_OK;
 }
 
@@ -1074,6 +1239,7 @@ int pisp_solve_host(pisp_handle* h, const double* values_host, const double* D_h
                     int32_t R, double* x_host, int32_t sweeps) {
   if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
   NvtxRange nvtx_("pisp_solve_host");
+  h->graph_valid = false;
   if (!h->analyzed) return fail(h, PISP_ERR_NOT_ANALYZED, "pisp_analyze has not succeeded");
   if (R < 1) return fail(h, PISP_ERR_INVALID_ARG, "R must be >= 1");
   const pisp::Symbolic& S = h->sym;

@@ -48,6 +48,9 @@ struct SymDev {
   const int32_t* row_inst;   // [N] instance of each original row
   const int64_t* row_ptr;    // [N+1] CSR of A (original order)
   const int32_t* col;        // [nnz]
+  const int64_t* at_ptr;     // [N+1] CSC of A: entries of column j at at_ptr[j]..at_ptr[j+1]
+  const int32_t* at_row;     //   their rows
+  const int32_t* at_src;     //   their CSR entry indices
   int64_t N;
   int32_t S;
 };
@@ -177,12 +180,13 @@ constexpr int kSolveChunk = 8;  // largest RHS chunk of a task (segment tasks us
 // One launch solving every level of the forest (forward = L, bottom-up, or
 // backward = U, top-down).  ticket (1 int) and done (S*K ints) must be zero;
 // nch[s] is the number of RHS chunks (tasks) per (front s, k); err is set to 1
-// if a bounded dependency wait gave up.
+// if a bounded dependency wait gave up after `polls` polls (<= 0: the default
+// limit of 2^22 polls).
 int launch_solve_persistent(int precision, bool forward, const SymDev& sd, const SolveUnit* units,
                             int nunits, int* ticket, int* done, int* err, const int* nch,
                             const int32_t* d_all, const void* fronts, const double* rhs,
                             int rhs_mode, void* V, double* out, double* acc, int32_t R, int32_t K,
-                            int32_t max_blk_F, cudaStream_t st);
+                            int32_t max_blk_F, int64_t polls, cudaStream_t st);
 // RHS chunk for the CTAs solving one big front at a time (persistent schedule)
 int pick_chunk(int fronts_in_level, int K, int R);
 int launch_forward_level(int precision, bool trans, const SymDev& sd, const LevelPlan& lp,
@@ -196,6 +200,10 @@ int launch_combine(const SymDev& sd, const double* X, const Shifts& sh, int32_t 
 int launch_residual_per_k(const SymDev& sd, const double* vals, const double* D,
                           const Shifts& sh, const double* b, const double* X, int32_t R,
                           double* Rk, cudaStream_t st);
+// FP64 residuals of the transposed perturbed systems (adjoint sweeps)
+int launch_residual_T_per_k(const SymDev& sd, const double* vals, const double* D,
+                            const Shifts& sh, const double* g, const double* Lam, int32_t R,
+                            double* Rk, cudaStream_t st);
 int launch_residual(const SymDev& sd, const double* vals, const double* b, const double* x,
                     int32_t R, double* r, cudaStream_t st);
 int launch_axpy(int64_t n, const double* y, double* x, cudaStream_t st);

@@ -173,7 +173,7 @@ __device__ __forceinline__ double load_rhs(const SymDev& sd, const double* rhs, 
 // gives up sets *err (reported as PISP_ERR_TIMEOUT) and the task proceeds, so
 // no wait can hang the GPU.
 // ---------------------------------------------------------------------------
-constexpr int64_t kWaitPolls = 1 << 22;
+constexpr int64_t kWaitPolls = 1 << 22;  // default poll limit of a dependency wait
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -195,9 +195,10 @@ struct Sync {
   int* done;          // nullptr: level-synchronous launches, nothing to wait for
   int* err;
   const int* nch;     // [S] RHS chunks per (front, k) in the persistent schedule
+  int64_t polls;      // polls before a wait gives up
   __device__ void wait_ge(const int* f, int need) const {
     if (ld_acquire(f) >= need) return;
-    for (int64_t i = 0; i < kWaitPolls; ++i) {
+    for (int64_t i = 0; i < polls; ++i) {
       __nanosleep(64);
       if (ld_acquire(f) >= need) return;
     }
@@ -224,11 +225,11 @@ struct Sync {
       const int need = nch[c];
       if (ld_relaxed(f) >= need) continue;
       int64_t i = 0;
-      for (; i < kWaitPolls; ++i) {
+      for (; i < polls; ++i) {
         __nanosleep(64);
         if (ld_relaxed(f) >= need) break;
       }
-      if (i == kWaitPolls) atomicExch(err, 1);
+      if (i == polls) atomicExch(err, 1);
     }
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
   }
@@ -680,7 +681,7 @@ __global__ void __launch_bounds__(256, 2) k_forward_seg(SymDev sd, const int32_t
   const int64_t sg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / SEG;
   const SegTask t = seg_task(sd, list, sg, nseg, R, K);
   seg_forward<T, SEG>(sd, t, threadIdx.x % SEG, buf[threadIdx.x / SEG], fronts, rhs, rhs_mode, V, R,
-                      K, Sync{nullptr, nullptr, nullptr});
+                      K, Sync{nullptr, nullptr, nullptr, 0});
 }
 
 template <typename T, int SEG>
@@ -690,7 +691,7 @@ __global__ void __launch_bounds__(256, 2) k_backward_seg(SymDev sd, const int32_
                                                          double* acc, int R, int K) {
   const int64_t sg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / SEG;
   const SegTask t = seg_task(sd, list, sg, nseg, R, K);
-  seg_backward<T, SEG>(sd, t, threadIdx.x % SEG, fronts, V, out, acc, R, K, Sync{nullptr, nullptr, nullptr});
+  seg_backward<T, SEG>(sd, t, threadIdx.x % SEG, fronts, V, out, acc, R, K, Sync{nullptr, nullptr, nullptr, 0});
 }
 
 template <typename T>
@@ -703,7 +704,7 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_forward_blk(SymDev sd, con
   const int r0 = blockIdx.z * rc;
   if (r0 >= R) return;
   blk_forward<T>(sd, list[blockIdx.x], blockIdx.y, r0, min(rc, R - r0), 0, smraw, fronts, rhs,
-                 rhs_mode, V, R, K, Sync{nullptr, nullptr, nullptr});
+                 rhs_mode, V, R, K, Sync{nullptr, nullptr, nullptr, 0});
 }
 
 template <typename T>
@@ -715,7 +716,7 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_backward_blk(SymDev sd, co
   const int r0 = blockIdx.z * rc;
   if (r0 >= R) return;
   blk_backward<T>(sd, list[blockIdx.x], blockIdx.y, r0, min(rc, R - r0), 0, smraw, fronts, V, out,
-                  acc, R, K, Sync{nullptr, nullptr, nullptr});
+                  acc, R, K, Sync{nullptr, nullptr, nullptr, 0});
 }
 
 // ---- persistent schedule: one launch per direction -------------------------
@@ -728,10 +729,10 @@ __global__ void __launch_bounds__(kSolveThreads, 2)
 k_solve_persistent(SymDev sd, const SolveUnit* __restrict__ units, int nunits, int* ticket,
                    int* done, int* err, const int* __restrict__ nch, const int32_t* __restrict__ all,
                    const T* __restrict__ fronts, const double* __restrict__ rhs, int rhs_mode,
-                   T* __restrict__ V, double* out, double* acc, int R, int K) {
+                   T* __restrict__ V, double* out, double* acc, int R, int K, int64_t polls) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_unit;
-  const Sync sy{done, err, nch};
+  const Sync sy{done, err, nch, polls};
   const int tid = threadIdx.x;
   for (;;) {
     if (tid == 0) s_unit = atomicAdd(ticket, 1);
@@ -826,6 +827,30 @@ __global__ void k_residual_per_k(SymDev sd, const double* __restrict__ vals,
     for (int64_t e = e0; e < e1; ++e)
       a -= vals[e] * X[((int64_t)sd.iperm[sd.col[e]] * K + k) * R + r];
     Rk[(pi * K + k) * R + r] = a;
+  }
+}
+
+// Rk[pj][k][r] = g[j][r] - sum_i A_ij Lam[pi][k][r] - t_k D_j Lam[pj][k][r]  (FP64):
+// the residual of the transposed perturbed system (A + t_k D)^T lambda_k = g,
+// one warp per original column j (A's columns through the CSC arrays).
+__global__ void k_residual_T_per_k(SymDev sd, const double* __restrict__ vals,
+                                   const double* __restrict__ D, Shifts sh,
+                                   const double* __restrict__ g, const double* __restrict__ Lam, int R,
+                                   double* __restrict__ Rk) {
+  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (j >= sd.N) return;
+  const int K = sh.K;
+  const int KR = K * R;
+  const int64_t pj = sd.iperm[j];
+  const int64_t q0 = sd.at_ptr[j], q1 = sd.at_ptr[j + 1];
+  const double dj = D[j];
+  for (int q = lane; q < KR; q += 32) {
+    const int k = q / R, r = q % R;
+    double a = g[j * R + r] - sh.t[k] * dj * Lam[(pj * K + k) * R + r];
+    for (int64_t e = q0; e < q1; ++e)
+      a -= vals[sd.at_src[e]] * Lam[((int64_t)sd.iperm[sd.at_row[e]] * K + k) * R + r];
+    Rk[(pj * K + k) * R + r] = a;
   }
 }
 
@@ -1021,7 +1046,8 @@ template <typename T>
 int persistent_impl(bool forward, const SymDev& sd, const SolveUnit* units, int nunits, int* ticket,
                     int* done, int* err, const int* nch, const int32_t* d_all, const void* fronts, const double* rhs,
                     int rhs_mode, void* V, double* out, double* acc, int R, int K, int max_blk_F,
-                    cudaStream_t st) {
+                    int64_t polls, cudaStream_t st) {
+  if (polls <= 0) polls = kWaitPolls;
   if (nunits == 0) return 0;
   static std::atomic<int> nsm_dev[kMaxDevices];
   int occ_f = 0, occ_b = 0;
@@ -1044,10 +1070,12 @@ int persistent_impl(bool forward, const SymDev& sd, const SolveUnit* units, int 
   const int grid = std::max(1, std::min(nunits, occ * std::max(nsm, 1)));
   if (forward)
     k_solve_persistent<T, true><<<grid, kSolveThreads, smem, st>>>(
-        sd, units, nunits, ticket, done, err, nch, d_all, (const T*)fronts, rhs, rhs_mode, (T*)V, out, acc, R, K);
+        sd, units, nunits, ticket, done, err, nch, d_all, (const T*)fronts, rhs, rhs_mode, (T*)V, out, acc, R, K,
+        polls);
   else
     k_solve_persistent<T, false><<<grid, kSolveThreads, smem, st>>>(
-        sd, units, nunits, ticket, done, err, nch, d_all, (const T*)fronts, rhs, rhs_mode, (T*)V, out, acc, R, K);
+        sd, units, nunits, ticket, done, err, nch, d_all, (const T*)fronts, rhs, rhs_mode, (T*)V, out, acc, R, K,
+        polls);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
@@ -1057,12 +1085,12 @@ int launch_solve_persistent(int precision, bool forward, const SymDev& sd, const
                             int nunits, int* ticket, int* done, int* err, const int* nch,
                             const int32_t* d_all, const void* fronts, const double* rhs,
                             int rhs_mode, void* V, double* out, double* acc, int32_t R, int32_t K,
-                            int32_t max_blk_F, cudaStream_t st) {
+                            int32_t max_blk_F, int64_t polls, cudaStream_t st) {
   if (precision == PISP_FP32)
     return persistent_impl<float>(forward, sd, units, nunits, ticket, done, err, nch, d_all, fronts,
-                                  rhs, rhs_mode, V, out, acc, R, K, max_blk_F, st);
+                                  rhs, rhs_mode, V, out, acc, R, K, max_blk_F, polls, st);
   return persistent_impl<double>(forward, sd, units, nunits, ticket, done, err, nch, d_all, fronts,
-                                 rhs, rhs_mode, V, out, acc, R, K, max_blk_F, st);
+                                 rhs, rhs_mode, V, out, acc, R, K, max_blk_F, polls, st);
 }
 
 int launch_combine(const SymDev& sd, const double* X, const Shifts& sh, int32_t R, double* x,
@@ -1078,6 +1106,14 @@ int launch_residual_per_k(const SymDev& sd, const double* vals, const double* D,
                           double* Rk, cudaStream_t st) {
   if (sd.N == 0) return 0;
   k_residual_per_k<<<blocks_for(sd.N * 32, 256), 256, 0, st>>>(sd, vals, D, sh, b, X, R, Rk);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_residual_T_per_k(const SymDev& sd, const double* vals, const double* D,
+                            const Shifts& sh, const double* g, const double* Lam, int32_t R,
+                            double* Rk, cudaStream_t st) {
+  if (sd.N == 0) return 0;
+  k_residual_T_per_k<<<blocks_for(sd.N * 32, 256), 256, 0, st>>>(sd, vals, D, sh, g, Lam, R, Rk);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 

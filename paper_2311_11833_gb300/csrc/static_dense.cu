@@ -116,6 +116,10 @@ extern "C" int pisp_dense_solve_static(void* stream, int32_t n, const double* A,
   StaticShifts sh{};
   if (pisp_weights(t, K, sh.w) != PISP_OK) return PISP_ERR_INVALID_ARG;
   for (int k = 0; k < K; ++k) sh.t[k] = t[k];
+  // An error already pending on this host thread belongs to the caller: leave
+  // it in place for them to read (peek, do not clear) and launch nothing, since
+  // a launch failure of this call could not be told apart from it.
+  if (cudaPeekAtLastError() != cudaSuccess) return PISP_ERR_CUDA;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PISP_ERR_CUDA;
   double* scratch = nullptr;
@@ -139,6 +143,7 @@ extern "C" int pisp_dense_solve_static(void* stream, int32_t n, const double* A,
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t smem = ((size_t)n * n + (size_t)n * R) * sizeof(double);
   k_dense_perturbed_solve<<<K, 256, smem, st>>>(n, A, D, sh, b, R, scratch);
+  if (cudaGetLastError() != cudaSuccess) return PISP_ERR_CUDA;  // nothing else enqueued
   k_dense_combine<<<(n * R + 255) / 256, 256, 0, st>>>(n, R, K, sh, scratch, x);
   return cudaGetLastError() == cudaSuccess ? PISP_OK : PISP_ERR_CUDA;
 }

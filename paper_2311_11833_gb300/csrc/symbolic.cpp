@@ -8,6 +8,7 @@
 #include "symbolic.h"
 
 #include <algorithm>
+#include <system_error>
 #include <thread>
 #include <functional>
 #include <atomic>
@@ -389,22 +390,30 @@ std::string analyze_instance(int32_t ng, int64_t off, const int64_t* row_ptr, co
   return std::string();
 }
 
-// Runs body(g) for g = 0..G-1, on up to 16 host threads when there are
-// several instances; each g is run exactly once.
-void for_each_instance(int32_t G, const std::function<void(int32_t)>& body) {
+// Runs body(g) for g = 0..G-1, on up to `threads` host threads (0 = the
+// hardware concurrency, at most 16) when there are several instances; each g
+// is run exactly once.  If a worker thread cannot be started, the instances
+// nobody has taken run on the calling thread.
+void for_each_instance(int32_t G, int threads, const std::function<void(int32_t)>& body) {
   const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-  const int32_t T = (int32_t)std::min<unsigned>(std::min<unsigned>(hw, 16u), (unsigned)G);
+  const unsigned cap = threads > 0 ? (unsigned)threads : std::min(hw, 16u);
+  const int32_t T = (int32_t)std::min<unsigned>(cap, (unsigned)std::max<int32_t>(G, 1));
   if (T <= 1) {
     for (int32_t g = 0; g < G; ++g) body(g);
     return;
   }
   std::atomic<int32_t> next(0);
+  auto work = [&]() {
+    for (int32_t g = next.fetch_add(1); g < G; g = next.fetch_add(1)) body(g);
+  };
   std::vector<std::thread> pool;
   pool.reserve(T);
-  for (int32_t t = 0; t < T; ++t)
-    pool.emplace_back([&]() {
-      for (int32_t g = next.fetch_add(1); g < G; g = next.fetch_add(1)) body(g);
-    });
+  try {
+    for (int32_t t = 0; t < T; ++t) pool.emplace_back(work);
+  } catch (const std::system_error&) {
+    // fewer threads than asked for: the ones running and this thread share the rest
+  }
+  work();
   for (auto& th : pool) th.join();
 }
 
@@ -434,8 +443,17 @@ std::string analyze(int32_t G, const int32_t* n, const int64_t* row_ptr,
   S.col_sn.assign(S.N, -1);
 
   std::vector<InstanceResult> res(G);
-  for_each_instance(G, [&](int32_t g) {
-    if (n[g] > 0) res[g].err = analyze_instance(n[g], S.inst_off[g], row_ptr, col, opt, res[g]);
+  for_each_instance(G, opt.threads, [&](int32_t g) {
+    if (n[g] <= 0) return;
+    // an exception must not leave a worker thread (that would terminate the
+    // process): it becomes this instance's error message
+    try {
+      res[g].err = analyze_instance(n[g], S.inst_off[g], row_ptr, col, opt, res[g]);
+    } catch (const std::bad_alloc&) {
+      res[g].err = "out of host memory in the symbolic analysis";
+    } catch (const std::exception& e) {
+      res[g].err = std::string("symbolic analysis failed: ") + e.what();
+    }
   });
   for (int32_t g = 0; g < G; ++g)
     if (!res[g].err.empty()) return res[g].err;

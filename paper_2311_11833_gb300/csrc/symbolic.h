@@ -18,6 +18,7 @@ struct SymbolicOptions {
                                // while the merged pivot block has <= this many columns
   double relax_zeros = 0.05;   // else merge if explicit zeros stay <= this fraction
   int ordering = 0;            // 0 = minimum degree, 1 = natural (given order)
+  int threads = 0;             // host threads for the instances of a batch (0 = auto)
 };
 
 // One supernode = one frontal matrix.  Columns [c0, c1) of the permuted

@@ -87,7 +87,7 @@ class Solver:
 
     def __init__(self, n, row_ptr, col, device: int | None = None, ordering: int = 0,
                  relax_small: int = -1, relax_zeros: float = -1.0, solve_schedule: int = 0,
-                 factor_policy: int = 0):
+                 factor_policy: int = 0, analyze_threads: int = 0):
         self._lib = _lib.load()
         if not torch.cuda.is_available():
             raise RuntimeError("libpisp needs a CUDA device")
@@ -107,7 +107,7 @@ class Solver:
         h = ctypes.c_void_p()
         check(self._lib.pisp_create(ctypes.byref(h), self.device, None))
         self._h = h
-        opt = PispOptions(ordering, relax_small, relax_zeros, solve_schedule, factor_policy)
+        opt = PispOptions(ordering, relax_small, relax_zeros, solve_schedule, factor_policy, analyze_threads)
         check(self._lib.pisp_analyze(self._h, self.G, sizes.ctypes.data_as(ctypes.c_void_p),
                                      rp.ctypes.data_as(ctypes.c_void_p),
                                      cl.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opt)), self._h)
@@ -194,11 +194,14 @@ class Solver:
         return x.reshape(-1) if vec else x
 
     def adjoint(self, g: torch.Tensor, weights=None, need_b=True, need_values=True,
-                out_b: torch.Tensor | None = None, out_values: torch.Tensor | None = None):
+                out_b: torch.Tensor | None = None, out_values: torch.Tensor | None = None,
+                sweeps: int = 0):
         """pisp_adjoint: (dL/db, dL/dvalues) for dL/dx = g of the last solve.
 
         out_b / out_values: preallocated outputs (e.g. inside a CUDA graph);
-        without them the outputs that are needed are allocated."""
+        without them the outputs that are needed are allocated.  sweeps: FP64
+        residual corrections of the transposed solves (use the forward
+        solve's count with FP32 factors)."""
         g2 = self._dev(g, "g").reshape(self.N, -1)
         if g2.shape[1] != self.R:
             raise ValueError(f"g has {g2.shape[1]} columns, the last solve had R = {self.R}")
@@ -213,10 +216,52 @@ class Solver:
         w = None if weights is None else _host_f64(weights)
         self._sync_stream()
         check(self._lib.pisp_adjoint(self._h, _ptr(g2), None if w is None else w.ctypes.data_as(ctypes.c_void_p),
-                                     _ptr(gb), _ptr(gv)), self._h)
+                                     _ptr(gb), _ptr(gv), int(sweeps)), self._h)
         if gb is not None and out_b is None and g.dim() == 1:
             gb = gb.reshape(-1)
         return gb, gv
+
+    def graph_capture(self, values: torch.Tensor, D: torch.Tensor, t, b: torch.Tensor, x: torch.Tensor,
+                      precision="fp64", sweeps: int = 0, weights=None, g: torch.Tensor | None = None,
+                      out_b: torch.Tensor | None = None, out_values: torch.Tensor | None = None,
+                      adjoint_sweeps: int = 0):
+        """pisp_graph_capture: one factor + solve (+ adjoint) step captured into a
+        library-owned CUDA graph; graph_launch() replays it on the current
+        stream, reading the current contents of these same tensors."""
+        values = self._dev(values, "values", (self.nnz,))
+        D = self._dev(D, "D", (self.N,))
+        b2 = self._dev(b, "b")
+        if b2.data_ptr() != b.data_ptr() or b2.numel() % max(self.N, 1):
+            raise ValueError("b must be a contiguous [N] or [N, R] tensor")
+        R = b2.numel() // self.N if self.N else 1
+        x = self._dev_out(x, "x", self.N * R)
+        tt = _host_f64(t)
+        w = None if weights is None else _host_f64(weights)
+        gg = gb = gv = None
+        if g is not None:
+            gg = self._dev(g, "g")
+            if gg.data_ptr() != g.data_ptr() or gg.numel() != self.N * R:
+                raise ValueError("g must be contiguous with N * R entries")
+            gb = self._dev_out(out_b, "out_b", self.N * R) if out_b is not None else None
+            gv = self._dev_out(out_values, "out_values", self.nnz) if out_values is not None else None
+        self._sync_stream()
+        check(self._lib.pisp_graph_capture(
+            self._h, _ptr(values), _ptr(D), tt.ctypes.data_as(ctypes.c_void_p), len(tt), _PREC[precision],
+            _ptr(b2), R, None if w is None else w.ctypes.data_as(ctypes.c_void_p), _ptr(x), int(sweeps),
+            _ptr(gg), _ptr(gb), _ptr(gv), int(adjoint_sweeps)), self._h)
+        self.K, self.t, self.precision, self.R = len(tt), tt, _PREC[precision], R
+        self._graph_refs = (values, D, b, x, g, out_b, out_values)   # keep the buffers alive
+        return self
+
+    def graph_launch(self):
+        """pisp_graph_launch: replays the captured step on the current stream."""
+        self._sync_stream()
+        check(self._lib.pisp_graph_launch(self._h), self._h)
+
+    def set_wait_limit(self, polls: int = 0, unreachable: bool = False):
+        """pisp_set_wait_limit: poll limit of the solves' dependency waits (0 = default);
+        unreachable=True makes one wait run out on purpose (test hook)."""
+        check(self._lib.pisp_set_wait_limit(self._h, int(polls), 1 if unreachable else 0), self._h)
 
     def status(self):
         """pisp_get_status: (worst code, per-(instance, k) codes, first failing columns)."""
@@ -225,7 +270,7 @@ class Solver:
         self._sync_stream()
         worst = self._lib.pisp_get_status(self._h, st.ctypes.data_as(ctypes.c_void_p),
                                           bc.ctypes.data_as(ctypes.c_void_p))
-        if worst not in (0, 4, 5):
+        if worst not in (0, 4, 5, 6):
             check(worst, self._h)
         return worst, st.reshape(self.G, self.K), bc.reshape(self.G, self.K)
 
@@ -318,7 +363,9 @@ class _PerturbedSolve(torch.autograd.Function):
     """x = sum_k beta_k (A + t_k D)^{-1} b with gradients for values and b.
 
     The backward pass reuses the K factors of the forward pass transposed
-    (pisp_adjoint); D and t are held fixed.
+    (pisp_adjoint) with as many FP64 residual sweeps as the forward solve
+    used, so FP32 factors give gradients at the accuracy of the forward
+    result; D and t are held fixed.
     """
 
     @staticmethod
@@ -326,6 +373,7 @@ class _PerturbedSolve(torch.autograd.Function):
         solver.factor(values.detach(), D, t, precision)
         x = solver.solve(b.detach(), sweeps=sweeps)
         ctx.solver = solver
+        ctx.sweeps = sweeps
         ctx.vec = b.dim() == 1
         return x
 
@@ -333,7 +381,7 @@ class _PerturbedSolve(torch.autograd.Function):
     def backward(ctx, gx):
         s = ctx.solver
         need_v, need_b = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
-        gb, gv = s.adjoint(gx.contiguous(), need_b=need_b, need_values=need_v)
+        gb, gv = s.adjoint(gx.contiguous(), need_b=need_b, need_values=need_v, sweeps=ctx.sweeps)
         return gv, gb, None, None, None, None, None
 
 

@@ -57,7 +57,8 @@ class HostSymbolic:
         sizes = np.asarray(sizes, np.int32)
         rp = np.ascontiguousarray(row_ptr, np.int64)
         cl = np.ascontiguousarray(col, np.int32)
-        o = PispOptions(opt.get("ordering", 0), opt.get("relax_small", -1), opt.get("relax_zeros", -1.0), 0, 0)
+        o = PispOptions(opt.get("ordering", 0), opt.get("relax_small", -1), opt.get("relax_zeros", -1.0), 0, 0,
+                        opt.get("analyze_threads", 0))
         self.rc = lib.pisp_analyze(self.h, len(sizes), sizes.ctypes.data_as(ctypes.c_void_p),
                                    rp.ctypes.data_as(ctypes.c_void_p), cl.ctypes.data_as(ctypes.c_void_p),
                                    ctypes.byref(o))
@@ -239,3 +240,26 @@ def test_workload_structures_are_stable(lib, wl, n, S, levels, max_front, n_wide
     finally:
         a.close()
         b.close()
+
+
+def test_analyze_thread_cap_gives_the_same_structure(lib):
+    """pisp_options.analyze_threads only changes how many host threads share the
+    instances of a batch: 1 thread and the default give the same structure."""
+    insts = [pfgen.make_instance("batching", g) for g in range(12)]
+    rp, cols, off = [0], [], 0
+    for I in insts:
+        rp.extend((I.row_ptr[1:] + rp[-1]).tolist())
+        cols.append(I.col + off)
+        off += I.n
+    sizes = [I.n for I in insts]
+    rp = np.array(rp, np.int64)
+    col = np.concatenate(cols).astype(np.int32)
+    a = HostSymbolic(lib, sizes, rp, col)
+    b = HostSymbolic(lib, sizes, rp, col, analyze_threads=1)
+    assert a.rc == 0 and b.rc == 0
+    assert np.array_equal(a.perm, b.perm) and np.array_equal(a.c0, b.c0)
+    assert np.array_equal(a.ms, b.ms) and np.array_equal(a.rows, b.rows)
+    c = HostSymbolic(lib, sizes, rp, col, analyze_threads=-1)
+    assert c.rc == 1                                   # PISP_ERR_INVALID_ARG
+    for h in (a, b, c):
+        h.close()

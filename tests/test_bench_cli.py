@@ -35,3 +35,16 @@ def test_product_arm_fails_loudly_without_a_gpu():
                        capture_output=True, text=True, timeout=300)
     assert r.returncode != 0
     assert not any(l.strip().startswith("{") for l in r.stdout.splitlines())
+
+
+def test_minimum_bytes_count_indices_once_for_all_shifts():
+    """The roofline's algorithmic bytes of a solve launch: K copies of the
+    triangle's factor entries, ONE copy of their int32 indices, the vectors."""
+    sys.path.insert(0, ROOT)
+    import bench
+    st = {"N": 10, "nnzA": 30, "nnzF_stored": 50}
+    K, R, p = 4, 2, 4
+    nnzU, nnzL = 30, 20                       # (nnzF + N) / 2, (nnzF - N) / 2
+    assert bench.min_bytes_per_launch("backward", st, K, R, p) == K * p * nnzU + 4 * nnzU + K * p * 10 * R + 8 * 10 * R
+    assert bench.min_bytes_per_launch("forward", st, K, R, p) == K * p * nnzL + 4 * nnzL + 8 * 10 * R + K * p * 10 * R
+    assert bench.min_bytes_per_launch("factor_small", st, K, R, p) is None

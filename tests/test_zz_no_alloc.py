@@ -1,12 +1,15 @@
-"""The allocation-free entry point checked against the regular path.
+"""The allocation-free entry point against the oracle and the regular path.
 
 pisp_dense_solve_static serves callers that may not allocate device memory
 when they call (a budget fixed at start-up, host callbacks or real-time loops
 that cannot take cudaMalloc's implicit synchronisation, frameworks that pass
 only their own input and output buffers).  It keeps its per-perturbation
 solutions in a static device array instead of allocated workspace, so its
-answer must equal that of pisp_factor_perturbed + pisp_solve on the same
-system, and it must stay right when the array is reused by the next call.
+answer must equal the oracle's x_hat and that of pisp_factor_perturbed +
+pisp_solve on the same system, and it must stay right when the array is
+reused by the next call -- also when that call is smaller than the one
+before, so that stale entries of the larger call sit beyond the part it
+writes.
 """
 import ctypes
 
@@ -15,6 +18,7 @@ import pytest
 
 import oracle
 import pfgen
+from _parity import entrywise_err
 
 pytestmark = pytest.mark.gpu
 
@@ -47,21 +51,26 @@ def _static_solve(torch, lib, A, D, t, b):
     return rc, x.cpu().numpy()
 
 
-def test_static_entry_matches_regular_path_on_two_calls(env):
+def test_static_entry_matches_oracle_and_regular_path_on_consecutive_calls(env):
     torch, pisp, lib = env
-    cases = [(96, 4, 3, 11), (128, 6, 5, 12)]
+    # small, then the largest size the entry point takes, then small again:
+    # the third call runs over the larger leftovers of the second
+    cases = [(96, 4, 3, 11), (128, 16, 64, 12), (96, 4, 3, 11), (37, 2, 1, 13)]
     for n, K, R, seed in cases:
         inst = pfgen.random_sparse(n, 0.08, seed=seed)
         A = oracle.to_dense(inst)
         t = pfgen.symmetric_shifts(K)
         b = pfgen.rhs(n, R, seed)
+        ref = oracle.x_hat(A, inst.D, t, b)
+        rc, x = _static_solve(torch, lib, A, inst.D, t, b)
+        assert rc == 0
+        assert entrywise_err(x, ref) <= TOL64
         # the regular (allocating) entry points on the same system
         s = pisp.Solver(n, inst.row_ptr, inst.col)
         s.factor(torch.tensor(inst.val, device="cuda"), torch.tensor(inst.D, device="cuda"), t, "fp64")
-        x_ref = s.solve(torch.tensor(b, device="cuda")).cpu().numpy()
-        rc, x = _static_solve(torch, lib, A, inst.D, t, b)
-        assert rc == 0
-        assert np.max(oracle.rel_err(x, x_ref)) <= TOL64
+        x_reg = s.solve(torch.tensor(b, device="cuda")).cpu().numpy()
+        s.close()
+        assert entrywise_err(x, x_reg) <= TOL64
 
 
 def test_static_entry_rejects_sizes_beyond_its_limits(env):
@@ -72,3 +81,5 @@ def test_static_entry_rejects_sizes_beyond_its_limits(env):
     assert rc == 10                           # PISP_ERR_UNSUPPORTED
     rc, _ = _static_solve(torch, lib, np.eye(4), np.ones(4), t, np.ones((4, 65)))
     assert rc == 10
+    rc, _ = _static_solve(torch, lib, np.eye(4), np.ones(4), np.linspace(0.01, 0.17, 17), np.ones((4, 1)))
+    assert rc == 10                           # K = 17 > PISP_K_MAX
