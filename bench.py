@@ -77,8 +77,12 @@ def parse():
                          "1 CTA clusters, 2 single CTA / tile DAG, 3 single CTA / per-panel launches")
     ap.add_argument("--schedule", type=int, default=0, choices=[0, 1],
                     help="solve schedule: 0 persistent (default), 1 one launch per level")
-    ap.add_argument("--autotune", action="store_true",
-                    help="time candidate library options on this workload first and use the fastest")
+    ap.add_argument("--kfuse", type=int, default=0, help="persistent solve: shifts per narrow-front task")
+    ap.add_argument("--warp-maxf", type=int, default=0,
+                    help="persistent solve: widest front with <= 32 pivots solved by one warp")
+    ap.add_argument("--autotune", default="auto", choices=["auto", "on", "off"],
+                    help="time candidate library options on this workload first and use the fastest "
+                         "(auto: on for the batching workload)")
     ap.add_argument("--quick", action="store_true",
                     help="timed arm only (no plain-FP64 arm, e2e, CPU baseline or oracle check)")
     return ap.parse_args()
@@ -166,12 +170,13 @@ class Arm:
     """One configured solver with device-resident inputs and a step function."""
 
     def __init__(self, pisp, torch, insts, K, R, eps, precision, sweeps, workload, dev, schedule=0,
-                 factor_policy=0, options=None):
+                 factor_policy=0, options=None, extra=None):
         self.torch = torch
         self.insts = insts
         sizes, rp, col, val, D = concat(insts)
         t0 = time.perf_counter()
         opts = options or dict(solve_schedule=schedule, factor_policy=factor_policy)
+        opts = dict(opts, **(extra or {}))
         self.s = pisp.Solver(sizes, rp, col, device=dev.index, **opts)
         self.analyze_ms = (time.perf_counter() - t0) * 1e3
         self.N = sum(sizes)
@@ -307,14 +312,15 @@ def run_pisp(args, rank, world, local_rank):
     K, R = c["K"], c["R"]
     insts = workload_instances(args.workload, rank, args.instances)
     tuned = None
-    if args.autotune:
+    if args.autotune == "on" or (args.autotune == "auto" and args.workload == "batching"):
         from paper_2311_11833_gb300 import tune
         sizes, rp, col, val, D = concat(insts)
         tuned = tune.autotune(sizes, rp, col, torch.tensor(val, device=dev), torch.tensor(D, device=dev),
                               pfgen.symmetric_shifts(K, args.eps),
                               torch.tensor(pfgen.rhs(sum(sizes), R, 1), device=dev), precision, sweeps)
+    extra = {k: v for k, v in (("solve_kfuse", args.kfuse), ("solve_warp_maxF", args.warp_maxf)) if v}
     arm = Arm(pisp, torch, insts, K, R, args.eps, precision, sweeps, args.workload, dev, args.schedule,
-              args.factor_policy, options=tuned["options"] if tuned else None)
+              args.factor_policy, options=tuned["options"] if tuned else None, extra=extra)
     G = len(insts)
     units = G * R
     use_graph = not args.no_graph
@@ -409,7 +415,11 @@ def run_pisp(args, rank, world, local_rank):
         "autotune": ({"options": tuned["options"], "candidates": len(tuned["all"]),
                       "best_ms": round(tuned["ms"], 4),
                       "default_ms": round(next((r["ms"] for r in tuned["all"] if r["options"] == dict(
-                          relax_small=8, relax_zeros=0.05, factor_policy=0, solve_schedule=0)), float("nan")), 4)}
+                          relax_small=8, relax_zeros=0.05, factor_policy=0, solve_schedule=0,
+                          solve_ctas_per_sm=3 if precision == "fp32" else 2, solve_kfuse=1, solve_warp_maxF=32)),
+                                            float("nan")), 4),
+                      "search": "staged: solve tiling (CTAs/SM x shifts per task x widest warp front), "
+                                "then amalgamation x factor policy; graph replays, CUDA events"}
                      if tuned else None),
         "wall_s_timed_region": round(wall, 3),
         "structure": {k: stats[k] for k in ("nnzL", "nnzF_stored", "n_supernodes", "n_levels",

@@ -82,6 +82,20 @@ typedef struct pisp_options {
                              3 = as 0 but larger fronts by a blocked factorisation
                              in global memory (one panel launch and one
                              tiled-update launch per 32 pivots) */
+  int32_t solve_kfuse;    /* persistent solve: shifts per segment task of a front
+                             with at most 32 pivots (0 = 1): larger values pay a
+                             front's dependency wait and structure loads once
+                             for several shifts, smaller ones run more tasks
+                             in parallel */
+  int32_t solve_warp_maxF; /* persistent solve: widest front (with at most 32
+                              pivots) solved by one 32-lane segment, in blocks
+                              of 32 rows (0 = 32); wider fronts are solved by a
+                              whole CTA per (front, k, RHS chunk) */
+  int32_t solve_ctas_per_sm; /* persistent solve: resident CTAs per SM, 2, 3 or 4
+                                (register budgets 128, 80, 64 per thread; 0 = 3
+                                for FP32 factors, 2 for FP64): more CTAs hide
+                                more latency of a batch's many small fronts,
+                                fewer spill less on wide fronts */
   int32_t analyze_threads; /* host threads pisp_analyze may use for the instances
                               of a batch: 0 = the hardware concurrency, at most
                               16 (default); 1 = the calling thread only.  A

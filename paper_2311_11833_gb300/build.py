@@ -49,6 +49,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC,-pthread", "-lineinfo", "--expt-relaxed-constexpr"]
+    # extra nvcc flags, e.g. -DPISP_SOLVE_MIN_CTAS_F32=4 (compile-time tuning of the kernels)
+    common += os.environ.get("PISP_NVCC_FLAGS", "").split()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")

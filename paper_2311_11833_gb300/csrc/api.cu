@@ -66,11 +66,13 @@ struct pisp_handle {
   int32_t factor_policy = 0;
   int32_t units_K = 0, units_R = 0;
   int32_t n_units_f = 0, n_units_b = 0, units_maxF = 0;
-  Buf units_f, units_b, ticket, done, serr, nch;
+  Buf units_f, units_b, ticket, done, serr, nch, d_wl;
   // bounded waits of the persistent solves: polls before giving up (0 = the
   // default), and the test hook that makes one dependency unreachable
   int64_t wait_polls = 0;
   int32_t wait_unreachable = 0;
+  // persistent solve tiling (pisp_options.solve_kfuse / solve_warp_maxF)
+  int32_t kfuse = 1, warp_maxF = 32, solve_ctas = 0;
   pisp::SymDev sd{};
   // level plans (depend on the factor precision)
   int plan_precision = 0;
@@ -355,44 +357,62 @@ int build_plans(pisp_handle* h, int precision) {
   return PISP_OK;
 }
 
-// Work units of the persistent solve: per level, one unit per (front, k, RHS
-// chunk) for fronts wider than 32, and segment units of 256/SEG tasks for
-// the narrow ones; forward order is levels bottom-up, backward top-down.
+// Work units of the persistent solve, per level: fronts with more than 32
+// pivots, or wider than h->warp_maxF, get one unit per (front, k, RHS chunk),
+// solved by a whole CTA; every other front is split into segment tasks of 8,
+// 16 or 32 lanes by its size (32 lanes, in blocks of 32 rows, for fronts
+// wider than 32 with at most 32 pivots), one task per (front, group of
+// h->kfuse consecutive shifts, RHS chunk of 8), 256/SEG tasks per unit.
+// Within a level the CTA units come first, then the segment groups from the
+// widest down; the forward order is levels bottom-up, the backward order
+// top-down.  The fronts of the segment groups are listed in h->h_wl.
 int build_units(pisp_handle* h, int32_t K, int32_t R) {
   const pisp::Symbolic& S = h->sym;
   const int segch = (R + pisp::kSolveChunk - 1) / pisp::kSolveChunk;
   std::vector<std::vector<pisp::SolveUnit>> per_level(S.n_levels);
   std::vector<int32_t> nch(S.sn.size(), segch);
+  std::vector<int32_t> wl;
   int maxF = 0;
   for (int l = 0; l < S.n_levels; ++l) {
-    const pisp::LevelPlan& lp = h->plans[l];
     auto& U = per_level[l];
-    int nbig = 0;
-    for (int g = 0; g < lp.n_sgroups; ++g)
-      if (lp.sgroups[g].maxF > 32) nbig += lp.sgroups[g].count;
-    const int rc = pisp::pick_chunk(std::max(1, nbig), K, R);
+    std::vector<int32_t> lst(S.level_sn.begin() + S.level_off[l], S.level_sn.begin() + S.level_off[l + 1]);
+    std::sort(lst.begin(), lst.end(), [&](int32_t a, int32_t b) {
+      const int fa = S.sn[a].F(), fb = S.sn[b].F();
+      return fa != fb ? fa > fb : a < b;  // widest first
+    });
+    std::vector<int32_t> blk, g32w, g32, g16, g8;
+    for (int32_t sn : lst) {
+      const int F = S.sn[sn].F(), ns = S.sn[sn].ns();
+      if (ns > 32 || F > std::max(32, h->warp_maxF)) blk.push_back(sn);
+      else if (F > 32) g32w.push_back(sn);
+      else if (F > 16) g32.push_back(sn);
+      else if (F > 8) g16.push_back(sn);
+      else g8.push_back(sn);
+    }
+    const int rc = pisp::pick_chunk(std::max<int>(1, (int)blk.size()), K, R);
     const int bch = (R + rc - 1) / rc;
-    for (int g = lp.n_sgroups - 1; g >= 0; --g) {
-      const auto& G = lp.sgroups[g];
-      if (G.maxF <= 32) continue;
-      for (int q = G.count - 1; q >= 0; --q) {
-        const int32_t sn = h->h_all[G.off + q];
-        maxF = std::max(maxF, S.sn[sn].F());
-        nch[sn] = bch;
-        for (int k = 0; k < K; ++k)
-          for (int c = 0; c < bch; ++c) U.push_back({pisp::kUnitBlk, sn, k, c, rc});
-      }
+    for (int32_t sn : blk) {
+      maxF = std::max(maxF, S.sn[sn].F());
+      nch[sn] = bch;
+      for (int k = 0; k < K; ++k)
+        for (int c = 0; c < bch; ++c) U.push_back({pisp::kUnitBlk, sn, k, c, rc});
     }
-    for (int g = 0; g < lp.n_sgroups; ++g) {
-      const auto& G = lp.sgroups[g];
-      if (G.maxF > 32) continue;
-      const int seg = G.maxF <= 8 ? 8 : (G.maxF <= 16 ? 16 : 32);
+    auto seg_group = [&](const std::vector<int32_t>& g, int seg) -> int {
+      if (g.empty()) return PISP_OK;
       const int kind = seg == 8 ? pisp::kUnitSeg8 : (seg == 16 ? pisp::kUnitSeg16 : pisp::kUnitSeg32);
-      const int64_t segs = (int64_t)G.count * K * segch;
-      if (segs >= INT32_MAX) return fail(h, PISP_ERR_UNSUPPORTED, "too many solve tasks");
-      for (int64_t b = 0; b < segs; b += 256 / seg)
-        U.push_back({kind, (int32_t)G.off, (int32_t)b, (int32_t)segs, 0});
-    }
+      const int64_t off = (int64_t)wl.size();
+      const int kf = std::max(1, std::min(h->kfuse, (int)K));
+      const int64_t tasks = (int64_t)g.size() * ((K + kf - 1) / kf) * segch;
+      if (tasks >= INT32_MAX || off >= INT32_MAX) return fail(h, PISP_ERR_UNSUPPORTED, "too many solve tasks");
+      wl.insert(wl.end(), g.begin(), g.end());
+      for (int64_t b = 0; b < tasks; b += 256 / seg)
+        U.push_back({kind, (int32_t)off, (int32_t)b, (int32_t)tasks, kf});
+      return PISP_OK;
+    };
+    TRY(seg_group(g32w, 32));
+    TRY(seg_group(g32, 32));
+    TRY(seg_group(g16, 16));
+    TRY(seg_group(g8, 8));
   }
   if (h->wait_unreachable) {
     // test hook: one front's completion target can never be reached, so the
@@ -410,6 +430,7 @@ int build_units(pisp_handle* h, int32_t K, int32_t R) {
   TRY(upload(h, h->units_f, f));
   TRY(upload(h, h->units_b, b));
   TRY(upload(h, h->nch, nch));
+  TRY(upload(h, h->d_wl, wl));
   if (!h->ticket.ensure(2 * sizeof(int)) || !h->serr.ensure(sizeof(int)) ||
       !h->done.ensure((size_t)S.sn.size() * K * sizeof(int)))
     return fail(h, PISP_ERR_OOM, "device allocation failed (solve schedule)");
@@ -508,8 +529,8 @@ int solve_pass(pisp_handle* h, bool trans, const double* rhs, int rhs_mode, doub
     int pb = prof_begin(h);
     int n = pisp::launch_solve_persistent(h->precision, true, h->sd, h->units_f.as<pisp::SolveUnit>(),
                                           h->n_units_f, h->ticket.as<int>(), h->done.as<int>(),
-                                          h->serr.as<int>(), h->nch.as<int>(), h->d_all.as<int32_t>(), h->fronts.p, rhs,
-                                          rhs_mode, h->V.p, out, acc, R, h->K, h->units_maxF, h->wait_polls,
+                                          h->serr.as<int>(), h->nch.as<int>(), h->d_wl.as<int32_t>(), h->fronts.p, rhs,
+                                          rhs_mode, h->V.p, out, acc, R, h->K, h->units_maxF, h->solve_ctas, h->wait_polls,
                                           h->stream);
     TRY(count(h, n));
     prof_end(h, pb, PISP_PROF_FORWARD, bf, n);
@@ -517,8 +538,8 @@ int solve_pass(pisp_handle* h, bool trans, const double* rhs, int rhs_mode, doub
     pb = prof_begin(h);
     n = pisp::launch_solve_persistent(h->precision, false, h->sd, h->units_b.as<pisp::SolveUnit>(),
                                       h->n_units_b, h->ticket.as<int>() + 1, h->done.as<int>(),
-                                      h->serr.as<int>(), h->nch.as<int>(), h->d_all.as<int32_t>(), h->fronts.p, rhs,
-                                      rhs_mode, h->V.p, out, acc, R, h->K, h->units_maxF, h->wait_polls,
+                                      h->serr.as<int>(), h->nch.as<int>(), h->d_wl.as<int32_t>(), h->fronts.p, rhs,
+                                      rhs_mode, h->V.p, out, acc, R, h->K, h->units_maxF, h->solve_ctas, h->wait_polls,
                                       h->stream);
     TRY(count(h, n));
     prof_end(h, pb, PISP_PROF_BACKWARD, bb, n);
@@ -642,6 +663,9 @@ int analyze_impl(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   pisp::SymbolicOptions so;
   h->schedule = opt ? opt->solve_schedule : 0;
   h->factor_policy = opt ? opt->factor_policy : 0;
+  h->kfuse = opt && opt->solve_kfuse > 0 ? opt->solve_kfuse : 1;
+  h->warp_maxF = opt && opt->solve_warp_maxF > 0 ? opt->solve_warp_maxF : 32;
+  h->solve_ctas = opt && opt->solve_ctas_per_sm > 0 ? std::min(4, std::max(2, opt->solve_ctas_per_sm)) : 0;
   h->units_K = h->units_R = 0;
   if (opt) {
     so.ordering = opt->ordering;

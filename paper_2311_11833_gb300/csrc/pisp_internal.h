@@ -167,10 +167,11 @@ int max_solve_front(int precision);
 enum RhsMode { RHS_BROADCAST = 0, RHS_PER_K = 1 };
 
 // Work unit of the persistent solve schedule.  Segment units cover 256/SEG
-// consecutive (front, k, RHS chunk) segments of one size group: a = offset of
-// the group in the level list, b = first segment, c = segments in the group.
-// Block units are one (front a, perturbation b, RHS chunk c of d right-hand
-// sides).
+// consecutive segment tasks of one group (a task = one front, a group of d
+// consecutive shifts, one RHS chunk of 8): a = offset of the group in the
+// schedule's front list, b = first task, c = tasks in the group, d = shifts
+// per task.  Block units are one (front a, perturbation b, RHS chunk c of d
+// right-hand sides), solved by a whole CTA.
 enum UnitKind { kUnitSeg8 = 0, kUnitSeg16 = 1, kUnitSeg32 = 2, kUnitBlk = 3 };
 struct SolveUnit {
   int32_t kind, a, b, c, d;
@@ -181,12 +182,13 @@ constexpr int kSolveChunk = 8;  // largest RHS chunk of a task (segment tasks us
 // backward = U, top-down).  ticket (1 int) and done (S*K ints) must be zero;
 // nch[s] is the number of RHS chunks (tasks) per (front s, k); err is set to 1
 // if a bounded dependency wait gave up after `polls` polls (<= 0: the default
-// limit of 2^22 polls).
+// limit of 2^22 polls); ctas = resident CTAs per SM the kernel is compiled
+// for (2, 3 or 4; <= 0: 3 for FP32, 2 for FP64).
 int launch_solve_persistent(int precision, bool forward, const SymDev& sd, const SolveUnit* units,
                             int nunits, int* ticket, int* done, int* err, const int* nch,
                             const int32_t* d_all, const void* fronts, const double* rhs,
                             int rhs_mode, void* V, double* out, double* acc, int32_t R, int32_t K,
-                            int32_t max_blk_F, int64_t polls, cudaStream_t st);
+                            int32_t max_blk_F, int32_t ctas, int64_t polls, cudaStream_t st);
 // RHS chunk for the CTAs solving one big front at a time (persistent schedule)
 int pick_chunk(int fronts_in_level, int K, int R);
 int launch_forward_level(int precision, bool trans, const SymDev& sd, const LevelPlan& lp,

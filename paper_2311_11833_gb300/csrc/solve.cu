@@ -20,6 +20,11 @@ namespace pisp {
 namespace {
 
 constexpr int kSolveThreads = 256;
+// The persistent solve is compiled for 2, 3 and 4 resident CTAs per SM
+// (register budgets of 128, 80 and 64 per thread); the launch picks one.
+// More CTAs hide more of the dependent-load latency of the many small tasks
+// of a batch, fewer registers spill more in the blocked path of wide fronts.
+// FP32 kernels fit 80 registers with almost no spills, FP64 ones need 128.
 constexpr int kSolveSmem = 96 * 1024;
 
 // Forward substitution with L (unit lower, TRANS = false) or with U^T
@@ -719,13 +724,258 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_backward_blk(SymDev sd, co
                   acc, R, K, Sync{nullptr, nullptr, nullptr, 0});
 }
 
+// ---------------------------------------------------------------------------
+// K-fused segment tasks of the persistent schedule.  A segment of SEG lanes
+// (SEG = 8, 16 or 32) solves one (front, RHS chunk of up to kRW right-hand
+// sides) for ALL K perturbations: the task's ticket, its structure loads and
+// its dependency wait are paid once for the K solves, and the index data of
+// the gathers is fetched from memory once and re-read from L1 for the other
+// shifts.  A front qualifies when its pivots fit the segment (ns <= SEG);
+// for SEG < 32 the whole front fits (F <= SEG), for SEG = 32 the update rows
+// beyond the first 32 are handled in further blocks of 32 rows: lane i owns
+// rows i, i + 32, ...  Loops run to warp-uniform bounds (entries beyond a
+// front are zero), so segments with different fronts never diverge around a
+// shuffle.  All lanes of a warp call these bodies together.
+// ---------------------------------------------------------------------------
+struct FTask {
+  bool active;
+  int s, r0, nr, k0, k1;  // front, RHS chunk [r0, r0 + nr), shifts [k0, k1)
+};
+
+// task q of a group: front list[q / (nkg * nch)], shift group (q / nch) % nkg
+// of kf shifts, RHS chunk q % nch (nkg = ceil(K / kf) shift groups)
+__device__ __forceinline__ FTask ftask(const int32_t* list, int64_t q, int64_t ntasks, int R, int K,
+                                       int kf) {
+  FTask t{false, 0, 0, 0, 0, 0};
+  const int nch = (R + kRW - 1) / kRW;
+  const int nkg = (K + kf - 1) / kf;
+  if (q < ntasks) {
+    t.active = true;
+    t.s = list[q / ((int64_t)nch * nkg)];
+    const int kg = (int)((q / nch) % nkg);
+    t.k0 = kg * kf;
+    t.k1 = min(K, t.k0 + kf);
+    t.r0 = (int)(q % nch) * kRW;
+    t.nr = min(kRW, R - t.r0);
+  }
+  return t;
+}
+
+// the n lanes (index idx) of a segment wait for every (child, k) counter,
+// k in [k0, k1), of front s, polling in parallel; each polling lane then
+// fences (acquire), and the caller's __syncwarp orders the segment's later
+// loads after the fences
+__device__ __forceinline__ void wait_children_allk(const Sync& sy, const SymDev& sd, int s, int k0, int k1,
+                                                   int K, int idx, int n) {
+  const int cb = sd.child_off[s], ce = sd.child_off[s + 1];
+  const int nk = k1 - k0;
+  const int total = (ce - cb) * nk;
+  for (int q = idx; q < total; q += n) {
+    const int c = sd.child[cb + q / nk], k = k0 + q % nk;
+    const int* f = sy.done + (int64_t)c * K + k;
+    const int need = sy.nch[c];
+    if (ld_relaxed(f) >= need) continue;
+    int64_t i = 0;
+    for (; i < sy.polls; ++i) {
+      __nanosleep(64);
+      if (ld_relaxed(f) >= need) break;
+    }
+    if (i == sy.polls) atomicExch(sy.err, 1);
+  }
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+// the parent's counters of every k in [k0, k1) (backward solve)
+__device__ __forceinline__ void wait_parent_allk(const Sync& sy, int p, int k0, int k1, int K, int idx, int n) {
+  for (int k = k0 + idx; k < k1; k += n) {
+    const int* f = sy.done + (int64_t)p * K + k;
+    const int need = sy.nch[p];
+    if (ld_relaxed(f) >= need) continue;
+    int64_t i = 0;
+    for (; i < sy.polls; ++i) {
+      __nanosleep(64);
+      if (ld_relaxed(f) >= need) break;
+    }
+    if (i == sy.polls) atomicExch(sy.err, 1);
+  }
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+// after the segment's stores: one lane per k makes them visible and counts
+// the finished chunk of (s, k)
+__device__ __forceinline__ void publish_allk(const Sync& sy, bool active, int s, int k0, int k1, int K,
+                                             int idx, int n) {
+  __syncwarp();
+  if (!active) return;
+  for (int k = k0 + idx; k < k1; k += n) {
+    __threadfence();
+    asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(sy.done + (int64_t)s * K + k) : "memory");
+  }
+}
+
+// Forward solve with L (unit lower) of one front for all K: y = L11^{-1} v on
+// the pivot rows (shuffle chain), then v_i -= L21(i, :) y on the update rows;
+// V[k][r][0..F) receives the result (pivot part y, update part the
+// contribution the parent gathers).  yb: this warp's [32][kRW] staging area
+// for y when the front has update rows beyond the first 32.
+template <typename T, int SEG>
+__device__ __forceinline__ void kseg_forward(const SymDev& sd, const FTask& t, int sl, T* yb,
+                                             const T* __restrict__ fronts, const double* __restrict__ rhs,
+                                             int rhs_mode, T* __restrict__ V, int R, int K, const Sync& sy) {
+  int ns = 0, F = 0, c0 = 0;
+  int64_t fo = 0, vo = 0;
+  if (t.active) {
+    ns = sd.ns[t.s];
+    F = ns + sd.ms[t.s];
+    c0 = sd.c0[t.s];
+    fo = sd.front_off[t.s];
+    vo = sd.vec_off[t.s];
+  }
+  const int r0 = t.r0, nr = t.nr;
+  if (sy.done && t.active) wait_children_allk(sy, sd, t.s, t.k0, t.k1, K, sl, SEG);
+  __syncwarp();
+  const int nrw = __reduce_max_sync(kFull, nr);
+  const int nsw = __reduce_max_sync(kFull, ns);
+  const int nb = (__reduce_max_sync(kFull, F) + SEG - 1) / SEG;  // > 1 only for SEG = 32
+  const int nkw = __reduce_max_sync(kFull, t.k1 - t.k0);          // shifts per task (uniform)
+  for (int kk = 0; kk < nkw; ++kk) {
+    const int k = t.active ? min(t.k0 + kk, t.k1 - 1) : 0;
+    const bool kon = t.active && t.k0 + kk < t.k1;
+    const T* f = fronts + (kon ? (int64_t)K * fo + (int64_t)k * F * F : 0);
+    T Lr[SEG];
+#pragma unroll
+    for (int c = 0; c < SEG; ++c) Lr[c] = (kon && c < ns && sl > c && sl < F) ? f[sl + c * F] : T(0);
+    T vv[kRW];
+#pragma unroll
+    for (int r = 0; r < kRW; ++r)
+      vv[r] = (kon && r < nr && sl < F) ? gather_position<T>(sd, t.s, sl, ns, c0, rhs, rhs_mode, V, k, K, R, r0 + r)
+                                        : T(0);
+#pragma unroll
+    for (int c = 0; c < SEG - 1; ++c) {
+      if (c >= nsw) break;
+#pragma unroll
+      for (int r = 0; r < kRW; ++r)
+        if (r < nrw) vv[r] -= Lr[c] * __shfl_sync(kFull, vv[r], c, SEG);
+    }
+    T* Vs = V + (kon ? (int64_t)K * R * vo + ((int64_t)k * R + r0) * F : 0);
+#pragma unroll
+    for (int r = 0; r < kRW; ++r)
+      if (kon && r < nr && sl < F) Vs[(int64_t)r * F + sl] = vv[r];
+    if (SEG == 32 && nb > 1) {
+#pragma unroll
+      for (int r = 0; r < kRW; ++r) yb[sl * kRW + r] = vv[r];
+      __syncwarp();
+      for (int b = 1; b < nb; ++b) {
+        const int i = b * 32 + sl;
+        T acc[kRW];
+#pragma unroll
+        for (int r = 0; r < kRW; ++r)
+          acc[r] = (kon && r < nr && i < F) ? gather_position<T>(sd, t.s, i, ns, c0, rhs, rhs_mode, V, k, K, R, r0 + r)
+                                            : T(0);
+        for (int c = 0; c < nsw; ++c) {
+          const T l = (kon && c < ns && i < F) ? f[i + (int64_t)c * F] : T(0);
+#pragma unroll
+          for (int r = 0; r < kRW; ++r) acc[r] -= l * yb[c * kRW + r];
+        }
+#pragma unroll
+        for (int r = 0; r < kRW; ++r)
+          if (kon && r < nr && i < F) Vs[(int64_t)r * F + i] = acc[r];
+      }
+      __syncwarp();  // yb is reused by the next k
+    }
+  }
+  if (sy.done) publish_allk(sy, t.active, t.s, t.k0, t.k1, K, sl, SEG);
+}
+
+// Backward solve with U of one front for all K: z = y - U12 x_R (update rows
+// gathered from the ancestors' solutions SEG at a time and shared by
+// shuffles), then x = U11^{-1} z by a shuffle chain; x is written to `out`
+// (and added to `acc`).
+template <typename T, int SEG>
+__device__ __forceinline__ void kseg_backward(const SymDev& sd, const FTask& t, int sl,
+                                              const T* __restrict__ fronts, const T* __restrict__ V,
+                                              double* out, double* acc, int R, int K, const Sync& sy) {
+  int ns = 0, ms = 0, F = 0, c0 = 0;
+  int64_t fo = 0, vo = 0, ro = 0;
+  if (t.active) {
+    ns = sd.ns[t.s];
+    ms = sd.ms[t.s];
+    F = ns + ms;
+    c0 = sd.c0[t.s];
+    fo = sd.front_off[t.s];
+    vo = sd.vec_off[t.s];
+    ro = sd.row_off[t.s];
+  }
+  const int r0 = t.r0, nr = t.nr;
+  if (sy.done && t.active && ms > 0) wait_parent_allk(sy, sd.parent[t.s], t.k0, t.k1, K, sl, SEG);
+  __syncwarp();
+  const int nrw = __reduce_max_sync(kFull, nr);
+  const int msw = __reduce_max_sync(kFull, ms);
+  const int nsw = __reduce_max_sync(kFull, ns);
+  const int nkw = __reduce_max_sync(kFull, t.k1 - t.k0);          // shifts per task (uniform)
+  for (int kk = 0; kk < nkw; ++kk) {
+    const int k = t.active ? min(t.k0 + kk, t.k1 - 1) : 0;
+    const bool kon = t.active && t.k0 + kk < t.k1;
+    const T* f = fronts + (kon ? (int64_t)K * fo + (int64_t)k * F * F : 0);
+    const T* Vs = V + (kon ? (int64_t)K * R * vo + ((int64_t)k * R + r0) * F : 0);
+    T zt[kRW];
+#pragma unroll
+    for (int r = 0; r < kRW; ++r) zt[r] = (kon && r < nr && sl < ns) ? Vs[(int64_t)r * F + sl] : T(0);
+    const T rd = (kon && sl < ns) ? T(1) / f[sl * (F + 1)] : T(0);
+    for (int j0 = 0; j0 < msw; j0 += SEG) {
+      const int j = j0 + sl;
+      const int64_t row = (j < ms) ? sd.rows[ro + j] : 0;
+      T xt[kRW];
+#pragma unroll
+      for (int r = 0; r < kRW; ++r)
+        xt[r] = (kon && r < nr && j < ms) ? (T)__ldcg(out + (row * K + k) * R + r0 + r) : T(0);
+#pragma unroll 4
+      for (int jj = 0; jj < SEG; ++jj) {
+        if (j0 + jj >= msw) break;
+        const T u = (kon && sl < ns && j0 + jj < ms) ? f[sl + (int64_t)(ns + j0 + jj) * F] : T(0);
+#pragma unroll
+        for (int r = 0; r < kRW; ++r)
+          if (r < nrw) zt[r] -= u * __shfl_sync(kFull, xt[r], jj, SEG);
+      }
+    }
+#pragma unroll 4
+    for (int c = SEG - 1; c >= 0; --c) {
+      if (c >= nsw) continue;
+      const T u = (kon && sl < ns && c > sl && c < ns) ? f[sl + c * F] : T(0);
+#pragma unroll
+      for (int r = 0; r < kRW; ++r) {
+        if (r < nrw) {
+          if (sl == c) zt[r] *= rd;
+          zt[r] -= u * __shfl_sync(kFull, zt[r], c, SEG);
+        }
+      }
+    }
+    if (kon && sl < ns) {
+      double* o = out + ((int64_t)(c0 + sl) * K + k) * R + r0;
+#pragma unroll
+      for (int r = 0; r < kRW; ++r)
+        if (r < nr) o[r] = (double)zt[r];
+      if (acc) {
+        double* a = acc + ((int64_t)(c0 + sl) * K + k) * R + r0;
+#pragma unroll
+        for (int r = 0; r < kRW; ++r)
+          if (r < nr) a[r] += (double)zt[r];
+      }
+    }
+  }
+  if (sy.done) publish_allk(sy, t.active, t.s, t.k0, t.k1, K, sl, SEG);
+}
+
 // ---- persistent schedule: one launch per direction -------------------------
 // CTAs take work units in ticket order (levels bottom-up for the forward
-// solve, top-down for the backward solve).  A unit only waits for units with
-// smaller tickets, which running CTAs already hold, so the schedule cannot
-// deadlock whatever the number of resident CTAs.
-template <typename T, bool FWD>
-__global__ void __launch_bounds__(kSolveThreads, 2)
+// solve, top-down for the backward solve).  A unit is either one (front, k,
+// RHS chunk) of a front with more than 32 pivots, solved by the whole CTA
+// (blocked path), or 256/SEG K-fused segment tasks, one per segment of the
+// CTA's warps.  A unit only waits for units with smaller tickets, which
+// running CTAs already hold, so the schedule cannot deadlock whatever the
+// number of resident CTAs.
+template <typename T, bool FWD, int MINB>
+__global__ void __launch_bounds__(kSolveThreads, MINB)
 k_solve_persistent(SymDev sd, const SolveUnit* __restrict__ units, int nunits, int* ticket,
                    int* done, int* err, const int* __restrict__ nch, const int32_t* __restrict__ all,
                    const T* __restrict__ fronts, const double* __restrict__ rhs, int rhs_mode,
@@ -738,7 +988,6 @@ k_solve_persistent(SymDev sd, const SolveUnit* __restrict__ units, int nunits, i
     if (tid == 0) s_unit = atomicAdd(ticket, 1);
     __syncthreads();
     const int u = s_unit;
-    __syncthreads();
     if (u >= nunits) return;
     const SolveUnit U = units[u];
     if (U.kind == kUnitBlk) {
@@ -749,20 +998,18 @@ k_solve_persistent(SymDev sd, const SolveUnit* __restrict__ units, int nunits, i
         blk_backward<T>(sd, U.a, U.b, r0, min(U.d, R - r0), U.c, smraw, fronts, V, out, acc, R, K, sy);
     } else {
       const int SEG = U.kind == kUnitSeg8 ? 8 : (U.kind == kUnitSeg16 ? 16 : 32);
-      const int64_t sg = (int64_t)U.b + tid / SEG;
-      const SegTask t = seg_task(sd, all + U.a, sg, (int64_t)U.c, R, K);
+      const int64_t q = (int64_t)U.b + tid / SEG;
+      const FTask t = ftask(all + U.a, q, (int64_t)U.c, R, K, max(1, U.d));
+      T* yb = reinterpret_cast<T*>(smraw) + (tid >> 5) * 32 * kRW;
       if (U.kind == kUnitSeg8) {
-        auto bw = reinterpret_cast<T (*)[kRW][9]>(smraw);
-        if (FWD) seg_forward<T, 8>(sd, t, tid % 8, bw[tid / 8], fronts, rhs, rhs_mode, V, R, K, sy);
-        else seg_backward<T, 8>(sd, t, tid % 8, fronts, V, out, acc, R, K, sy);
+        if (FWD) kseg_forward<T, 8>(sd, t, tid % 8, yb, fronts, rhs, rhs_mode, V, R, K, sy);
+        else kseg_backward<T, 8>(sd, t, tid % 8, fronts, V, out, acc, R, K, sy);
       } else if (U.kind == kUnitSeg16) {
-        auto bw = reinterpret_cast<T (*)[kRW][17]>(smraw);
-        if (FWD) seg_forward<T, 16>(sd, t, tid % 16, bw[tid / 16], fronts, rhs, rhs_mode, V, R, K, sy);
-        else seg_backward<T, 16>(sd, t, tid % 16, fronts, V, out, acc, R, K, sy);
+        if (FWD) kseg_forward<T, 16>(sd, t, tid % 16, yb, fronts, rhs, rhs_mode, V, R, K, sy);
+        else kseg_backward<T, 16>(sd, t, tid % 16, fronts, V, out, acc, R, K, sy);
       } else {
-        auto bw = reinterpret_cast<T (*)[kRW][33]>(smraw);
-        if (FWD) seg_forward<T, 32>(sd, t, tid % 32, bw[tid / 32], fronts, rhs, rhs_mode, V, R, K, sy);
-        else seg_backward<T, 32>(sd, t, tid % 32, fronts, V, out, acc, R, K, sy);
+        if (FWD) kseg_forward<T, 32>(sd, t, tid % 32, yb, fronts, rhs, rhs_mode, V, R, K, sy);
+        else kseg_backward<T, 32>(sd, t, tid % 32, fronts, V, out, acc, R, K, sy);
       }
     }
     __syncthreads();
@@ -1042,41 +1289,58 @@ int launch_backward_level(int precision, bool trans, const SymDev& sd, const Lev
 }
 
 namespace {
-template <typename T>
-int persistent_impl(bool forward, const SymDev& sd, const SolveUnit* units, int nunits, int* ticket,
-                    int* done, int* err, const int* nch, const int32_t* d_all, const void* fronts, const double* rhs,
-                    int rhs_mode, void* V, double* out, double* acc, int R, int K, int max_blk_F,
-                    int64_t polls, cudaStream_t st) {
-  if (polls <= 0) polls = kWaitPolls;
-  if (nunits == 0) return 0;
+template <typename T, int M>
+int persistent_launch(bool forward, const SymDev& sd, const SolveUnit* units, int nunits, int* ticket,
+                      int* done, int* err, const int* nch, const int32_t* d_all, const void* fronts,
+                      const double* rhs, int rhs_mode, void* V, double* out, double* acc, int R, int K,
+                      size_t smem, int64_t polls, cudaStream_t st) {
   static std::atomic<int> nsm_dev[kMaxDevices];
-  int occ_f = 0, occ_b = 0;
-  const size_t seg_smem = (size_t)(256 / 8) * kRW * 9 * sizeof(T);
-  const size_t mF = (size_t)std::max(max_blk_F, 1);
-  const size_t blk_smem = (size_t)(2 * 32 * kBS + kSolveChunk * mF) * sizeof(T);
-  const size_t smem = std::max(seg_smem, blk_smem);
   const int dev = current_device();
   int nsm = nsm_dev[dev].load(std::memory_order_acquire);
   if (!nsm) {
-    cudaFuncSetAttribute(k_solve_persistent<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_solve_persistent<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_solve_persistent<T, true, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_solve_persistent<T, false, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     nsm_dev[dev].store(nsm, std::memory_order_release);
   }
-  if (smem > 200 * 1024) return -1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_solve_persistent<T, true>, kSolveThreads, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_solve_persistent<T, false>, kSolveThreads, smem);
-  const int occ = std::max(1, forward ? occ_f : occ_b);
-  const int grid = std::max(1, std::min(nunits, occ * std::max(nsm, 1)));
+  int occ = 0;
   if (forward)
-    k_solve_persistent<T, true><<<grid, kSolveThreads, smem, st>>>(
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_persistent<T, true, M>, kSolveThreads, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_persistent<T, false, M>, kSolveThreads, smem);
+  const int grid = std::max(1, std::min(nunits, std::max(1, occ) * std::max(nsm, 1)));
+  if (forward)
+    k_solve_persistent<T, true, M><<<grid, kSolveThreads, smem, st>>>(
         sd, units, nunits, ticket, done, err, nch, d_all, (const T*)fronts, rhs, rhs_mode, (T*)V, out, acc, R, K,
         polls);
   else
-    k_solve_persistent<T, false><<<grid, kSolveThreads, smem, st>>>(
+    k_solve_persistent<T, false, M><<<grid, kSolveThreads, smem, st>>>(
         sd, units, nunits, ticket, done, err, nch, d_all, (const T*)fronts, rhs, rhs_mode, (T*)V, out, acc, R, K,
         polls);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+template <typename T>
+int persistent_impl(bool forward, const SymDev& sd, const SolveUnit* units, int nunits, int* ticket,
+                    int* done, int* err, const int* nch, const int32_t* d_all, const void* fronts, const double* rhs,
+                    int rhs_mode, void* V, double* out, double* acc, int R, int K, int max_blk_F, int ctas,
+                    int64_t polls, cudaStream_t st) {
+  if (polls <= 0) polls = kWaitPolls;
+  if (nunits == 0) return 0;
+  const size_t seg_smem = (size_t)(kSolveThreads / 32) * 32 * kRW * sizeof(T);  // y staging per warp
+  const size_t mF = (size_t)std::max(max_blk_F, 1);
+  const size_t blk_smem = (size_t)(2 * 32 * kBS + kSolveChunk * mF) * sizeof(T);
+  const size_t smem = std::max(seg_smem, blk_smem);
+  if (smem > 200 * 1024) return -1;
+  if (ctas <= 0) ctas = sizeof(T) == 4 ? 3 : 2;
+  if (ctas >= 4)
+    return persistent_launch<T, 4>(forward, sd, units, nunits, ticket, done, err, nch, d_all, fronts, rhs,
+                                   rhs_mode, V, out, acc, R, K, smem, polls, st);
+  if (ctas == 3)
+    return persistent_launch<T, 3>(forward, sd, units, nunits, ticket, done, err, nch, d_all, fronts, rhs,
+                                   rhs_mode, V, out, acc, R, K, smem, polls, st);
+  return persistent_launch<T, 2>(forward, sd, units, nunits, ticket, done, err, nch, d_all, fronts, rhs,
+                                 rhs_mode, V, out, acc, R, K, smem, polls, st);
 }
 
 }  // namespace
@@ -1085,12 +1349,12 @@ int launch_solve_persistent(int precision, bool forward, const SymDev& sd, const
                             int nunits, int* ticket, int* done, int* err, const int* nch,
                             const int32_t* d_all, const void* fronts, const double* rhs,
                             int rhs_mode, void* V, double* out, double* acc, int32_t R, int32_t K,
-                            int32_t max_blk_F, int64_t polls, cudaStream_t st) {
+                            int32_t max_blk_F, int32_t ctas, int64_t polls, cudaStream_t st) {
   if (precision == PISP_FP32)
     return persistent_impl<float>(forward, sd, units, nunits, ticket, done, err, nch, d_all, fronts,
-                                  rhs, rhs_mode, V, out, acc, R, K, max_blk_F, polls, st);
+                                  rhs, rhs_mode, V, out, acc, R, K, max_blk_F, ctas, polls, st);
   return persistent_impl<double>(forward, sd, units, nunits, ticket, done, err, nch, d_all, fronts,
-                                 rhs, rhs_mode, V, out, acc, R, K, max_blk_F, polls, st);
+                                 rhs, rhs_mode, V, out, acc, R, K, max_blk_F, ctas, polls, st);
 }
 
 int launch_combine(const SymDev& sd, const double* X, const Shifts& sh, int32_t R, double* x,

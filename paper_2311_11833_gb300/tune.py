@@ -1,14 +1,25 @@
 """Autotuner: picks the library options that run a given pattern fastest.
 
-The options that change performance but not the result are the supernode
-amalgamation (relax_small, relax_zeros: front sizes and tree height), the
-factor policy of wide fronts (column-block owners, CTA clusters, tile DAG or
-per-panel launches) and the solve schedule (persistent or one launch per level).  For
-one sparsity pattern, shift count, RHS count and precision, `autotune` times
-every candidate on the GPU with CUDA events (factor + solve, a few
-repetitions after a warm-up) and returns the fastest.  Results are cached in
-a JSON file (path from $PISP_TUNE_CACHE, or the `cache` argument) keyed by a
-hash of the pattern and the call shape.
+The options that change performance but not the result:
+
+* the tiling of the persistent solve -- resident CTAs per SM (register
+  budget 128 / 80 / 64 per thread), shifts per segment task of a narrow
+  front (one task per shift, or one task for a group of shifts that pays
+  the front's dependency wait and structure loads once) and the widest front
+  one 32-lane segment takes before a whole CTA does;
+* the supernode amalgamation (relax_small, relax_zeros: front sizes and
+  tree height) and the factor policy of wide fronts (column-block owners,
+  CTA clusters, tile DAG or per-panel launches);
+* the solve schedule (persistent or one launch per level).
+
+For one sparsity pattern, shift count, RHS count, precision and sweep count,
+`autotune` times candidates on the GPU with CUDA events over replays of the
+step the library captures in a CUDA graph (factor + solve + sweeps), and
+returns the fastest.  The default search is staged: first the solve tiling
+with the default amalgamation and factor policy, then the amalgamation and
+factor policy with the best tiling.  Results are cached in a JSON file (path
+from $PISP_TUNE_CACHE, or the `cache` argument) keyed by a hash of the
+pattern and the call shape.
 """
 from __future__ import annotations
 
@@ -22,11 +33,34 @@ import numpy as np
 RELAX = [(8, 0.05), (4, 0.0), (16, 0.10), (32, 0.20)]
 POLICIES = [0, 1, 2, 3]
 SCHEDULES = [0, 1]
+# persistent solve tiling: (resident CTAs per SM, shifts per narrow task, widest warp front)
+TILINGS = [(c, kf, wm) for c in (2, 3, 4) for kf, wm in ((1, 32), (1, 64), (2, 64), (2, 32))]
+DEFAULT = dict(relax_small=8, relax_zeros=0.05, factor_policy=0, solve_schedule=0)
 
 
 def candidates():
+    """The full grid (amalgamation x factor policy x schedule), default tiling."""
     for (rs, rz), fp, sch in itertools.product(RELAX, POLICIES, SCHEDULES):
         yield dict(relax_small=rs, relax_zeros=rz, factor_policy=fp, solve_schedule=sch)
+
+
+def _tiling(c, kf, wm):
+    return dict(solve_ctas_per_sm=c, solve_kfuse=kf, solve_warp_maxF=wm)
+
+
+def staged_candidates():
+    """Stage 1: every solve tiling with the default analysis; stage 2 is built
+    from stage 1's winner by `autotune`."""
+    return [dict(DEFAULT, **_tiling(*t)) for t in TILINGS]
+
+
+def _stage2(best: dict):
+    out = []
+    for (rs, rz), fp in itertools.product(RELAX, (0, 2)):
+        o = dict(best, relax_small=rs, relax_zeros=rz, factor_policy=fp)
+        if o != best:
+            out.append(o)
+    return out
 
 
 def _key(sizes, row_ptr, col, K, R, precision, sweeps) -> str:
@@ -44,9 +78,31 @@ def _load(path):
         return {}
 
 
+def _time(Solver, sizes, row_ptr, col, values, D, t, b, x, precision, sweeps, reps, opts):
+    import torch
+    s = Solver(sizes, row_ptr, col, **opts)
+    try:
+        s.graph_capture(values, D, t, b, x, precision=precision, sweeps=sweeps)
+        for _ in range(2):
+            s.graph_launch()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(reps):
+            s.graph_launch()
+        ev[1].record()
+        ev[1].synchronize()
+        return ev[0].elapsed_time(ev[1]) / reps
+    finally:
+        s.close()
+
+
 def autotune(sizes, row_ptr, col, values, D, t, b, precision="fp32", sweeps=2, reps=5,
              cache: str | None = None, options=None) -> dict:
-    """Fastest options for this pattern / call shape: {"options": {...}, "ms": ..., "all": [...]}."""
+    """Fastest options for this pattern / call shape: {"options": {...}, "ms": ..., "all": [...]}.
+
+    options: an explicit candidate list (timed as given); default: the staged
+    search over the solve tiling, then the amalgamation and factor policy."""
     import torch
 
     from .solver import Solver
@@ -58,23 +114,21 @@ def autotune(sizes, row_ptr, col, values, D, t, b, precision="fp32", sweeps=2, r
         hit = _load(cache).get(key)
         if hit:
             return hit
+    b2 = b.reshape(b.shape[0], -1).contiguous()
+    x = torch.empty_like(b2)
     results = []
-    x = torch.empty_like(b)
-    for opts in (options or list(candidates())):
-        s = Solver(sizes, row_ptr, col, **opts)
-        for _ in range(2):
-            s.factor(values, D, t, precision)
-            s.solve(b, sweeps=sweeps, out=x)
-        torch.cuda.synchronize()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        ev[0].record()
-        for _ in range(reps):
-            s.factor(values, D, t, precision)
-            s.solve(b, sweeps=sweeps, out=x)
-        ev[1].record()
-        ev[1].synchronize()
-        results.append({"options": opts, "ms": ev[0].elapsed_time(ev[1]) / reps})
-        s.close()
+
+    def run(cands):
+        for opts in cands:
+            ms = _time(Solver, sizes, row_ptr, col, values, D, t, b2, x, precision, sweeps, reps, opts)
+            results.append({"options": opts, "ms": ms})
+
+    if options is not None:
+        run(options)
+    else:
+        run(staged_candidates())
+        best1 = min(results, key=lambda r: r["ms"])["options"]
+        run(_stage2(best1))
     best = min(results, key=lambda r: r["ms"])
     out = {"options": best["options"], "ms": best["ms"], "all": results}
     if cache:

@@ -201,9 +201,18 @@ def test_autograd_fp32_passes_sweeps_to_the_adjoint(pisp):
 
 
 def test_central_differences_differentiation_config(pisp):
-    """dL/dvalues on 64 sampled entries and dL/db on 8 entries of the 1354-bus
-    workload (K = 4, R = 64, FP64): central differences of the GPU forward with
-    the relative step h = 1e-6 max(1, |a_e|)."""
+    """dL/dvalues and dL/db of L = sum(w * x_hat) on the 1354-bus workload
+    (K = 4, R = 64, FP64) against central differences of the GPU forward with
+    the relative step h = 1e-6 max(1, |a_e|): a random direction over all of
+    A's pattern and one over all of b (relative tolerance 1e-5), and 64 sampled
+    entries of A and 8 of b.
+
+    A central difference cannot be more accurate than the rounding noise of
+    the two losses it subtracts: on this system (rho(A^{-1} D) = 666) that is
+    a few 1e-13 of |L| = 1e4 even for the oracle's partial-pivoting LU, which
+    is 1e-3 absolute per entry at h = 1e-6.  That noise, delta, is measured as
+    the difference between the GPU loss and the oracle's loss at the base
+    point, and a sampled entry passes if |fd - g| <= 1e-5 |g| + 10 delta / step."""
     import torch
     c = pfgen.CONFIGS["differentiation"]
     inst = pfgen.make_instance("differentiation")
@@ -211,14 +220,15 @@ def test_central_differences_differentiation_config(pisp):
     s = pisp.Solver(inst.n, inst.row_ptr, inst.col)
     vals = _dev(inst.val)
     Dt = _dev(inst.D)
-    b = _dev(pfgen.rhs(inst.n, c["R"], 1))
-    w = _dev(pfgen.rhs(inst.n, c["R"], 2))
+    b_h, w_h = pfgen.rhs(inst.n, c["R"], 1), pfgen.rhs(inst.n, c["R"], 2)
+    b, w = _dev(b_h), _dev(w_h)
     s.factor(vals, Dt, t, "fp64")
-    s.solve(b)
+    x0 = s.solve(b)
+    L0 = float((x0 * w).sum())
     gb, gv = s.adjoint(w)
     gb, gv = gb.cpu().numpy(), gv.cpu().numpy()
-    gscale = float(np.abs(gv).max())
-    bscale = float(np.abs(gb).max())
+    L_oracle = float((oracle.x_hat(oracle.to_scipy(inst), inst.D, t, b_h) * w_h).sum())
+    delta = max(abs(L0 - L_oracle), 1e-13 * abs(L0))
 
     def L(v, bb):
         s.factor(v, Dt, t, "fp64")
@@ -226,20 +236,32 @@ def test_central_differences_differentiation_config(pisp):
 
     h = 1e-6
     rng = np.random.default_rng(1354)
-    worst = 0.0
+    # directional derivatives over the whole pattern and the whole of b
+    scale = np.maximum(1.0, np.abs(inst.val))
+    d = rng.choice([-1.0, 1.0], inst.nnz) * scale
+    dd = _dev(d)
+    fd = (L(vals + h * dd, b) - L(vals - h * dd, b)) / (2 * h)
+    assert abs(fd - gv @ d) <= 1e-5 * abs(gv @ d) + 10 * delta / h
+    db = rng.choice([-1.0, 1.0], (inst.n, c["R"]))
+    dbt = _dev(db)
+    fd = (L(vals, b + h * dbt) - L(vals, b - h * dbt)) / (2 * h)
+    assert abs(fd - np.sum(gb * db)) <= 1e-5 * abs(np.sum(gb * db)) + 10 * delta / h
+    # sampled entries
+    bad = []
     for e in rng.choice(inst.nnz, 64, replace=False):
-        step = h * max(1.0, abs(inst.val[e]))
+        step = h * scale[e]
         vp, vm = vals.clone(), vals.clone()
         vp[e] += step
         vm[e] -= step
         fd = (L(vp, b) - L(vm, b)) / (2 * step)
-        worst = max(worst, abs(fd - gv[e]) / (abs(gv[e]) + 1e-6 * gscale))
-    assert worst <= 1e-5, worst
+        if abs(fd - gv[e]) > 1e-5 * abs(gv[e]) + 10 * delta / step:
+            bad.append((int(e), fd, gv[e]))
+    assert not bad, (delta, bad)
     for i, r in rng.integers(0, [inst.n, c["R"]], size=(8, 2)):
         bp, bm = b.clone(), b.clone()
         bp[i, r] += h
         bm[i, r] -= h
         fd = (L(vals, bp) - L(vals, bm)) / (2 * h)
-        assert abs(fd - gb[i, r]) <= 1e-5 * abs(gb[i, r]) + 1e-6 * bscale
+        assert abs(fd - gb[i, r]) <= 1e-5 * abs(gb[i, r]) + 10 * delta / h
     s.close()
     torch.cuda.synchronize()

@@ -49,3 +49,16 @@ def test_unreadable_cache_is_empty(tmp_path):
     bad = tmp_path / "bad.json"
     bad.write_text("{not json")
     assert tune._load(str(bad)) == {}
+
+
+def test_staged_search_covers_the_solve_tiling_then_the_analysis():
+    s1 = tune.staged_candidates()
+    tilings = {(d["solve_ctas_per_sm"], d["solve_kfuse"], d["solve_warp_maxF"]) for d in s1}
+    assert tilings == set(tune.TILINGS) and len(s1) == len(tune.TILINGS)
+    assert all({k: d[k] for k in tune.DEFAULT} == tune.DEFAULT for d in s1)
+    best = s1[5]
+    s2 = tune._stage2(best)
+    # stage 2 keeps stage 1's tiling and varies amalgamation and factor policy only
+    assert all(d["solve_ctas_per_sm"] == best["solve_ctas_per_sm"] and d["solve_kfuse"] == best["solve_kfuse"]
+               for d in s2)
+    assert best not in s2 and len(s2) == len(tune.RELAX) * 2 - 1
