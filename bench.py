@@ -72,9 +72,10 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=None)
     ap.add_argument("--eps", type=float, default=1e-2)
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of a CUDA graph")
-    ap.add_argument("--factor-policy", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--factor-policy", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="fronts wider than 64: 0 single CTA / column-block owners (default), "
-                         "1 CTA clusters, 2 single CTA / tile DAG, 3 single CTA / per-panel launches")
+                         "1 CTA clusters, 2 single CTA / tile DAG, 3 single CTA / per-panel launches, "
+                         "4 one persistent launch for the whole factorisation")
     ap.add_argument("--schedule", type=int, default=0, choices=[0, 1],
                     help="solve schedule: 0 persistent (default), 1 one launch per level")
     ap.add_argument("--kfuse", type=int, default=0, help="persistent solve: shifts per narrow-front task")
@@ -406,7 +407,9 @@ def run_pisp(args, rank, world, local_rank):
                    "factor_precision": precision, "combine_precision": "fp64", "sweeps": sweeps,
                    "graph": "library (pisp_graph_capture)" if use_graph else None,
                    "solve_schedule": ["persistent", "per-level"][args.schedule],
-                   "factor_policy": ["single-CTA/column-block-owners", "clusters", "single-CTA/tile-DAG", "single-CTA/per-panel"][args.factor_policy], "l2": "flushed between steps (256 MB write outside the events)",
+                   "factor_policy": ["single-CTA/column-block-owners", "clusters", "single-CTA/tile-DAG",
+                                     "single-CTA/per-panel", "one-launch-persistent"][
+                       (tuned["options"].get("factor_policy", 0) if tuned else args.factor_policy)], "l2": "flushed between steps (256 MB write outside the events)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "families": families,
@@ -516,7 +519,7 @@ def study_dense(args):
             e1.record()
             e1.synchronize()
             prof = arm.s.profile_read()
-            fac = (prof["factor_small"]["ms"] + prof["factor_big"]["ms"]) / reps
+            fac = (prof["factor_small"]["ms"] + prof["factor_big"]["ms"] + prof["factor_persistent"]["ms"]) / reps
             sol = (prof["forward"]["ms"] + prof["backward"]["ms"]) / reps
             rows.append({"n": n, "G": G, "ms_step": round(e0.elapsed_time(e1) / reps, 4),
                          "ms_factor": round(fac, 4), "ms_solve": round(sol, 4)})

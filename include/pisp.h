@@ -81,7 +81,13 @@ typedef struct pisp_options {
                              launch per level, with look-ahead);
                              3 = as 0 but larger fronts by a blocked factorisation
                              in global memory (one panel launch and one
-                             tiled-update launch per 32 pivots) */
+                             tiled-update launch per 32 pivots);
+                             4 = ONE persistent launch for every level, shift
+                             and instance: fronts of at most 32 one warp each,
+                             fronts up to 128 (FP32) / 64 (FP64) one CTA each
+                             in shared memory, wider fronts as owner tiles;
+                             a task waits (boundedly) only for its children's
+                             completion counters */
   int32_t solve_kfuse;    /* persistent solve: shifts per segment task of a front
                              with at most 32 pivots (0 = 1): larger values pay a
                              front's dependency wait and structure loads once
@@ -391,7 +397,8 @@ enum {
   PISP_PROF_BACKWARD = 3,     /* backward substitution */
   PISP_PROF_RESIDUAL = 4,     /* FP64 residuals of the sweeps */
   PISP_PROF_COMBINE = 5,      /* expansion-weighted combine */
-  PISP_PROF_FAMILIES = 6
+  PISP_PROF_FACTOR = 6,       /* the whole factorisation in one launch (factor policy 4) */
+  PISP_PROF_FAMILIES = 7
 };
 
 /* on != 0: start recording brackets (forgets the previous recording); the

@@ -78,7 +78,7 @@ _SIGS = {
     "pisp_profile_reset": (c_int32, [c_void_p]),
     "pisp_profile_name": (ctypes.c_char_p, [c_int32]),
 }
-PROF_FAMILIES = 6
+PROF_FAMILIES = 7
 
 _lib = None
 

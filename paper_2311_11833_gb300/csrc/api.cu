@@ -82,6 +82,12 @@ struct pisp_handle {
   std::vector<pisp::DagTask> h_dag;
   int32_t dag_max_flags = 0;
   Buf d_small, d_big, d_all, d_dag, dag_ticket, dag_flags;
+  // one-launch factorisation (factor policy 4): all-level task list, the
+  // warp-front list, completion targets, counters and owner release flags
+  int32_t n_ftasks = 0, fac_CH = 32, fac_nflags = 0;
+  size_t fac_smem = 0;
+  double fac_bytes = 0;
+  Buf d_ftasks, d_fwl, d_fneed, fdone, fflags, fticket;
   // numeric state
   int32_t K = 0, precision = 0, K_hint = 1, plan_K = 0;
   double t[PISP_K_MAX] = {}, beta[PISP_K_MAX] = {}, w_last[PISP_K_MAX] = {};
@@ -210,6 +216,72 @@ int upload(pisp_handle* h, Buf& b, const std::vector<T>& v) {
 int factor_path(const pisp_handle* h, int F, int precision) {
   if (h->factor_policy == 1) return pisp::front_cluster_size(F, precision);
   return F <= pisp::small_front_limit(precision) ? 0 : -1;
+}
+
+// Task list of the one-launch factorisation (factor policy 4): per level,
+// bottom-up, the owner tiles of the fronts wider than the shared-memory
+// limit (in (block, chunk) order, every tile after the ones it waits for),
+// then one task per (front, k) for the shared-memory fronts, then groups of
+// 8 (front, k) warp tasks for the fronts of at most 32.
+int build_persistent_factor(pisp_handle* h, int precision, int32_t K) {
+  const pisp::Symbolic& S = h->sym;
+  const int Fc = pisp::persistent_cta_front_limit(precision);
+  int maxBig = 0, maxCta = 0;
+  for (const auto& sn : S.sn) {
+    if (sn.F() > Fc) maxBig = std::max(maxBig, sn.F());
+    else if (sn.F() > 32) maxCta = std::max(maxCta, sn.F());
+  }
+  const int CH = maxBig > 0 ? pisp::owner_chunk_rows(precision, maxBig) : 32;
+  std::vector<pisp::FactorTask> ft;
+  std::vector<int32_t> wl, need(S.sn.size(), 1);
+  int64_t nflags = 0;
+  for (int l = 0; l < S.n_levels; ++l) {
+    std::vector<int32_t> lst(S.level_sn.begin() + S.level_off[l], S.level_sn.begin() + S.level_off[l + 1]);
+    std::sort(lst.begin(), lst.end(), [&](int32_t a, int32_t b) {
+      const int fa = S.sn[a].F(), fb = S.sn[b].F();
+      return fa != fb ? fa > fb : a < b;
+    });
+    std::vector<int32_t> big, cta, warp;
+    for (int32_t sn : lst) {
+      const int F = S.sn[sn].F();
+      (F > Fc ? big : (F > 32 ? cta : warp)).push_back(sn);
+    }
+    if (!big.empty()) {
+      std::vector<pisp::BigFrontHost> bh;
+      for (int32_t sn : big) bh.push_back({S.sn[sn].F(), S.sn[sn].ns()});
+      std::vector<pisp::DagTask> tk;
+      int32_t nfl = 0;
+      pisp::build_owner_tasks(bh.data(), (int32_t)bh.size(), K, CH, tk, nfl);
+      for (const auto& t : tk)
+        ft.push_back({pisp::kFacOwner, big[t.b], t.k, t.p, t.j, (int32_t)(nflags + t.flags)});
+      for (size_t b = 0; b < big.size(); ++b)
+        need[big[b]] = ((bh[b].F + 31) / 32) * ((bh[b].F + CH - 1) / CH);
+      nflags += nfl;
+      if (nflags >= INT32_MAX) return fail(h, PISP_ERR_UNSUPPORTED, "too many factor flags");
+    }
+    for (int32_t sn : cta)
+      for (int k = 0; k < K; ++k) ft.push_back({pisp::kFacCta, sn, k, 0, 0, 0});
+    if (!warp.empty()) {
+      const int64_t off = (int64_t)wl.size(), tasks = (int64_t)warp.size() * K;
+      if (off + (int64_t)warp.size() >= INT32_MAX || tasks >= INT32_MAX)
+        return fail(h, PISP_ERR_UNSUPPORTED, "too many factor tasks");
+      wl.insert(wl.end(), warp.begin(), warp.end());
+      for (int64_t b = 0; b < tasks; b += 8)
+        ft.push_back({pisp::kFacWarp, (int32_t)off, 0, (int32_t)b, (int32_t)tasks, 0});
+    }
+  }
+  if ((int64_t)ft.size() >= INT32_MAX) return fail(h, PISP_ERR_UNSUPPORTED, "too many factor tasks");
+  TRY(upload(h, h->d_ftasks, ft));
+  TRY(upload(h, h->d_fwl, wl));
+  TRY(upload(h, h->d_fneed, need));
+  if (!h->fdone.ensure(S.sn.size() * (size_t)K * sizeof(int)) || !h->fflags.ensure((size_t)nflags * sizeof(int)) ||
+      !h->fticket.ensure(sizeof(int)))
+    return fail(h, PISP_ERR_OOM, "device allocation failed (factor schedule)");
+  h->n_ftasks = (int32_t)ft.size();
+  h->fac_CH = CH;
+  h->fac_nflags = (int32_t)nflags;
+  h->fac_smem = pisp::factor_persistent_smem(precision, CH, maxBig > 0, maxCta);
+  return PISP_OK;
 }
 
 // Groups the supernodes of every level by front size: small fronts into
@@ -352,6 +424,11 @@ int build_plans(pisp_handle* h, int precision) {
   TRY(upload(h, h->d_dag, h->h_dag));
   if (!h->dag_ticket.ensure(sizeof(int)) || !h->dag_flags.ensure((size_t)h->dag_max_flags * sizeof(int)))
     return fail(h, PISP_ERR_OOM, "device allocation failed (factor schedule)");
+  if (h->factor_policy == 4) {
+    TRY(build_persistent_factor(h, precision, h->K_hint));
+    h->fac_bytes = 0;
+    for (const auto& lp : h->plans) h->fac_bytes += lp.bytes_fsmall + lp.bytes_fbig;
+  }
   h->plan_precision = precision;
   h->units_K = h->units_R = 0;
   return PISP_OK;
@@ -464,8 +541,8 @@ pisp::Shifts make_shifts(const pisp_handle* h, const double* w) {
   return sh;
 }
 
-const char* kFamilyNames[PISP_PROF_FAMILIES] = {"factor_small", "factor_big", "forward",
-                                                "backward",     "residual",   "combine"};
+const char* kFamilyNames[PISP_PROF_FAMILIES] = {"factor_small", "factor_big", "forward",          "backward",
+                                                "residual",     "combine",    "factor_persistent"};
 
 // Event record that also works inside a stream capture: there it must become
 // an event-record node of the graph (external record) to be timed on replay.
@@ -857,7 +934,7 @@ int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
   // the owner tiles (policy 0) take fronts of any size; the per-panel path,
   // which the other policies fall back to, needs a panel in shared memory
   if (S.max_front > pisp::max_solve_front(precision) ||
-      (h->factor_policy != 0 && S.max_front > pisp::max_big_front(precision)))
+      (h->factor_policy != 0 && h->factor_policy != 4 && S.max_front > pisp::max_big_front(precision)))
     return fail(h, PISP_ERR_UNSUPPORTED, "front too large for this precision");
   double beta[PISP_K_MAX];
   if (pisp_weights(t, K, beta) != PISP_OK) return fail(h, PISP_ERR_INVALID_ARG, g_last_error);
@@ -886,6 +963,22 @@ int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
   CK(cudaMemsetAsync(h->serr.p, 0, sizeof(int), h->stream));
   h->launches = 0;
   const pisp::Shifts sh = make_shifts(h, h->beta);
+  if (h->factor_policy == 4) {
+    // every level, every shift and every instance in one persistent launch
+    CK(cudaMemsetAsync(h->fticket.p, 0, sizeof(int), h->stream));
+    CK(cudaMemsetAsync(h->fdone.p, 0, S.sn.size() * (size_t)K * sizeof(int), h->stream));
+    if (h->fac_nflags) CK(cudaMemsetAsync(h->fflags.p, 0, (size_t)h->fac_nflags * sizeof(int), h->stream));
+    const int pb = prof_begin(h);
+    const int n = pisp::launch_factor_persistent(
+        precision, h->sd, h->d_ftasks.as<pisp::FactorTask>(), h->n_ftasks, h->fticket.as<int>(), h->fdone.as<int>(),
+        h->d_fneed.as<int>(), h->fflags.as<int>(), h->serr.as<int>(), h->d_fwl.as<int32_t>(), h->vals.as<double>(),
+        h->D.as<double>(), sh, h->fronts.p, h->status.as<int32_t>(), h->badcol.as<int32_t>(), h->fac_CH,
+        h->fac_smem, h->wait_polls, h->stream);
+    TRY(count(h, n));
+    prof_end(h, pb, PISP_PROF_FACTOR, K * h->fac_bytes, n);
+    h->factored = true;
+    return PISP_OK;
+  }
   for (int l = 0; l < S.n_levels; ++l) {
     // The fronts of a level are independent: its wide fronts (owner kernel)
     // and each size class of its narrow ones go to their own streams, forked

@@ -115,8 +115,8 @@ __device__ __forceinline__ void panel_eliminate(T* P, int ld, int Mr, int nb, co
 template <typename T>
 __device__ __forceinline__ void extend_add_columns(const SymDev& sd, int s, int k, int K,
                                                    const T* __restrict__ fronts, T* dst, int ld,
-                                                   int d0, int w, int R0, int R1) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+                                                   int d0, int w, int R0, int R1, int wid, int nw) {
+  const int lane = threadIdx.x & 31;
   const int64_t vo = sd.vec_off[s];
   for (int dc = wid; dc < w; dc += nw) {
     const int64_t e0 = sd.inv_off[vo + d0 + dc], e1 = sd.inv_off[vo + d0 + dc + 1];
@@ -163,15 +163,14 @@ __device__ __forceinline__ void extend_add_columns(const SymDev& sd, int s, int 
 // ---------------------------------------------------------------------------
 // Small fronts: whole front in shared memory, one CTA per (front, k).
 // ---------------------------------------------------------------------------
+// One (front s, perturbation k) in the shared-memory buffer f (F*F
+// elements): assembly (original entries, t_k D, children's Schur complements
+// in child order per element), ns steps of pivot-free elimination, write to
+// the front storage.  Any number of threads that is a multiple of 32.
 template <typename T>
-__global__ void k_front_small(SymDev sd, const int32_t* __restrict__ list,
-                              const double* __restrict__ vals, const double* __restrict__ D,
-                              Shifts sh, T* __restrict__ fronts, int32_t* status,
-                              int32_t* badcol) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* f = reinterpret_cast<T*>(smraw);
-  const int s = list[blockIdx.x];
-  const int k = blockIdx.y;
+__device__ __forceinline__ void front_cta(const SymDev& sd, int s, int k, const double* __restrict__ vals,
+                                          const double* __restrict__ D, const Shifts& sh,
+                                          T* __restrict__ fronts, int32_t* status, int32_t* badcol, T* f) {
   const int K = sh.K;
   const int ns = sd.ns[s], ms = sd.ms[s], F = ns + ms;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -187,7 +186,7 @@ __global__ void k_front_small(SymDev sd, const int32_t* __restrict__ list,
   for (int c = tid; c < ns; c += nt) atomicAdd(&f[c * (F + 1)], (T)(tk * D[sd.perm[c0 + c]]));
   __syncthreads();
   // 1c. extend-add of the children's Schur complements (child order per element)
-  extend_add_columns<T>(sd, s, k, K, fronts, f, F, 0, F, 0, F);
+  extend_add_columns<T>(sd, s, k, K, fronts, f, F, 0, F, 0, F, tid >> 5, nt >> 5);
   __syncthreads();
   // 2. ns steps of pivot-free elimination
   for (int p = 0; p < ns; ++p) {
@@ -211,6 +210,58 @@ __global__ void k_front_small(SymDev sd, const int32_t* __restrict__ list,
   }
   T* out = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * FF;
   for (int q = tid; q < FF; q += nt) out[q] = f[q];
+}
+
+template <typename T>
+__global__ void k_front_small(SymDev sd, const int32_t* __restrict__ list,
+                              const double* __restrict__ vals, const double* __restrict__ D,
+                              Shifts sh, T* __restrict__ fronts, int32_t* status,
+                              int32_t* badcol) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  front_cta<T>(sd, list[blockIdx.x], blockIdx.y, vals, D, sh, fronts, status, badcol,
+               reinterpret_cast<T*>(smraw));
+}
+
+// One (front s, perturbation k) with F <= 32 by one warp, in its F x F
+// shared-memory area f (column-major): the same assembly and the same
+// per-element sequence of operations as front_cta, with the warp's lanes as
+// rows and no block barrier.
+template <typename T>
+__device__ __forceinline__ void front_warp(const SymDev& sd, int s, int k, const double* __restrict__ vals,
+                                           const double* __restrict__ D, const Shifts& sh,
+                                           T* __restrict__ fronts, int32_t* status, int32_t* badcol, T* f) {
+  const int K = sh.K;
+  const int lane = threadIdx.x & 31;
+  const int ns = sd.ns[s], ms = sd.ms[s], F = ns + ms;
+  const int FF = F * F;
+  for (int q = lane; q < FF; q += 32) f[q] = T(0);
+  __syncwarp();
+  const int64_t a0 = sd.amap_off[s], a1 = sd.amap_off[s + 1];
+  for (int64_t q = a0 + lane; q < a1; q += 32) atomicAdd(&f[sd.amap_dst[q]], (T)vals[sd.amap_src[q]]);
+  const double tk = sh.t[k];
+  const int c0 = sd.c0[s];
+  for (int c = lane; c < ns; c += 32) atomicAdd(&f[c * (F + 1)], (T)(tk * D[sd.perm[c0 + c]]));
+  __syncwarp();
+  extend_add_columns<T>(sd, s, k, K, fronts, f, F, 0, F, 0, F, 0, 1);
+  __syncwarp();
+  for (int p = 0; p < ns; ++p) {
+    const T piv = f[p * (F + 1)];
+    if (lane == 0) check_pivot(piv, sd, s, k, K, c0 + p, status, badcol);
+    const T rp = T(1) / piv;
+    const int i = p + 1 + lane;  // this lane's row (F <= 32: one row per lane)
+    T l = T(0);
+    if (i < F) {
+      l = f[i + p * F] * rp;
+      f[i + p * F] = l;
+    }
+    for (int j = p + 1; j < F; ++j) {
+      const T u = f[p + j * F];
+      if (i < F) f[i + j * F] -= l * u;
+    }
+    __syncwarp();
+  }
+  T* out = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * FF;
+  for (int q = lane; q < FF; q += 32) out[q] = f[q];
 }
 
 // ---------------------------------------------------------------------------
@@ -959,6 +1010,139 @@ __device__ __forceinline__ void own_eliminate_rows(T* Bt, int ld, int R0, int i0
   }
 }
 
+// One owner tile: the 32-column block j of front s, perturbation k,
+// restricted to the row chunk q of CH rows (see above).  `flags` points at
+// the (front, k) pair's release flags.  Needs kOwnThreads threads and the
+// shared memory layout of the owner kernels (Us, Ls, Bt, rinv).
+template <typename T>
+__device__ __forceinline__ void owner_tile(const SymDev& sd, int s, int k, int j, int q, int* flags, int CH,
+                                           int* err, const double* __restrict__ vals,
+                                           const double* __restrict__ D, const Shifts& sh,
+                                           T* __restrict__ fronts, int32_t* status, int32_t* badcol,
+                                           T* Us, T* Ls, T* Bt, T* rinv) {
+  const int K = sh.K;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int ld = CH + 1;
+  const int ns = sd.ns[s], F = ns + sd.ms[s];
+  const int P = (ns + 31) >> 5, J = (F + 31) >> 5, Q = (F + CH - 1) / CH;
+  const int j0 = j << 5, w = min(32, F - j0);
+  const int R0 = q * CH, R1 = min(F, R0 + CH);
+  int* Lf = flags;            // [P][Q]: rows of chunk q of panel block p final
+  int* Uf = Lf + P * Q;       // [P][J]: U rows of panel p in block j final
+  T* f = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * F * F;
+  const int64_t vo = sd.vec_off[s];
+
+  // 1. assembly of the tile: rows [R0, R1) of columns [j0, j0 + w)
+  for (int e = tid; e < ld * w; e += nt) Bt[e] = T(0);
+  __syncthreads();
+  {
+    const int64_t a0 = sd.amap_coff[vo + j0], a1 = sd.amap_coff[vo + j0 + w];
+    for (int64_t e = a0 + tid; e < a1; e += nt) {
+      const int d = sd.amap_dst[e];
+      const int c = d / F, i = d - c * F;
+      if (i >= R0 && i < R1) atomicAdd(&Bt[(i - R0) + (c - j0) * ld], (T)vals[sd.amap_src[e]]);
+    }
+    const double tk = sh.t[k];
+    const int c0 = sd.c0[s];
+    for (int c = max(j0, R0) + tid; c < min(min(j0 + w, ns), R1); c += nt)
+      atomicAdd(&Bt[(c - R0) + (c - j0) * ld], (T)(tk * D[sd.perm[c0 + c]]));
+  }
+  __syncthreads();
+  extend_add_columns<T>(sd, s, k, K, fronts, Bt, ld, j0, w, R0, R1, (int)(threadIdx.x >> 5), (int)(blockDim.x >> 5));
+  __syncthreads();
+
+  // 2. the updates of every earlier panel, in pivot order; panels whose
+  //    pivot rows lie below the tile do not touch it
+  const int pe = min(j, P);
+  for (int p = 0; p < pe; ++p) {
+    const int r0 = p << 5, nb = min(32, ns - r0), qp = r0 / CH;
+    if (q < qp) break;
+    if (q == qp) {
+      // the tile holds panel p's pivot rows: solve this block's U rows
+      if (tid == 0) dag_wait(Lf + p * Q + qp, 1, err);
+      __syncthreads();
+      for (int e = tid; e < 32 * 32; e += nt) {
+        const int r = e & 31, c = e >> 5;
+        Ls[r * 33 + c] = (r < nb && c < r) ? __ldcg(f + (r0 + r) + (int64_t)(r0 + c) * F) : T(0);
+      }
+      __syncthreads();
+      own_trsm<T>(Bt + (r0 - R0), ld, 0, nb, w, Ls, Us);
+      __syncthreads();
+      if (qp + 1 < Q) {  // chunks below read these U rows
+        for (int c = wid; c < w; c += nw)
+          for (int r = lane; r < nb; r += 32) f[(r0 + r) + (int64_t)(j0 + c) * F] = Bt[(r0 - R0 + r) + c * ld];
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) dag_st_release(Uf + p * J + j, 1);
+      }
+      own_update_rows<T>(Bt, ld, R0, f, F, r0, nb, Us, r0 + nb, R1, w);
+      __syncthreads();
+    } else {
+      // a chunk below panel p: its U rows of this block come from the
+      // chunk holding the pivot rows, its L rows from this chunk's tile of
+      // panel p
+      if (tid == 0) {
+        dag_wait(Uf + p * J + j, 1, err);
+        dag_wait(Lf + p * Q + q, 1, err);
+      }
+      __syncthreads();
+      for (int e = tid; e < 32 * 32; e += nt) {
+        const int r = e >> 5, c = e & 31;
+        Us[e] = (r < nb && c < w) ? __ldcg(f + (r0 + r) + (int64_t)(j0 + c) * F) : T(0);
+      }
+      __syncthreads();
+      own_update_rows<T>(Bt, ld, R0, f, F, r0, nb, Us, R0, R1, w);
+      __syncthreads();
+    }
+  }
+
+  // 3. the block's own pivots
+  const int qj = j0 / CH;
+  if (j < P) {
+    const int np = min(32, ns - j0);
+    if (q == qj) {
+      own_factor_diag<T>(Bt + (j0 - R0), ld, np, w, Us, rinv, sd, s, k, K, sd.c0[s] + j0, status, badcol);
+      __syncthreads();
+      own_eliminate_rows<T>(Bt, ld, R0, j0 + np, R1, np, w, Us, rinv);
+      __syncthreads();
+    } else if (q > qj) {
+      // rows below the diagonal block's chunk: its factored rows come from
+      // the front storage once that tile has released them
+      if (tid == 0) dag_wait(Lf + j * Q + qj, 1, err);
+      __syncthreads();
+      for (int e = tid; e < 32 * 32; e += nt) {
+        const int r = e >> 5, c = e & 31;
+        Us[e] = (r < np && c < w && c >= r) ? __ldcg(f + (j0 + r) + (int64_t)(j0 + c) * F) : T(0);
+      }
+      if (tid < np) rinv[tid] = T(1) / __ldcg(f + (int64_t)(j0 + tid) * (F + 1));
+      __syncthreads();
+      own_eliminate_rows<T>(Bt, ld, R0, R0, R1, np, w, Us, rinv);
+      __syncthreads();
+    }
+  }
+
+  // 4. write the tile; tiles holding L rows of this block release them
+  //    (rows from the first pivot down first, then the U rows above)
+  const bool rel = j < P && q >= qj;
+  const int rs = (rel && q == qj) ? j0 : R0;
+  for (int c = wid; c < w; c += nw) {
+    T* dst = f + (int64_t)(j0 + c) * F;
+    const T* src = Bt + c * ld;
+    for (int i = rs + lane; i < R1; i += 32) dst[i] = src[i - R0];
+  }
+  if (rel) {
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) dag_st_release(Lf + j * Q + q, 1);
+  }
+  for (int c = wid; c < w; c += nw) {
+    T* dst = f + (int64_t)(j0 + c) * F;
+    const T* src = Bt + c * ld;
+    for (int i = R0 + lane; i < rs; i += 32) dst[i] = src[i - R0];
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kOwnThreads) k_front_owner(SymDev sd, const int32_t* __restrict__ big,
                                                              const DagTask* __restrict__ tasks, int ntasks,
@@ -973,10 +1157,7 @@ __global__ void __launch_bounds__(kOwnThreads) k_front_owner(SymDev sd, const in
   T* Us = reinterpret_cast<T*>(smraw);  // 32 x 32 row-major: U rows of the current panel
   T* Ls = Us + 32 * 32;                 // 32 x 33 row-major: unit-lower L11 of the current panel
   T* Bt = Ls + 32 * 33;                 // (CH + 1) x 32 column-major: the owned tile
-  const int K = sh.K;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-  const int ld = CH + 1;
+  const int tid = threadIdx.x;
   for (;;) {
     __syncthreads();  // the previous task is done with shared memory and s_t
     if (tid == 0) s_t = atomicAdd(ticket, 1);
@@ -984,125 +1165,121 @@ __global__ void __launch_bounds__(kOwnThreads) k_front_owner(SymDev sd, const in
     const int u = s_t;
     if (u >= ntasks) return;
     const DagTask t = tasks[u];
-    const int s = big[t.b], k = t.k, j = t.j, q = t.p;
-    const int ns = sd.ns[s], F = ns + sd.ms[s];
-    const int P = (ns + 31) >> 5, J = (F + 31) >> 5, Q = (F + CH - 1) / CH;
-    const int j0 = j << 5, w = min(32, F - j0);
-    const int R0 = q * CH, R1 = min(F, R0 + CH);
-    int* Lf = flags + t.flags;  // [P][Q]: rows of chunk q of panel block p final
-    int* Uf = Lf + P * Q;       // [P][J]: U rows of panel p in block j final
-    T* f = fronts + (int64_t)K * sd.front_off[s] + (int64_t)k * F * F;
-    const int64_t vo = sd.vec_off[s];
+    owner_tile<T>(sd, big[t.b], t.k, t.j, t.p, flags + t.flags, CH, err, vals, D, sh, fronts, status, badcol,
+                  Us, Ls, Bt, rinv);
+  }
+}
 
-    // 1. assembly of the tile: rows [R0, R1) of columns [j0, j0 + w)
-    for (int e = tid; e < ld * w; e += nt) Bt[e] = T(0);
+// ---------------------------------------------------------------------------
+// The whole factorisation as ONE persistent launch over every level of the
+// assembly forest, all K shifts and all instances of a batch.  Tasks, taken in
+// ticket order (levels bottom-up; within a level the owner tiles first, then
+// the shared-memory fronts, then the warp fronts):
+//   kFacWarp : up to 8 (front, k) pairs with F <= 32, one per warp, each in
+//              its warp's shared-memory area (front_warp);
+//   kFacCta  : one (front, k) pair of a front that fits in shared memory
+//              (front_cta);
+//   kFacOwner: one owner tile of a wider front (owner_tile).
+// Before its assembly a task waits until every child's completion counter
+// for its k, fdone[child * K + k], has reached need[child] (1 for warp and
+// shared-memory fronts, the number of tiles for an owner front); a finished
+// task adds 1 to its own counter after its writes are visible.  Every wait is
+// on a task with a smaller ticket (a child, or an earlier tile of the same
+// front), which a running CTA already holds, so the schedule cannot deadlock
+// whatever the residency, and every wait is bounded.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void fac_wait_children(const SymDev& sd, const int* fdone, const int* need, int s,
+                                                  int k, int K, int idx, int n, int* err, int64_t polls) {
+  const int cb = sd.child_off[s], ce = sd.child_off[s + 1];
+  for (int ci = cb + idx; ci < ce; ci += n) {
+    const int c = sd.child[ci];
+    const int* f = fdone + (int64_t)c * K + k;
+    const int want = need[c];
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+    if (v >= want) continue;
+    int64_t i = 0;
+    for (; i < polls; ++i) {
+      __nanosleep(64);
+      asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+      if (v >= want) break;
+    }
+    if (i == polls) atomicExch(err, 1);
+  }
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+__device__ __forceinline__ void fac_publish(int* fdone, int s, int k, int K) {
+  __threadfence();
+  asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(fdone + (int64_t)s * K + k) : "memory");
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kOwnThreads, 2)
+k_factor_persistent(SymDev sd, const FactorTask* __restrict__ tasks, int ntasks, int* ticket, int* fdone,
+                    const int* __restrict__ need, int* flags, int* err, const int32_t* __restrict__ wlist,
+                    const double* __restrict__ vals, const double* __restrict__ D, Shifts sh,
+                    T* __restrict__ fronts, int32_t* status, int32_t* badcol, int CH, int64_t polls) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_t;
+  __shared__ T rinv[32];
+  T* sm = reinterpret_cast<T*>(smraw);
+  const int K = sh.K;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  for (;;) {
+    __syncthreads();  // the previous task is done with shared memory and s_t
+    if (tid == 0) s_t = atomicAdd(ticket, 1);
     __syncthreads();
-    {
-      const int64_t a0 = sd.amap_coff[vo + j0], a1 = sd.amap_coff[vo + j0 + w];
-      for (int64_t e = a0 + tid; e < a1; e += nt) {
-        const int d = sd.amap_dst[e];
-        const int c = d / F, i = d - c * F;
-        if (i >= R0 && i < R1) atomicAdd(&Bt[(i - R0) + (c - j0) * ld], (T)vals[sd.amap_src[e]]);
+    const int u = s_t;
+    if (u >= ntasks) return;
+    const FactorTask t = tasks[u];
+    if (t.kind == kFacWarp) {
+      const int q = t.q + wid;
+      if (q < t.j) {
+        const int s = wlist[t.s + q / K], k = q % K;
+        fac_wait_children(sd, fdone, need, s, k, K, lane, 32, err, polls);
+        __syncwarp();
+        front_warp<T>(sd, s, k, vals, D, sh, fronts, status, badcol, sm + wid * 32 * 32);
+        __syncwarp();
+        if (lane == 0) fac_publish(fdone, s, k, K);
       }
-      const double tk = sh.t[k];
-      const int c0 = sd.c0[s];
-      for (int c = max(j0, R0) + tid; c < min(min(j0 + w, ns), R1); c += nt)
-        atomicAdd(&Bt[(c - R0) + (c - j0) * ld], (T)(tk * D[sd.perm[c0 + c]]));
-    }
-    __syncthreads();
-    extend_add_columns<T>(sd, s, k, K, fronts, Bt, ld, j0, w, R0, R1);
-    __syncthreads();
-
-    // 2. the updates of every earlier panel, in pivot order; panels whose
-    //    pivot rows lie below the tile do not touch it
-    const int pe = min(j, P);
-    for (int p = 0; p < pe; ++p) {
-      const int r0 = p << 5, nb = min(32, ns - r0), qp = r0 / CH;
-      if (q < qp) break;
-      if (q == qp) {
-        // the tile holds panel p's pivot rows: solve this block's U rows
-        if (tid == 0) dag_wait(Lf + p * Q + qp, 1, err);
-        __syncthreads();
-        for (int e = tid; e < 32 * 32; e += nt) {
-          const int r = e & 31, c = e >> 5;
-          Ls[r * 33 + c] = (r < nb && c < r) ? __ldcg(f + (r0 + r) + (int64_t)(r0 + c) * F) : T(0);
-        }
-        __syncthreads();
-        own_trsm<T>(Bt + (r0 - R0), ld, 0, nb, w, Ls, Us);
-        __syncthreads();
-        if (qp + 1 < Q) {  // chunks below read these U rows
-          for (int c = wid; c < w; c += nw)
-            for (int r = lane; r < nb; r += 32) f[(r0 + r) + (int64_t)(j0 + c) * F] = Bt[(r0 - R0 + r) + c * ld];
-          __threadfence();
-          __syncthreads();
-          if (tid == 0) dag_st_release(Uf + p * J + j, 1);
-        }
-        own_update_rows<T>(Bt, ld, R0, f, F, r0, nb, Us, r0 + nb, R1, w);
-        __syncthreads();
-      } else {
-        // a chunk below panel p: its U rows of this block come from the
-        // chunk holding the pivot rows, its L rows from this chunk's tile of
-        // panel p
-        if (tid == 0) {
-          dag_wait(Uf + p * J + j, 1, err);
-          dag_wait(Lf + p * Q + q, 1, err);
-        }
-        __syncthreads();
-        for (int e = tid; e < 32 * 32; e += nt) {
-          const int r = e >> 5, c = e & 31;
-          Us[e] = (r < nb && c < w) ? __ldcg(f + (r0 + r) + (int64_t)(j0 + c) * F) : T(0);
-        }
-        __syncthreads();
-        own_update_rows<T>(Bt, ld, R0, f, F, r0, nb, Us, R0, R1, w);
-        __syncthreads();
-      }
-    }
-
-    // 3. the block's own pivots
-    const int qj = j0 / CH;
-    if (j < P) {
-      const int np = min(32, ns - j0);
-      if (q == qj) {
-        own_factor_diag<T>(Bt + (j0 - R0), ld, np, w, Us, rinv, sd, s, k, K, sd.c0[s] + j0, status, badcol);
-        __syncthreads();
-        own_eliminate_rows<T>(Bt, ld, R0, j0 + np, R1, np, w, Us, rinv);
-        __syncthreads();
-      } else if (q > qj) {
-        // rows below the diagonal block's chunk: its factored rows come from
-        // the front storage once that tile has released them
-        if (tid == 0) dag_wait(Lf + j * Q + qj, 1, err);
-        __syncthreads();
-        for (int e = tid; e < 32 * 32; e += nt) {
-          const int r = e >> 5, c = e & 31;
-          Us[e] = (r < np && c < w && c >= r) ? __ldcg(f + (j0 + r) + (int64_t)(j0 + c) * F) : T(0);
-        }
-        if (tid < np) rinv[tid] = T(1) / __ldcg(f + (int64_t)(j0 + tid) * (F + 1));
-        __syncthreads();
-        own_eliminate_rows<T>(Bt, ld, R0, R0, R1, np, w, Us, rinv);
-        __syncthreads();
-      }
-    }
-
-    // 4. write the tile; tiles holding L rows of this block release them
-    //    (rows from the first pivot down first, then the U rows above)
-    const bool rel = j < P && q >= qj;
-    const int rs = (rel && q == qj) ? j0 : R0;
-    for (int c = wid; c < w; c += nw) {
-      T* dst = f + (int64_t)(j0 + c) * F;
-      const T* src = Bt + c * ld;
-      for (int i = rs + lane; i < R1; i += 32) dst[i] = src[i - R0];
-    }
-    if (rel) {
-      __threadfence();
+    } else {
+      fac_wait_children(sd, fdone, need, t.s, t.k, K, tid, nt, err, polls);
       __syncthreads();
-      if (tid == 0) dag_st_release(Lf + j * Q + q, 1);
-    }
-    for (int c = wid; c < w; c += nw) {
-      T* dst = f + (int64_t)(j0 + c) * F;
-      const T* src = Bt + c * ld;
-      for (int i = R0 + lane; i < rs; i += 32) dst[i] = src[i - R0];
+      if (t.kind == kFacCta)
+        front_cta<T>(sd, t.s, t.k, vals, D, sh, fronts, status, badcol, sm);
+      else
+        owner_tile<T>(sd, t.s, t.k, t.j, t.q, flags + t.flags, CH, err, vals, D, sh, fronts, status, badcol,
+                      sm, sm + 32 * 32, sm + 32 * 32 + 32 * 33, rinv);
+      __syncthreads();
+      if (tid == 0) fac_publish(fdone, t.s, t.k, K);
     }
   }
+}
+
+template <typename T>
+int factor_persistent_impl(const SymDev& sd, const FactorTask* tasks, int ntasks, int* ticket, int* fdone,
+                           const int* need, int* flags, int* err, const int32_t* wlist, const double* vals,
+                           const double* D, const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol,
+                           int CH, size_t smem, int64_t polls, cudaStream_t st) {
+  if (ntasks == 0) return 0;
+  static std::atomic<int> nsm_dev[kMaxDevices];
+  const int dev = current_device();
+  int nsm = nsm_dev[dev].load(std::memory_order_acquire);
+  if (!nsm) {
+    cudaFuncSetAttribute(k_factor_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    nsm_dev[dev].store(nsm, std::memory_order_release);
+  }
+  if (smem > (size_t)kSmemCap) return -1;
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_factor_persistent<T>, kOwnThreads, smem);
+  const int grid = std::max(1, std::min(ntasks, std::max(1, occ) * std::max(nsm, 1)));
+  k_factor_persistent<T><<<grid, kOwnThreads, smem, st>>>(sd, tasks, ntasks, ticket, fdone, need, flags, err,
+                                                          wlist, vals, D, sh, (T*)fronts, status, badcol, CH,
+                                                          polls > 0 ? polls : kDagWaitPolls);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 template <typename T>
@@ -1384,6 +1561,28 @@ int launch_factor_big_dag(int precision, const SymDev& sd, const LevelPlan& lp, 
                                badcol, st);
   return big_dag_impl<double>(sd, lp, d_big, tasks, ticket, flags, err, vals, D, sh, fronts, status,
                               badcol, st);
+}
+
+int persistent_cta_front_limit(int precision) { return precision == PISP_FP32 ? 128 : 64; }
+
+size_t factor_persistent_smem(int precision, int CH, bool has_owner, int maxCtaF) {
+  const size_t es = precision == PISP_FP32 ? 4 : 8;
+  size_t e = (size_t)(kOwnThreads / 32) * 32 * 32;                          // warp fronts
+  e = std::max(e, (size_t)maxCtaF * maxCtaF);                                // shared-memory fronts
+  if (has_owner) e = std::max(e, (size_t)(CH + 1) * 32 + 32 * 32 + 32 * 33);  // owner tiles
+  return e * es;
+}
+
+int launch_factor_persistent(int precision, const SymDev& sd, const FactorTask* tasks, int ntasks, int* ticket,
+                             int* fdone, const int* need, int* flags, int* err, const int32_t* wlist,
+                             const double* vals, const double* D, const Shifts& sh, void* fronts,
+                             int32_t* status, int32_t* badcol, int CH, size_t smem, int64_t polls,
+                             cudaStream_t st) {
+  if (precision == PISP_FP32)
+    return factor_persistent_impl<float>(sd, tasks, ntasks, ticket, fdone, need, flags, err, wlist, vals, D, sh,
+                                         fronts, status, badcol, CH, smem, polls, st);
+  return factor_persistent_impl<double>(sd, tasks, ntasks, ticket, fdone, need, flags, err, wlist, vals, D, sh,
+                                        fronts, status, badcol, CH, smem, polls, st);
 }
 
 int launch_factor_big(int precision, const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,

@@ -114,6 +114,19 @@ struct DagTask {
   int32_t kind, b, k, p, j, flags;
 };
 
+// Tasks of the one-launch factorisation (factor policy 4), all levels:
+//   kFacWarp : s = offset of a group in the warp-front list, q = first task,
+//              j = tasks in the group; task i is (front list[s + i / K],
+//              k = i % K), 8 tasks (one per warp) per record;
+//   kFacCta  : front s, perturbation k, factored in shared memory;
+//   kFacOwner: owner tile (column block j, row chunk q) of front s,
+//              perturbation k; flags = offset of the (front, k) pair's
+//              release flags.
+enum FactorKind { kFacWarp = 0, kFacCta = 1, kFacOwner = 2 };
+struct FactorTask {
+  int32_t kind, s, k, q, j, flags;
+};
+
 // Builds the task list of one level (b indexes the level's big-front list).
 void build_dag_tasks(const BigFrontHost* big, int32_t nbig, int32_t K, std::vector<DagTask>& out,
                      int32_t& nflags);
@@ -148,6 +161,18 @@ int launch_factor_big_dag(int precision, const SymDev& sd, const LevelPlan& lp, 
                           const DagTask* tasks, int* ticket, int* flags, int* err,
                           const double* vals, const double* D, const Shifts& sh, void* fronts,
                           int32_t* status, int32_t* badcol, cudaStream_t st);
+// The whole factorisation in one persistent launch (factor policy 4): ticket
+// (1 int), fdone (S*K ints) and flags must be zero; need[s] = 1 for warp and
+// shared-memory fronts, tiles per (front, k) for owner fronts.
+int launch_factor_persistent(int precision, const SymDev& sd, const FactorTask* tasks, int ntasks, int* ticket,
+                             int* fdone, const int* need, int* flags, int* err, const int32_t* wlist,
+                             const double* vals, const double* D, const Shifts& sh, void* fronts,
+                             int32_t* status, int32_t* badcol, int CH, size_t smem, int64_t polls,
+                             cudaStream_t st);
+// widest front the one-launch factorisation keeps in shared memory (wider:
+// owner tiles), and its dynamic shared memory per CTA
+int persistent_cta_front_limit(int precision);
+size_t factor_persistent_smem(int precision, int CH, bool has_owner, int maxCtaF);
 // largest front the tile-DAG path takes (its panel must fit in shared memory)
 int max_dag_front(int precision);
 // rows per owner tile for a level whose widest front is maxF

@@ -56,7 +56,7 @@ def staged_candidates():
 
 def _stage2(best: dict):
     out = []
-    for (rs, rz), fp in itertools.product(RELAX, (0, 2)):
+    for (rs, rz), fp in itertools.product(RELAX, (0, 2, 4)):
         o = dict(best, relax_small=rs, relax_zeros=rz, factor_policy=fp)
         if o != best:
             out.append(o)

@@ -95,11 +95,12 @@ def test_random_systems_fp64(pisp, n, K, R, density):
     assert _maxrel(x, _oracle_xhat(inst, t, b)) <= TOL64
 
 
-def test_factor_entries_match_pivot_free_lu(pisp):
+@pytest.mark.parametrize("policy", [0, 4])
+def test_factor_entries_match_pivot_free_lu(pisp, policy):
     """The pivot-free factor is unique: front entries equal dense Doolittle's."""
     inst = pfgen.make_instance("plain")
     t = pfgen.symmetric_shifts(4)
-    s, val, D = _solver(pisp, [inst])
+    s, val, D = _solver(pisp, [inst], factor_policy=policy)
     s.factor(_dev(val), _dev(D), t, "fp64")
     perm = s.perm()
     c0, c1, ms, rows = s.supernodes()
@@ -146,10 +147,12 @@ def test_pivot_range_matches_pivot_free_lu(pisp, prec, rtol):
     (220, 0.03, "fp64", 1), (300, 0.03, "fp64", 1), (300, 0.03, "fp32", 1), (420, 0.02, "fp32", 1),
     (700, 0.012, "fp32", 1), (300, 0.03, "fp64", 2), (700, 0.012, "fp32", 2),
     (1200, 0.006, "fp32", 0), (220, 0.03, "fp64", 3), (700, 0.012, "fp32", 3),
-    (1200, 0.012, "fp64", 0)])
+    (1200, 0.012, "fp64", 0), (220, 0.03, "fp64", 4), (300, 0.03, "fp32", 4), (700, 0.012, "fp32", 4),
+    (1200, 0.006, "fp32", 4), (1200, 0.012, "fp64", 4)])
 def test_factor_entries_large_fronts(pisp, n, density, prec, policy):
     """Fronts factored in shared memory, by CTA clusters, by column-block owners, as a
-    tile DAG or by per-panel launches equal dense Doolittle's."""
+    tile DAG, by per-panel launches or in the one-launch factorisation equal dense
+    Doolittle's."""
     inst = pfgen.random_sparse(n, density, seed=n)
     t = pfgen.symmetric_shifts(2)
     s, val, D = _solver(pisp, [inst], factor_policy=policy)
@@ -176,7 +179,7 @@ def test_factor_entries_large_fronts(pisp, n, density, prec, policy):
                                        atol=tol * scale)
 
 
-@pytest.mark.parametrize("schedule,policy", [(0, 0), (1, 0), (0, 2), (0, 3)])
+@pytest.mark.parametrize("schedule,policy", [(0, 0), (1, 0), (0, 2), (0, 3), (0, 4), (1, 4)])
 def test_precision_config_fp64_big_fronts(pisp, schedule, policy):
     """2000-bus grid: its top fronts exceed the shared-memory path (blocked path)."""
     inst = pfgen.make_instance("precision")
@@ -403,14 +406,15 @@ def test_fp32_front_taller_than_a_shared_memory_column(pisp):
     assert _maxrel(x, _oracle_xhat(inst, t, b)) <= TOL64
 
 
-def test_full_scale_config_fp32_sweeps(pisp):
+@pytest.mark.parametrize("policy", [0, 4])
+def test_full_scale_config_fp32_sweeps(pisp, policy):
     """10000-bus grid: 23 fronts wider than the shared-memory limit, several per level,
     up to the dense F = 1594 root (column-block owners); FP32 factors plus sweeps reach
     the FP64 definition for every right-hand side."""
     c = pfgen.CONFIGS["scale"]
     inst = pfgen.make_instance("scale")
     t = pfgen.symmetric_shifts(c["K"])
-    s, val, D = _solver(pisp, [inst])
+    s, val, D = _solver(pisp, [inst], factor_policy=policy)
     assert s.stats()["max_front"] > 1000
     s.factor(_dev(val), _dev(D), t, "fp32")
     b = pfgen.rhs(inst.n, 4, 11)
@@ -437,12 +441,16 @@ def test_full_differentiation_config(pisp):
     assert grad_entrywise_err(gv.cpu().numpy(), rv) <= TOL64
 
 
-def test_full_batching_config_sampled(pisp):
-    """All 256 grids in one factor/solve; sampled instances checked against the oracle."""
+@pytest.mark.parametrize("opts", [dict(), dict(factor_policy=4, solve_ctas_per_sm=4, solve_kfuse=2,
+                                                  solve_warp_maxF=64)])
+def test_full_batching_config_sampled(pisp, opts):
+    """All 256 grids in one factor/solve (per-level factor launches, or the
+    one-launch factorisation with a retiled solve); sampled instances checked
+    against the oracle."""
     c = pfgen.CONFIGS["batching"]
     insts = [pfgen.make_instance("batching", g) for g in range(c["G"])]
     t = pfgen.symmetric_shifts(c["K"])
-    s, val, D = _solver(pisp, insts)
+    s, val, D = _solver(pisp, insts, **opts)
     s.factor(_dev(val), _dev(D), t, "fp32")
     N = sum(I.n for I in insts)
     b = pfgen.rhs(N, c["R"], 3)
