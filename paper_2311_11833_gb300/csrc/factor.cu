@@ -185,9 +185,21 @@ __device__ __forceinline__ void front_cta(const SymDev& sd, int s, int k, const 
   const int c0 = sd.c0[s];
   for (int c = tid; c < ns; c += nt) atomicAdd(&f[c * (F + 1)], (T)(tk * D[sd.perm[c0 + c]]));
   __syncthreads();
-  // 1c. extend-add of the children's Schur complements (child order per element)
-  extend_add_columns<T>(sd, s, k, K, fronts, f, F, 0, F, 0, F, tid >> 5, nt >> 5);
-  __syncthreads();
+  // 1c. extend-add of the children's Schur complements, child by child (each
+  // element receives its contributions in child order): the threads take the
+  // entries of one child's update block, which land on distinct elements
+  for (int ci = sd.child_off[s]; ci < sd.child_off[s + 1]; ++ci) {
+    const int c = sd.child[ci];
+    const int cns = sd.ns[c], cms = sd.ms[c], cF = cns + cms;
+    const T* cf = fronts + (int64_t)K * sd.front_off[c] + (int64_t)k * cF * cF;
+    const int32_t* em = sd.emap + sd.row_off[c];
+    const int n2 = cms * cms;
+    for (int q = tid; q < n2; q += nt) {
+      const int a = q % cms, b = q / cms;  // child update row a, column b
+      f[em[a] + em[b] * F] += cf[(cns + a) + (int64_t)(cns + b) * cF];
+    }
+    __syncthreads();
+  }
   // 2. ns steps of pivot-free elimination
   for (int p = 0; p < ns; ++p) {
     const T piv = f[p * (F + 1)];
@@ -242,8 +254,22 @@ __device__ __forceinline__ void front_warp(const SymDev& sd, int s, int k, const
   const int c0 = sd.c0[s];
   for (int c = lane; c < ns; c += 32) atomicAdd(&f[c * (F + 1)], (T)(tk * D[sd.perm[c0 + c]]));
   __syncwarp();
-  extend_add_columns<T>(sd, s, k, K, fronts, f, F, 0, F, 0, F, 0, 1);
-  __syncwarp();
+  // extend-add, child by child (each element receives its children's
+  // contributions in child order, as in the column-owner form): the lanes
+  // take the entries of the child's cms x cms update block, which land on
+  // distinct elements of this front
+  for (int ci = sd.child_off[s]; ci < sd.child_off[s + 1]; ++ci) {
+    const int c = sd.child[ci];
+    const int cns = sd.ns[c], cms = sd.ms[c], cF = cns + cms;
+    const T* cf = fronts + (int64_t)K * sd.front_off[c] + (int64_t)k * cF * cF;
+    const int32_t* em = sd.emap + sd.row_off[c];
+    const int n2 = cms * cms;
+    for (int q = lane; q < n2; q += 32) {
+      const int a = q % cms, b = q / cms;  // child update row a, column b
+      f[em[a] + em[b] * F] += cf[(cns + a) + (int64_t)(cns + b) * cF];
+    }
+    __syncwarp();
+  }
   for (int p = 0; p < ns; ++p) {
     const T piv = f[p * (F + 1)];
     if (lane == 0) check_pivot(piv, sd, s, k, K, c0 + p, status, badcol);

@@ -266,6 +266,31 @@ __device__ __forceinline__ T gather_position(const SymDev& sd, int s, int j, int
 }
 
 // ---------------------------------------------------------------------------
+// gather_position for every right-hand side r < nr of one position j at
+// once: the index entries of the inverse extend-add map are read once and
+// each serves the nr right-hand sides (the same per-RHS order of additions).
+// nr = 0 (an inactive lane, or j outside the front) returns zeros.
+template <typename T>
+__device__ __forceinline__ void gather_position_rhs(const SymDev& sd, int s, int j, int ns, int c0,
+                                                    const double* rhs, int rhs_mode, const T* V, int k, int K,
+                                                    int R, int r0, int nr, T (&a)[kSolveChunk]) {
+#pragma unroll
+  for (int r = 0; r < kSolveChunk; ++r)
+    a[r] = (j < ns && r < nr) ? (T)load_rhs(sd, rhs, rhs_mode, c0 + j, k, K, R, r0 + r) : T(0);
+  if (nr <= 0) return;  // no position here (j beyond the front): touch no index array
+  const int64_t e1 = sd.inv_off[sd.vec_off[s] + j + 1];
+  const int64_t kR = (int64_t)K * R;
+  for (int64_t e = sd.inv_off[sd.vec_off[s] + j]; e < e1; ++e) {
+    const int cF = sd.inv_cF[e];
+    const T* src = V + kR * sd.inv_vbase[e] + ((int64_t)k * R + r0) * cF + sd.inv_col[e];
+    T v[kSolveChunk];
+#pragma unroll
+    for (int r = 0; r < kSolveChunk; ++r) v[r] = r < nr ? __ldcg(src + (int64_t)r * cF) : T(0);
+#pragma unroll
+    for (int r = 0; r < kSolveChunk; ++r) a[r] += v[r];
+  }
+}
+
 // Fronts with F <= SEG (SEG = 8, 16 or 32): a warp is split into 32/SEG
 // segments and every segment solves one (front, k, chunk of kRW right-hand
 // sides).  Lane i of a segment owns row i of its front; the factor entries it
@@ -846,10 +871,7 @@ __device__ __forceinline__ void kseg_forward(const SymDev& sd, const FTask& t, i
 #pragma unroll
     for (int c = 0; c < SEG; ++c) Lr[c] = (kon && c < ns && sl > c && sl < F) ? f[sl + c * F] : T(0);
     T vv[kRW];
-#pragma unroll
-    for (int r = 0; r < kRW; ++r)
-      vv[r] = (kon && r < nr && sl < F) ? gather_position<T>(sd, t.s, sl, ns, c0, rhs, rhs_mode, V, k, K, R, r0 + r)
-                                        : T(0);
+    gather_position_rhs<T>(sd, t.s, sl, ns, c0, rhs, rhs_mode, V, k, K, R, r0, (kon && sl < F) ? nr : 0, vv);
 #pragma unroll
     for (int c = 0; c < SEG - 1; ++c) {
       if (c >= nsw) break;
@@ -868,10 +890,7 @@ __device__ __forceinline__ void kseg_forward(const SymDev& sd, const FTask& t, i
       for (int b = 1; b < nb; ++b) {
         const int i = b * 32 + sl;
         T acc[kRW];
-#pragma unroll
-        for (int r = 0; r < kRW; ++r)
-          acc[r] = (kon && r < nr && i < F) ? gather_position<T>(sd, t.s, i, ns, c0, rhs, rhs_mode, V, k, K, R, r0 + r)
-                                            : T(0);
+        gather_position_rhs<T>(sd, t.s, i, ns, c0, rhs, rhs_mode, V, k, K, R, r0, (kon && i < F) ? nr : 0, acc);
         for (int c = 0; c < nsw; ++c) {
           const T l = (kon && c < ns && i < F) ? f[i + (int64_t)c * F] : T(0);
 #pragma unroll
