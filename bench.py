@@ -280,11 +280,16 @@ def min_bytes_per_launch(fam, st, K, R, p):
     bytes of the roofline): factor entries of the triangle it uses for all K
     shifts, their int32 indices read ONCE for all K, the vectors in and out.
     nnzU = (nnzF + N) / 2 entries of U (diagonal included), nnzL = (nnzF - N) / 2
-    entries strictly below it.  None for the factor families (several launches
+    entries strictly below it.  The one-launch factorisation moves at least
+    A's values, D, the factor pattern (once for all K) and the K factors; the
+    Schur complements a multifrontal factorisation writes and reads back are
+    not counted.  None for the per-level factor families (several launches
     per step, each over part of the fronts: the library's per-launch count is
     used there)."""
     N, nnzA, nnzF = float(st["N"]), float(st["nnzA"]), float(st["nnzF_stored"])
     nnzU, nnzL = (nnzF + N) / 2, (nnzF - N) / 2
+    if fam == "factor_persistent":
+        return 8 * nnzA + 8 * N + 4 * (nnzF + N) + K * p * nnzF
     if fam == "backward":       # U factors, indices, y in (factor precision), x out (FP64)
         return K * p * nnzU + 4 * nnzU + K * p * N * R + 8 * N * R
     if fam == "forward":        # L factors, indices, b in (FP64), y out (factor precision)
@@ -390,6 +395,17 @@ def run_pisp(args, rank, world, local_rank):
                 "library_bytes_per_launch": lib_bytes,
                 "avg_launch_us": round(1e3 * launch_ms, 3),
                 "share_of_step": round(pf["ms"] / total_ms, 4) if world == 1 else None}
+    def fam_roofline(f):
+        v = prof[f]
+        if v["launches"] == 0 or v["ms"] <= 0:
+            return None
+        lm = v["ms"] / v["launches"]
+        mbf = min_bytes_per_launch(f, stats, K, R, p)
+        by = mbf if mbf is not None else v["bytes"] / v["launches"]
+        ach = by / (lm / 1e3) / 1e9
+        return {"kernel": f, "achieved": round(ach, 2), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 5),
+                "algorithmic_bytes_per_launch": by, "avg_launch_us": round(1e3 * lm, 3),
+                "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, f, G))}
     families = {f: {"ms_per_step": round(v["ms"] / args.steps, 4),
                     "launches_per_step": v["launches"] / args.steps,
                     "min_GBps": (round(min_bytes_per_launch(f, stats, K, R, p) / (v["ms"] / v["launches"] / 1e3) / 1e9, 2)
@@ -412,6 +428,7 @@ def run_pisp(args, rank, world, local_rank):
                        (tuned["options"].get("factor_policy", 0) if tuned else args.factor_policy)], "l2": "flushed between steps (256 MB write outside the events)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
+        "roofline_backward": fam_roofline("backward"),
         "families": families,
         "gpu_launches": int(stats["gpu_launches"]) * args.steps,
         "analyze_ms": round(arm.analyze_ms, 2),

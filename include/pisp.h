@@ -84,8 +84,8 @@ typedef struct pisp_options {
                              tiled-update launch per 32 pivots);
                              4 = ONE persistent launch for every level, shift
                              and instance: fronts of at most 32 one warp each,
-                             fronts up to 128 (FP32) / 64 (FP64) one CTA each
-                             in shared memory, wider fronts as owner tiles;
+                             fronts up to factor_smem_maxF one CTA each in
+                             shared memory, wider fronts as owner tiles;
                              a task waits (boundedly) only for its children's
                              completion counters */
   int32_t solve_kfuse;    /* persistent solve: shifts per segment task of a front
@@ -102,6 +102,9 @@ typedef struct pisp_options {
                                 for FP32 factors, 2 for FP64): more CTAs hide
                                 more latency of a batch's many small fronts,
                                 fewer spill less on wide fronts */
+  int32_t factor_smem_maxF; /* factor policy 4: widest front factored by one CTA
+                               in shared memory (0 = the limit: 160 in FP32,
+                               112 in FP64); wider fronts become owner tiles */
   int32_t analyze_threads; /* host threads pisp_analyze may use for the instances
                               of a batch: 0 = the hardware concurrency, at most
                               16 (default); 1 = the calling thread only.  A

@@ -73,6 +73,7 @@ struct pisp_handle {
   int32_t wait_unreachable = 0;
   // persistent solve tiling (pisp_options.solve_kfuse / solve_warp_maxF)
   int32_t kfuse = 1, warp_maxF = 32, solve_ctas = 0;
+  int32_t factor_smem_maxF = 0;  // one-launch factorisation: widest shared-memory front (0 = limit)
   pisp::SymDev sd{};
   // level plans (depend on the factor precision)
   int plan_precision = 0;
@@ -225,7 +226,8 @@ int factor_path(const pisp_handle* h, int F, int precision) {
 // 8 (front, k) warp tasks for the fronts of at most 32.
 int build_persistent_factor(pisp_handle* h, int precision, int32_t K) {
   const pisp::Symbolic& S = h->sym;
-  const int Fc = pisp::persistent_cta_front_limit(precision);
+  const int Fc = h->factor_smem_maxF > 0 ? std::min(h->factor_smem_maxF, pisp::persistent_cta_front_limit(precision))
+                                         : pisp::persistent_cta_front_limit(precision);
   int maxBig = 0, maxCta = 0;
   for (const auto& sn : S.sn) {
     if (sn.F() > Fc) maxBig = std::max(maxBig, sn.F());
@@ -743,6 +745,7 @@ int analyze_impl(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   h->kfuse = opt && opt->solve_kfuse > 0 ? opt->solve_kfuse : 1;
   h->warp_maxF = opt && opt->solve_warp_maxF > 0 ? opt->solve_warp_maxF : 32;
   h->solve_ctas = opt && opt->solve_ctas_per_sm > 0 ? std::min(4, std::max(2, opt->solve_ctas_per_sm)) : 0;
+  h->factor_smem_maxF = opt && opt->factor_smem_maxF > 0 ? opt->factor_smem_maxF : 0;
   h->units_K = h->units_R = 0;
   if (opt) {
     so.ordering = opt->ordering;

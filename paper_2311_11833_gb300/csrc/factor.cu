@@ -1589,7 +1589,7 @@ int launch_factor_big_dag(int precision, const SymDev& sd, const LevelPlan& lp, 
                               badcol, st);
 }
 
-int persistent_cta_front_limit(int precision) { return precision == PISP_FP32 ? 128 : 64; }
+int persistent_cta_front_limit(int precision) { return precision == PISP_FP32 ? 160 : 112; }
 
 size_t factor_persistent_smem(int precision, int CH, bool has_owner, int maxCtaF) {
   const size_t es = precision == PISP_FP32 ? 4 : 8;

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 
 #include "pisp_internal.h"
 
@@ -266,6 +267,54 @@ __device__ __forceinline__ T gather_position(const SymDev& sd, int s, int j, int
 }
 
 // ---------------------------------------------------------------------------
+// x[r] = p[r] for r < n (FP64 to T, zero beyond n): the 8 right-hand sides
+// of one row are contiguous, so a full aligned chunk is read with 16-byte
+// loads (L2 only: the values come from other CTAs of the same launch)
+template <typename T>
+__device__ __forceinline__ void ld_rhs8(const double* p, int n, T (&x)[kSolveChunk]) {
+  if (n == kSolveChunk && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int i = 0; i < kSolveChunk / 2; ++i) {
+      const double2 v = __ldcg(q + i);
+      x[2 * i] = (T)v.x;
+      x[2 * i + 1] = (T)v.y;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < kSolveChunk; ++r) x[r] = r < n ? (T)__ldcg(p + r) : T(0);
+  }
+}
+
+// p[r] = x[r] (and acc[r] += x[r] when acc is given) for r < n, 16-byte
+// stores for a full aligned chunk
+template <typename T>
+__device__ __forceinline__ void st_rhs8(double* p, double* acc, int n, const T (&x)[kSolveChunk]) {
+  if (n == kSolveChunk && (reinterpret_cast<uintptr_t>(p) & 15) == 0 &&
+      (!acc || (reinterpret_cast<uintptr_t>(acc) & 15) == 0)) {
+    double2* q = reinterpret_cast<double2*>(p);
+#pragma unroll
+    for (int i = 0; i < kSolveChunk / 2; ++i) q[i] = make_double2((double)x[2 * i], (double)x[2 * i + 1]);
+    if (acc) {
+      double2* qa = reinterpret_cast<double2*>(acc);
+#pragma unroll
+      for (int i = 0; i < kSolveChunk / 2; ++i) {
+        double2 v = qa[i];
+        v.x += (double)x[2 * i];
+        v.y += (double)x[2 * i + 1];
+        qa[i] = v;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < kSolveChunk; ++r)
+      if (r < n) {
+        p[r] = (double)x[r];
+        if (acc) acc[r] += (double)x[r];
+      }
+  }
+}
+
 // gather_position for every right-hand side r < nr of one position j at
 // once: the index entries of the inverse extend-add map are read once and
 // each serves the nr right-hand sides (the same per-RHS order of additions).
@@ -274,9 +323,14 @@ template <typename T>
 __device__ __forceinline__ void gather_position_rhs(const SymDev& sd, int s, int j, int ns, int c0,
                                                     const double* rhs, int rhs_mode, const T* V, int k, int K,
                                                     int R, int r0, int nr, T (&a)[kSolveChunk]) {
+  if (j < ns && nr > 0) {
+    const double* p = rhs_mode == RHS_BROADCAST ? rhs + (int64_t)sd.perm[c0 + j] * R + r0
+                                                : rhs + ((int64_t)(c0 + j) * K + k) * R + r0;
+    ld_rhs8<T>(p, nr, a);
+  } else {
 #pragma unroll
-  for (int r = 0; r < kSolveChunk; ++r)
-    a[r] = (j < ns && r < nr) ? (T)load_rhs(sd, rhs, rhs_mode, c0 + j, k, K, R, r0 + r) : T(0);
+    for (int r = 0; r < kSolveChunk; ++r) a[r] = T(0);
+  }
   if (nr <= 0) return;  // no position here (j beyond the front): touch no index array
   const int64_t e1 = sd.inv_off[sd.vec_off[s] + j + 1];
   const int64_t kR = (int64_t)K * R;
@@ -945,9 +999,7 @@ __device__ __forceinline__ void kseg_backward(const SymDev& sd, const FTask& t, 
       const int j = j0 + sl;
       const int64_t row = (j < ms) ? sd.rows[ro + j] : 0;
       T xt[kRW];
-#pragma unroll
-      for (int r = 0; r < kRW; ++r)
-        xt[r] = (kon && r < nr && j < ms) ? (T)__ldcg(out + (row * K + k) * R + r0 + r) : T(0);
+      ld_rhs8<T>(out + (row * K + k) * R + r0, (kon && j < ms) ? nr : 0, xt);
 #pragma unroll 4
       for (int jj = 0; jj < SEG; ++jj) {
         if (j0 + jj >= msw) break;
@@ -970,16 +1022,8 @@ __device__ __forceinline__ void kseg_backward(const SymDev& sd, const FTask& t, 
       }
     }
     if (kon && sl < ns) {
-      double* o = out + ((int64_t)(c0 + sl) * K + k) * R + r0;
-#pragma unroll
-      for (int r = 0; r < kRW; ++r)
-        if (r < nr) o[r] = (double)zt[r];
-      if (acc) {
-        double* a = acc + ((int64_t)(c0 + sl) * K + k) * R + r0;
-#pragma unroll
-        for (int r = 0; r < kRW; ++r)
-          if (r < nr) a[r] += (double)zt[r];
-      }
+      const int64_t o = ((int64_t)(c0 + sl) * K + k) * R + r0;
+      st_rhs8<T>(out + o, acc ? acc + o : nullptr, nr, zt);
     }
   }
   if (sy.done) publish_allk(sy, t.active, t.s, t.k0, t.k1, K, sl, SEG);

@@ -48,3 +48,5 @@ def test_minimum_bytes_count_indices_once_for_all_shifts():
     assert bench.min_bytes_per_launch("backward", st, K, R, p) == K * p * nnzU + 4 * nnzU + K * p * 10 * R + 8 * 10 * R
     assert bench.min_bytes_per_launch("forward", st, K, R, p) == K * p * nnzL + 4 * nnzL + 8 * 10 * R + K * p * 10 * R
     assert bench.min_bytes_per_launch("factor_small", st, K, R, p) is None
+    # the whole factorisation: A's values, D, the pattern once, K factors
+    assert bench.min_bytes_per_launch("factor_persistent", st, K, R, p) == 8 * 30 + 8 * 10 + 4 * (50 + 10) + K * p * 50
