@@ -518,10 +518,13 @@ def study_dense(args):
     K, R = 10, 1
     rows = []
     clocks = ClockSampler(0)
-    for n in (64, 150, 300, 531):
-        for G in (1, 2, 4, 8, 16):
+    variants = [("fp64", 0, {}), ("fp32", 2, dict(factor_policy=4)),
+                ("fp32", 2, dict(factor_policy=4, factor_tc=1))]
+    for (prec, sw, extra), n, G in ((v, n, G) for v in variants for n in (64, 150, 300, 531)
+                                    for G in (1, 2, 4, 8, 16)):
+        if True:
             insts = [_dense_instance(n, 1000 * n + g) for g in range(G)]
-            arm = Arm(pisp, torch, insts, K, R, args.eps, "fp64", 0, "dense", dev)
+            arm = Arm(pisp, torch, insts, K, R, args.eps, prec, sw, "dense", dev, extra=extra)
             arm.capture(profile=True)
             for _ in range(3):
                 arm.run()
@@ -538,11 +541,12 @@ def study_dense(args):
             prof = arm.s.profile_read()
             fac = (prof["factor_small"]["ms"] + prof["factor_big"]["ms"] + prof["factor_persistent"]["ms"]) / reps
             sol = (prof["forward"]["ms"] + prof["backward"]["ms"]) / reps
-            rows.append({"n": n, "G": G, "ms_step": round(e0.elapsed_time(e1) / reps, 4),
+            rows.append({"precision": prec, "sweeps": sw, "options": extra, "n": n, "G": G,
+                         "ms_step": round(e0.elapsed_time(e1) / reps, 4),
                          "ms_factor": round(fac, 4), "ms_solve": round(sol, 4)})
             arm.s.close()
     clk = clocks.stop()
-    return {"study": "dense batches (next row f4)", "K": K, "R": R, "precision": "fp64",
+    return {"study": "dense batches (next row f4)", "K": K, "R": R,
             "shifts": "symmetric +-eps*alpha", "eps": args.eps,
             "family": "Gaussian, diagonal +-2 sqrt(n) (dense)", "timing": "CUDA events over 20 graph replays",
             "table": rows, "clocks": clk}

@@ -105,6 +105,13 @@ typedef struct pisp_options {
   int32_t factor_smem_maxF; /* factor policy 4: widest front factored by one CTA
                                in shared memory (0 = the limit: 160 in FP32,
                                112 in FP64); wider fronts become owner tiles */
+  int32_t factor_tc;       /* 1: the trailing updates of FP32 owner tiles (the
+                              L21 U12 products of wide, dense fronts) run on the
+                              tensor cores: tcgen05.mma kind::tf32 with each FP32
+                              operand split as hi + lo, hi*hi + hi*lo + lo*hi,
+                              FP32 accumulation in tensor memory (FP32-level
+                              accuracy); 0 (default): FP32 FMA.  Ignored for
+                              FP64 factors. */
   int32_t analyze_threads; /* host threads pisp_analyze may use for the instances
                               of a batch: 0 = the hardware concurrency, at most
                               16 (default); 1 = the calling thread only.  A

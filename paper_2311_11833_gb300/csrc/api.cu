@@ -74,6 +74,7 @@ struct pisp_handle {
   // persistent solve tiling (pisp_options.solve_kfuse / solve_warp_maxF)
   int32_t kfuse = 1, warp_maxF = 32, solve_ctas = 0;
   int32_t factor_smem_maxF = 0;  // one-launch factorisation: widest shared-memory front (0 = limit)
+  int32_t factor_tc = 0;         // FP32 owner-tile updates on the tensor cores
   pisp::SymDev sd{};
   // level plans (depend on the factor precision)
   int plan_precision = 0;
@@ -233,7 +234,7 @@ int build_persistent_factor(pisp_handle* h, int precision, int32_t K) {
     if (sn.F() > Fc) maxBig = std::max(maxBig, sn.F());
     else if (sn.F() > 32) maxCta = std::max(maxCta, sn.F());
   }
-  const int CH = maxBig > 0 ? pisp::owner_chunk_rows(precision, maxBig) : 32;
+  const int CH = maxBig > 0 ? pisp::owner_chunk_rows(precision, maxBig, h->factor_tc) : 32;
   std::vector<pisp::FactorTask> ft;
   std::vector<int32_t> wl, need(S.sn.size(), 1);
   int64_t nflags = 0;
@@ -372,7 +373,7 @@ int build_plans(pisp_handle* h, int precision) {
       std::vector<pisp::DagTask> tk;
       int32_t nfl = 0;
       if (owner) {
-        lp.own_ch = pisp::owner_chunk_rows(precision, lp.big_maxF);
+        lp.own_ch = pisp::owner_chunk_rows(precision, lp.big_maxF, h->factor_tc);
         pisp::build_owner_tasks(h->h_bigF.data() + lp.big_off, lp.big_count, h->K_hint, lp.own_ch, tk, nfl);
       }
       else
@@ -746,6 +747,7 @@ int analyze_impl(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   h->warp_maxF = opt && opt->solve_warp_maxF > 0 ? opt->solve_warp_maxF : 32;
   h->solve_ctas = opt && opt->solve_ctas_per_sm > 0 ? std::min(4, std::max(2, opt->solve_ctas_per_sm)) : 0;
   h->factor_smem_maxF = opt && opt->factor_smem_maxF > 0 ? opt->factor_smem_maxF : 0;
+  h->factor_tc = opt && opt->factor_tc ? 1 : 0;
   h->units_K = h->units_R = 0;
   if (opt) {
     so.ordering = opt->ordering;
@@ -976,7 +978,7 @@ int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
         precision, h->sd, h->d_ftasks.as<pisp::FactorTask>(), h->n_ftasks, h->fticket.as<int>(), h->fdone.as<int>(),
         h->d_fneed.as<int>(), h->fflags.as<int>(), h->serr.as<int>(), h->d_fwl.as<int32_t>(), h->vals.as<double>(),
         h->D.as<double>(), sh, h->fronts.p, h->status.as<int32_t>(), h->badcol.as<int32_t>(), h->fac_CH,
-        h->fac_smem, h->wait_polls, h->stream);
+        h->fac_smem, h->wait_polls, h->factor_tc, h->stream);
     TRY(count(h, n));
     prof_end(h, pb, PISP_PROF_FACTOR, K * h->fac_bytes, n);
     h->factored = true;
@@ -1004,7 +1006,7 @@ int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
                                         h->d_dag.as<pisp::DagTask>(), h->dag_ticket.as<int>(),
                                         h->dag_flags.as<int>(), h->serr.as<int>(), h->vals.as<double>(),
                                         h->D.as<double>(), sh, h->fronts.p, h->status.as<int32_t>(),
-                                        h->badcol.as<int32_t>(), bst);
+                                        h->badcol.as<int32_t>(), h->factor_tc, bst);
       } else {
         n = pisp::launch_factor_big(precision, h->sd, lp, h->d_big.as<int32_t>(), h->h_bigF.data(),
                                     h->vals.as<double>(), h->D.as<double>(), sh, h->fronts.p,

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <type_traits>
 #include <vector>
 
 #include "pisp_internal.h"
@@ -1036,16 +1037,175 @@ __device__ __forceinline__ void own_eliminate_rows(T* Bt, int ld, int R0, int i0
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core form of an owner tile's trailing update (FP32 factors only):
+//     x(i, c) -= sum_{cc < nb} L(i, r0 + cc) U(cc, c)
+// for the tile's rows, 128 rows at a time, on the 5th-generation tensor cores
+// (tcgen05.mma, kind::tf32, M = 128, N = 32, K = 8 per instruction, FP32
+// accumulator in tensor memory).  TF32 keeps 10 mantissa bits, so every FP32
+// operand is split as hi + lo (hi = TF32 rounding of x, lo = TF32 rounding of
+// x - hi) and the product is formed as hi*hi + hi*lo + lo*hi ("3xTF32"): the
+// dropped lo*lo term and the rounding of lo are below FP32 rounding of the
+// sum, so the update keeps FP32 accuracy.  Operands are staged in shared
+// memory in the no-swizzle K-major core-matrix layout: 8 rows x 16 bytes per
+// core matrix, K-adjacent core matrices 128 bytes apart, 8-row groups 1024
+// bytes apart.
+// ---------------------------------------------------------------------------
+struct TcCtx {
+  int on;          // 1: owner-tile updates on the tensor cores
+  float* sA;       // [2][128 * 32] hi / lo of 128 rows of L
+  float* sB;       // [2][32 * 32]  hi / lo of the 32 U rows (as N x K)
+  uint32_t tmem;   // 32 tensor-memory columns: the 128 x 32 FP32 accumulator
+  uint32_t mbar;   // shared-memory address of the MMA-completion barrier
+  uint32_t phase;  // parity of the next completion of that barrier
+};
+constexpr int kTcSmemFloats = 2 * 128 * 32 + 2 * 32 * 32;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// offset of element (row r, k) of a rows x 32 K-major operand
+__device__ __forceinline__ int tc_kmaj(int r, int k) {
+  return (r >> 3) * 256 + (k >> 2) * 32 + (r & 7) * 4 + (k & 3);
+}
+
+// shared-memory matrix descriptor: start address, leading-dimension (K) and
+// stride-dimension (8-row group) byte offsets, fixed field 0b001, no swizzle
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(128 >> 4) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Allocates the CTA's 32 tensor-memory columns (warp 0) and initialises the
+// completion barrier; every thread of the CTA calls it.
+__device__ __forceinline__ void tc_setup(TcCtx& tc, uint32_t* s_taddr, uint64_t* s_mbar) {
+  if (!tc.on) return;
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_addr(s_taddr)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(s_mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  tc.tmem = *s_taddr;
+  tc.mbar = smem_addr(s_mbar);
+  tc.phase = 0;
+}
+
+// Frees the tensor memory; every thread of the CTA calls it before exiting.
+__device__ __forceinline__ void tc_teardown(const TcCtx& tc) {
+  if (!tc.on) return;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tc.tmem));
+}
+
+// rows [i0, i1) of the tile (stored from row R0): x(i, c) -= L(i, r0..r0+nb-1) U
+// for c < w, L from the front storage, U from Us (32 x 32 row-major, zero
+// beyond nb rows and w columns).  Needs kOwnThreads (8 warps) threads.
+__device__ __noinline__ void tc_update_rows(float* Bt, int ld, int R0, const float* f, int F, int r0, int nb,
+                                               const float* Us, int i0, int i1, int w, TcCtx& tc, int* err) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  float* sAh = tc.sA;
+  float* sAl = tc.sA + 128 * 32;
+  float* sBh = tc.sB;
+  float* sBl = tc.sB + 32 * 32;
+  for (int q = tid; q < 32 * 32; q += nt) {  // B(k, n) = U(k, n), staged as N x K
+    const int n = q & 31, k = q >> 5;
+    const float u = Us[k * 32 + n], hi = tf32_round(u);
+    sBh[tc_kmaj(n, k)] = hi;
+    sBl[tc_kmaj(n, k)] = tf32_round(u - hi);
+  }
+  const int ksteps = (nb + 7) >> 3;
+  // instruction descriptor: FP32 accumulator, TF32 A and B, both K-major,
+  // N = 32, M = 128
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+  for (int m0 = i0; m0 < i1; m0 += 128) {
+    for (int q = tid; q < 128 * 32; q += nt) {  // A(r, k) = L(m0 + r, r0 + k), zero outside
+      const int r = q & 127, k = q >> 7, i = m0 + r;
+      const float a = (i < i1 && k < nb) ? __ldcg(f + i + (int64_t)(r0 + k) * F) : 0.f;
+      const float hi = tf32_round(a);
+      sAh[tc_kmaj(r, k)] = hi;
+      sAl[tc_kmaj(r, k)] = tf32_round(a - hi);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      uint32_t acc = 0;
+      for (int ks = 0; ks < ksteps; ++ks) {
+        for (int term = 0; term < 3; ++term) {  // hi*hi, hi*lo, lo*hi
+          const uint64_t da = tc_sdesc(smem_addr(term == 2 ? sAl : sAh) + ks * 256);
+          const uint64_t db = tc_sdesc(smem_addr(term == 1 ? sBl : sBh) + ks * 256);
+          asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tc.tmem),
+                       "l"(da), "l"(db), "r"(idesc), "r"(acc));
+          acc = 1;
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc.mbar));
+    }
+    {  // bounded wait for the MMAs of this block
+      uint32_t done = 0;
+      for (int it = 0; it < (1 << 24) && !done; ++it)
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(tc.mbar), "r"(tc.phase));
+      if (!done && tid == 0) atomicExch(err, 1);
+      tc.phase ^= 1;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (rows), columns
+    // 16 (w / 4) .. + 15
+    uint32_t v[16];
+    const uint32_t ta = tc.tmem + ((uint32_t)(32 * (wid & 3)) << 16) + 16 * (wid >> 2);
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                   "=r"(v[15])
+                 : "r"(ta));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int row = m0 + 32 * (wid & 3) + lane;
+    if (row < i1) {
+      float* x = Bt + (row - R0);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int col = 16 * (wid >> 2) + c;
+        if (col < w) x[col * ld] -= __uint_as_float(v[c]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // sA / the accumulator are reused by the next block
+  }
+}
+
 // One owner tile: the 32-column block j of front s, perturbation k,
 // restricted to the row chunk q of CH rows (see above).  `flags` points at
 // the (front, k) pair's release flags.  Needs kOwnThreads threads and the
 // shared memory layout of the owner kernels (Us, Ls, Bt, rinv).
-template <typename T>
+template <typename T, bool TC>
 __device__ __forceinline__ void owner_tile(const SymDev& sd, int s, int k, int j, int q, int* flags, int CH,
                                            int* err, const double* __restrict__ vals,
                                            const double* __restrict__ D, const Shifts& sh,
                                            T* __restrict__ fronts, int32_t* status, int32_t* badcol,
-                                           T* Us, T* Ls, T* Bt, T* rinv) {
+                                           T* Us, T* Ls, T* Bt, T* rinv, TcCtx& tc) {
   const int K = sh.K;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
@@ -1102,7 +1262,10 @@ __device__ __forceinline__ void owner_tile(const SymDev& sd, int s, int k, int j
         __syncthreads();
         if (tid == 0) dag_st_release(Uf + p * J + j, 1);
       }
-      own_update_rows<T>(Bt, ld, R0, f, F, r0, nb, Us, r0 + nb, R1, w);
+      if constexpr (TC && std::is_same<T, float>::value)
+        tc_update_rows(Bt, ld, R0, f, F, r0, nb, Us, r0 + nb, R1, w, tc, err);
+      else
+        own_update_rows<T>(Bt, ld, R0, f, F, r0, nb, Us, r0 + nb, R1, w);
       __syncthreads();
     } else {
       // a chunk below panel p: its U rows of this block come from the
@@ -1118,7 +1281,10 @@ __device__ __forceinline__ void owner_tile(const SymDev& sd, int s, int k, int j
         Us[e] = (r < nb && c < w) ? __ldcg(f + (r0 + r) + (int64_t)(j0 + c) * F) : T(0);
       }
       __syncthreads();
-      own_update_rows<T>(Bt, ld, R0, f, F, r0, nb, Us, R0, R1, w);
+      if constexpr (TC && std::is_same<T, float>::value)
+        tc_update_rows(Bt, ld, R0, f, F, r0, nb, Us, R0, R1, w, tc, err);
+      else
+        own_update_rows<T>(Bt, ld, R0, f, F, r0, nb, Us, R0, R1, w);
       __syncthreads();
     }
   }
@@ -1169,7 +1335,7 @@ __device__ __forceinline__ void owner_tile(const SymDev& sd, int s, int k, int j
   }
 }
 
-template <typename T>
+template <typename T, bool TC>
 __global__ void __launch_bounds__(kOwnThreads) k_front_owner(SymDev sd, const int32_t* __restrict__ big,
                                                              const DagTask* __restrict__ tasks, int ntasks,
                                                              int* ticket, int* flags, int* err,
@@ -1180,20 +1346,26 @@ __global__ void __launch_bounds__(kOwnThreads) k_front_owner(SymDev sd, const in
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_t;
   __shared__ T rinv[32];
+  __shared__ uint32_t s_taddr;
+  __shared__ __align__(8) uint64_t s_mbar;
   T* Us = reinterpret_cast<T*>(smraw);  // 32 x 32 row-major: U rows of the current panel
   T* Ls = Us + 32 * 32;                 // 32 x 33 row-major: unit-lower L11 of the current panel
   T* Bt = Ls + 32 * 33;                 // (CH + 1) x 32 column-major: the owned tile
+  float* tcs = reinterpret_cast<float*>(Bt + (size_t)(CH + 1) * 32);  // tensor-core staging (FP32 only)
+  TcCtx tc{TC ? 1 : 0, tcs, tcs + 2 * 128 * 32, 0, 0, 0};
+  if constexpr (TC) tc_setup(tc, &s_taddr, &s_mbar);
   const int tid = threadIdx.x;
   for (;;) {
     __syncthreads();  // the previous task is done with shared memory and s_t
     if (tid == 0) s_t = atomicAdd(ticket, 1);
     __syncthreads();
     const int u = s_t;
-    if (u >= ntasks) return;
+    if (u >= ntasks) break;
     const DagTask t = tasks[u];
-    owner_tile<T>(sd, big[t.b], t.k, t.j, t.p, flags + t.flags, CH, err, vals, D, sh, fronts, status, badcol,
-                  Us, Ls, Bt, rinv);
+    owner_tile<T, TC>(sd, big[t.b], t.k, t.j, t.p, flags + t.flags, CH, err, vals, D, sh, fronts, status, badcol,
+                  Us, Ls, Bt, rinv, tc);
   }
+  if constexpr (TC) tc_teardown(tc);
 }
 
 // ---------------------------------------------------------------------------
@@ -1240,16 +1412,22 @@ __device__ __forceinline__ void fac_publish(int* fdone, int s, int k, int K) {
   asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(fdone + (int64_t)s * K + k) : "memory");
 }
 
-template <typename T>
+template <typename T, bool TC>
 __global__ void __launch_bounds__(kOwnThreads, 2)
 k_factor_persistent(SymDev sd, const FactorTask* __restrict__ tasks, int ntasks, int* ticket, int* fdone,
                     const int* __restrict__ need, int* flags, int* err, const int32_t* __restrict__ wlist,
                     const double* __restrict__ vals, const double* __restrict__ D, Shifts sh,
-                    T* __restrict__ fronts, int32_t* status, int32_t* badcol, int CH, int64_t polls) {
+                    T* __restrict__ fronts, int32_t* status, int32_t* badcol, int CH, int64_t polls,
+                    size_t tc_off) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_t;
   __shared__ T rinv[32];
+  __shared__ uint32_t s_taddr;
+  __shared__ __align__(8) uint64_t s_mbar;
   T* sm = reinterpret_cast<T*>(smraw);
+  float* tcs = reinterpret_cast<float*>(smraw + tc_off);  // tensor-core staging (FP32 owner tiles)
+  TcCtx tc{TC ? 1 : 0, tcs, tcs + 2 * 128 * 32, 0, 0, 0};
+  if constexpr (TC) tc_setup(tc, &s_taddr, &s_mbar);
   const int K = sh.K;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5;
@@ -1258,7 +1436,7 @@ k_factor_persistent(SymDev sd, const FactorTask* __restrict__ tasks, int ntasks,
     if (tid == 0) s_t = atomicAdd(ticket, 1);
     __syncthreads();
     const int u = s_t;
-    if (u >= ntasks) return;
+    if (u >= ntasks) break;
     const FactorTask t = tasks[u];
     if (t.kind == kFacWarp) {
       const int q = t.q + wid;
@@ -1276,58 +1454,79 @@ k_factor_persistent(SymDev sd, const FactorTask* __restrict__ tasks, int ntasks,
       if (t.kind == kFacCta)
         front_cta<T>(sd, t.s, t.k, vals, D, sh, fronts, status, badcol, sm);
       else
-        owner_tile<T>(sd, t.s, t.k, t.j, t.q, flags + t.flags, CH, err, vals, D, sh, fronts, status, badcol,
-                      sm, sm + 32 * 32, sm + 32 * 32 + 32 * 33, rinv);
+        owner_tile<T, TC>(sd, t.s, t.k, t.j, t.q, flags + t.flags, CH, err, vals, D, sh, fronts, status,
+                          badcol, sm, sm + 32 * 32, sm + 32 * 32 + 32 * 33, rinv, tc);
       __syncthreads();
       if (tid == 0) fac_publish(fdone, t.s, t.k, K);
     }
   }
+  if constexpr (TC) tc_teardown(tc);
 }
 
 template <typename T>
 int factor_persistent_impl(const SymDev& sd, const FactorTask* tasks, int ntasks, int* ticket, int* fdone,
                            const int* need, int* flags, int* err, const int32_t* wlist, const double* vals,
                            const double* D, const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol,
-                           int CH, size_t smem, int64_t polls, cudaStream_t st) {
+                           int CH, size_t smem, int64_t polls, int tc, cudaStream_t st) {
   if (ntasks == 0) return 0;
+  const int tc_on = tc && sizeof(T) == 4 ? 1 : 0;
+  const size_t tc_off = smem;  // the staging follows everything the other task kinds use
+  if (tc_on) smem += (size_t)kTcSmemFloats * sizeof(float);
   static std::atomic<int> nsm_dev[kMaxDevices];
   const int dev = current_device();
   int nsm = nsm_dev[dev].load(std::memory_order_acquire);
   if (!nsm) {
-    cudaFuncSetAttribute(k_factor_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    cudaFuncSetAttribute(k_factor_persistent<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    cudaFuncSetAttribute(k_factor_persistent<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     nsm_dev[dev].store(nsm, std::memory_order_release);
   }
   if (smem > (size_t)kSmemCap) return -1;
   int occ = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_factor_persistent<T>, kOwnThreads, smem);
+  if (tc_on) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_factor_persistent<T, true>, kOwnThreads, smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_factor_persistent<T, false>, kOwnThreads, smem);
   const int grid = std::max(1, std::min(ntasks, std::max(1, occ) * std::max(nsm, 1)));
-  k_factor_persistent<T><<<grid, kOwnThreads, smem, st>>>(sd, tasks, ntasks, ticket, fdone, need, flags, err,
-                                                          wlist, vals, D, sh, (T*)fronts, status, badcol, CH,
-                                                          polls > 0 ? polls : kDagWaitPolls);
+  const int64_t pl = polls > 0 ? polls : kDagWaitPolls;
+  if (tc_on)
+    k_factor_persistent<T, true><<<grid, kOwnThreads, smem, st>>>(sd, tasks, ntasks, ticket, fdone, need, flags,
+                                                                  err, wlist, vals, D, sh, (T*)fronts, status,
+                                                                  badcol, CH, pl, tc_off);
+  else
+    k_factor_persistent<T, false><<<grid, kOwnThreads, smem, st>>>(sd, tasks, ntasks, ticket, fdone, need, flags,
+                                                                   err, wlist, vals, D, sh, (T*)fronts, status,
+                                                                   badcol, CH, pl, tc_off);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 template <typename T>
 int owner_impl(const SymDev& sd, const LevelPlan& lp, const int32_t* d_big, const DagTask* tasks,
                int* ticket, int* flags, int* err, const double* vals, const double* D,
-               const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol, cudaStream_t st) {
+               const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol, int tc, cudaStream_t st) {
   static std::atomic<int> nsm_dev[kMaxDevices];
   const int dev = current_device();
   int nsm = nsm_dev[dev].load(std::memory_order_acquire);
   if (!nsm) {
-    cudaFuncSetAttribute(k_front_owner<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    cudaFuncSetAttribute(k_front_owner<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    cudaFuncSetAttribute(k_front_owner<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     nsm_dev[dev].store(nsm, std::memory_order_release);
   }
-  const size_t smem = ((size_t)(lp.own_ch + 1) * 32 + 32 * 32 + 32 * 33) * sizeof(T);
+  const int tc_on = tc && sizeof(T) == 4 ? 1 : 0;
+  const size_t smem = ((size_t)(lp.own_ch + 1) * 32 + 32 * 32 + 32 * 33) * sizeof(T) +
+                      (tc_on ? (size_t)kTcSmemFloats * sizeof(float) : 0);
   if (lp.own_ch < 32 || lp.own_ch % 32 || smem > (size_t)kSmemCap) return -1;
   int occ = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_front_owner<T>, kOwnThreads, smem);
+  if (tc_on) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_front_owner<T, true>, kOwnThreads, smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_front_owner<T, false>, kOwnThreads, smem);
   const int grid = std::max(1, std::min(lp.dag_tasks, std::max(1, occ) * std::max(nsm, 1)));
-  k_front_owner<T><<<grid, kOwnThreads, smem, st>>>(sd, d_big + lp.big_off, tasks + lp.dag_task_off,
-                                                    lp.dag_tasks, ticket, flags, err, vals, D, sh,
-                                                    (T*)fronts, status, badcol, lp.own_ch);
+  if (tc_on)
+    k_front_owner<T, true><<<grid, kOwnThreads, smem, st>>>(sd, d_big + lp.big_off, tasks + lp.dag_task_off,
+                                                            lp.dag_tasks, ticket, flags, err, vals, D, sh,
+                                                            (T*)fronts, status, badcol, lp.own_ch);
+  else
+    k_front_owner<T, false><<<grid, kOwnThreads, smem, st>>>(sd, d_big + lp.big_off, tasks + lp.dag_task_off,
+                                                             lp.dag_tasks, ticket, flags, err, vals, D, sh,
+                                                             (T*)fronts, status, badcol, lp.own_ch);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
@@ -1497,7 +1696,7 @@ int launch_factor_small_group(int precision, const SymDev& sd, const LevelPlan& 
 
 int max_dag_front(int precision) { return kSmemCap / (32 * (precision == PISP_FP32 ? 4 : 8)) - 1; }
 
-int owner_chunk_rows(int precision, int maxF) {
+int owner_chunk_rows(int precision, int maxF, int tc) {
   // Rows per tile.  FP64 elimination runs at a small fraction of the FP32
   // rate on this part, so one SM per 32-column block is the bottleneck of a
   // panel step: 32-row tiles spread a block's update and elimination over
@@ -1507,7 +1706,8 @@ int owner_chunk_rows(int precision, int maxF) {
   // tile is a whole column block while it fits in shared memory.
   const int full = (maxF + 31) / 32 * 32;
   if (precision != PISP_FP32) return std::min(32, full);
-  const int fit = ((kSmemCap / 4 - 32 * 32 - 32 * 33) / 32 - 1) / 32 * 32;  // (CH + 1) * 32 + 2080 floats
+  // (CH + 1) * 32 + 2080 floats, plus the tensor-core staging when it is on
+  const int fit = ((kSmemCap / 4 - 32 * 32 - 32 * 33 - (tc ? kTcSmemFloats : 0)) / 32 - 1) / 32 * 32;
   return std::min(full, fit);
 }
 
@@ -1574,13 +1774,13 @@ void build_dag_tasks(const BigFrontHost* big, int32_t nbig, int32_t K, std::vect
 int launch_factor_big_dag(int precision, const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,
                           const DagTask* tasks, int* ticket, int* flags, int* err,
                           const double* vals, const double* D, const Shifts& sh, void* fronts,
-                          int32_t* status, int32_t* badcol, cudaStream_t st) {
+                          int32_t* status, int32_t* badcol, int tc, cudaStream_t st) {
   if (lp.dag_owner) {
     if (precision == PISP_FP32)
       return owner_impl<float>(sd, lp, d_big, tasks, ticket, flags, err, vals, D, sh, fronts, status,
-                               badcol, st);
+                               badcol, tc, st);
     return owner_impl<double>(sd, lp, d_big, tasks, ticket, flags, err, vals, D, sh, fronts, status,
-                              badcol, st);
+                              badcol, tc, st);
   }
   if (precision == PISP_FP32)
     return big_dag_impl<float>(sd, lp, d_big, tasks, ticket, flags, err, vals, D, sh, fronts, status,
@@ -1602,13 +1802,13 @@ size_t factor_persistent_smem(int precision, int CH, bool has_owner, int maxCtaF
 int launch_factor_persistent(int precision, const SymDev& sd, const FactorTask* tasks, int ntasks, int* ticket,
                              int* fdone, const int* need, int* flags, int* err, const int32_t* wlist,
                              const double* vals, const double* D, const Shifts& sh, void* fronts,
-                             int32_t* status, int32_t* badcol, int CH, size_t smem, int64_t polls,
+                             int32_t* status, int32_t* badcol, int CH, size_t smem, int64_t polls, int tc,
                              cudaStream_t st) {
   if (precision == PISP_FP32)
     return factor_persistent_impl<float>(sd, tasks, ntasks, ticket, fdone, need, flags, err, wlist, vals, D, sh,
-                                         fronts, status, badcol, CH, smem, polls, st);
+                                         fronts, status, badcol, CH, smem, polls, tc, st);
   return factor_persistent_impl<double>(sd, tasks, ntasks, ticket, fdone, need, flags, err, wlist, vals, D, sh,
-                                        fronts, status, badcol, CH, smem, polls, st);
+                                        fronts, status, badcol, CH, smem, polls, tc, st);
 }
 
 int launch_factor_big(int precision, const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,

@@ -156,18 +156,19 @@ int launch_factor_big(int precision, const SymDev& sd, const LevelPlan& lp, cons
 // Big fronts of one level as one persistent launch over the level's task
 // list (tile DAG, or owner tiles when lp.dag_owner); ticket (1 int)
 // and flags (lp.dag_flags ints) must be zero; err is set if a bounded
-// dependency wait gave up.
+// dependency wait gave up.  tc != 0: FP32 owner-tile updates on the tensor
+// cores (3xTF32, tcgen05).
 int launch_factor_big_dag(int precision, const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,
                           const DagTask* tasks, int* ticket, int* flags, int* err,
                           const double* vals, const double* D, const Shifts& sh, void* fronts,
-                          int32_t* status, int32_t* badcol, cudaStream_t st);
+                          int32_t* status, int32_t* badcol, int tc, cudaStream_t st);
 // The whole factorisation in one persistent launch (factor policy 4): ticket
 // (1 int), fdone (S*K ints) and flags must be zero; need[s] = 1 for warp and
 // shared-memory fronts, tiles per (front, k) for owner fronts.
 int launch_factor_persistent(int precision, const SymDev& sd, const FactorTask* tasks, int ntasks, int* ticket,
                              int* fdone, const int* need, int* flags, int* err, const int32_t* wlist,
                              const double* vals, const double* D, const Shifts& sh, void* fronts,
-                             int32_t* status, int32_t* badcol, int CH, size_t smem, int64_t polls,
+                             int32_t* status, int32_t* badcol, int CH, size_t smem, int64_t polls, int tc,
                              cudaStream_t st);
 // widest front the one-launch factorisation keeps in shared memory (wider:
 // owner tiles), and its dynamic shared memory per CTA
@@ -175,8 +176,9 @@ int persistent_cta_front_limit(int precision);
 size_t factor_persistent_smem(int precision, int CH, bool has_owner, int maxCtaF);
 // largest front the tile-DAG path takes (its panel must fit in shared memory)
 int max_dag_front(int precision);
-// rows per owner tile for a level whose widest front is maxF
-int owner_chunk_rows(int precision, int maxF);
+// rows per owner tile for a level whose widest front is maxF (tc != 0: leave
+// room for the tensor-core staging)
+int owner_chunk_rows(int precision, int maxF, int tc);
 // largest front (in elements of the given precision) the shared-memory path takes
 int small_front_limit(int precision);
 // CTAs per cluster for a front of size F factored in distributed shared

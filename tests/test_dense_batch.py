@@ -65,17 +65,20 @@ def test_dense_family_is_safe_without_pivoting():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision,sweeps", [("fp64", 0), ("fp32", 2)])
-def test_dense_batch_on_the_gpu(precision, sweeps):
+@pytest.mark.parametrize("precision,sweeps,opts,extra", [
+    ("fp64", 0, {}, ()), ("fp32", 2, {}, ()),
+    # one launch, owner-tile updates on the tensor cores, with the paper's n = 531
+    ("fp32", 2, dict(factor_policy=4, factor_tc=1), (531,))])
+def test_dense_batch_on_the_gpu(precision, sweeps, opts, extra):
     import torch
     import paper_2311_11833_gb300 as pisp
-    insts = [_dense(n) for n in SIZES]
+    insts = [_dense(n) for n in SIZES + extra]
     sizes, rp, col, val, D = _concat(insts)
     t = pfgen.symmetric_shifts(4)
     R = 3
     N = sum(sizes)
     b = pfgen.rhs(N, R, 5)
-    s = pisp.Solver(sizes, rp, col)
+    s = pisp.Solver(sizes, rp, col, **opts)
     try:
         s.factor(torch.tensor(val, device="cuda"), torch.tensor(D, device="cuda"), t, precision)
         assert s.status()[0] == 0

@@ -153,11 +153,35 @@ def test_factor_entries_large_fronts(pisp, n, density, prec, policy):
     """Fronts factored in shared memory, by CTA clusters, by column-block owners, as a
     tile DAG, by per-panel launches or in the one-launch factorisation equal dense
     Doolittle's."""
-    inst = pfgen.random_sparse(n, density, seed=n)
+    _check_factor_entries(pisp, n, density, prec, factor_policy=policy)
+
+
+@pytest.mark.parametrize("n,density,policy", [(300, 0.03, 0), (700, 0.012, 0), (1200, 0.006, 0),
+                                              (700, 0.012, 4), (1200, 0.006, 4)])
+def test_factor_entries_tensor_core_updates(pisp, n, density, policy):
+    """FP32 owner tiles with their trailing updates on the tensor cores (3xTF32,
+    tcgen05): the factor entries still equal dense Doolittle's to FP32 accuracy."""
+    _check_factor_entries(pisp, n, density, "fp32", factor_policy=policy, factor_tc=1)
+
+
+@pytest.mark.parametrize("policy,tc", [(0, 0), (4, 0), (0, 1), (4, 1)])
+def test_factor_entries_row_chunked_fp32_tiles(pisp, policy, tc):
+    """A front of 1774 rows: taller than one FP32 owner tile's rows (1728, or 1408
+    when the tensor-core staging takes its share of shared memory), so its column
+    blocks are split into row chunks.  The matrix is the 2200-node pattern with a
+    diagonal boost large enough that FP32 pivot-free factor entries are accurate
+    (with the default boost the element growth is 5.6e4 and a plain FP32
+    Doolittle on the host already misses 2e-4 relative on 541 entries)."""
+    _check_factor_entries(pisp, 2200, 0.008, "fp32", diag_boost=40.0, min_front=1728, factor_policy=policy,
+                          factor_tc=tc)
+
+
+def _check_factor_entries(pisp, n, density, prec, diag_boost=4.0, min_front=100, **opts):
+    inst = pfgen.random_sparse(n, density, seed=n, diag_boost=diag_boost)
     t = pfgen.symmetric_shifts(2)
-    s, val, D = _solver(pisp, [inst], factor_policy=policy)
+    s, val, D = _solver(pisp, [inst], **opts)
     s.factor(_dev(val), _dev(D), t, prec)
-    assert s.stats()["max_front"] > 100
+    assert s.stats()["max_front"] > min_front
     perm = s.perm()
     c0, c1, ms, rows = s.supernodes()
     A = oracle.to_dense(inst)
@@ -406,15 +430,15 @@ def test_fp32_front_taller_than_a_shared_memory_column(pisp):
     assert _maxrel(x, _oracle_xhat(inst, t, b)) <= TOL64
 
 
-@pytest.mark.parametrize("policy", [0, 4])
-def test_full_scale_config_fp32_sweeps(pisp, policy):
+@pytest.mark.parametrize("policy,tc", [(0, 0), (4, 0), (0, 1), (4, 1)])
+def test_full_scale_config_fp32_sweeps(pisp, policy, tc):
     """10000-bus grid: 23 fronts wider than the shared-memory limit, several per level,
     up to the dense F = 1594 root (column-block owners); FP32 factors plus sweeps reach
     the FP64 definition for every right-hand side."""
     c = pfgen.CONFIGS["scale"]
     inst = pfgen.make_instance("scale")
     t = pfgen.symmetric_shifts(c["K"])
-    s, val, D = _solver(pisp, [inst], factor_policy=policy)
+    s, val, D = _solver(pisp, [inst], factor_policy=policy, factor_tc=tc)
     assert s.stats()["max_front"] > 1000
     s.factor(_dev(val), _dev(D), t, "fp32")
     b = pfgen.rhs(inst.n, 4, 11)
