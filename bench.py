@@ -81,6 +81,10 @@ def parse():
     ap.add_argument("--kfuse", type=int, default=0, help="persistent solve: shifts per narrow-front task")
     ap.add_argument("--warp-maxf", type=int, default=0,
                     help="persistent solve: widest front with <= 32 pivots solved by one warp")
+    ap.add_argument("--ctas", type=int, default=0, help="persistent solve: resident CTAs per SM (2, 3, 4)")
+    ap.add_argument("--relax-small", type=int, default=-1, help="supernode amalgamation: pivot block size")
+    ap.add_argument("--relax-zeros", type=float, default=-1.0, help="supernode amalgamation: zero fraction")
+    ap.add_argument("--factor-tc", type=int, default=0, help="1: FP32 owner-tile updates on the tensor cores")
     ap.add_argument("--autotune", default="auto", choices=["auto", "on", "off"],
                     help="time candidate library options on this workload first and use the fastest "
                          "(auto: on for the batching workload)")
@@ -324,7 +328,12 @@ def run_pisp(args, rank, world, local_rank):
         tuned = tune.autotune(sizes, rp, col, torch.tensor(val, device=dev), torch.tensor(D, device=dev),
                               pfgen.symmetric_shifts(K, args.eps),
                               torch.tensor(pfgen.rhs(sum(sizes), R, 1), device=dev), precision, sweeps)
-    extra = {k: v for k, v in (("solve_kfuse", args.kfuse), ("solve_warp_maxF", args.warp_maxf)) if v}
+    extra = {k: v for k, v in (("solve_kfuse", args.kfuse), ("solve_warp_maxF", args.warp_maxf),
+                               ("solve_ctas_per_sm", args.ctas), ("factor_tc", args.factor_tc)) if v}
+    if args.relax_small >= 0:
+        extra["relax_small"] = args.relax_small
+    if args.relax_zeros >= 0:
+        extra["relax_zeros"] = args.relax_zeros
     arm = Arm(pisp, torch, insts, K, R, args.eps, precision, sweeps, args.workload, dev, args.schedule,
               args.factor_policy, options=tuned["options"] if tuned else None, extra=extra)
     G = len(insts)
@@ -433,6 +442,8 @@ def run_pisp(args, rank, world, local_rank):
         "gpu_launches": int(stats["gpu_launches"]) * args.steps,
         "analyze_ms": round(arm.analyze_ms, 2),
         "autotune": ({"options": tuned["options"], "candidates": len(tuned["all"]),
+                      "rejected_for_accuracy": tuned.get("rejected"), "tol": tuned.get("tol"),
+                      "best_err_vs_fp64_factor_solve": tuned.get("err"),
                       "best_ms": round(tuned["ms"], 4),
                       "default_ms": round(next((r["ms"] for r in tuned["all"] if r["options"] == dict(
                           relax_small=8, relax_zeros=0.05, factor_policy=0, solve_schedule=0,

@@ -15,7 +15,12 @@ The options that change performance but not the result:
 For one sparsity pattern, shift count, RHS count, precision and sweep count,
 `autotune` times candidates on the GPU with CUDA events over replays of the
 step the library captures in a CUDA graph (factor + solve + sweeps), and
-returns the fastest.  The default search is staged: first the solve tiling
+returns the fastest among those whose result stays accurate: the options
+change only rounding, but with FP32 factors a different amalgamation can
+leave the sweeps short of the FP64 result, so every candidate's x is compared
+entry by entry with an FP64-factor solve (no sweeps, default options) of the
+same inputs and rejected beyond `tol` (max |x - ref| / max |ref| per
+right-hand side).  The default search is staged: first the solve tiling
 with the default amalgamation and factor policy, then the amalgamation and
 factor policy with the best tiling.  Results are cached in a JSON file (path
 from $PISP_TUNE_CACHE, or the `cache` argument) keyed by a hash of the
@@ -78,7 +83,15 @@ def _load(path):
         return {}
 
 
-def _time(Solver, sizes, row_ptr, col, values, D, t, b, x, precision, sweeps, reps, opts):
+def _entrywise(x, ref) -> float:
+    """max over right-hand sides of max |x - ref| / max |ref| (on the device)."""
+    import torch
+    scale = ref.abs().amax(dim=0).clamp_min(torch.finfo(ref.dtype).tiny)
+    err = ((x - ref).abs().amax(dim=0) / scale).max()
+    return float(err) if torch.isfinite(err) else float("inf")
+
+
+def _time(Solver, sizes, row_ptr, col, values, D, t, b, x, precision, sweeps, reps, opts, ref=None):
     import torch
     s = Solver(sizes, row_ptr, col, **opts)
     try:
@@ -92,13 +105,14 @@ def _time(Solver, sizes, row_ptr, col, values, D, t, b, x, precision, sweeps, re
             s.graph_launch()
         ev[1].record()
         ev[1].synchronize()
-        return ev[0].elapsed_time(ev[1]) / reps
+        err = _entrywise(x, ref) if ref is not None else None
+        return ev[0].elapsed_time(ev[1]) / reps, err
     finally:
         s.close()
 
 
 def autotune(sizes, row_ptr, col, values, D, t, b, precision="fp32", sweeps=2, reps=5,
-             cache: str | None = None, options=None) -> dict:
+             cache: str | None = None, options=None, tol: float = 3e-11) -> dict:
     """Fastest options for this pattern / call shape: {"options": {...}, "ms": ..., "all": [...]}.
 
     options: an explicit candidate list (timed as given); default: the staged
@@ -116,21 +130,32 @@ def autotune(sizes, row_ptr, col, values, D, t, b, precision="fp32", sweeps=2, r
             return hit
     b2 = b.reshape(b.shape[0], -1).contiguous()
     x = torch.empty_like(b2)
+    # the accuracy reference: FP64 factors, no sweeps, default options
+    sref = Solver(sizes, row_ptr, col)
+    try:
+        sref.factor(values, D, t, "fp64")
+        ref = sref.solve(b2).clone()
+    finally:
+        sref.close()
     results = []
 
     def run(cands):
         for opts in cands:
-            ms = _time(Solver, sizes, row_ptr, col, values, D, t, b2, x, precision, sweeps, reps, opts)
-            results.append({"options": opts, "ms": ms})
+            ms, err = _time(Solver, sizes, row_ptr, col, values, D, t, b2, x, precision, sweeps, reps, opts, ref)
+            results.append({"options": opts, "ms": ms, "err": err, "ok": bool(err <= tol)})
+
+    def fastest():
+        ok = [r for r in results if r["ok"]]
+        return min(ok or results, key=lambda r: (r["ms"] if r["ok"] else float("inf"), r["err"]))
 
     if options is not None:
         run(options)
     else:
         run(staged_candidates())
-        best1 = min(results, key=lambda r: r["ms"])["options"]
-        run(_stage2(best1))
-    best = min(results, key=lambda r: r["ms"])
-    out = {"options": best["options"], "ms": best["ms"], "all": results}
+        run(_stage2(fastest()["options"]))
+    best = fastest()
+    out = {"options": best["options"], "ms": best["ms"], "err": best["err"], "tol": tol,
+           "rejected": sum(1 for r in results if not r["ok"]), "all": results}
     if cache:
         data = _load(cache)
         data[key] = out

@@ -519,6 +519,9 @@ def test_autotune_picks_a_candidate_and_caches(pisp, tmp_path):
     r = tune.autotune([inst.n], inst.row_ptr, inst.col, _dev(inst.val), _dev(inst.D), t, b, "fp64", 0,
                       reps=2, cache=cache, options=opts)
     assert r["options"] in opts and len(r["all"]) == 2 and r["ms"] > 0
+    # every candidate's x was checked against an FP64-factor solve of the same inputs
+    assert all(c["err"] is not None and c["ok"] == (c["err"] <= r["tol"]) for c in r["all"])
+    assert r["err"] <= r["tol"]
     again = tune.autotune([inst.n], inst.row_ptr, inst.col, _dev(inst.val), _dev(inst.D), t, b, "fp64", 0,
                           reps=2, cache=cache, options=opts)
     assert again["options"] == r["options"]
