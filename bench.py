@@ -45,7 +45,12 @@ L2_BYTES = 129 * 1024 * 1024
 # on a workload, from an ncu capture of that kernel on that workload (scaled
 # to the full workload where the capture ran a reduced batch); an entry is
 # removed when its kernel changes.
+# Keys: (workload, family, instances, library options as sorted (name, value) pairs).
+BATCH_TUNED = (("factor_policy", 4), ("relax_small", 16), ("relax_zeros", 0.1), ("solve_ctas_per_sm", 4),
+               ("solve_kfuse", 2), ("solve_schedule", 0), ("solve_warp_maxF", 64))
 TRAFFIC_PER_LAUNCH = {
+    ("batching", "backward", 256, BATCH_TUNED): 662.64e6,          # 580.96 MB read + 81.68 MB written
+    ("batching", "factor_persistent", 256, BATCH_TUNED): 1348.22e6,  # 611.18 MB read + 737.04 MB written
 }
 
 BENCH = {
@@ -182,6 +187,7 @@ class Arm:
         t0 = time.perf_counter()
         opts = options or dict(solve_schedule=schedule, factor_policy=factor_policy)
         opts = dict(opts, **(extra or {}))
+        self.options = opts
         self.s = pisp.Solver(sizes, rp, col, device=dev.index, **opts)
         self.analyze_ms = (time.perf_counter() - t0) * 1e3
         self.N = sum(sizes)
@@ -395,7 +401,8 @@ def run_pisp(args, rank, world, local_rank):
     mb = min_bytes_per_launch(fam, stats, K, R, p)
     alg = mb if mb is not None else lib_bytes
     achieved = alg / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else 0.0
-    traffic = TRAFFIC_PER_LAUNCH.get((args.workload, fam, G))
+    opts_key = tuple(sorted(arm.options.items()))
+    traffic = TRAFFIC_PER_LAUNCH.get((args.workload, fam, G, opts_key))
     roofline = {"bound": "hbm", "kernel": fam, "achieved": round(achieved, 2), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 5), "peak_source": peak_kind,
                 "traffic": traffic, "algorithmic_bytes_per_launch": alg,
@@ -414,7 +421,7 @@ def run_pisp(args, rank, world, local_rank):
         ach = by / (lm / 1e3) / 1e9
         return {"kernel": f, "achieved": round(ach, 2), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 5),
                 "algorithmic_bytes_per_launch": by, "avg_launch_us": round(1e3 * lm, 3),
-                "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, f, G))}
+                "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, f, G, opts_key))}
     families = {f: {"ms_per_step": round(v["ms"] / args.steps, 4),
                     "launches_per_step": v["launches"] / args.steps,
                     "min_GBps": (round(min_bytes_per_launch(f, stats, K, R, p) / (v["ms"] / v["launches"] / 1e3) / 1e9, 2)
