@@ -58,7 +58,7 @@ BENCH = {
     "precision": dict(precision="fp32", sweeps=2),
     "batching": dict(precision="fp32", sweeps=3),
     "differentiation": dict(precision="fp64", sweeps=0),
-    "scale": dict(precision="fp32", sweeps=2),
+    "scale": dict(precision="fp32", sweeps=3),
 }
 
 

@@ -433,8 +433,9 @@ def test_fp32_front_taller_than_a_shared_memory_column(pisp):
 @pytest.mark.parametrize("policy,tc", [(0, 0), (4, 0), (0, 1), (4, 1)])
 def test_full_scale_config_fp32_sweeps(pisp, policy, tc):
     """10000-bus grid: 23 fronts wider than the shared-memory limit, several per level,
-    up to the dense F = 1594 root (column-block owners); FP32 factors plus sweeps reach
-    the FP64 definition for every right-hand side."""
+    up to the dense F = 1594 root (column-block owners); FP32 factors plus 3 sweeps reach
+    the FP64 definition for every right-hand side (2 sweeps end within a few 1e-10 of it
+    entry-wise, so the benchmark uses 3 on this grid too)."""
     c = pfgen.CONFIGS["scale"]
     inst = pfgen.make_instance("scale")
     t = pfgen.symmetric_shifts(c["K"])
@@ -442,7 +443,7 @@ def test_full_scale_config_fp32_sweeps(pisp, policy, tc):
     assert s.stats()["max_front"] > 1000
     s.factor(_dev(val), _dev(D), t, "fp32")
     b = pfgen.rhs(inst.n, 4, 11)
-    x = s.solve(_dev(b), sweeps=2).cpu().numpy()
+    x = s.solve(_dev(b), sweeps=3).cpu().numpy()
     assert _maxrel(x, _oracle_xhat(inst, t, b)) <= TOL64
 
 
