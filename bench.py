@@ -90,6 +90,9 @@ def parse():
     ap.add_argument("--relax-small", type=int, default=-1, help="supernode amalgamation: pivot block size")
     ap.add_argument("--relax-zeros", type=float, default=-1.0, help="supernode amalgamation: zero fraction")
     ap.add_argument("--factor-tc", type=int, default=0, help="1: FP32 owner-tile updates on the tensor cores")
+    ap.add_argument("--factor-ctas", type=int, default=0, help="one-launch factorisation: resident CTAs per SM")
+    ap.add_argument("--factor-smem-maxf", type=int, default=0,
+                    help="one-launch factorisation: widest front kept in one CTA's shared memory")
     ap.add_argument("--autotune", default="auto", choices=["auto", "on", "off"],
                     help="time candidate library options on this workload first and use the fastest "
                          "(auto: on for the batching workload)")
@@ -335,7 +338,9 @@ def run_pisp(args, rank, world, local_rank):
                               pfgen.symmetric_shifts(K, args.eps),
                               torch.tensor(pfgen.rhs(sum(sizes), R, 1), device=dev), precision, sweeps)
     extra = {k: v for k, v in (("solve_kfuse", args.kfuse), ("solve_warp_maxF", args.warp_maxf),
-                               ("solve_ctas_per_sm", args.ctas), ("factor_tc", args.factor_tc)) if v}
+                               ("solve_ctas_per_sm", args.ctas), ("factor_tc", args.factor_tc),
+                               ("factor_ctas_per_sm", args.factor_ctas),
+                               ("factor_smem_maxF", args.factor_smem_maxf)) if v}
     if args.relax_small >= 0:
         extra["relax_small"] = args.relax_small
     if args.relax_zeros >= 0:

@@ -112,6 +112,10 @@ typedef struct pisp_options {
                               FP32 accumulation in tensor memory (FP32-level
                               accuracy); 0 (default): FP32 FMA.  Ignored for
                               FP64 factors. */
+  int32_t factor_ctas_per_sm; /* factor policy 4: resident CTAs per SM, 2 (128
+                                 registers per thread) or 3 (80; 0 = 2); with 3 the
+                                 shared-memory fronts should be narrowed
+                                 (factor_smem_maxF) so that three CTAs fit */
   int32_t analyze_threads; /* host threads pisp_analyze may use for the instances
                               of a batch: 0 = the hardware concurrency, at most
                               16 (default); 1 = the calling thread only.  A

@@ -29,7 +29,8 @@ class PispOptions(ctypes.Structure):
     _fields_ = [("ordering", c_int32), ("relax_small", c_int32), ("relax_zeros", c_double),
                 ("solve_schedule", c_int32), ("factor_policy", c_int32), ("solve_kfuse", c_int32),
                 ("solve_warp_maxF", c_int32), ("solve_ctas_per_sm", c_int32),
-                ("factor_smem_maxF", c_int32), ("factor_tc", c_int32), ("analyze_threads", c_int32)]
+                ("factor_smem_maxF", c_int32), ("factor_tc", c_int32), ("factor_ctas_per_sm", c_int32),
+                ("analyze_threads", c_int32)]
 
 
 class PispStats(ctypes.Structure):

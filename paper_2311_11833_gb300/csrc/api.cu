@@ -75,6 +75,7 @@ struct pisp_handle {
   int32_t kfuse = 1, warp_maxF = 32, solve_ctas = 0;
   int32_t factor_smem_maxF = 0;  // one-launch factorisation: widest shared-memory front (0 = limit)
   int32_t factor_tc = 0;         // FP32 owner-tile updates on the tensor cores
+  int32_t factor_ctas = 0;       // one-launch factorisation: resident CTAs per SM (2 or 3; 0 = 2)
   pisp::SymDev sd{};
   // level plans (depend on the factor precision)
   int plan_precision = 0;
@@ -748,6 +749,7 @@ int analyze_impl(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   h->solve_ctas = opt && opt->solve_ctas_per_sm > 0 ? std::min(4, std::max(2, opt->solve_ctas_per_sm)) : 0;
   h->factor_smem_maxF = opt && opt->factor_smem_maxF > 0 ? opt->factor_smem_maxF : 0;
   h->factor_tc = opt && opt->factor_tc ? 1 : 0;
+  h->factor_ctas = opt && opt->factor_ctas_per_sm > 0 ? opt->factor_ctas_per_sm : 0;
   h->units_K = h->units_R = 0;
   if (opt) {
     so.ordering = opt->ordering;
@@ -978,7 +980,7 @@ int pisp_factor_perturbed(pisp_handle* h, const double* values, const double* D,
         precision, h->sd, h->d_ftasks.as<pisp::FactorTask>(), h->n_ftasks, h->fticket.as<int>(), h->fdone.as<int>(),
         h->d_fneed.as<int>(), h->fflags.as<int>(), h->serr.as<int>(), h->d_fwl.as<int32_t>(), h->vals.as<double>(),
         h->D.as<double>(), sh, h->fronts.p, h->status.as<int32_t>(), h->badcol.as<int32_t>(), h->fac_CH,
-        h->fac_smem, h->wait_polls, h->factor_tc, h->stream);
+        h->fac_smem, h->wait_polls, h->factor_tc, h->factor_ctas, h->stream);
     TRY(count(h, n));
     prof_end(h, pb, PISP_PROF_FACTOR, K * h->fac_bytes, n);
     h->factored = true;

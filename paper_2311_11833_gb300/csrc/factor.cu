@@ -1412,8 +1412,8 @@ __device__ __forceinline__ void fac_publish(int* fdone, int s, int k, int K) {
   asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(fdone + (int64_t)s * K + k) : "memory");
 }
 
-template <typename T, bool TC>
-__global__ void __launch_bounds__(kOwnThreads, 2)
+template <typename T, bool TC, int MINB>
+__global__ void __launch_bounds__(kOwnThreads, MINB)
 k_factor_persistent(SymDev sd, const FactorTask* __restrict__ tasks, int ntasks, int* ticket, int* fdone,
                     const int* __restrict__ need, int* flags, int* err, const int32_t* __restrict__ wlist,
                     const double* __restrict__ vals, const double* __restrict__ D, Shifts sh,
@@ -1463,39 +1463,49 @@ k_factor_persistent(SymDev sd, const FactorTask* __restrict__ tasks, int ntasks,
   if constexpr (TC) tc_teardown(tc);
 }
 
-template <typename T>
-int factor_persistent_impl(const SymDev& sd, const FactorTask* tasks, int ntasks, int* ticket, int* fdone,
-                           const int* need, int* flags, int* err, const int32_t* wlist, const double* vals,
-                           const double* D, const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol,
-                           int CH, size_t smem, int64_t polls, int tc, cudaStream_t st) {
-  if (ntasks == 0) return 0;
-  const int tc_on = tc && sizeof(T) == 4 ? 1 : 0;
-  const size_t tc_off = smem;  // the staging follows everything the other task kinds use
-  if (tc_on) smem += (size_t)kTcSmemFloats * sizeof(float);
+template <typename T, bool TC, int M>
+int factor_persistent_launch(const SymDev& sd, const FactorTask* tasks, int ntasks, int* ticket, int* fdone,
+                             const int* need, int* flags, int* err, const int32_t* wlist, const double* vals,
+                             const double* D, const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol,
+                             int CH, size_t smem, size_t tc_off, int64_t polls, cudaStream_t st) {
   static std::atomic<int> nsm_dev[kMaxDevices];
   const int dev = current_device();
   int nsm = nsm_dev[dev].load(std::memory_order_acquire);
   if (!nsm) {
-    cudaFuncSetAttribute(k_factor_persistent<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
-    cudaFuncSetAttribute(k_factor_persistent<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+    cudaFuncSetAttribute(k_factor_persistent<T, TC, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     nsm_dev[dev].store(nsm, std::memory_order_release);
   }
-  if (smem > (size_t)kSmemCap) return -1;
   int occ = 1;
-  if (tc_on) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_factor_persistent<T, true>, kOwnThreads, smem);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_factor_persistent<T, false>, kOwnThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_factor_persistent<T, TC, M>, kOwnThreads, smem);
   const int grid = std::max(1, std::min(ntasks, std::max(1, occ) * std::max(nsm, 1)));
-  const int64_t pl = polls > 0 ? polls : kDagWaitPolls;
-  if (tc_on)
-    k_factor_persistent<T, true><<<grid, kOwnThreads, smem, st>>>(sd, tasks, ntasks, ticket, fdone, need, flags,
-                                                                  err, wlist, vals, D, sh, (T*)fronts, status,
-                                                                  badcol, CH, pl, tc_off);
-  else
-    k_factor_persistent<T, false><<<grid, kOwnThreads, smem, st>>>(sd, tasks, ntasks, ticket, fdone, need, flags,
-                                                                   err, wlist, vals, D, sh, (T*)fronts, status,
-                                                                   badcol, CH, pl, tc_off);
+  k_factor_persistent<T, TC, M><<<grid, kOwnThreads, smem, st>>>(sd, tasks, ntasks, ticket, fdone, need, flags,
+                                                                 err, wlist, vals, D, sh, (T*)fronts, status,
+                                                                 badcol, CH, polls > 0 ? polls : kDagWaitPolls,
+                                                                 tc_off);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+// ctas: resident CTAs per SM the kernel is compiled for, 2 (128 registers per
+// thread) or 3 (80; the owner tiles' register arrays then spill a little)
+template <typename T>
+int factor_persistent_impl(const SymDev& sd, const FactorTask* tasks, int ntasks, int* ticket, int* fdone,
+                           const int* need, int* flags, int* err, const int32_t* wlist, const double* vals,
+                           const double* D, const Shifts& sh, void* fronts, int32_t* status, int32_t* badcol,
+                           int CH, size_t smem, int64_t polls, int tc, int ctas, cudaStream_t st) {
+  if (ntasks == 0) return 0;
+  const int tc_on = tc && sizeof(T) == 4 ? 1 : 0;
+  const size_t tc_off = smem;  // the staging follows everything the other task kinds use
+  if (tc_on) smem += (size_t)kTcSmemFloats * sizeof(float);
+  if (smem > (size_t)kSmemCap) return -1;
+  if (tc_on)
+    return factor_persistent_launch<T, true, 2>(sd, tasks, ntasks, ticket, fdone, need, flags, err, wlist, vals, D,
+                                                sh, fronts, status, badcol, CH, smem, tc_off, polls, st);
+  if (ctas >= 3)
+    return factor_persistent_launch<T, false, 3>(sd, tasks, ntasks, ticket, fdone, need, flags, err, wlist, vals,
+                                                 D, sh, fronts, status, badcol, CH, smem, tc_off, polls, st);
+  return factor_persistent_launch<T, false, 2>(sd, tasks, ntasks, ticket, fdone, need, flags, err, wlist, vals, D,
+                                               sh, fronts, status, badcol, CH, smem, tc_off, polls, st);
 }
 
 template <typename T>
@@ -1803,12 +1813,12 @@ int launch_factor_persistent(int precision, const SymDev& sd, const FactorTask* 
                              int* fdone, const int* need, int* flags, int* err, const int32_t* wlist,
                              const double* vals, const double* D, const Shifts& sh, void* fronts,
                              int32_t* status, int32_t* badcol, int CH, size_t smem, int64_t polls, int tc,
-                             cudaStream_t st) {
+                             int ctas, cudaStream_t st) {
   if (precision == PISP_FP32)
     return factor_persistent_impl<float>(sd, tasks, ntasks, ticket, fdone, need, flags, err, wlist, vals, D, sh,
-                                         fronts, status, badcol, CH, smem, polls, tc, st);
+                                         fronts, status, badcol, CH, smem, polls, tc, ctas, st);
   return factor_persistent_impl<double>(sd, tasks, ntasks, ticket, fdone, need, flags, err, wlist, vals, D, sh,
-                                        fronts, status, badcol, CH, smem, polls, tc, st);
+                                        fronts, status, badcol, CH, smem, polls, tc, ctas, st);
 }
 
 int launch_factor_big(int precision, const SymDev& sd, const LevelPlan& lp, const int32_t* d_big,

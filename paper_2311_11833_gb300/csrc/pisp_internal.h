@@ -169,7 +169,7 @@ int launch_factor_persistent(int precision, const SymDev& sd, const FactorTask* 
                              int* fdone, const int* need, int* flags, int* err, const int32_t* wlist,
                              const double* vals, const double* D, const Shifts& sh, void* fronts,
                              int32_t* status, int32_t* badcol, int CH, size_t smem, int64_t polls, int tc,
-                             cudaStream_t st);
+                             int ctas, cudaStream_t st);
 // widest front the one-launch factorisation keeps in shared memory (wider:
 // owner tiles), and its dynamic shared memory per CTA
 int persistent_cta_front_limit(int precision);

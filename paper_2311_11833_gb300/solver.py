@@ -89,7 +89,7 @@ class Solver:
                  relax_small: int = -1, relax_zeros: float = -1.0, solve_schedule: int = 0,
                  factor_policy: int = 0, solve_kfuse: int = 0, solve_warp_maxF: int = 0,
                  solve_ctas_per_sm: int = 0, factor_smem_maxF: int = 0, factor_tc: int = 0,
-                 analyze_threads: int = 0):
+                 factor_ctas_per_sm: int = 0, analyze_threads: int = 0):
         self._lib = _lib.load()
         if not torch.cuda.is_available():
             raise RuntimeError("libpisp needs a CUDA device")
@@ -110,7 +110,8 @@ class Solver:
         check(self._lib.pisp_create(ctypes.byref(h), self.device, None))
         self._h = h
         opt = PispOptions(ordering, relax_small, relax_zeros, solve_schedule, factor_policy, solve_kfuse,
-                          solve_warp_maxF, solve_ctas_per_sm, factor_smem_maxF, factor_tc, analyze_threads)
+                          solve_warp_maxF, solve_ctas_per_sm, factor_smem_maxF, factor_tc, factor_ctas_per_sm,
+                          analyze_threads)
         check(self._lib.pisp_analyze(self._h, self.G, sizes.ctypes.data_as(ctypes.c_void_p),
                                      rp.ctypes.data_as(ctypes.c_void_p),
                                      cl.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opt)), self._h)

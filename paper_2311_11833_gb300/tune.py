@@ -8,8 +8,9 @@ The options that change performance but not the result:
   the front's dependency wait and structure loads once) and the widest front
   one 32-lane segment takes before a whole CTA does;
 * the supernode amalgamation (relax_small, relax_zeros: front sizes and
-  tree height) and the factor policy of wide fronts (column-block owners,
-  CTA clusters, tile DAG or per-panel launches);
+  tree height) and the factor policy (column-block owners per level, CTA
+  clusters, tile DAG, per-panel launches, or the whole factorisation in one
+  launch, at 2 or 3 resident CTAs per SM);
 * the solve schedule (persistent or one launch per level).
 
 For one sparsity pattern, shift count, RHS count, precision and sweep count,
@@ -60,9 +61,16 @@ def staged_candidates():
 
 
 def _stage2(best: dict):
+    """Amalgamation x factor policy (per-level owners, tile DAG, one launch),
+    plus the one launch at 3 resident CTAs per SM with shared-memory fronts up
+    to 128 wide (so that three CTAs fit)."""
     out = []
     for (rs, rz), fp in itertools.product(RELAX, (0, 2, 4)):
         o = dict(best, relax_small=rs, relax_zeros=rz, factor_policy=fp)
+        if o != best:
+            out.append(o)
+    for rs, rz in RELAX:
+        o = dict(best, relax_small=rs, relax_zeros=rz, factor_policy=4, factor_ctas_per_sm=3, factor_smem_maxF=128)
         if o != best:
             out.append(o)
     return out

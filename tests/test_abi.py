@@ -58,7 +58,7 @@ class HostSymbolic:
         rp = np.ascontiguousarray(row_ptr, np.int64)
         cl = np.ascontiguousarray(col, np.int32)
         o = PispOptions(opt.get("ordering", 0), opt.get("relax_small", -1), opt.get("relax_zeros", -1.0), 0, 0,
-                        0, 0, 0, 0, 0, opt.get("analyze_threads", 0))
+                        0, 0, 0, 0, 0, 0, opt.get("analyze_threads", 0))
         self.rc = lib.pisp_analyze(self.h, len(sizes), sizes.ctypes.data_as(ctypes.c_void_p),
                                    rp.ctypes.data_as(ctypes.c_void_p), cl.ctypes.data_as(ctypes.c_void_p),
                                    ctypes.byref(o))

@@ -61,4 +61,5 @@ def test_staged_search_covers_the_solve_tiling_then_the_analysis():
     # stage 2 keeps stage 1's tiling and varies amalgamation and factor policy only
     assert all(d["solve_ctas_per_sm"] == best["solve_ctas_per_sm"] and d["solve_kfuse"] == best["solve_kfuse"]
                for d in s2)
-    assert best not in s2 and len(s2) == len(tune.RELAX) * 3 - 1
+    assert best not in s2 and len(s2) == len(tune.RELAX) * 4 - 1
+    assert sum(1 for d in s2 if d.get("factor_ctas_per_sm") == 3) == len(tune.RELAX)
