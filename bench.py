@@ -242,16 +242,22 @@ def _entrywise(x, ref):
     return np.max(np.abs(x - ref), axis=0) / scale
 
 
-def oracle_check(arm, max_instances=12):
+def sample_instances(insts, max_instances=12):
+    """Instances spread over the size range, smallest and largest included."""
+    G = len(insts)
+    order = np.argsort([I.n for I in insts], kind="stable")
+    return sorted(set(int(order[i]) for i in np.linspace(0, G - 1, min(G, max_instances)).round().astype(int)))
+
+
+def oracle_check(arm, max_instances=12, xs=None):
     """Error of the last x against the CPU oracle for every right-hand side of a
     sample of instances spread over the size range (smallest and largest
-    included): entry-wise (max |x - ref| / max |ref| per RHS) and normwise."""
+    included): entry-wise (max |x - ref| / max |ref| per RHS) and normwise.
+    xs: the solution to check ([N][R], default arm.x)."""
     import oracle
-    x = arm.x.cpu().numpy()
+    x = arm.x.cpu().numpy() if xs is None else xs
     offs = np.concatenate([[0], np.cumsum([I.n for I in arm.insts])])
-    G = len(arm.insts)
-    order = np.argsort([I.n for I in arm.insts], kind="stable")
-    pick = sorted(set(int(order[i]) for i in np.linspace(0, G - 1, min(G, max_instances)).round().astype(int)))
+    pick = sample_instances(arm.insts, max_instances)
     per = []
     for g in pick:
         I = arm.insts[g]
@@ -478,6 +484,11 @@ def run_pisp(args, rank, world, local_rank):
         # one after another, eager launches, no graph
         plain_ms = []
         arms = [Arm(pisp, torch, [I], K, R, args.eps, "fp64", 0, args.workload, dev) for I in insts]
+        offs = np.concatenate([[0], np.cumsum([I.n for I in insts])])
+        for g, a in enumerate(arms):  # the same right-hand sides as the batched arm
+            a.b_host = arm.b_host[offs[g]:offs[g + 1]].copy()
+            a.b = torch.tensor(a.b_host, device=dev)
+            a.x = torch.empty_like(a.b)
         n_plain_steps = 5 if G > 1 else min(args.steps, 20)
         for a in arms:
             a.step()
@@ -491,10 +502,17 @@ def run_pisp(args, rank, world, local_rank):
             e1.record()
             e1.synchronize()
             plain_ms.append(e0.elapsed_time(e1))
-        plain_err = oracle_check(arms[0], 1)["max_entrywise"]
+        # the plain path's x on the main arm's sample of instances
+        xp = np.zeros_like(arm.b_host)
+        for g in sample_instances(insts):
+            xp[offs[g]:offs[g + 1]] = arms[g].x.cpu().numpy()
+        plain_chk = oracle_check(arm, xs=xp)
+        plain_err = plain_chk["max_entrywise"]
         pv = units / (statistics.mean(plain_ms) / 1e3)
         out["plain_fp64_path"] = {"value": round(pv, 2), "ms_per_step": round(statistics.mean(plain_ms), 4),
                                   "steps": n_plain_steps, "max_rel_err_vs_oracle": plain_err,
+                                  "results_checked": plain_chk["results"],
+                                  "within_tol": plain_chk["all_within_tol"],
                                   "speedup_of_value": round(value / world / pv, 3)}
         del arms
         # end to end through the public API with host buffers (pinned): the

@@ -19,9 +19,11 @@ step the library captures in a CUDA graph (factor + solve + sweeps), and
 returns the fastest among those whose result stays accurate: the options
 change only rounding, but with FP32 factors a different amalgamation can
 leave the sweeps short of the FP64 result, so every candidate's x is compared
-entry by entry with an FP64-factor solve (no sweeps, default options) of the
-same inputs and rejected beyond `tol` (max |x - ref| / max |ref| per
-right-hand side).  The default search is staged: first the solve tiling
+entry by entry with an FP64-factor solve with two FP64 residual sweeps
+(default options) of the same inputs and rejected beyond `tol` (max |x - ref|
+/ max |ref| per right-hand side).  The sweeps matter for the reference too: a
+pivot-free FP64 solve alone can be 5e-10 away from the definition on an
+ill-conditioned instance of a batch.  The default search is staged: first the solve tiling
 with the default amalgamation and factor policy, then the amalgamation and
 factor policy with the best tiling.  Results are cached in a JSON file (path
 from $PISP_TUNE_CACHE, or the `cache` argument) keyed by a hash of the
@@ -138,11 +140,11 @@ def autotune(sizes, row_ptr, col, values, D, t, b, precision="fp32", sweeps=2, r
             return hit
     b2 = b.reshape(b.shape[0], -1).contiguous()
     x = torch.empty_like(b2)
-    # the accuracy reference: FP64 factors, no sweeps, default options
+    # the accuracy reference: FP64 factors and two FP64 sweeps, default options
     sref = Solver(sizes, row_ptr, col)
     try:
         sref.factor(values, D, t, "fp64")
-        ref = sref.solve(b2).clone()
+        ref = sref.solve(b2, sweeps=2).clone()
     finally:
         sref.close()
     results = []
