@@ -53,12 +53,14 @@ TRAFFIC_PER_LAUNCH = {
     ("batching", "factor_persistent", 256, BATCH_TUNED): 1348.22e6,  # 611.18 MB read + 737.04 MB written
 }
 
+# factor precision and FP64 residual sweeps per workload; refine_tol > 0:
+# adaptive sweeps (pisp_set_refinement), `sweeps` is then the maximum
 BENCH = {
-    "plain": dict(precision="fp64", sweeps=0),
-    "precision": dict(precision="fp32", sweeps=2),
-    "batching": dict(precision="fp32", sweeps=3),
-    "differentiation": dict(precision="fp64", sweeps=0),
-    "scale": dict(precision="fp32", sweeps=3),
+    "plain": dict(precision="fp64", sweeps=0, refine_tol=0.0),
+    "precision": dict(precision="fp32", sweeps=8, refine_tol=1e-12),
+    "batching": dict(precision="fp32", sweeps=8, refine_tol=1e-12),
+    "differentiation": dict(precision="fp64", sweeps=0, refine_tol=0.0),
+    "scale": dict(precision="fp32", sweeps=8, refine_tol=1e-12),
 }
 
 
@@ -74,7 +76,10 @@ def parse():
     ap.add_argument("--study", default=None, choices=["dense", "newton"],
                     help="timing study of next row f4 (dense batches vs n and G) or f2 (Newton loop)")
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
-    ap.add_argument("--sweeps", type=int, default=None)
+    ap.add_argument("--sweeps", type=int, default=None,
+                    help="FP64 residual sweeps (with adaptive sweeps: the maximum)")
+    ap.add_argument("--refine-tol", type=float, default=None,
+                    help="stopping tolerance of the adaptive sweeps (0: fixed sweeps; default per workload)")
     ap.add_argument("--eps", type=float, default=1e-2)
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of a CUDA graph")
     ap.add_argument("--factor-policy", type=int, default=0, choices=[0, 1, 2, 3, 4],
@@ -183,7 +188,7 @@ class Arm:
     """One configured solver with device-resident inputs and a step function."""
 
     def __init__(self, pisp, torch, insts, K, R, eps, precision, sweeps, workload, dev, schedule=0,
-                 factor_policy=0, options=None, extra=None):
+                 factor_policy=0, options=None, extra=None, refine_tol=0.0):
         self.torch = torch
         self.insts = insts
         sizes, rp, col, val, D = concat(insts)
@@ -193,6 +198,8 @@ class Arm:
         self.options = opts
         self.s = pisp.Solver(sizes, rp, col, device=dev.index, **opts)
         self.analyze_ms = (time.perf_counter() - t0) * 1e3
+        self.refine_tol = refine_tol
+        self.s.set_refinement(refine_tol)
         self.N = sum(sizes)
         self.K, self.R, self.precision, self.sweeps = K, R, precision, sweeps
         self.t = pfgen.symmetric_shifts(K, eps)
@@ -242,35 +249,70 @@ def _entrywise(x, ref):
     return np.max(np.abs(x - ref), axis=0) / scale
 
 
-def sample_instances(insts, max_instances=12):
-    """Instances spread over the size range, smallest and largest included."""
-    G = len(insts)
-    order = np.argsort([I.n for I in insts], kind="stable")
-    return sorted(set(int(order[i]) for i in np.linspace(0, G - 1, min(G, max_instances)).round().astype(int)))
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
 
 
-def oracle_check(arm, max_instances=12, xs=None):
-    """Error of the last x against the CPU oracle for every right-hand side of a
-    sample of instances spread over the size range (smallest and largest
-    included): entry-wise (max |x - ref| / max |ref| per RHS) and normwise.
-    xs: the solution to check ([N][R], default arm.x)."""
+def _oracle_job(job):
+    """One instance's x_hat by the CPU oracle (also run in spawned workers)."""
+    import oracle
+    inst, t, b = job
+    return oracle.x_hat(oracle.to_scipy(inst), inst.D, t, b)
+
+
+def oracle_refs(insts, t, b_host):
+    """The oracle's x_hat of every instance: in this process for a single
+    instance (BLAS threads = host cores), else in a pool of spawned processes
+    with one BLAS thread each, largest instances first."""
+    offs = np.concatenate([[0], np.cumsum([I.n for I in insts])])
+    jobs = [(I, t, b_host[offs[g]:offs[g + 1]]) for g, I in enumerate(insts)]
+    if len(jobs) == 1:
+        return [_oracle_job(jobs[0])]
+    import multiprocessing as mp
+    order = sorted(range(len(jobs)), key=lambda g: -insts[g].n)
+    saved = {k: os.environ.get(k) for k in THREAD_VARS}
+    os.environ.update({k: "1" for k in THREAD_VARS})
+    try:
+        with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:
+            res = pool.map(_oracle_job, [jobs[g] for g in order], chunksize=1)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    out = [None] * len(jobs)
+    for g, r in zip(order, res):
+        out[g] = r
+    return out
+
+
+def oracle_check(arm, refs, xs=None, detail=12):
+    """Error of x against the CPU oracle for every right-hand side of EVERY
+    instance: entry-wise (max |x - ref| / max |ref| per instance and RHS) and
+    normwise.  refs: oracle_refs of the arm's inputs; xs: the solution to
+    check ([N][R], default arm.x).  Per-instance figures are listed for at
+    most `detail` instances (else the five worst)."""
     import oracle
     x = arm.x.cpu().numpy() if xs is None else xs
     offs = np.concatenate([[0], np.cumsum([I.n for I in arm.insts])])
-    pick = sample_instances(arm.insts, max_instances)
     per = []
-    for g in pick:
-        I = arm.insts[g]
+    for g, I in enumerate(arm.insts):
         sl = slice(offs[g], offs[g + 1])
-        ref = oracle.x_hat(oracle.to_scipy(I), I.D, arm.t, arm.b_host[sl])
-        ew = _entrywise(x[sl], ref)
-        nw = oracle.rel_err(x[sl], ref)
+        ew = _entrywise(x[sl], refs[g])
+        nw = oracle.rel_err(x[sl], refs[g])
         per.append({"instance": g, "n": I.n, "entrywise": [float(f"{v:.3e}") for v in ew],
                     "normwise": [float(f"{v:.3e}") for v in nw]})
     mx = max(max(p["entrywise"]) for p in per)
-    return {"tol": TOL, "instances": len(pick), "results": sum(len(p["entrywise"]) for p in per),
-            "max_entrywise": mx, "max_normwise": max(max(p["normwise"]) for p in per),
-            "all_within_tol": bool(mx <= TOL), "per_instance": per}
+    out = {"tol": TOL, "instances": len(per), "results": sum(len(p["entrywise"]) for p in per),
+           "max_entrywise": mx, "max_normwise": max(max(p["normwise"]) for p in per),
+           "all_within_tol": bool(mx <= TOL)}
+    if len(per) <= detail:
+        out["per_instance"] = per
+    else:
+        worst = sorted(per, key=lambda p: -max(p["entrywise"]))[:5]
+        out["worst_instances"] = [{"instance": p["instance"], "n": p["n"], "entrywise": max(p["entrywise"])}
+                                  for p in worst]
+    return out
 
 
 def cpu_baseline(insts, K, R, eps, budget_s=12.0):
@@ -332,6 +374,7 @@ def run_pisp(args, rank, world, local_rank):
     bcfg = BENCH[args.workload]
     precision = args.precision or bcfg["precision"]
     sweeps = bcfg["sweeps"] if args.sweeps is None else args.sweeps
+    refine_tol = bcfg["refine_tol"] if args.refine_tol is None else args.refine_tol
     if precision == "fp64" and args.sweeps is None:
         sweeps = 0
     K, R = c["K"], c["R"]
@@ -342,7 +385,8 @@ def run_pisp(args, rank, world, local_rank):
         sizes, rp, col, val, D = concat(insts)
         tuned = tune.autotune(sizes, rp, col, torch.tensor(val, device=dev), torch.tensor(D, device=dev),
                               pfgen.symmetric_shifts(K, args.eps),
-                              torch.tensor(pfgen.rhs(sum(sizes), R, 1), device=dev), precision, sweeps)
+                              torch.tensor(pfgen.rhs(sum(sizes), R, 1), device=dev), precision, sweeps,
+                              refine_tol=refine_tol)
     extra = {k: v for k, v in (("solve_kfuse", args.kfuse), ("solve_warp_maxF", args.warp_maxf),
                                ("solve_ctas_per_sm", args.ctas), ("factor_tc", args.factor_tc),
                                ("factor_ctas_per_sm", args.factor_ctas),
@@ -352,7 +396,7 @@ def run_pisp(args, rank, world, local_rank):
     if args.relax_zeros >= 0:
         extra["relax_zeros"] = args.relax_zeros
     arm = Arm(pisp, torch, insts, K, R, args.eps, precision, sweeps, args.workload, dev, args.schedule,
-              args.factor_policy, options=tuned["options"] if tuned else None, extra=extra)
+              args.factor_policy, options=tuned["options"] if tuned else None, extra=extra, refine_tol=refine_tol)
     G = len(insts)
     units = G * R
     use_graph = not args.no_graph
@@ -397,6 +441,18 @@ def run_pisp(args, rank, world, local_rank):
     value = units * world * args.steps / (total_ms / 1e3)
     prof = arm.s.profile_read()
     stats = arm.s.stats()
+    # adaptive sweeps: captured in the graph they are one device-side loop
+    # (family sweep_loop; forward and backward then hold the first solve
+    # only); run eagerly, launch s of the solve and residual families covers
+    # only the instances still iterating, and the roofline counts full-launch
+    # equivalents (the fraction of front entries or rows each launch covered)
+    nsw, work, rows = arm.s.refinement_stats(sweeps, rows=True)
+    eager_gated = refine_tol > 0 and sweeps > 0 and not use_graph
+    gated = {"forward": float(work.sum()), "backward": float(work.sum()), "residual": float(rows.sum())}
+
+    def full_launches_per_step(f):
+        per = prof[f]["launches"] / args.steps
+        return per - sweeps + gated[f] if f in gated and eager_gated else per
     if not use_graph:
         arm.s.profile(False)
     if rank != 0:
@@ -404,11 +460,12 @@ def run_pisp(args, rank, world, local_rank):
     # roofline of the dominant kernel family: minimum bytes per launch over the
     # family's average launch time (CUDA events on the library's stream)
     peak, peak_kind = load_peaks()
-    fam = max(prof, key=lambda f: prof[f]["ms"])
+    fam = max((f for f in prof if f != "sweep_loop"), key=lambda f: prof[f]["ms"])  # a kernel, not the loop
     pf = prof[fam]
     p = 4 if precision == "fp32" else 8
-    launch_ms = pf["ms"] / max(1, pf["launches"])
-    lib_bytes = pf["bytes"] / max(1, pf["launches"])
+    fl = full_launches_per_step(fam) * args.steps
+    launch_ms = pf["ms"] / max(1e-9, fl)
+    lib_bytes = pf["bytes"] / max(1e-9, fl)
     mb = min_bytes_per_launch(fam, stats, K, R, p)
     alg = mb if mb is not None else lib_bytes
     achieved = alg / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else 0.0
@@ -421,24 +478,31 @@ def run_pisp(args, rank, world, local_rank):
                 else "library count",
                 "library_bytes_per_launch": lib_bytes,
                 "avg_launch_us": round(1e3 * launch_ms, 3),
+                "launch_basis": "full-launch equivalents" if fam in gated and eager_gated else "launches",
                 "share_of_step": round(pf["ms"] / total_ms, 4) if world == 1 else None}
+
     def fam_roofline(f):
         v = prof[f]
         if v["launches"] == 0 or v["ms"] <= 0:
             return None
-        lm = v["ms"] / v["launches"]
+        lm = v["ms"] / (full_launches_per_step(f) * args.steps)
         mbf = min_bytes_per_launch(f, stats, K, R, p)
-        by = mbf if mbf is not None else v["bytes"] / v["launches"]
+        by = mbf if mbf is not None else v["bytes"] / (full_launches_per_step(f) * args.steps)
         ach = by / (lm / 1e3) / 1e9
         return {"kernel": f, "achieved": round(ach, 2), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 5),
                 "algorithmic_bytes_per_launch": by, "avg_launch_us": round(1e3 * lm, 3),
                 "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, f, G, opts_key))}
-    families = {f: {"ms_per_step": round(v["ms"] / args.steps, 4),
-                    "launches_per_step": v["launches"] / args.steps,
-                    "min_GBps": (round(min_bytes_per_launch(f, stats, K, R, p) / (v["ms"] / v["launches"] / 1e3) / 1e9, 2)
-                                 if v["ms"] > 0 and min_bytes_per_launch(f, stats, K, R, p) is not None else None),
-                    "library_GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 2) if v["ms"] > 0 else 0.0}
-                for f, v in prof.items() if v["launches"] > 0}
+
+    def fam_summary(f, v):
+        fl = full_launches_per_step(f)
+        mbf = min_bytes_per_launch(f, stats, K, R, p)
+        return {"ms_per_step": round(v["ms"] / args.steps, 4),
+                "launches_per_step": v["launches"] / args.steps,
+                "full_launch_equivalents_per_step": round(fl, 4),
+                "min_GBps": (round(mbf * fl / (v["ms"] / args.steps / 1e3) / 1e9, 2)
+                             if v["ms"] > 0 and mbf is not None else None),
+                "library_GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 2) if v["ms"] > 0 else 0.0}
+    families = {f: fam_summary(f, v) for f, v in prof.items() if v["launches"] > 0}
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
@@ -448,6 +512,8 @@ def run_pisp(args, rank, world, local_rank):
         "config": {"workload": args.workload, "instances": G, "N": arm.N, "nnzA": int(stats["nnzA"]),
                    "K": K, "R": R, "shifts": "symmetric +-eps*alpha", "eps": args.eps,
                    "factor_precision": precision, "combine_precision": "fp64", "sweeps": sweeps,
+                   "sweeps_mode": (f"adaptive per instance, at most {sweeps}, stop tol {refine_tol:g}"
+                                   if refine_tol > 0 and sweeps else "fixed"),
                    "graph": "library (pisp_graph_capture)" if use_graph else None,
                    "solve_schedule": ["persistent", "per-level"][args.schedule],
                    "factor_policy": ["single-CTA/column-block-owners", "clusters", "single-CTA/tile-DAG",
@@ -470,6 +536,7 @@ def run_pisp(args, rank, world, local_rank):
                       "search": "staged: solve tiling (CTAs/SM x shifts per task x widest warp front), "
                                 "then amalgamation x factor policy; graph replays, CUDA events"}
                      if tuned else None),
+        "sweeps_per_instance": {str(k): int(v) for k, v in zip(*np.unique(nsw, return_counts=True))},
         "wall_s_timed_region": round(wall, 3),
         "structure": {k: stats[k] for k in ("nnzL", "nnzF_stored", "n_supernodes", "n_levels",
                                             "max_front", "etree_height")},
@@ -477,7 +544,10 @@ def run_pisp(args, rank, world, local_rank):
     if clk:
         out["clocks"] = clk
     if not args.quick:
-        chk = oracle_check(arm)
+        t_or = time.perf_counter()
+        refs = oracle_refs(insts, arm.t, arm.b_host)
+        chk = oracle_check(arm, refs)
+        chk["oracle_wall_s"] = round(time.perf_counter() - t_or, 2)
         out["oracle_check"] = chk
         out["max_rel_err_vs_oracle"] = chk["max_entrywise"]
         # plain FP64 single-instance path: FP64 factors, no sweeps, instances
@@ -502,11 +572,11 @@ def run_pisp(args, rank, world, local_rank):
             e1.record()
             e1.synchronize()
             plain_ms.append(e0.elapsed_time(e1))
-        # the plain path's x on the main arm's sample of instances
+        # the plain path's x on every instance
         xp = np.zeros_like(arm.b_host)
-        for g in sample_instances(insts):
+        for g in range(G):
             xp[offs[g]:offs[g + 1]] = arms[g].x.cpu().numpy()
-        plain_chk = oracle_check(arm, xs=xp)
+        plain_chk = oracle_check(arm, refs, xs=xp)
         plain_err = plain_chk["max_entrywise"]
         pv = units / (statistics.mean(plain_ms) / 1e3)
         out["plain_fp64_path"] = {"value": round(pv, 2), "ms_per_step": round(statistics.mean(plain_ms), 4),

@@ -136,7 +136,9 @@ typedef struct pisp_stats {
   int32_t etree_height;  /* height of the column elimination tree */
   int32_t K;             /* perturbations of the last factorisation */
   int32_t precision;     /* PISP_FP32 / PISP_FP64 of the last factorisation */
-  int32_t gpu_launches;  /* kernels launched by the last factor + solve calls */
+  int32_t gpu_launches;  /* kernels launched by the last factor + solve calls (adaptive sweeps
+                            captured as a device-side loop: with the iterations the last run
+                            of the loop took; reading them synchronises the stream) */
   double flops_factor;   /* per perturbation */
   double flops_solve;    /* per perturbation per RHS (forward + back) */
   double analyze_ms;     /* host time of pisp_analyze */
@@ -317,6 +319,40 @@ int pisp_graph_launch(pisp_handle* h);
  * polls < 0. */
 int pisp_set_wait_limit(pisp_handle* h, int64_t polls, int32_t unreachable);
 
+/* Adaptive FP64 residual sweeps (no counterpart in the paper, which solves
+ * in FP64; a mixed-precision use of its Alg. 1).  With tol > 0 the `sweeps`
+ * of pisp_solve / pisp_refine become a maximum, and each instance of a batch
+ * stops on its own, by the stopping test of extra-precise iterative
+ * refinement (Demmel, Hida, Kahan, Li, Mukherjee, Riedy, ACM TOMS 32(2),
+ * 2006) with the contraction estimated from successive corrections: per RHS
+ * r, with d_s = the largest |correction| of sweep s over the instance's
+ * rows and all k, and rho = d_s / d_{s-1} (d_0 = the largest |x_k|), r has
+ * converged when d_s = 0 or when rho < 1/2 and rho / (1 - rho) d_s <=
+ * tol * max |x_k|, and has stagnated when rho >= 1/2 from the second sweep on.
+ * The instance stops when all its right-hand sides have converged or
+ * stagnated; the later sweeps skip its rows and fronts (the solve kernels
+ * walk only the work units of the instances still iterating).  tol = 0
+ * restores fixed sweeps (every instance, every sweep).  Applies from the
+ * next pisp_solve / pisp_refine / pisp_graph_capture (a captured step keeps
+ * the mode it was captured with).  The transposed sweeps of pisp_adjoint
+ * stay fixed.  Returns PISP_ERR_INVALID_ARG for tol < 0 or not finite. */
+int pisp_set_refinement(pisp_handle* h, double tol);
+
+/* The sweeps of the last pisp_solve (or of the last solve inside
+ * pisp_refine or a graph replay):
+ *   sweeps_per_instance  host int32 [G] (or NULL): the sweeps instance g
+ *                        took (with fixed sweeps: the sweep count for all)
+ *   work                 host FP64 [max_sweeps] (or NULL): for s = 1 ..
+ *                        max_sweeps, the fraction of the solve work (front
+ *                        entries of the factors) that sweep s covered; 0
+ *                        past the last sweep
+ *   rows                 host FP64 [max_sweeps] (or NULL): the same for the
+ *                        rows (the residuals' work)
+ * Synchronises the stream.  Returns PISP_ERR_NOT_FACTORED before any solve,
+ * PISP_ERR_INVALID_ARG for max_sweeps < 0. */
+int pisp_refinement_stats(pisp_handle* h, int32_t* sweeps_per_instance, double* work, double* rows,
+                          int32_t max_sweeps);
+
 /* Synchronises the stream and copies host [G*K] status codes of the last
  * factorisation: 0 ok, PISP_ERR_ZERO_PIVOT or PISP_ERR_NONFINITE.  If
  * first_bad_col is not NULL it receives host [G*K] the first failing
@@ -412,7 +448,10 @@ enum {
   PISP_PROF_RESIDUAL = 4,     /* FP64 residuals of the sweeps */
   PISP_PROF_COMBINE = 5,      /* expansion-weighted combine */
   PISP_PROF_FACTOR = 6,       /* the whole factorisation in one launch (factor policy 4) */
-  PISP_PROF_FAMILIES = 7
+  PISP_PROF_REFINE = 7,       /* stopping tests of the adaptive sweeps (pisp_set_refinement) */
+  PISP_PROF_SWEEP_LOOP = 8,   /* adaptive sweeps captured as one device-side loop (residuals,
+                                 solves and stopping tests of every iteration) */
+  PISP_PROF_FAMILIES = 9
 };
 
 /* on != 0: start recording brackets (forgets the previous recording); the
@@ -421,7 +460,10 @@ enum {
 int pisp_profile(pisp_handle* h, int32_t on);
 
 /* Synchronises the stream and adds the elapsed time, algorithmic bytes and
- * kernel launches of every recorded bracket to the per-family totals. */
+ * kernel launches of every recorded bracket to the per-family totals.  The
+ * bytes of a launch of adaptive sweep s count only the instances that sweep
+ * covered (front entries for the solves, rows for the residuals and the
+ * stopping tests), as the last solve's pisp_refinement_stats gives them. */
 int pisp_profile_collect(pisp_handle* h);
 
 /* Per-family totals since the last pisp_profile_reset: device milliseconds,

@@ -62,6 +62,8 @@ _SIGS = {
                                      c_int32]),
     "pisp_graph_launch": (c_int32, [c_void_p]),
     "pisp_set_wait_limit": (c_int32, [c_void_p, c_int64, c_int32]),
+    "pisp_set_refinement": (c_int32, [c_void_p, c_double]),
+    "pisp_refinement_stats": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32]),
     "pisp_weights": (c_int32, [c_void_p, c_int32, c_void_p]),
     "pisp_match_rows": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p]),
     "pisp_get_status": (c_int32, [c_void_p, c_void_p, c_void_p]),
@@ -80,7 +82,7 @@ _SIGS = {
     "pisp_profile_reset": (c_int32, [c_void_p]),
     "pisp_profile_name": (ctypes.c_char_p, [c_int32]),
 }
-PROF_FAMILIES = 7
+PROF_FAMILIES = 9
 
 _lib = None
 

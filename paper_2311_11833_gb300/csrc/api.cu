@@ -67,6 +67,19 @@ struct pisp_handle {
   int32_t units_K = 0, units_R = 0;
   int32_t n_units_f = 0, n_units_b = 0, units_maxF = 0;
   Buf units_f, units_b, ticket, done, serr, nch, d_wl;
+  // adaptive FP64 residual sweeps (pisp_set_refinement): stopping tolerance
+  // (0 = every sweep for every instance), the instance range [lo, hi] of
+  // each persistent solve unit, the compacted unit lists and their lengths,
+  // per-instance flags / sweep counts / correction sizes, instance offsets
+  double sweep_tol = 0.0;
+  int32_t last_sweeps = 0;
+  bool last_adaptive = false, any_solve = false;
+  bool last_loop = false;       // the last solve's sweeps were captured as a device-side loop
+  int32_t loop_kernels = 0;     // kernels per iteration of that loop
+  cudaStream_t body_stream = nullptr;  // captures the loop's body
+  std::vector<double> inst_w;  // solve work of each instance (front entries)
+  Buf rng_f, rng_b, units_fc, units_bc, ucount, r_act, r_pre, r_dmax, r_xmax, r_prevd, r_nsw, d_inst_off;
+  Buf r_nact, r_ai, r_arow, r_ccnt, r_sweep;
   // bounded waits of the persistent solves: polls before giving up (0 = the
   // default), and the test hook that makes one dependency unreachable
   int64_t wait_polls = 0;
@@ -116,9 +129,16 @@ struct pisp_handle {
     graph_valid = false;
   }
   // profiling: CUDA events bracketing each kernel family per level
+  // sweep >= 1: a launch of adaptive sweep `sweep` in a host loop (bytes for
+  // every instance, scaled at collection by the share the sweep covered);
+  // -1: a whole device-side sweep loop (launches per iteration, and the bytes
+  // of one sweep over every instance split into rows and solve work, scaled
+  // at collection per iteration)
   struct Bracket {
     int fam, e0, e1, launches;
     double bytes;
+    int sweep;
+    double bytes_rows, bytes_work;
   };
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_ev;
@@ -135,6 +155,7 @@ struct pisp_handle {
   ~pisp_handle() {
     drop_graph();
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (body_stream) cudaStreamDestroy(body_stream);
     if (cap_ev) cudaEventDestroy(cap_ev);
     for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
     for (int i = 0; i < kSide; ++i) {
@@ -452,10 +473,12 @@ int build_units(pisp_handle* h, int32_t K, int32_t R) {
   const int segch = (R + pisp::kSolveChunk - 1) / pisp::kSolveChunk;
   std::vector<std::vector<pisp::SolveUnit>> per_level(S.n_levels);
   std::vector<int32_t> nch(S.sn.size(), segch);
+  std::vector<std::vector<int32_t>> per_level_rng(S.n_levels);  // [lo, hi] instance range per unit
   std::vector<int32_t> wl;
   int maxF = 0;
   for (int l = 0; l < S.n_levels; ++l) {
     auto& U = per_level[l];
+    auto& UR = per_level_rng[l];
     std::vector<int32_t> lst(S.level_sn.begin() + S.level_off[l], S.level_sn.begin() + S.level_off[l + 1]);
     std::sort(lst.begin(), lst.end(), [&](int32_t a, int32_t b) {
       const int fa = S.sn[a].F(), fb = S.sn[b].F();
@@ -476,7 +499,11 @@ int build_units(pisp_handle* h, int32_t K, int32_t R) {
       maxF = std::max(maxF, S.sn[sn].F());
       nch[sn] = bch;
       for (int k = 0; k < K; ++k)
-        for (int c = 0; c < bch; ++c) U.push_back({pisp::kUnitBlk, sn, k, c, rc});
+        for (int c = 0; c < bch; ++c) {
+          U.push_back({pisp::kUnitBlk, sn, k, c, rc});
+          UR.push_back(S.sn[sn].instance);
+          UR.push_back(S.sn[sn].instance);
+        }
     }
     auto seg_group = [&](const std::vector<int32_t>& g, int seg) -> int {
       if (g.empty()) return PISP_OK;
@@ -486,8 +513,18 @@ int build_units(pisp_handle* h, int32_t K, int32_t R) {
       const int64_t tasks = (int64_t)g.size() * ((K + kf - 1) / kf) * segch;
       if (tasks >= INT32_MAX || off >= INT32_MAX) return fail(h, PISP_ERR_UNSUPPORTED, "too many solve tasks");
       wl.insert(wl.end(), g.begin(), g.end());
-      for (int64_t b = 0; b < tasks; b += 256 / seg)
+      const int64_t per_front = (int64_t)((K + kf - 1) / kf) * segch;
+      for (int64_t b = 0; b < tasks; b += 256 / seg) {
         U.push_back({kind, (int32_t)off, (int32_t)b, (int32_t)tasks, kf});
+        int32_t lo = INT32_MAX, hi = -1;
+        for (int64_t q = b; q < std::min(tasks, b + 256 / seg); q += 1) {
+          const int32_t in = S.sn[g[q / per_front]].instance;
+          lo = std::min(lo, in);
+          hi = std::max(hi, in);
+        }
+        UR.push_back(lo);
+        UR.push_back(hi);
+      }
       return PISP_OK;
     };
     TRY(seg_group(g32w, 32));
@@ -506,10 +543,22 @@ int build_units(pisp_handle* h, int32_t K, int32_t R) {
       }
   }
   std::vector<pisp::SolveUnit> f, b;
-  for (int l = 0; l < S.n_levels; ++l) f.insert(f.end(), per_level[l].begin(), per_level[l].end());
-  for (int l = S.n_levels - 1; l >= 0; --l) b.insert(b.end(), per_level[l].begin(), per_level[l].end());
+  std::vector<int32_t> rf, rb;
+  for (int l = 0; l < S.n_levels; ++l) {
+    f.insert(f.end(), per_level[l].begin(), per_level[l].end());
+    rf.insert(rf.end(), per_level_rng[l].begin(), per_level_rng[l].end());
+  }
+  for (int l = S.n_levels - 1; l >= 0; --l) {
+    b.insert(b.end(), per_level[l].begin(), per_level[l].end());
+    rb.insert(rb.end(), per_level_rng[l].begin(), per_level_rng[l].end());
+  }
   TRY(upload(h, h->units_f, f));
   TRY(upload(h, h->units_b, b));
+  TRY(upload(h, h->rng_f, rf));
+  TRY(upload(h, h->rng_b, rb));
+  if (!h->units_fc.ensure(f.size() * sizeof(pisp::SolveUnit)) ||
+      !h->units_bc.ensure(b.size() * sizeof(pisp::SolveUnit)) || !h->ucount.ensure(2 * sizeof(int32_t)))
+    return fail(h, PISP_ERR_OOM, "device allocation failed (solve schedule)");
   TRY(upload(h, h->nch, nch));
   TRY(upload(h, h->d_wl, wl));
   if (!h->ticket.ensure(2 * sizeof(int)) || !h->serr.ensure(sizeof(int)) ||
@@ -545,8 +594,9 @@ pisp::Shifts make_shifts(const pisp_handle* h, const double* w) {
   return sh;
 }
 
-const char* kFamilyNames[PISP_PROF_FAMILIES] = {"factor_small", "factor_big", "forward",          "backward",
-                                                "residual",     "combine",    "factor_persistent"};
+const char* kFamilyNames[PISP_PROF_FAMILIES] = {"factor_small", "factor_big", "forward",
+                                                "backward",     "residual",   "combine",
+                                                "factor_persistent", "refine_control", "sweep_loop"};
 
 // Event record that also works inside a stream capture: there it must become
 // an event-record node of the graph (external record) to be timed on replay.
@@ -575,10 +625,11 @@ int prof_begin(pisp_handle* h, cudaStream_t st = nullptr) {
 }
 
 // Closes the bracket on the stream it was opened on (default: the handle's).
-void prof_end(pisp_handle* h, int i, int fam, double bytes, int launches, cudaStream_t st = nullptr) {
+void prof_end(pisp_handle* h, int i, int fam, double bytes, int launches, cudaStream_t st = nullptr,
+              int sweep = 0) {
   if (i < 0 || launches <= 0) return;
   record_event(h, h->prof_ev[i + 1], st ? st : h->stream);
-  h->prof_br.push_back({fam, i, i + 1, launches, bytes});
+  h->prof_br.push_back({fam, i, i + 1, launches, bytes, sweep, 0.0, 0.0});
 }
 
 int count(pisp_handle* h, int n) {
@@ -592,9 +643,11 @@ int count(pisp_handle* h, int n) {
 
 // forward + backward over all levels; `rhs` broadcast [N][R] (original order)
 // or per-perturbation [N][K][R] (permuted order); results to `out`
-// (and added to `acc` when given).
+// (and added to `acc` when given).  Adaptive sweeps (persistent schedule):
+// act skips the fronts of instances that have stopped and the compacted unit
+// lists are walked; `sweep` tags the profiling brackets.
 int solve_pass(pisp_handle* h, bool trans, const double* rhs, int rhs_mode, double* out,
-               double* acc, int32_t R) {
+               double* acc, int32_t R, const uint8_t* act = nullptr, int sweep = 0) {
   const int L = h->sym.n_levels;
   if (!trans && h->schedule == 0) {
     if (h->units_K != h->K || h->units_R != R) TRY(build_units(h, h->K, R));
@@ -607,23 +660,26 @@ int solve_pass(pisp_handle* h, bool trans, const double* rhs, int rhs_mode, doub
     if (acc) bb += 16.0 * h->sym.N * h->K * R;
     CK(cudaMemsetAsync(h->ticket.p, 0, 2 * sizeof(int), h->stream));
     CK(cudaMemsetAsync(h->done.p, 0, nd, h->stream));
+    const bool cmp = act != nullptr;  // gated: the compacted lists (whole lists before the first test)
+    const int* ucf = cmp ? h->ucount.as<int>() : nullptr;
+    const int* ucb = cmp ? h->ucount.as<int>() + 1 : nullptr;
     int pb = prof_begin(h);
-    int n = pisp::launch_solve_persistent(h->precision, true, h->sd, h->units_f.as<pisp::SolveUnit>(),
-                                          h->n_units_f, h->ticket.as<int>(), h->done.as<int>(),
-                                          h->serr.as<int>(), h->nch.as<int>(), h->d_wl.as<int32_t>(), h->fronts.p, rhs,
-                                          rhs_mode, h->V.p, out, acc, R, h->K, h->units_maxF, h->solve_ctas, h->wait_polls,
-                                          h->stream);
+    int n = pisp::launch_solve_persistent(
+        h->precision, true, h->sd, (cmp ? h->units_fc : h->units_f).as<pisp::SolveUnit>(), h->n_units_f, ucf, act,
+        h->ticket.as<int>(), h->done.as<int>(), h->serr.as<int>(), h->nch.as<int>(), h->d_wl.as<int32_t>(),
+        h->fronts.p, rhs, rhs_mode, h->V.p, out, acc, R, h->K, h->units_maxF, h->solve_ctas, h->wait_polls,
+        h->stream);
     TRY(count(h, n));
-    prof_end(h, pb, PISP_PROF_FORWARD, bf, n);
+    prof_end(h, pb, PISP_PROF_FORWARD, bf, n, nullptr, act ? sweep : 0);
     CK(cudaMemsetAsync(h->done.p, 0, nd, h->stream));
     pb = prof_begin(h);
-    n = pisp::launch_solve_persistent(h->precision, false, h->sd, h->units_b.as<pisp::SolveUnit>(),
-                                      h->n_units_b, h->ticket.as<int>() + 1, h->done.as<int>(),
-                                      h->serr.as<int>(), h->nch.as<int>(), h->d_wl.as<int32_t>(), h->fronts.p, rhs,
-                                      rhs_mode, h->V.p, out, acc, R, h->K, h->units_maxF, h->solve_ctas, h->wait_polls,
-                                      h->stream);
+    n = pisp::launch_solve_persistent(
+        h->precision, false, h->sd, (cmp ? h->units_bc : h->units_b).as<pisp::SolveUnit>(), h->n_units_b, ucb, act,
+        h->ticket.as<int>() + 1, h->done.as<int>(), h->serr.as<int>(), h->nch.as<int>(), h->d_wl.as<int32_t>(),
+        h->fronts.p, rhs, rhs_mode, h->V.p, out, acc, R, h->K, h->units_maxF, h->solve_ctas, h->wait_polls,
+        h->stream);
     TRY(count(h, n));
-    prof_end(h, pb, PISP_PROF_BACKWARD, bb, n);
+    prof_end(h, pb, PISP_PROF_BACKWARD, bb, n, nullptr, act ? sweep : 0);
     return PISP_OK;
   }
   for (int l = 0; l < L; ++l) {
@@ -646,21 +702,198 @@ int solve_pass(pisp_handle* h, bool trans, const double* rhs, int rhs_mode, doub
   return PISP_OK;
 }
 
+// Sweeps per instance of the last solve, and for s = 1 .. max_sweeps the
+// fraction of the solve work (front entries, fs[s]) and of the rows (fr[s])
+// that sweep s covered (index 0 unused).  Synchronises the stream.
+int sweep_fractions(pisp_handle* h, int max_sweeps, std::vector<int32_t>& nsw, std::vector<double>& fs,
+                    std::vector<double>& fr) {
+  const int32_t G = h->sym.G;
+  nsw.assign(G, h->last_sweeps);
+  if (h->last_adaptive) {
+    CK(cudaMemcpyAsync(nsw.data(), h->r_nsw.p, (size_t)G * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  fs.assign(max_sweeps + 1, 0.0);
+  fr.assign(max_sweeps + 1, 0.0);
+  double ws = 0.0, wr = 0.0;
+  for (int g = 0; g < G; ++g) {
+    const double rows = (double)(h->sym.inst_off[g + 1] - h->sym.inst_off[g]);
+    ws += h->inst_w[g];
+    wr += rows;
+    for (int s = 1; s <= std::min(max_sweeps, nsw[g]); ++s) {
+      fs[s] += h->inst_w[g];
+      fr[s] += rows;
+    }
+  }
+  for (int s = 1; s <= max_sweeps; ++s) {
+    fs[s] = ws > 0 ? fs[s] / ws : 0.0;
+    fr[s] = wr > 0 ? fr[s] / wr : 0.0;
+  }
+  return PISP_OK;
+}
+
+// Algorithmic bytes of one forward + backward pass of the persistent
+// schedule with accumulation (all instances), as the brackets count them.
+double solve_bytes(const pisp_handle* h, int32_t R) {
+  double b = 16.0 * h->sym.N * h->K * R;
+  for (int l = 0; l < h->sym.n_levels; ++l)
+    b += h->K * (h->plans[l].bytes_fwd_a + h->plans[l].bytes_fwd_b * R + h->plans[l].bytes_bwd_a +
+                 h->plans[l].bytes_bwd_b * R);
+  return b;
+}
+
+// One adaptive sweep for the instances still iterating: the FP64 residuals
+// of their rows, the gated solves of their corrections (compacted unit lists
+// of the persistent schedule; the per-level schedule solves every row, with
+// zero residuals outside the active set), their correction and solution
+// sizes, the stopping test and the active set and unit lists of the next
+// sweep.  s_host: the sweep number in a host loop (brackets and launch
+// accounting), 0 inside a device-side loop (no brackets: a conditional body
+// holds no events).  has_cond: the stopping test drives the loop's
+// conditional `cond`.
+int sweep_body(pisp_handle* h, const double* rhs, double* X_out, int32_t R, int32_t S, const pisp::Shifts& sh,
+               int s_host, cudaGraphConditionalHandle cond, int has_cond) {
+  const double N = (double)h->sym.N, KR = (double)h->K * R;
+  const bool persistent = h->schedule == 0;
+  const int32_t G = h->sym.G;
+  uint8_t* act = h->r_act.as<uint8_t>();
+  const pisp::ActiveSet as{act, h->r_nact.as<int32_t>(), h->r_ai.as<int32_t>(), h->r_arow.as<int64_t>(),
+                           h->d_inst_off.as<int64_t>()};
+  int pb = s_host > 0 ? prof_begin(h) : -1;
+  int n = pisp::launch_residual_per_k(h->sd, h->vals.as<double>(), h->D.as<double>(), sh, rhs, X_out, R,
+                                      h->Rk.as<double>(), as, persistent ? pisp::kResActive : pisp::kResZeroStopped,
+                                      h->stream);
+  TRY(count(h, n));
+  prof_end(h, pb, PISP_PROF_RESIDUAL, h->sym.nnzA * 12.0 + N * 20.0 + N * R * 8.0 + 2.0 * N * KR * 8.0, n,
+           nullptr, s_host);
+  const bool prof_was = h->prof_on;
+  if (s_host == 0) h->prof_on = false;
+  const int rc = solve_pass(h, false, h->Rk.as<double>(), pisp::RHS_PER_K, h->Y.as<double>(), X_out, R,
+                            persistent ? act : nullptr, s_host);
+  h->prof_on = prof_was;
+  TRY(rc);
+  pb = s_host > 0 ? prof_begin(h) : -1;
+  n = pisp::launch_refine_stats(h->sd, as, 0, X_out, h->Y.as<double>(), h->K, R, h->r_dmax.as<unsigned long long>(),
+                                h->r_xmax.as<unsigned long long>(), h->stream);
+  TRY(count(h, n));
+  int m = pisp::launch_refine_decide(G, R, h->sweep_tol, S, h->r_sweep.as<int32_t>(), cond, has_cond, act,
+                                     h->r_dmax.as<unsigned long long>(), h->r_xmax.as<unsigned long long>(),
+                                     h->r_prevd.as<double>(), h->r_nsw.as<int32_t>(), h->r_pre.as<int32_t>(),
+                                     h->r_nact.as<int32_t>(), h->r_ai.as<int32_t>(), h->r_arow.as<int64_t>(),
+                                     h->d_inst_off.as<int64_t>(), h->stream);
+  TRY(count(h, m));
+  if (persistent && s_host < S) {
+    const int c = pisp::launch_compact_units(
+        h->units_f.as<pisp::SolveUnit>(), h->rng_f.as<int32_t>(), h->n_units_f, h->units_fc.as<pisp::SolveUnit>(),
+        h->units_b.as<pisp::SolveUnit>(), h->rng_b.as<int32_t>(), h->n_units_b, h->units_bc.as<pisp::SolveUnit>(),
+        h->r_pre.as<int32_t>(), h->r_ccnt.as<int32_t>(), h->ucount.as<int32_t>(), h->stream);
+    TRY(count(h, c));
+    m += c;
+  }
+  prof_end(h, pb, PISP_PROF_REFINE, 2.0 * N * KR * 8.0, n + m, nullptr, s_host);
+  return PISP_OK;
+}
+
+// The adaptive sweeps as a device-side loop inside the stream capture in
+// progress on h->stream: a WHILE conditional node (its body one sweep_body,
+// captured on a side stream into the node's body graph) that runs while the
+// stopping test leaves an instance active, at most S times.
+int sweep_loop_node(pisp_handle* h, const double* rhs, double* X_out, int32_t R, int32_t S,
+                    const pisp::Shifts& sh) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  CK(cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &g, &deps, nullptr, &ndeps));
+  if (cs != cudaStreamCaptureStatusActive || !g) return fail(h, PISP_ERR_CUDA, "no stream capture in progress");
+  cudaGraphConditionalHandle cond = 0;
+  CK(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+  CK(cudaGraphAddNode(&node, g, dv.data(), nullptr, dv.size(), &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  if (!h->body_stream) CK(cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking));
+  CK(cudaStreamBeginCaptureToGraph(h->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  const cudaStream_t outer = h->stream;
+  h->stream = h->body_stream;
+  const int launches0 = h->launches;
+  const int rc = sweep_body(h, rhs, X_out, R, S, sh, 0, cond, 1);
+  h->loop_kernels = h->launches - launches0;
+  h->stream = outer;
+  cudaGraph_t body_out = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(h->body_stream, &body_out);
+  TRY(rc);
+  if (e != cudaSuccess) return fail(h, PISP_ERR_CUDA, std::string("sweep loop capture: ") + cudaGetErrorString(e));
+  CK(cudaStreamUpdateCaptureDependencies(h->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return PISP_OK;
+}
+
 // Per-perturbation solves of `rhs` (broadcast, original order) into X_out,
-// followed by `sweeps` FP64 residual corrections of every x_k.
+// followed by at most `sweeps` FP64 residual corrections of every x_k: all of
+// them for every instance, or (pisp_set_refinement) per instance until its
+// stopping test holds, as a host loop, or as a device-side loop when the
+// stream is being captured.
 int solve_core(pisp_handle* h, const double* rhs, double* X_out, int32_t R, int32_t sweeps,
                const pisp::Shifts& sh) {
   TRY(solve_pass(h, false, rhs, pisp::RHS_BROADCAST, X_out, nullptr, R));
   const double N = (double)h->sym.N, KR = (double)h->K * R;
-  for (int it = 0; it < sweeps; ++it) {
-    const int pb = prof_begin(h);
-    const int n = pisp::launch_residual_per_k(h->sd, h->vals.as<double>(), h->D.as<double>(), sh,
-                                              rhs, X_out, R, h->Rk.as<double>(), h->stream);
-    TRY(count(h, n));
-    prof_end(h, pb, PISP_PROF_RESIDUAL,
-             h->sym.nnzA * 12.0 + N * 20.0 + N * R * 8.0 + 2.0 * N * KR * 8.0, n);
-    TRY(solve_pass(h, false, h->Rk.as<double>(), pisp::RHS_PER_K, h->Y.as<double>(), X_out, R));
+  const bool adapt = h->sweep_tol > 0.0 && sweeps > 0;
+  const int32_t G = h->sym.G;
+  h->last_sweeps = sweeps;
+  h->last_adaptive = adapt;
+  h->last_loop = false;
+  h->any_solve = true;
+  if (!adapt) {
+    const pisp::ActiveSet none{};
+    for (int it = 0; it < sweeps; ++it) {
+      const int pb = prof_begin(h);
+      const int n = pisp::launch_residual_per_k(h->sd, h->vals.as<double>(), h->D.as<double>(), sh, rhs, X_out, R,
+                                                h->Rk.as<double>(), none, pisp::kResAll, h->stream);
+      TRY(count(h, n));
+      prof_end(h, pb, PISP_PROF_RESIDUAL, h->sym.nnzA * 12.0 + N * 20.0 + N * R * 8.0 + 2.0 * N * KR * 8.0, n);
+      TRY(solve_pass(h, false, h->Rk.as<double>(), pisp::RHS_PER_K, h->Y.as<double>(), X_out, R));
+    }
+    return PISP_OK;
   }
+  const size_t gr = (size_t)G * R * sizeof(unsigned long long);
+  if (!h->r_act.ensure((size_t)G) || !h->r_pre.ensure((size_t)(G + 1) * sizeof(int32_t)) ||
+      !h->r_nsw.ensure((size_t)G * sizeof(int32_t)) || !h->r_dmax.ensure(gr) || !h->r_xmax.ensure(gr) ||
+      !h->r_prevd.ensure((size_t)G * R * sizeof(double)) || !h->r_nact.ensure(sizeof(int32_t)) ||
+      !h->r_ai.ensure((size_t)G * sizeof(int32_t)) || !h->r_arow.ensure((size_t)(G + 1) * sizeof(int64_t)) ||
+      !h->r_sweep.ensure(sizeof(int32_t)) ||
+      !h->r_ccnt.ensure((size_t)pisp::compact_scratch(h->n_units_f, h->n_units_b) * sizeof(int32_t)))
+    return fail(h, PISP_ERR_OOM, "device allocation failed (adaptive sweeps)");
+  // every instance active; the compacted unit lists are the whole lists
+  CK(cudaMemsetAsync(h->r_dmax.p, 0, gr, h->stream));
+  CK(cudaMemsetAsync(h->r_xmax.p, 0, gr, h->stream));
+  TRY(count(h, pisp::launch_refine_init(G, h->r_act.as<uint8_t>(), h->r_pre.as<int32_t>(), h->r_nact.as<int32_t>(),
+                                        h->r_ai.as<int32_t>(), h->r_arow.as<int64_t>(),
+                                        h->d_inst_off.as<int64_t>(), h->r_sweep.as<int32_t>(), h->stream)));
+  if (h->schedule == 0)
+    TRY(count(h, pisp::launch_compact_units(
+                     h->units_f.as<pisp::SolveUnit>(), h->rng_f.as<int32_t>(), h->n_units_f,
+                     h->units_fc.as<pisp::SolveUnit>(), h->units_b.as<pisp::SolveUnit>(), h->rng_b.as<int32_t>(),
+                     h->n_units_b, h->units_bc.as<pisp::SolveUnit>(), h->r_pre.as<int32_t>(),
+                     h->r_ccnt.as<int32_t>(), h->ucount.as<int32_t>(), h->stream)));
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(h->stream, &cs));
+  if (cs == cudaStreamCaptureStatusActive) {
+    const int pb = prof_begin(h);
+    TRY(sweep_loop_node(h, rhs, X_out, R, sweeps, sh));
+    h->last_loop = true;
+    if (pb >= 0) {  // the loop as one bracket; bytes and launches are scaled at collection
+      record_event(h, h->prof_ev[pb + 1], h->stream);
+      h->prof_br.push_back({PISP_PROF_SWEEP_LOOP, pb, pb + 1, h->loop_kernels, 0.0, -1,
+                            h->sym.nnzA * 12.0 + N * 20.0 + N * R * 8.0 + 4.0 * N * KR * 8.0, solve_bytes(h, R)});
+    }
+    return PISP_OK;
+  }
+  for (int s = 1; s <= sweeps; ++s) TRY(sweep_body(h, rhs, X_out, R, sweeps, sh, s, 0, 0));
   return PISP_OK;
 }
 
@@ -759,6 +992,7 @@ int analyze_impl(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
     so.threads = opt->analyze_threads;
   }
   h->analyzed = h->factored = h->solved = false;
+  h->any_solve = h->last_adaptive = false;
   h->plan_precision = 0;
   const auto t0 = std::chrono::steady_clock::now();
   std::string msg = pisp::analyze(G, n, row_ptr, col_idx, so, h->sym);
@@ -808,6 +1042,9 @@ int analyze_impl(pisp_handle* h, int32_t G, const int32_t* n, const int64_t* row
   TRY(upload(h, h->perm, S.perm));
   TRY(upload(h, h->iperm, S.iperm));
   TRY(upload(h, h->row_inst, row_inst));
+  TRY(upload(h, h->d_inst_off, S.inst_off));
+  h->inst_w.assign(G, 0.0);
+  for (int s = 0; s < nS; ++s) h->inst_w[S.sn[s].instance] += (double)S.sn[s].F() * S.sn[s].F();
   TRY(upload(h, h->row_ptr, rp));
   TRY(upload(h, h->col, cl));
   TRY(upload(h, h->parent, par));
@@ -1216,6 +1453,31 @@ int pisp_set_wait_limit(pisp_handle* h, int64_t polls, int32_t unreachable) {
   return PISP_OK;
 }
 
+int pisp_set_refinement(pisp_handle* h, double tol) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(h, PISP_ERR_INVALID_ARG, "tol must be finite and >= 0");
+  h->sweep_tol = tol;
+  return PISP_OK;
+}
+
+int pisp_refinement_stats(pisp_handle* h, int32_t* sweeps_per_instance, double* work, double* rows,
+                          int32_t max_sweeps) {
+  if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
+  if (max_sweeps < 0) return fail(h, PISP_ERR_INVALID_ARG, "max_sweeps must be >= 0");
+  if (!h->any_solve) return fail(h, PISP_ERR_NOT_FACTORED, "no solve");
+  DeviceScope dev_scope_;
+  TRY(set_device(h, dev_scope_));
+  std::vector<int32_t> nsw;
+  std::vector<double> fs, fr;
+  TRY(sweep_fractions(h, std::max(max_sweeps, 1), nsw, fs, fr));
+  if (sweeps_per_instance) std::copy(nsw.begin(), nsw.end(), sweeps_per_instance);
+  for (int q = 0; q < max_sweeps; ++q) {
+    if (work) work[q] = fs[q + 1];
+    if (rows) rows[q] = fr[q + 1];
+  }
+  return PISP_OK;
+}
+
 int pisp_get_status(pisp_handle* h, int32_t* per_instance_k, int32_t* first_bad_col) {
   if (!h) return fail(h, PISP_ERR_INVALID_ARG, "null handle");
   if (!h->factored) return fail(h, PISP_ERR_NOT_FACTORED, "no factorisation");
@@ -1262,6 +1524,17 @@ int pisp_get_stats(const pisp_handle* h, pisp_stats* o) {
   o->K = h->K;
   o->precision = h->precision;
   o->gpu_launches = h->launches;
+  if (h->last_loop && h->loop_kernels > 0 && h->r_sweep.p) {
+    // a device-side sweep loop was captured once: add its further iterations
+    pisp_handle* hh = const_cast<pisp_handle*>(h);
+    DeviceScope dev_scope_;
+    if (set_device(hh, dev_scope_) == PISP_OK) {
+      int32_t iters = 0;
+      if (cudaMemcpyAsync(&iters, h->r_sweep.p, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream) == cudaSuccess &&
+          cudaStreamSynchronize(h->stream) == cudaSuccess && iters > 1)
+        o->gpu_launches += h->loop_kernels * (iters - 1);
+    }
+  }
   o->flops_factor = S.flops_factor;
   o->flops_solve = S.flops_solve;
   o->analyze_ms = h->analyze_ms;
@@ -1409,11 +1682,31 @@ int pisp_profile_collect(pisp_handle* h) {
   DeviceScope dev_scope_;
   TRY(set_device(h, dev_scope_));
   CK(cudaStreamSynchronize(h->stream));
+  int max_sweep = 0;
+  for (const auto& b : h->prof_br) max_sweep = std::max(max_sweep, b.sweep == -1 ? h->last_sweeps : b.sweep);
+  std::vector<int32_t> nsw;
+  std::vector<double> fs, fr;
+  if (max_sweep > 0 && h->last_adaptive) TRY(sweep_fractions(h, max_sweep, nsw, fs, fr));
   for (const auto& b : h->prof_br) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, h->prof_ev[b.e0], h->prof_ev[b.e1]));
     h->prof_ms[b.fam] += ms;
-    h->prof_bytes[b.fam] += b.bytes;
+    if (b.sweep == -1) {  // a device-side loop: one iteration per sweep any instance took
+      int iters = 0;
+      double by = 0.0;
+      for (int s = 1; s < (int)fs.size(); ++s)
+        if (fr[s] > 0.0) {
+          ++iters;
+          by += fr[s] * b.bytes_rows + fs[s] * b.bytes_work;
+        }
+      h->prof_bytes[b.fam] += by;
+      h->prof_launches[b.fam] += (int64_t)b.launches * iters;
+      continue;
+    }
+    double scale = 1.0;
+    if (b.sweep > 0 && !fs.empty())
+      scale = (b.fam == PISP_PROF_FORWARD || b.fam == PISP_PROF_BACKWARD) ? fs[b.sweep] : fr[b.sweep];
+    h->prof_bytes[b.fam] += b.bytes * scale;
     h->prof_launches[b.fam] += b.launches;
   }
   return PISP_OK;

@@ -210,12 +210,14 @@ constexpr int kSolveChunk = 8;  // largest RHS chunk of a task (segment tasks us
 // nch[s] is the number of RHS chunks (tasks) per (front s, k); err is set to 1
 // if a bounded dependency wait gave up after `polls` polls (<= 0: the default
 // limit of 2^22 polls); ctas = resident CTAs per SM the kernel is compiled
-// for (2, 3 or 4; <= 0: 3 for FP32, 2 for FP64).
+// for (2, 3 or 4; <= 0: 3 for FP32, 2 for FP64).  Adaptive sweeps: ucount
+// (device, or nullptr) holds the length of a compacted list (nunits is then
+// its capacity), act[g] (device, or nullptr) = 0 skips instance g's fronts.
 int launch_solve_persistent(int precision, bool forward, const SymDev& sd, const SolveUnit* units,
-                            int nunits, int* ticket, int* done, int* err, const int* nch,
-                            const int32_t* d_all, const void* fronts, const double* rhs,
-                            int rhs_mode, void* V, double* out, double* acc, int32_t R, int32_t K,
-                            int32_t max_blk_F, int32_t ctas, int64_t polls, cudaStream_t st);
+                            int nunits, const int* ucount, const uint8_t* act, int* ticket, int* done,
+                            int* err, const int* nch, const int32_t* d_all, const void* fronts,
+                            const double* rhs, int rhs_mode, void* V, double* out, double* acc, int32_t R,
+                            int32_t K, int32_t max_blk_F, int32_t ctas, int64_t polls, cudaStream_t st);
 // RHS chunk for the CTAs solving one big front at a time (persistent schedule)
 int pick_chunk(int fronts_in_level, int K, int R);
 int launch_forward_level(int precision, bool trans, const SymDev& sd, const LevelPlan& lp,
@@ -226,9 +228,52 @@ int launch_backward_level(int precision, bool trans, const SymDev& sd, const Lev
                           double* acc, int32_t R, int32_t K, cudaStream_t st);
 int launch_combine(const SymDev& sd, const double* X, const Shifts& sh, int32_t R, double* x,
                    cudaStream_t st);
+// The instances still iterating in the adaptive sweeps (device arrays
+// written by the stopping test): act[g] flags, their number *nact, their ids
+// ai[0..nact) in increasing order, and arow[q] = the rows of ai[0..q)
+// (arow[nact] = all their rows).  Active row a belongs to instance ai[q] for
+// the largest q with arow[q] <= a, at original row inst_off[ai[q]] + a - arow[q].
+struct ActiveSet {
+  const uint8_t* act;
+  const int32_t* nact;
+  const int32_t* ai;
+  const int64_t* arow;
+  const int64_t* inst_off;  // [G+1] first original row of each instance
+};
+// Rows a residual launch covers: every row; every row with Rk = 0 on the rows
+// of instances that have stopped (whose correction is then exactly 0, for a
+// solve that is not gated); only the rows of the active set.
+enum ResidualMode { kResAll = 0, kResZeroStopped = 1, kResActive = 2 };
 int launch_residual_per_k(const SymDev& sd, const double* vals, const double* D,
                           const Shifts& sh, const double* b, const double* X, int32_t R,
-                          double* Rk, cudaStream_t st);
+                          double* Rk, const ActiveSet& as, int mode, cudaStream_t st);
+// Per instance g of the active set (all != 0: every instance) and RHS r: the
+// largest |Y| and |X| over its rows and all k, atomically maxed into
+// dmax/xmax [G][R] (zero on entry) as bit patterns.
+int launch_refine_stats(const SymDev& sd, const ActiveSet& as, int all, const double* X, const double* Y,
+                        int32_t K, int32_t R, unsigned long long* dmax, unsigned long long* xmax,
+                        cudaStream_t st);
+// One CTA: the stopping test after sweep s = *sweep + 1 (s >= S: every
+// instance stops), *sweep = s, nsw[g] = the sweeps instance g took, dmax /
+// xmax zeroed again, then the active set: pre[g] = the active instances
+// before g (G+1 ints), *nact, ai [G], arow [G+1].  has_cond: sets the
+// conditional `cond` of a device-side sweep loop to continue while an
+// instance is active and s < S.
+int launch_refine_decide(int32_t G, int32_t R, double tol, int32_t S, int32_t* sweep,
+                         cudaGraphConditionalHandle cond, int has_cond, uint8_t* act, unsigned long long* dmax,
+                         unsigned long long* xmax, double* prevd, int32_t* nsw, int32_t* pre, int32_t* nact,
+                         int32_t* ai, int64_t* arow, const int64_t* inst_off, cudaStream_t st);
+// Every instance active, no sweep done: act, pre, *nact, ai, arow, *sweep.
+int launch_refine_init(int32_t G, uint8_t* act, int32_t* pre, int32_t* nact, int32_t* ai, int64_t* arow,
+                       const int64_t* inst_off, int32_t* sweep, cudaStream_t st);
+// In-order compaction of the forward and backward unit lists to the units
+// whose instance range [lo, hi] (rf, rb: int32 pairs) holds an active
+// instance, into cf / cb with lengths in ucount[0..1]; cnt holds
+// compact_scratch(nf, nb) ints of scratch.  Returns the kernels launched.
+int compact_scratch(int32_t nf, int32_t nb);
+int launch_compact_units(const SolveUnit* uf, const int32_t* rf, int32_t nf, SolveUnit* cf, const SolveUnit* ub,
+                         const int32_t* rb, int32_t nb, SolveUnit* cb, const int32_t* pre, int32_t* cnt,
+                         int32_t* ucount, cudaStream_t st);
 // FP64 residuals of the transposed perturbed systems (adjoint sweeps)
 int launch_residual_T_per_k(const SymDev& sd, const double* vals, const double* D,
                             const Shifts& sh, const double* g, const double* Lam, int32_t R,

@@ -504,6 +504,10 @@ __device__ __forceinline__ void seg_backward(const SymDev& sd, const SegTask& t,
 // the solve instead of following it.
 // ---------------------------------------------------------------------------
 constexpr int kBS = 33;  // padded row stride of a staged 32x32 block
+// shared memory of the blocked path besides its nr x F vectors (elements):
+// two staged diagonal blocks, and the backward solve's partial sums of the
+// U12 product for a group of 4 right-hand sides
+constexpr int kBlkExtra = 2 * 32 * kBS + 4 * kSolveThreads;
 
 // rows prefetched per thread before the diagonal solve: more would push the
 // persistent kernel past its 128-register budget (two CTAs per SM) and spill
@@ -690,10 +694,14 @@ __device__ __forceinline__ void blk_backward(const SymDev& sd, int s, int k, int
   __syncthreads();
   if (ms > 0) {
     // z[r][p] -= sum_j U12[p][j] xr[r][j]; thread (p, jj) takes every JG-th j
+    // for a group of 4 right-hand sides.  With JG > 1 the JG partial sums of
+    // an (r, p) meet in shared memory and are added in jj order, so that the
+    // result does not depend on the order in which threads finish.
     const int JG = max(1, min(32, nt / ns));
-    for (int q = tid; q < ns * JG; q += nt) {
-      const int p = q % ns, jj = q / ns;
-      for (int rr = 0; rr < nr; rr += 4) {
+    T* part = z + nr * ns;  // [JG][4][ns], JG * ns <= nt
+    for (int rr = 0; rr < nr; rr += 4) {
+      for (int q = tid; q < ns * JG; q += nt) {
+        const int p = q % ns, jj = q / ns;
         T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         for (int j = jj; j < ms; j += JG) {
           const T u = f[p + (int64_t)(ns + j) * F];
@@ -703,10 +711,28 @@ __device__ __forceinline__ void blk_backward(const SymDev& sd, int s, int k, int
           if (rr + 2 < nr) a2 += u * x0[2 * ms];
           if (rr + 3 < nr) a3 += u * x0[3 * ms];
         }
-        atomicAdd(&z[rr * ns + p], -a0);
-        if (rr + 1 < nr) atomicAdd(&z[(rr + 1) * ns + p], -a1);
-        if (rr + 2 < nr) atomicAdd(&z[(rr + 2) * ns + p], -a2);
-        if (rr + 3 < nr) atomicAdd(&z[(rr + 3) * ns + p], -a3);
+        if (JG == 1) {  // one thread per (r, p)
+          z[rr * ns + p] -= a0;
+          if (rr + 1 < nr) z[(rr + 1) * ns + p] -= a1;
+          if (rr + 2 < nr) z[(rr + 2) * ns + p] -= a2;
+          if (rr + 3 < nr) z[(rr + 3) * ns + p] -= a3;
+        } else {
+          T* pq = part + jj * 4 * ns + p;
+          pq[0] = a0;
+          pq[ns] = a1;
+          pq[2 * ns] = a2;
+          pq[3 * ns] = a3;
+        }
+      }
+      if (JG > 1) {  // CTA-uniform
+        __syncthreads();
+        for (int q = tid; q < min(4, nr - rr) * ns; q += nt) {
+          const int p = q % ns, r = q / ns;
+          T a = 0;
+          for (int jj = 0; jj < JG; ++jj) a += part[(jj * 4 + r) * ns + p];
+          z[(rr + r) * ns + p] -= a;
+        }
+        __syncthreads();  // part is reused by the next group
       }
     }
     __syncthreads();
@@ -823,14 +849,16 @@ struct FTask {
 
 // task q of a group: front list[q / (nkg * nch)], shift group (q / nch) % nkg
 // of kf shifts, RHS chunk q % nch (nkg = ceil(K / kf) shift groups)
+// (act: per-instance flags of the adaptive sweeps; a task of an instance
+// that has stopped is inactive, or nullptr: every task is active)
 __device__ __forceinline__ FTask ftask(const int32_t* list, int64_t q, int64_t ntasks, int R, int K,
-                                       int kf) {
+                                       int kf, const int32_t* inst, const uint8_t* act) {
   FTask t{false, 0, 0, 0, 0, 0};
   const int nch = (R + kRW - 1) / kRW;
   const int nkg = (K + kf - 1) / kf;
   if (q < ntasks) {
-    t.active = true;
     t.s = list[q / ((int64_t)nch * nkg)];
+    t.active = !act || act[inst[t.s]];
     const int kg = (int)((q / nch) % nkg);
     t.k0 = kg * kf;
     t.k1 = min(K, t.k0 + kf);
@@ -1036,17 +1064,22 @@ __device__ __forceinline__ void kseg_backward(const SymDev& sd, const FTask& t, 
 // (blocked path), or 256/SEG K-fused segment tasks, one per segment of the
 // CTA's warps.  A unit only waits for units with smaller tickets, which
 // running CTAs already hold, so the schedule cannot deadlock whatever the
-// number of resident CTAs.
+// number of resident CTAs.  In the later adaptive sweeps the list is the
+// in-order subsequence of the units that hold a front of an instance still
+// iterating, which keeps that property.
 template <typename T, bool FWD, int MINB>
 __global__ void __launch_bounds__(kSolveThreads, MINB)
-k_solve_persistent(SymDev sd, const SolveUnit* __restrict__ units, int nunits, int* ticket,
-                   int* done, int* err, const int* __restrict__ nch, const int32_t* __restrict__ all,
-                   const T* __restrict__ fronts, const double* __restrict__ rhs, int rhs_mode,
-                   T* __restrict__ V, double* out, double* acc, int R, int K, int64_t polls) {
+k_solve_persistent(SymDev sd, const SolveUnit* __restrict__ units, int nunits, const int* __restrict__ ucount,
+                   const uint8_t* __restrict__ act, int* ticket, int* done, int* err,
+                   const int* __restrict__ nch, const int32_t* __restrict__ all, const T* __restrict__ fronts,
+                   const double* __restrict__ rhs, int rhs_mode, T* __restrict__ V, double* out, double* acc,
+                   int R, int K, int64_t polls) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_unit;
   const Sync sy{done, err, nch, polls};
   const int tid = threadIdx.x;
+  // a compacted unit list (adaptive sweeps) has its length on the device
+  if (ucount) nunits = *ucount;
   for (;;) {
     if (tid == 0) s_unit = atomicAdd(ticket, 1);
     __syncthreads();
@@ -1054,15 +1087,19 @@ k_solve_persistent(SymDev sd, const SolveUnit* __restrict__ units, int nunits, i
     if (u >= nunits) return;
     const SolveUnit U = units[u];
     if (U.kind == kUnitBlk) {
-      const int r0 = U.c * U.d;
-      if (FWD)
-        blk_forward<T>(sd, U.a, U.b, r0, min(U.d, R - r0), U.c, smraw, fronts, rhs, rhs_mode, V, R, K, sy);
-      else
-        blk_backward<T>(sd, U.a, U.b, r0, min(U.d, R - r0), U.c, smraw, fronts, V, out, acc, R, K, sy);
+      // a front of an instance whose sweeps have stopped is skipped: no front
+      // of another instance depends on it (CTA-uniform test)
+      if (!act || act[sd.inst[U.a]]) {
+        const int r0 = U.c * U.d;
+        if (FWD)
+          blk_forward<T>(sd, U.a, U.b, r0, min(U.d, R - r0), U.c, smraw, fronts, rhs, rhs_mode, V, R, K, sy);
+        else
+          blk_backward<T>(sd, U.a, U.b, r0, min(U.d, R - r0), U.c, smraw, fronts, V, out, acc, R, K, sy);
+      }
     } else {
       const int SEG = U.kind == kUnitSeg8 ? 8 : (U.kind == kUnitSeg16 ? 16 : 32);
       const int64_t q = (int64_t)U.b + tid / SEG;
-      const FTask t = ftask(all + U.a, q, (int64_t)U.c, R, K, max(1, U.d));
+      const FTask t = ftask(all + U.a, q, (int64_t)U.c, R, K, max(1, U.d), sd.inst, act);
       T* yb = reinterpret_cast<T*>(smraw) + (tid >> 5) * 32 * kRW;
       if (U.kind == kUnitSeg8) {
         if (FWD) kseg_forward<T, 8>(sd, t, tid % 8, yb, fronts, rhs, rhs_mode, V, R, K, sy);
@@ -1092,15 +1129,23 @@ __global__ void k_combine(SymDev sd, const double* __restrict__ X, Shifts sh, in
   x[(int64_t)sd.perm[i] * R + r] = a;
 }
 
-// Rk[pi][k][r] = b[i][r] - sum_j A_ij X[pj][k][r] - t_k D_i X[pi][k][r]  (FP64),
-// one warp per original row i.
-__global__ void k_residual_per_k(SymDev sd, const double* __restrict__ vals,
-                                 const double* __restrict__ D, Shifts sh,
-                                 const double* __restrict__ b, const double* __restrict__ X, int R,
-                                 double* __restrict__ Rk) {
-  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (i >= sd.N) return;
+// largest q in [0, n] with arow[q] <= a (arow[0] = 0 <= a)
+__device__ __forceinline__ int active_slot(const int64_t* arow, int n, int64_t a) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (arow[mid] <= a) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Rk[pi][k][r] = b[i][r] - sum_j A_ij X[pj][k][r] - t_k D_i X[pi][k][r] for one
+// original row i (FP64), by one warp.
+__device__ __forceinline__ void residual_row(const SymDev& sd, const double* __restrict__ vals,
+                                             const double* __restrict__ D, const Shifts& sh,
+                                             const double* __restrict__ b, const double* __restrict__ X, int R,
+                                             double* __restrict__ Rk, int64_t i, int lane) {
   const int K = sh.K;
   const int KR = K * R;
   const int64_t pi = sd.iperm[i];
@@ -1140,6 +1185,37 @@ __global__ void k_residual_per_k(SymDev sd, const double* __restrict__ vals,
   }
 }
 
+// The FP64 residuals of the perturbed systems, one warp per row, warps
+// striding over the rows (rows as ResidualMode selects).
+
+__global__ void k_residual_per_k(SymDev sd, const double* __restrict__ vals,
+                                 const double* __restrict__ D, Shifts sh,
+                                 const double* __restrict__ b, const double* __restrict__ X, int R,
+                                 double* __restrict__ Rk, ActiveSet as, int mode) {
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  int nact = 0;
+  int64_t total = sd.N;
+  if (mode == kResActive) {
+    nact = *as.nact;
+    total = as.arow[nact];
+  }
+  for (int64_t a = w0; a < total; a += nw) {  // warp-uniform
+    int64_t i = a;
+    if (mode == kResActive) {
+      const int q = active_slot(as.arow, nact, a);
+      i = as.inst_off[as.ai[q]] + (a - as.arow[q]);
+    } else if (mode == kResZeroStopped && !as.act[sd.row_inst[i]]) {
+      const int KR = sh.K * R;
+      const int64_t pi = sd.iperm[i];
+      for (int q = lane; q < KR; q += 32) Rk[pi * KR + q] = 0.0;
+      continue;
+    }
+    residual_row(sd, vals, D, sh, b, X, R, Rk, i, lane);
+  }
+}
+
 // Rk[pj][k][r] = g[j][r] - sum_i A_ij Lam[pi][k][r] - t_k D_j Lam[pj][k][r]  (FP64):
 // the residual of the transposed perturbed system (A + t_k D)^T lambda_k = g,
 // one warp per original column j (A's columns through the CSC arrays).
@@ -1176,6 +1252,257 @@ __global__ void k_residual(SymDev sd, const double* __restrict__ vals, const dou
     for (int64_t e = e0; e < e1; ++e) a -= vals[e] * x[(int64_t)sd.col[e] * R + r];
     res[i * R + r] = a;
   }
+}
+
+// ---- adaptive FP64 residual sweeps -----------------------------------------
+// After sweep s, every instance g still iterating gets the size of its last
+// correction d_s and of its solution, per right-hand side r:
+//   dmax[g][r] = max over its rows i and over k of |Y[pi][k][r]|,
+//   xmax[g][r] = max over its rows i and over k of |X[pi][k][r]|.
+// CTAs stride over chunks of kStatRows rows of the active set (all = 1:
+// of every instance).  Within an instance the rows' (i, k) pairs form a
+// matrix of R columns: thread t keeps column c = t % RB of a pass (RB =
+// min(R, 256)) and every (256/RB)-th pair, so a warp's loads are
+// contiguous; the per-column maxima meet in shared memory and then in one
+// 64-bit atomicMax per (g, r) on the bit patterns (non-negative doubles
+// order as their bit patterns, and a NaN orders above +inf, so a NaN never
+// reads as converged).
+constexpr int kStatThreads = 256;
+constexpr int kStatRows = 64;
+
+__global__ void __launch_bounds__(kStatThreads)
+k_refine_stats(SymDev sd, ActiveSet as, int all, const double* __restrict__ X, const double* __restrict__ Y, int K,
+               int R, unsigned long long* __restrict__ dmax, unsigned long long* __restrict__ xmax) {
+  __shared__ unsigned long long s_d[kStatThreads], s_x[kStatThreads];
+  const int nact = all ? 0 : *as.nact;
+  const int64_t total = all ? sd.N : as.arow[nact];
+  const int tid = threadIdx.x;
+  const int RB = min(R, kStatThreads);
+  const int nj = kStatThreads / RB;
+  const int c = tid % RB, j = tid / RB;
+  for (int64_t a0 = (int64_t)blockIdx.x * kStatRows; a0 < total; a0 += (int64_t)gridDim.x * kStatRows) {
+    const int64_t a1 = min(total, a0 + kStatRows);
+    // the instances overlapping active rows [a0, a1), in order (CTA-uniform)
+    int q = all ? sd.row_inst[a0] : active_slot(as.arow, nact, a0);
+    for (;; ++q) {
+      const int g = all ? q : as.ai[q];
+      const int64_t s0 = all ? as.inst_off[g] : as.arow[q];
+      const int64_t s1 = all ? as.inst_off[g + 1] : as.arow[q + 1];
+      const int64_t lo = max(a0, s0), hi = min(a1, s1);
+      if (lo < hi) {
+        const int64_t i0 = as.inst_off[g] + (lo - s0);
+        const int64_t npair = (hi - lo) * K;
+        for (int rb = 0; rb < R; rb += RB) {
+          const int r = rb + c;
+          unsigned long long md = 0, mx = 0;
+          if (j < nj && r < R) {
+            for (int64_t m = j; m < npair; m += nj) {
+              const int64_t o = ((int64_t)sd.iperm[i0 + m / K] * K + (int)(m % K)) * R + r;
+              md = max(md, (unsigned long long)__double_as_longlong(fabs(Y[o])));
+              mx = max(mx, (unsigned long long)__double_as_longlong(fabs(X[o])));
+            }
+          }
+          s_d[tid] = md;
+          s_x[tid] = mx;
+          __syncthreads();
+          if (j == 0 && r < R) {
+            for (int t = 1; t < nj; ++t) {
+              md = max(md, s_d[t * RB + c]);
+              mx = max(mx, s_x[t * RB + c]);
+            }
+            atomicMax(dmax + (int64_t)g * R + r, md);
+            atomicMax(xmax + (int64_t)g * R + r, mx);
+          }
+          __syncthreads();
+        }
+      }
+      if (s1 >= a1) break;
+    }
+  }
+}
+
+// Exclusive prefix sum over the 1024 threads of a CTA (every thread calls);
+// total = the sum of all v.
+constexpr int kDecideThreads = 1024;
+
+template <typename V>
+__device__ V block_excl_scan(V v, V* sh, V& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  V x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const V y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    V y = sh[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const V z = __shfl_up_sync(kFull, y, o);
+      if (lane >= o) y += z;
+    }
+    sh[lane] = y;
+  }
+  __syncthreads();
+  total = sh[31];
+  const V r = x - v + (w > 0 ? sh[w - 1] : V(0));
+  __syncthreads();  // sh is reused by the next scan
+  return r;
+}
+
+// One CTA, after sweep s = *sweep + 1 (the count of sweeps done is kept on
+// the device, so that the same launch serves every sweep of a device-side
+// loop).  For each instance g still iterating: the stopping test of
+// extra-precise iterative refinement (Demmel, Hida, Kahan, Li, Mukherjee,
+// Riedy, ACM TOMS 2006), with the contraction per sweep estimated from
+// successive corrections.  Per right-hand side, rho = |d_s| / |d_{s-1}|
+// (|d_0| = the solution's size): converged when |d_s| = 0, or when rho < 1/2
+// and rho / (1 - rho) |d_s| <= tol |x| (the error that a contraction by rho
+// per sweep leaves); stagnating when rho >= 1/2 from the second sweep on
+// (further sweeps no longer reduce the error).  The instance stops when every
+// right-hand side has converged or stagnated, or after sweep S; nsw[g] = the
+// sweeps it took.  dmax / xmax are zeroed for the next sweep.  Then the
+// active set: pre[g] = the active instances before g (pre[G] = their number =
+// *nact), ai and arow as in ActiveSet.  With a conditional handle (the sweeps
+// as a device-side loop) the loop goes on while an instance is active and s <
+// S: at most S sweeps whatever the data.
+__global__ void __launch_bounds__(kDecideThreads)
+k_refine_decide(int G, int R, double tol, int S, int* __restrict__ sweep, cudaGraphConditionalHandle cond,
+                int has_cond, uint8_t* __restrict__ act, unsigned long long* __restrict__ dmax,
+                unsigned long long* __restrict__ xmax, double* __restrict__ prevd, int* __restrict__ nsw,
+                int* __restrict__ pre, int* __restrict__ nact, int* __restrict__ ai, int64_t* __restrict__ arow,
+                const int64_t* __restrict__ inst_off) {
+  __shared__ int sh[32];
+  __shared__ long long sh64[32];
+  const int s = *sweep + 1;
+  const bool last = s >= S;
+  for (int g = threadIdx.x; g < G; g += kDecideThreads) {
+    if (!act[g]) continue;
+    bool all = true;
+    for (int r = 0; r < R; ++r) {
+      const int64_t q = (int64_t)g * R + r;
+      const double d = __longlong_as_double((long long)dmax[q]);
+      const double x = __longlong_as_double((long long)xmax[q]);
+      dmax[q] = 0;
+      xmax[q] = 0;
+      const double p = s == 1 ? x : prevd[q];
+      prevd[q] = d;
+      bool done_r = d == 0.0;
+      if (!done_r) {
+        const double rho = d / p;  // NaN: neither test holds
+        done_r = rho < 0.5 ? rho / (1.0 - rho) * d <= tol * x : (s >= 2 && rho >= 0.5);
+      }
+      all = all && done_r;
+    }
+    if (all || last) {
+      act[g] = 0;
+      nsw[g] = s;
+    }
+  }
+  __syncthreads();
+  const int64_t per = ((int64_t)G + kDecideThreads - 1) / kDecideThreads;
+  const int64_t b = min((int64_t)G, (int64_t)threadIdx.x * per), e = min((int64_t)G, b + per);
+  int c = 0;
+  long long rows = 0;
+  for (int64_t g = b; g < e; ++g)
+    if (act[g]) {
+      ++c;
+      rows += inst_off[g + 1] - inst_off[g];
+    }
+  int total;
+  long long total_rows;
+  int o = block_excl_scan<int>(c, sh, total);
+  long long ro = block_excl_scan<long long>(rows, sh64, total_rows);
+  for (int64_t g = b; g < e; ++g) {
+    pre[g] = o;
+    if (act[g]) {
+      ai[o] = (int)g;
+      arow[o] = ro;
+      ++o;
+      ro += inst_off[g + 1] - inst_off[g];
+    }
+  }
+  if (threadIdx.x == 0) {
+    pre[G] = total;
+    *nact = total;
+    arow[total] = total_rows;
+    *sweep = s;
+    if (has_cond) cudaGraphSetConditional(cond, (!last && total > 0) ? 1u : 0u);
+  }
+}
+
+// Every instance active before the first sweep: act = 1, pre[g] = g,
+// *nact = G, ai[g] = g, arow = inst_off, no sweep done yet.
+__global__ void k_refine_init(int G, uint8_t* __restrict__ act, int* __restrict__ pre, int* __restrict__ nact,
+                              int* __restrict__ ai, int64_t* __restrict__ arow, const int64_t* __restrict__ inst_off,
+                              int* __restrict__ sweep) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < G) {
+    act[g] = 1;
+    ai[g] = g;
+  }
+  if (g <= G) {
+    pre[g] = g;
+    arow[g] = inst_off[g];
+  }
+  if (g == 0) {
+    *nact = G;
+    *sweep = 0;
+  }
+}
+
+// In-order compaction of the persistent solves' unit lists (blockIdx.y = 0:
+// forward, 1: backward) to the units whose instance range [rng.x, rng.y]
+// holds an active instance (pre = running count of active instances), in two
+// launches: CTA c counts its kCompactThreads units, then writes them at the
+// sum of the counts of CTAs 0..c-1; the last CTA stores the length.
+constexpr int kCompactThreads = 256;
+
+__device__ __forceinline__ bool unit_active(const int2* rng, int n, int u, const int* pre) {
+  return u < n && pre[rng[u].y + 1] > pre[rng[u].x];
+}
+
+__global__ void __launch_bounds__(kCompactThreads)
+k_compact_count(const int2* __restrict__ rf, int nf, const int2* __restrict__ rb, int nb, const int* __restrict__ pre,
+                int* __restrict__ cnt) {
+  const int y = blockIdx.y;
+  const int u = blockIdx.x * kCompactThreads + threadIdx.x;
+  const int c = __syncthreads_count(unit_active(y ? rb : rf, y ? nb : nf, u, pre));
+  if (threadIdx.x == 0) cnt[y * gridDim.x + blockIdx.x] = c;
+}
+
+__global__ void __launch_bounds__(kCompactThreads)
+k_compact_write(const SolveUnit* __restrict__ uf, const int2* __restrict__ rf, int nf, SolveUnit* __restrict__ cf,
+                const SolveUnit* __restrict__ ub, const int2* __restrict__ rb, int nb, SolveUnit* __restrict__ cb,
+                const int* __restrict__ pre, const int* __restrict__ cnt, int* __restrict__ ucount) {
+  __shared__ int s_part[kCompactThreads / 32], s_keep[kCompactThreads / 32];
+  const int y = blockIdx.y;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // offset of this CTA: the kept units of the CTAs before it
+  int part = 0;
+  for (int c = threadIdx.x; c < (int)blockIdx.x; c += kCompactThreads) part += cnt[y * gridDim.x + c];
+  part = __reduce_add_sync(kFull, part);
+  const int u = blockIdx.x * kCompactThreads + threadIdx.x;
+  const bool keep = unit_active(y ? rb : rf, y ? nb : nf, u, pre);
+  const unsigned bal = __ballot_sync(kFull, keep);
+  if (lane == 0) {
+    s_part[w] = part;
+    s_keep[w] = __popc(bal);
+  }
+  __syncthreads();
+  int off = 0, before = 0, kept = 0;
+  for (int q = 0; q < kCompactThreads / 32; ++q) {
+    off += s_part[q];
+    if (q < w) before += s_keep[q];
+    kept += s_keep[q];
+  }
+  if (keep) {
+    const int o = off + before + __popc(bal & ((1u << lane) - 1u));
+    (y ? cb : cf)[o] = (y ? ub : uf)[u];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) ucount[y] = off + kept;
 }
 
 __global__ void k_axpy(int64_t n, const double* __restrict__ y, double* __restrict__ x) {
@@ -1232,9 +1559,9 @@ void set_solve_attrs() {
   cudaFuncSetAttribute(k_backward<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSolveSmem);
   cudaFuncSetAttribute(k_backward<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSolveSmem);
   cudaFuncSetAttribute(k_forward_blk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kSolveSmem + 2 * 32 * kBS * (int)sizeof(T));
+                       kSolveSmem + kBlkExtra * (int)sizeof(T));
   cudaFuncSetAttribute(k_backward_blk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kSolveSmem + 2 * 32 * kBS * (int)sizeof(T));
+                       kSolveSmem + kBlkExtra * (int)sizeof(T));
   done_dev[dev].store(true, std::memory_order_release);
 }
 
@@ -1272,7 +1599,7 @@ int forward_impl(bool trans, const SymDev& sd, const LevelPlan& lp, const int32_
     }
     const int rc = pick_rc(G.count, K, R, G.maxF, sizeof(T));
     const dim3 grid(G.count, K, (R + rc - 1) / rc);
-    const size_t smem = (size_t)rc * G.maxF * sizeof(T) + (trans ? 0 : 2 * 32 * kBS * sizeof(T));
+    const size_t smem = (size_t)rc * G.maxF * sizeof(T) + (trans ? 0 : kBlkExtra * sizeof(T));
     if (trans)
       k_forward<T, true><<<grid, kSolveThreads, smem, st>>>(sd, d_all + G.off, (const T*)fronts, rhs,
                                                             rhs_mode, (T*)V, R, K, rc);
@@ -1309,7 +1636,7 @@ int backward_impl(bool trans, const SymDev& sd, const LevelPlan& lp, const int32
     }
     const int rc = pick_rc(G.count, K, R, G.maxF, sizeof(T));
     const dim3 grid(G.count, K, (R + rc - 1) / rc);
-    const size_t smem = (size_t)rc * G.maxF * sizeof(T) + (trans ? 0 : 2 * 32 * kBS * sizeof(T));
+    const size_t smem = (size_t)rc * G.maxF * sizeof(T) + (trans ? 0 : kBlkExtra * sizeof(T));
     if (trans)
       k_backward<T, true><<<grid, kSolveThreads, smem, st>>>(sd, d_all + G.off, (const T*)fronts,
                                                              (const T*)V, out, acc, R, K, rc);
@@ -1323,6 +1650,19 @@ int backward_impl(bool trans, const SymDev& sd, const LevelPlan& lp, const int32
 }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// SMs of the current device (read once per device)
+unsigned sm_count() {
+  static std::atomic<int> nsm_dev[kMaxDevices];
+  const int dev = current_device();
+  int nsm = nsm_dev[dev].load(std::memory_order_acquire);
+  if (!nsm) {
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    nsm = std::max(nsm, 1);
+    nsm_dev[dev].store(nsm, std::memory_order_release);
+  }
+  return (unsigned)nsm;
+}
 
 }  // namespace
 
@@ -1353,10 +1693,10 @@ int launch_backward_level(int precision, bool trans, const SymDev& sd, const Lev
 
 namespace {
 template <typename T, int M>
-int persistent_launch(bool forward, const SymDev& sd, const SolveUnit* units, int nunits, int* ticket,
-                      int* done, int* err, const int* nch, const int32_t* d_all, const void* fronts,
-                      const double* rhs, int rhs_mode, void* V, double* out, double* acc, int R, int K,
-                      size_t smem, int64_t polls, cudaStream_t st) {
+int persistent_launch(bool forward, const SymDev& sd, const SolveUnit* units, int nunits, const int* ucount,
+                      const uint8_t* act, int* ticket, int* done, int* err, const int* nch,
+                      const int32_t* d_all, const void* fronts, const double* rhs, int rhs_mode, void* V,
+                      double* out, double* acc, int R, int K, size_t smem, int64_t polls, cudaStream_t st) {
   static std::atomic<int> nsm_dev[kMaxDevices];
   const int dev = current_device();
   int nsm = nsm_dev[dev].load(std::memory_order_acquire);
@@ -1374,50 +1714,50 @@ int persistent_launch(bool forward, const SymDev& sd, const SolveUnit* units, in
   const int grid = std::max(1, std::min(nunits, std::max(1, occ) * std::max(nsm, 1)));
   if (forward)
     k_solve_persistent<T, true, M><<<grid, kSolveThreads, smem, st>>>(
-        sd, units, nunits, ticket, done, err, nch, d_all, (const T*)fronts, rhs, rhs_mode, (T*)V, out, acc, R, K,
-        polls);
+        sd, units, nunits, ucount, act, ticket, done, err, nch, d_all, (const T*)fronts, rhs, rhs_mode, (T*)V,
+        out, acc, R, K, polls);
   else
     k_solve_persistent<T, false, M><<<grid, kSolveThreads, smem, st>>>(
-        sd, units, nunits, ticket, done, err, nch, d_all, (const T*)fronts, rhs, rhs_mode, (T*)V, out, acc, R, K,
-        polls);
+        sd, units, nunits, ucount, act, ticket, done, err, nch, d_all, (const T*)fronts, rhs, rhs_mode, (T*)V,
+        out, acc, R, K, polls);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 template <typename T>
-int persistent_impl(bool forward, const SymDev& sd, const SolveUnit* units, int nunits, int* ticket,
-                    int* done, int* err, const int* nch, const int32_t* d_all, const void* fronts, const double* rhs,
-                    int rhs_mode, void* V, double* out, double* acc, int R, int K, int max_blk_F, int ctas,
-                    int64_t polls, cudaStream_t st) {
+int persistent_impl(bool forward, const SymDev& sd, const SolveUnit* units, int nunits, const int* ucount,
+                    const uint8_t* act, int* ticket, int* done, int* err, const int* nch, const int32_t* d_all,
+                    const void* fronts, const double* rhs, int rhs_mode, void* V, double* out, double* acc, int R,
+                    int K, int max_blk_F, int ctas, int64_t polls, cudaStream_t st) {
   if (polls <= 0) polls = kWaitPolls;
   if (nunits == 0) return 0;
   const size_t seg_smem = (size_t)(kSolveThreads / 32) * 32 * kRW * sizeof(T);  // y staging per warp
   const size_t mF = (size_t)std::max(max_blk_F, 1);
-  const size_t blk_smem = (size_t)(2 * 32 * kBS + kSolveChunk * mF) * sizeof(T);
+  const size_t blk_smem = (size_t)(kBlkExtra + kSolveChunk * mF) * sizeof(T);
   const size_t smem = std::max(seg_smem, blk_smem);
   if (smem > 200 * 1024) return -1;
   if (ctas <= 0) ctas = sizeof(T) == 4 ? 3 : 2;
   if (ctas >= 4)
-    return persistent_launch<T, 4>(forward, sd, units, nunits, ticket, done, err, nch, d_all, fronts, rhs,
-                                   rhs_mode, V, out, acc, R, K, smem, polls, st);
+    return persistent_launch<T, 4>(forward, sd, units, nunits, ucount, act, ticket, done, err, nch, d_all,
+                                   fronts, rhs, rhs_mode, V, out, acc, R, K, smem, polls, st);
   if (ctas == 3)
-    return persistent_launch<T, 3>(forward, sd, units, nunits, ticket, done, err, nch, d_all, fronts, rhs,
-                                   rhs_mode, V, out, acc, R, K, smem, polls, st);
-  return persistent_launch<T, 2>(forward, sd, units, nunits, ticket, done, err, nch, d_all, fronts, rhs,
-                                 rhs_mode, V, out, acc, R, K, smem, polls, st);
+    return persistent_launch<T, 3>(forward, sd, units, nunits, ucount, act, ticket, done, err, nch, d_all,
+                                   fronts, rhs, rhs_mode, V, out, acc, R, K, smem, polls, st);
+  return persistent_launch<T, 2>(forward, sd, units, nunits, ucount, act, ticket, done, err, nch, d_all,
+                                 fronts, rhs, rhs_mode, V, out, acc, R, K, smem, polls, st);
 }
 
 }  // namespace
 
 int launch_solve_persistent(int precision, bool forward, const SymDev& sd, const SolveUnit* units,
-                            int nunits, int* ticket, int* done, int* err, const int* nch,
-                            const int32_t* d_all, const void* fronts, const double* rhs,
-                            int rhs_mode, void* V, double* out, double* acc, int32_t R, int32_t K,
-                            int32_t max_blk_F, int32_t ctas, int64_t polls, cudaStream_t st) {
+                            int nunits, const int* ucount, const uint8_t* act, int* ticket, int* done,
+                            int* err, const int* nch, const int32_t* d_all, const void* fronts,
+                            const double* rhs, int rhs_mode, void* V, double* out, double* acc, int32_t R,
+                            int32_t K, int32_t max_blk_F, int32_t ctas, int64_t polls, cudaStream_t st) {
   if (precision == PISP_FP32)
-    return persistent_impl<float>(forward, sd, units, nunits, ticket, done, err, nch, d_all, fronts,
-                                  rhs, rhs_mode, V, out, acc, R, K, max_blk_F, ctas, polls, st);
-  return persistent_impl<double>(forward, sd, units, nunits, ticket, done, err, nch, d_all, fronts,
-                                 rhs, rhs_mode, V, out, acc, R, K, max_blk_F, ctas, polls, st);
+    return persistent_impl<float>(forward, sd, units, nunits, ucount, act, ticket, done, err, nch, d_all,
+                                  fronts, rhs, rhs_mode, V, out, acc, R, K, max_blk_F, ctas, polls, st);
+  return persistent_impl<double>(forward, sd, units, nunits, ucount, act, ticket, done, err, nch, d_all,
+                                 fronts, rhs, rhs_mode, V, out, acc, R, K, max_blk_F, ctas, polls, st);
 }
 
 int launch_combine(const SymDev& sd, const double* X, const Shifts& sh, int32_t R, double* x,
@@ -1430,10 +1770,56 @@ int launch_combine(const SymDev& sd, const double* X, const Shifts& sh, int32_t 
 
 int launch_residual_per_k(const SymDev& sd, const double* vals, const double* D,
                           const Shifts& sh, const double* b, const double* X, int32_t R,
-                          double* Rk, cudaStream_t st) {
+                          double* Rk, const ActiveSet& as, int mode, cudaStream_t st) {
   if (sd.N == 0) return 0;
-  k_residual_per_k<<<blocks_for(sd.N * 32, 256), 256, 0, st>>>(sd, vals, D, sh, b, X, R, Rk);
+  unsigned grid = blocks_for(sd.N * 32, 256);
+  if (mode == kResActive) grid = std::min<unsigned>(grid, 16u * sm_count());  // rows known on the device only
+  k_residual_per_k<<<grid, 256, 0, st>>>(sd, vals, D, sh, b, X, R, Rk, as, mode);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_refine_stats(const SymDev& sd, const ActiveSet& as, int all, const double* X, const double* Y,
+                        int32_t K, int32_t R, unsigned long long* dmax, unsigned long long* xmax,
+                        cudaStream_t st) {
+  if (sd.N == 0 || R < 1) return 0;
+  const unsigned grid = std::min<unsigned>((unsigned)((sd.N + kStatRows - 1) / kStatRows), 8u * sm_count());
+  k_refine_stats<<<grid, kStatThreads, 0, st>>>(sd, as, all, X, Y, K, R, dmax, xmax);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_refine_decide(int32_t G, int32_t R, double tol, int32_t S, int32_t* sweep,
+                         cudaGraphConditionalHandle cond, int has_cond, uint8_t* act, unsigned long long* dmax,
+                         unsigned long long* xmax, double* prevd, int32_t* nsw, int32_t* pre, int32_t* nact,
+                         int32_t* ai, int64_t* arow, const int64_t* inst_off, cudaStream_t st) {
+  if (G < 1) return 0;
+  k_refine_decide<<<1, kDecideThreads, 0, st>>>(G, R, tol, S, sweep, cond, has_cond, act, dmax, xmax, prevd, nsw,
+                                                pre, nact, ai, arow, inst_off);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_refine_init(int32_t G, uint8_t* act, int32_t* pre, int32_t* nact, int32_t* ai, int64_t* arow,
+                       const int64_t* inst_off, int32_t* sweep, cudaStream_t st) {
+  if (G < 1) return 0;
+  k_refine_init<<<blocks_for((int64_t)G + 1, 256), 256, 0, st>>>(G, act, pre, nact, ai, arow, inst_off, sweep);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int compact_scratch(int32_t nf, int32_t nb) {
+  return 2 * (int)((std::max(nf, nb) + kCompactThreads - 1) / kCompactThreads);
+}
+
+int launch_compact_units(const SolveUnit* uf, const int32_t* rf, int32_t nf, SolveUnit* cf, const SolveUnit* ub,
+                         const int32_t* rb, int32_t nb, SolveUnit* cb, const int32_t* pre, int32_t* cnt,
+                         int32_t* ucount, cudaStream_t st) {
+  const int gx = compact_scratch(nf, nb) / 2;
+  if (gx == 0) return 0;
+  const dim3 grid(gx, 2);
+  const int2* f2 = reinterpret_cast<const int2*>(rf);
+  const int2* b2 = reinterpret_cast<const int2*>(rb);
+  k_compact_count<<<grid, kCompactThreads, 0, st>>>(f2, nf, b2, nb, pre, cnt);
+  if (cudaGetLastError() != cudaSuccess) return -1;
+  k_compact_write<<<grid, kCompactThreads, 0, st>>>(uf, f2, nf, cf, ub, b2, nb, cb, pre, cnt, ucount);
+  return cudaGetLastError() == cudaSuccess ? 2 : -1;
 }
 
 int launch_residual_T_per_k(const SymDev& sd, const double* vals, const double* D,

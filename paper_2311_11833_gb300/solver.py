@@ -267,6 +267,27 @@ class Solver:
         unreachable=True makes one wait run out on purpose (test hook)."""
         check(self._lib.pisp_set_wait_limit(self._h, int(polls), 1 if unreachable else 0), self._h)
 
+    def set_refinement(self, tol: float = 0.0):
+        """pisp_set_refinement: tol > 0 makes `sweeps` a maximum and stops each
+        instance's FP64 residual sweeps on its own (converged or stagnated);
+        tol = 0 restores fixed sweeps."""
+        check(self._lib.pisp_set_refinement(self._h, float(tol)), self._h)
+        return self
+
+    def refinement_stats(self, max_sweeps: int = 0, rows: bool = False):
+        """pisp_refinement_stats: (sweeps each instance took in the last solve
+        [G], fraction of the solve work each sweep 1..max_sweeps covered[,
+        fraction of the rows]); rows=True adds the third array."""
+        nsw = np.zeros(self.G, dtype=np.int32)
+        work = np.zeros(max(int(max_sweeps), 0), dtype=np.float64)
+        frow = np.zeros_like(work)
+        self._sync_stream()
+        check(self._lib.pisp_refinement_stats(self._h, nsw.ctypes.data_as(ctypes.c_void_p),
+                                              work.ctypes.data_as(ctypes.c_void_p) if work.size else None,
+                                              frow.ctypes.data_as(ctypes.c_void_p) if frow.size else None,
+                                              int(max_sweeps)), self._h)
+        return (nsw, work, frow) if rows else (nsw, work)
+
     def status(self):
         """pisp_get_status: (worst code, per-(instance, k) codes, first failing columns)."""
         st = np.zeros(self.G * self.K, dtype=np.int32)

@@ -19,11 +19,13 @@ step the library captures in a CUDA graph (factor + solve + sweeps), and
 returns the fastest among those whose result stays accurate: the options
 change only rounding, but with FP32 factors a different amalgamation can
 leave the sweeps short of the FP64 result, so every candidate's x is compared
-entry by entry with an FP64-factor solve with two FP64 residual sweeps
-(default options) of the same inputs and rejected beyond `tol` (max |x - ref|
-/ max |ref| per right-hand side).  The sweeps matter for the reference too: a
-pivot-free FP64 solve alone can be 5e-10 away from the definition on an
-ill-conditioned instance of a batch.  The default search is staged: first the solve tiling
+entry by entry with an FP64-factor solve with FP64 residual sweeps (default
+options) of the same inputs and rejected beyond `tol` (max |x - ref| / max
+|ref| per instance and right-hand side).  The sweeps matter for the
+reference too: a pivot-free FP64 solve alone can be 2e-10 away from the
+definition on an ill-conditioned instance of a batch.  With refine_tol > 0
+the candidates and the reference run the adaptive sweeps of
+pisp_set_refinement.  The default search is staged: first the solve tiling
 with the default amalgamation and factor policy, then the amalgamation and
 factor policy with the best tiling.  Results are cached in a JSON file (path
 from $PISP_TUNE_CACHE, or the `cache` argument) keyed by a hash of the
@@ -78,11 +80,11 @@ def _stage2(best: dict):
     return out
 
 
-def _key(sizes, row_ptr, col, K, R, precision, sweeps) -> str:
+def _key(sizes, row_ptr, col, K, R, precision, sweeps, refine_tol=0.0) -> str:
     h = hashlib.sha256()
     for a in (np.asarray(sizes, np.int64), np.asarray(row_ptr, np.int64), np.asarray(col, np.int32)):
         h.update(np.ascontiguousarray(a).tobytes())
-    return f"{h.hexdigest()[:24]}-K{K}-R{R}-{precision}-s{sweeps}"
+    return f"{h.hexdigest()[:24]}-K{K}-R{R}-{precision}-s{sweeps}-a{refine_tol:g}"
 
 
 def _load(path):
@@ -93,18 +95,25 @@ def _load(path):
         return {}
 
 
-def _entrywise(x, ref) -> float:
-    """max over right-hand sides of max |x - ref| / max |ref| (on the device)."""
+def _entrywise(x, ref, inst) -> float:
+    """max over instances g and right-hand sides r of max_{i in g} |x_ir - ref_ir| /
+    max_{i in g} |ref_ir| (on the device; inst = the instance of each row)."""
     import torch
-    scale = ref.abs().amax(dim=0).clamp_min(torch.finfo(ref.dtype).tiny)
-    err = ((x - ref).abs().amax(dim=0) / scale).max()
+    G = int(inst[-1]) + 1 if inst.numel() else 0
+    idx = inst[:, None].expand_as(ref)
+    z = torch.zeros(G, ref.shape[1], dtype=ref.dtype, device=ref.device)
+    scale = z.scatter_reduce(0, idx, ref.abs(), "amax").clamp_min(torch.finfo(ref.dtype).tiny)
+    diff = z.scatter_reduce(0, idx, (x - ref).abs(), "amax")
+    err = (diff / scale).max()
     return float(err) if torch.isfinite(err) else float("inf")
 
 
-def _time(Solver, sizes, row_ptr, col, values, D, t, b, x, precision, sweeps, reps, opts, ref=None):
+def _time(Solver, sizes, row_ptr, col, values, D, t, b, x, precision, sweeps, reps, opts, ref=None, inst=None,
+          refine_tol=0.0):
     import torch
     s = Solver(sizes, row_ptr, col, **opts)
     try:
+        s.set_refinement(refine_tol)
         s.graph_capture(values, D, t, b, x, precision=precision, sweeps=sweeps)
         for _ in range(2):
             s.graph_launch()
@@ -115,43 +124,51 @@ def _time(Solver, sizes, row_ptr, col, values, D, t, b, x, precision, sweeps, re
             s.graph_launch()
         ev[1].record()
         ev[1].synchronize()
-        err = _entrywise(x, ref) if ref is not None else None
+        err = _entrywise(x, ref, inst) if ref is not None else None
         return ev[0].elapsed_time(ev[1]) / reps, err
     finally:
         s.close()
 
 
 def autotune(sizes, row_ptr, col, values, D, t, b, precision="fp32", sweeps=2, reps=5,
-             cache: str | None = None, options=None, tol: float = 3e-11) -> dict:
+             cache: str | None = None, options=None, tol: float = 5e-11, refine_tol: float = 0.0) -> dict:
     """Fastest options for this pattern / call shape: {"options": {...}, "ms": ..., "all": [...]}.
 
     options: an explicit candidate list (timed as given); default: the staged
-    search over the solve tiling, then the amalgamation and factor policy."""
+    search over the solve tiling, then the amalgamation and factor policy.
+    refine_tol > 0: the candidates run adaptive sweeps (pisp_set_refinement)
+    with at most `sweeps` sweeps.  tol bounds the entry-wise difference, per
+    instance, from the reference."""
     import torch
 
     from .solver import Solver
 
     cache = cache or os.environ.get("PISP_TUNE_CACHE")
     R = b.shape[1] if b.dim() == 2 else 1
-    key = _key(sizes, row_ptr, col, len(t), R, precision, sweeps)
+    key = _key(sizes, row_ptr, col, len(t), R, precision, sweeps, refine_tol)
     if cache:
         hit = _load(cache).get(key)
         if hit:
             return hit
     b2 = b.reshape(b.shape[0], -1).contiguous()
     x = torch.empty_like(b2)
-    # the accuracy reference: FP64 factors and two FP64 sweeps, default options
+    inst = torch.repeat_interleave(torch.arange(len(sizes), device=b2.device),
+                                   torch.as_tensor(np.asarray(sizes, np.int64), device=b2.device))
+    # the accuracy reference: FP64 factors, default options, FP64 sweeps (two
+    # fixed, or adaptive up to four)
     sref = Solver(sizes, row_ptr, col)
     try:
+        sref.set_refinement(refine_tol)
         sref.factor(values, D, t, "fp64")
-        ref = sref.solve(b2, sweeps=2).clone()
+        ref = sref.solve(b2, sweeps=4 if refine_tol > 0 else 2).clone()
     finally:
         sref.close()
     results = []
 
     def run(cands):
         for opts in cands:
-            ms, err = _time(Solver, sizes, row_ptr, col, values, D, t, b2, x, precision, sweeps, reps, opts, ref)
+            ms, err = _time(Solver, sizes, row_ptr, col, values, D, t, b2, x, precision, sweeps, reps, opts, ref,
+                            inst, refine_tol)
             results.append({"options": opts, "ms": ms, "err": err, "ok": bool(err <= tol)})
 
     def fastest():

@@ -3,6 +3,7 @@
 import json
 
 import numpy as np
+import pytest
 import torch
 
 import pfgen
@@ -28,6 +29,27 @@ def test_key_depends_on_pattern_and_call_shape():
               tune._key([inst.n], inst.row_ptr, inst.col, 4, 2, "fp64", 2),
               tune._key([inst.n], inst.row_ptr, inst.col, 4, 2, "fp32", 1)}
     assert k not in others and len(others) == 5
+
+
+def test_key_depends_on_adaptive_sweeps():
+    inst = pfgen.make_instance("plain")
+    a = tune._key([inst.n], inst.row_ptr, inst.col, 4, 2, "fp32", 8)
+    b = tune._key([inst.n], inst.row_ptr, inst.col, 4, 2, "fp32", 8, 1e-12)
+    c = tune._key([inst.n], inst.row_ptr, inst.col, 4, 2, "fp32", 8, 1e-11)
+    assert len({a, b, c}) == 3
+
+
+def test_accuracy_guard_is_per_instance():
+    """An error small against the batch's largest entry but large against its
+    own instance's entries is caught."""
+    ref = torch.tensor([[1000.0, 1.0], [-1000.0, 2.0], [1e-3, 1.0], [-2e-3, 4.0]], dtype=torch.float64)
+    x = ref.clone()
+    x[2, 0] += 1e-6
+    inst = torch.tensor([0, 0, 1, 1])
+    assert tune._entrywise(x, ref, inst) == pytest.approx(5e-4, rel=1e-9)
+    assert tune._entrywise(ref, ref, inst) == 0.0
+    x[3, 1] = float("nan")
+    assert tune._entrywise(x, ref, inst) == float("inf")
 
 
 def test_cache_hit_returns_without_timing(tmp_path):
