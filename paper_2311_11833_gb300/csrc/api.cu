@@ -732,10 +732,10 @@ int sweep_fractions(pisp_handle* h, int max_sweeps, std::vector<int32_t>& nsw, s
   return PISP_OK;
 }
 
-// Algorithmic bytes of one forward + backward pass of the persistent
-// schedule with accumulation (all instances), as the brackets count them.
+// Algorithmic bytes of one forward + backward pass (all instances), as the
+// brackets count them.
 double solve_bytes(const pisp_handle* h, int32_t R) {
-  double b = 16.0 * h->sym.N * h->K * R;
+  double b = 0.0;
   for (int l = 0; l < h->sym.n_levels; ++l)
     b += h->K * (h->plans[l].bytes_fwd_a + h->plans[l].bytes_fwd_b * R + h->plans[l].bytes_bwd_a +
                  h->plans[l].bytes_bwd_b * R);
@@ -745,9 +745,9 @@ double solve_bytes(const pisp_handle* h, int32_t R) {
 // One adaptive sweep for the instances still iterating: the FP64 residuals
 // of their rows, the gated solves of their corrections (compacted unit lists
 // of the persistent schedule; the per-level schedule solves every row, with
-// zero residuals outside the active set), their correction and solution
-// sizes, the stopping test and the active set and unit lists of the next
-// sweep.  s_host: the sweep number in a host loop (brackets and launch
+// zero residuals outside the active set), the corrections added to their
+// solutions with the correction and solution sizes, the stopping test and
+// the active set and unit lists of the next sweep.  s_host: the sweep number in a host loop (brackets and launch
 // accounting), 0 inside a device-side loop (no brackets: a conditional body
 // holds no events).  has_cond: the stopping test drives the loop's
 // conditional `cond`.
@@ -768,7 +768,8 @@ int sweep_body(pisp_handle* h, const double* rhs, double* X_out, int32_t R, int3
            nullptr, s_host);
   const bool prof_was = h->prof_on;
   if (s_host == 0) h->prof_on = false;
-  const int rc = solve_pass(h, false, h->Rk.as<double>(), pisp::RHS_PER_K, h->Y.as<double>(), X_out, R,
+  // the corrections go to Y only: the stats launch below adds them to X
+  const int rc = solve_pass(h, false, h->Rk.as<double>(), pisp::RHS_PER_K, h->Y.as<double>(), nullptr, R,
                             persistent ? act : nullptr, s_host);
   h->prof_on = prof_was;
   TRY(rc);
@@ -790,7 +791,7 @@ int sweep_body(pisp_handle* h, const double* rhs, double* X_out, int32_t R, int3
     TRY(count(h, c));
     m += c;
   }
-  prof_end(h, pb, PISP_PROF_REFINE, 2.0 * N * KR * 8.0, n + m, nullptr, s_host);
+  prof_end(h, pb, PISP_PROF_REFINE, 3.0 * N * KR * 8.0, n + m, nullptr, s_host);
   return PISP_OK;
 }
 
@@ -889,7 +890,7 @@ int solve_core(pisp_handle* h, const double* rhs, double* X_out, int32_t R, int3
     if (pb >= 0) {  // the loop as one bracket; bytes and launches are scaled at collection
       record_event(h, h->prof_ev[pb + 1], h->stream);
       h->prof_br.push_back({PISP_PROF_SWEEP_LOOP, pb, pb + 1, h->loop_kernels, 0.0, -1,
-                            h->sym.nnzA * 12.0 + N * 20.0 + N * R * 8.0 + 4.0 * N * KR * 8.0, solve_bytes(h, R)});
+                            h->sym.nnzA * 12.0 + N * 20.0 + N * R * 8.0 + 5.0 * N * KR * 8.0, solve_bytes(h, R)});
     }
     return PISP_OK;
   }

@@ -1255,8 +1255,10 @@ __global__ void k_residual(SymDev sd, const double* __restrict__ vals, const dou
 }
 
 // ---- adaptive FP64 residual sweeps -----------------------------------------
-// After sweep s, every instance g still iterating gets the size of its last
-// correction d_s and of its solution, per right-hand side r:
+// After the correction solves of sweep s, every instance g still iterating
+// takes its correction, X += Y (FP64, one addition per entry: the sum the
+// backward solve's accumulation would form), and gets the size of the
+// correction d_s and of the new solution, per right-hand side r:
 //   dmax[g][r] = max over its rows i and over k of |Y[pi][k][r]|,
 //   xmax[g][r] = max over its rows i and over k of |X[pi][k][r]|.
 // CTAs stride over chunks of kStatRows rows of the active set (all = 1:
@@ -1271,7 +1273,7 @@ constexpr int kStatThreads = 256;
 constexpr int kStatRows = 64;
 
 __global__ void __launch_bounds__(kStatThreads)
-k_refine_stats(SymDev sd, ActiveSet as, int all, const double* __restrict__ X, const double* __restrict__ Y, int K,
+k_refine_stats(SymDev sd, ActiveSet as, int all, double* __restrict__ X, const double* __restrict__ Y, int K,
                int R, unsigned long long* __restrict__ dmax, unsigned long long* __restrict__ xmax) {
   __shared__ unsigned long long s_d[kStatThreads], s_x[kStatThreads];
   const int nact = all ? 0 : *as.nact;
@@ -1298,8 +1300,11 @@ k_refine_stats(SymDev sd, ActiveSet as, int all, const double* __restrict__ X, c
           if (j < nj && r < R) {
             for (int64_t m = j; m < npair; m += nj) {
               const int64_t o = ((int64_t)sd.iperm[i0 + m / K] * K + (int)(m % K)) * R + r;
-              md = max(md, (unsigned long long)__double_as_longlong(fabs(Y[o])));
-              mx = max(mx, (unsigned long long)__double_as_longlong(fabs(X[o])));
+              const double y = Y[o];
+              const double xn = X[o] + y;
+              X[o] = xn;
+              md = max(md, (unsigned long long)__double_as_longlong(fabs(y)));
+              mx = max(mx, (unsigned long long)__double_as_longlong(fabs(xn)));
             }
           }
           s_d[tid] = md;
@@ -1778,11 +1783,11 @@ int launch_residual_per_k(const SymDev& sd, const double* vals, const double* D,
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
-int launch_refine_stats(const SymDev& sd, const ActiveSet& as, int all, const double* X, const double* Y,
+int launch_refine_stats(const SymDev& sd, const ActiveSet& as, int all, double* X, const double* Y,
                         int32_t K, int32_t R, unsigned long long* dmax, unsigned long long* xmax,
                         cudaStream_t st) {
   if (sd.N == 0 || R < 1) return 0;
-  const unsigned grid = std::min<unsigned>((unsigned)((sd.N + kStatRows - 1) / kStatRows), 8u * sm_count());
+  const unsigned grid = std::min<unsigned>((unsigned)((sd.N + kStatRows - 1) / kStatRows), 32u * sm_count());
   k_refine_stats<<<grid, kStatThreads, 0, st>>>(sd, as, all, X, Y, K, R, dmax, xmax);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
