@@ -46,11 +46,12 @@ L2_BYTES = 129 * 1024 * 1024
 # to the full workload where the capture ran a reduced batch); an entry is
 # removed when its kernel changes.
 # Keys: (workload, family, instances, library options as sorted (name, value) pairs).
-BATCH_TUNED = (("factor_policy", 4), ("relax_small", 16), ("relax_zeros", 0.1), ("solve_ctas_per_sm", 4),
-               ("solve_kfuse", 2), ("solve_schedule", 0), ("solve_warp_maxF", 64))
+BATCH_TUNED = (("factor_ctas_per_sm", 3), ("factor_policy", 4), ("factor_smem_maxF", 128), ("relax_small", 16),
+               ("relax_zeros", 0.1), ("solve_ctas_per_sm", 4), ("solve_kfuse", 1), ("solve_schedule", 0),
+               ("solve_warp_maxF", 64))
 TRAFFIC_PER_LAUNCH = {
-    ("batching", "backward", 256, BATCH_TUNED): 662.64e6,          # 580.96 MB read + 81.68 MB written
-    ("batching", "factor_persistent", 256, BATCH_TUNED): 1348.22e6,  # 611.18 MB read + 737.04 MB written
+    ("batching", "backward", 256, BATCH_TUNED): 670.31e6,            # 586.72 MB read + 83.59 MB written
+    ("batching", "factor_persistent", 256, BATCH_TUNED): 1378.02e6,  # 619.55 MB read + 758.47 MB written
 }
 
 # factor precision and FP64 residual sweeps per workload; refine_tol > 0:

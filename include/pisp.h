@@ -326,9 +326,10 @@ int pisp_set_wait_limit(pisp_handle* h, int64_t polls, int32_t unreachable);
  * refinement (Demmel, Hida, Kahan, Li, Mukherjee, Riedy, ACM TOMS 32(2),
  * 2006) with the contraction estimated from successive corrections: per RHS
  * r, with d_s = the largest |correction| of sweep s over the instance's
- * rows and all k, and rho = d_s / d_{s-1} (d_0 = the largest |x_k|), r has
+ * rows and all k, and from the second sweep on rho = d_s / d_{s-1}, r has
  * converged when d_s = 0 or when rho < 1/2 and rho / (1 - rho) d_s <=
- * tol * max |x_k|, and has stagnated when rho >= 1/2 from the second sweep on.
+ * tol * max |x_k|, and has stagnated when rho >= 1/2.  After the first sweep
+ * only d_1 = 0 stops an instance.
  * The instance stops when all its right-hand sides have converged or
  * stagnated; the later sweeps skip its rows and fronts (the solve kernels
  * walk only the work units of the instances still iterating).  tol = 0

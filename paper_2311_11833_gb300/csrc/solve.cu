@@ -1361,12 +1361,14 @@ __device__ V block_excl_scan(V v, V* sh, V& total) {
 // the device, so that the same launch serves every sweep of a device-side
 // loop).  For each instance g still iterating: the stopping test of
 // extra-precise iterative refinement (Demmel, Hida, Kahan, Li, Mukherjee,
-// Riedy, ACM TOMS 2006), with the contraction per sweep estimated from
-// successive corrections.  Per right-hand side, rho = |d_s| / |d_{s-1}|
-// (|d_0| = the solution's size): converged when |d_s| = 0, or when rho < 1/2
-// and rho / (1 - rho) |d_s| <= tol |x| (the error that a contraction by rho
-// per sweep leaves); stagnating when rho >= 1/2 from the second sweep on
-// (further sweeps no longer reduce the error).  The instance stops when every
+// Riedy, ACM TOMS 2006), with the contraction per sweep estimated from two
+// successive corrections, so from the second sweep on.  Per right-hand side,
+// rho = |d_s| / |d_{s-1}|: converged when |d_s| = 0, or (s >= 2) when rho <
+// 1/2 and rho / (1 - rho) |d_s| <= tol |x| (the error that a contraction by
+// rho per sweep leaves); stagnating when rho >= 1/2 (s >= 2: further sweeps
+// no longer reduce the error).  After the first sweep only |d_1| = 0 stops:
+// |d_1| / |x| is the first solve's error, which can understate the
+// contraction by orders of magnitude.  The instance stops when every
 // right-hand side has converged or stagnated, or after sweep S; nsw[g] = the
 // sweeps it took.  dmax / xmax are zeroed for the next sweep.  Then the
 // active set: pre[g] = the active instances before g (pre[G] = their number =
@@ -1392,12 +1394,12 @@ k_refine_decide(int G, int R, double tol, int S, int* __restrict__ sweep, cudaGr
       const double x = __longlong_as_double((long long)xmax[q]);
       dmax[q] = 0;
       xmax[q] = 0;
-      const double p = s == 1 ? x : prevd[q];
+      const double p = prevd[q];
       prevd[q] = d;
       bool done_r = d == 0.0;
-      if (!done_r) {
+      if (!done_r && s >= 2) {
         const double rho = d / p;  // NaN: neither test holds
-        done_r = rho < 0.5 ? rho / (1.0 - rho) * d <= tol * x : (s >= 2 && rho >= 0.5);
+        done_r = rho < 0.5 ? rho / (1.0 - rho) * d <= tol * x : rho >= 0.5;
       }
       all = all && done_r;
     }

@@ -92,6 +92,26 @@ def test_adaptive_fp32_every_instance(pisp, batch, opts):
     s.close()
 
 
+def test_no_stop_after_the_first_sweep(pisp, batch):
+    """The contraction is estimated from two successive corrections, so even a
+    loose tolerance stops no instance before its second sweep."""
+    s, x, nsw, work, errs = _run(pisp, batch, tol=1e-3)
+    assert (nsw == 2).all(), nsw.tolist()
+    s.close()
+
+
+def test_looser_tolerance_on_instances_that_converge_fast(pisp):
+    """Instances whose first solve is accurate: with tol 1e-11 the first
+    sweep's correction, divided by the solution, understates the contraction
+    of the sweeps; stopping only on two successive corrections keeps them
+    within the bound."""
+    data = _batch([130, 15, 211, 190, 234], 8)
+    s, x, nsw, work, errs = _run(pisp, data, tol=1e-11)
+    assert max(errs) <= TOL, (errs, nsw.tolist())
+    assert (nsw >= 2).all()
+    s.close()
+
+
 def test_fixed_three_sweeps_fall_short_on_the_hard_instances(pisp, batch):
     """The reason for the adaptive mode: three fixed sweeps miss the bound on
     an instance of the batch (a property of the inputs, kept as a guard that
