@@ -1141,14 +1141,13 @@ __device__ __forceinline__ int active_slot(const int64_t* arow, int n, int64_t a
 }
 
 // Rk[pi][k][r] = b[i][r] - sum_j A_ij X[pj][k][r] - t_k D_i X[pi][k][r] for one
-// original row i (FP64), by one warp.
+// row (original index i, permuted pi), FP64, by one warp.
 __device__ __forceinline__ void residual_row(const SymDev& sd, const double* __restrict__ vals,
                                              const double* __restrict__ D, const Shifts& sh,
                                              const double* __restrict__ b, const double* __restrict__ X, int R,
-                                             double* __restrict__ Rk, int64_t i, int lane) {
+                                             double* __restrict__ Rk, int64_t i, int64_t pi, int lane) {
   const int K = sh.K;
   const int KR = K * R;
-  const int64_t pi = sd.iperm[i];
   const int64_t e0 = sd.row_ptr[i], e1 = sd.row_ptr[i + 1];
   const double di = D[i];
   if (e1 - e0 <= 32) {
@@ -1186,7 +1185,9 @@ __device__ __forceinline__ void residual_row(const SymDev& sd, const double* __r
 }
 
 // The FP64 residuals of the perturbed systems, one warp per row, warps
-// striding over the rows (rows as ResidualMode selects).
+// striding over the rows (rows as ResidualMode selects) in the permuted order,
+// where an instance's rows keep its range: the writes of Rk and the reads of
+// the row's own X are sequential.
 
 __global__ void k_residual_per_k(SymDev sd, const double* __restrict__ vals,
                                  const double* __restrict__ D, Shifts sh,
@@ -1202,17 +1203,18 @@ __global__ void k_residual_per_k(SymDev sd, const double* __restrict__ vals,
     total = as.arow[nact];
   }
   for (int64_t a = w0; a < total; a += nw) {  // warp-uniform
-    int64_t i = a;
+    int64_t pi = a;  // an instance's permuted rows are its original range
     if (mode == kResActive) {
       const int q = active_slot(as.arow, nact, a);
-      i = as.inst_off[as.ai[q]] + (a - as.arow[q]);
-    } else if (mode == kResZeroStopped && !as.act[sd.row_inst[i]]) {
+      pi = as.inst_off[as.ai[q]] + (a - as.arow[q]);
+    }
+    const int64_t i = sd.perm[pi];
+    if (mode == kResZeroStopped && !as.act[sd.row_inst[i]]) {
       const int KR = sh.K * R;
-      const int64_t pi = sd.iperm[i];
       for (int q = lane; q < KR; q += 32) Rk[pi * KR + q] = 0.0;
       continue;
     }
-    residual_row(sd, vals, D, sh, b, X, R, Rk, i, lane);
+    residual_row(sd, vals, D, sh, b, X, R, Rk, i, pi, lane);
   }
 }
 
@@ -1292,6 +1294,8 @@ k_refine_stats(SymDev sd, ActiveSet as, int all, double* __restrict__ X, const d
       const int64_t s1 = all ? as.inst_off[g + 1] : as.arow[q + 1];
       const int64_t lo = max(a0, s0), hi = min(a1, s1);
       if (lo < hi) {
+        // the instance's permuted rows are its original range: its (row, k)
+        // pairs from i0 on are contiguous in X and Y
         const int64_t i0 = as.inst_off[g] + (lo - s0);
         const int64_t npair = (hi - lo) * K;
         for (int rb = 0; rb < R; rb += RB) {
@@ -1299,7 +1303,7 @@ k_refine_stats(SymDev sd, ActiveSet as, int all, double* __restrict__ X, const d
           unsigned long long md = 0, mx = 0;
           if (j < nj && r < R) {
             for (int64_t m = j; m < npair; m += nj) {
-              const int64_t o = ((int64_t)sd.iperm[i0 + m / K] * K + (int)(m % K)) * R + r;
+              const int64_t o = (i0 * K + m) * R + r;
               const double y = Y[o];
               const double xn = X[o] + y;
               X[o] = xn;
