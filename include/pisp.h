@@ -19,7 +19,10 @@
  *    library owns only its handle, the symbolic structure and its workspace
  *    (factors, per-perturbation solutions), all freed by pisp_destroy.
  *  - Work is enqueued on the stream given to pisp_create and is ordered on
- *    it; only pisp_get_status and pisp_solve_host synchronise the stream.
+ *    it; only the queries that read device results back (pisp_get_status,
+ *    pisp_refinement_stats, pisp_profile_collect, pisp_get_front /
+ *    pivot_range, and pisp_get_stats after a captured adaptive sweep loop)
+ *    and pisp_solve_host synchronise the stream.
  *  - A handle is not thread-safe; use one handle per host thread.
  *  - A call makes the handle's device current while it runs and restores
  *    the caller's current device before it returns.
@@ -395,7 +398,9 @@ int pisp_get_pivot_range(pisp_handle* h, double* min_abs, double* max_abs);
 
 /* End-to-end convenience: host buffers, copies inside.  Factor + solve +
  * combine of `values`, `D`, `b` given in host memory; x written to host.
- * Synchronises the stream. */
+ * b is copied on a stream of the handle's own, after values and D, while the
+ * factorisation runs (an overlap only when b_host is pinned).  Synchronises
+ * the stream. */
 int pisp_solve_host(pisp_handle* h, const double* values_host, const double* D_host,
                     const double* t, int32_t K, int32_t precision, const double* b_host,
                     int32_t R, double* x_host, int32_t sweeps);

@@ -111,8 +111,11 @@ struct pisp_handle {
   // solve state
   int32_t R = 0;
   Buf V, X, Y, Rk, Lam, X2, rtmp, dtmp;
-  // host-buffer entry point staging
+  // host-buffer entry point staging; b is copied on its own stream, after
+  // the values and D and during the factorisation
   Buf in_vals, in_D, in_b, out_x;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_ev[2] = {};
   int launches = 0;
   // library-owned CUDA graph of one factor + solve step (pisp_graph_capture)
   cudaGraph_t graph = nullptr;
@@ -155,6 +158,9 @@ struct pisp_handle {
   ~pisp_handle() {
     drop_graph();
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+    for (cudaEvent_t e : copy_ev)
+      if (e) cudaEventDestroy(e);
     if (body_stream) cudaStreamDestroy(body_stream);
     if (cap_ev) cudaEventDestroy(cap_ev);
     for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
@@ -1649,10 +1655,20 @@ int pisp_solve_host(pisp_handle* h, const double* values_host, const double* D_h
   const size_t nb = (size_t)S.N * R * sizeof(double);
   if (!h->in_vals.ensure(nv) || !h->in_D.ensure(nd) || !h->in_b.ensure(nb) || !h->out_x.ensure(nb))
     return fail(h, PISP_ERR_OOM, "device allocation failed (host staging)");
+  if (!h->copy_stream) {
+    CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : h->copy_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
   if (nv) CK(cudaMemcpyAsync(h->in_vals.p, values_host, nv, cudaMemcpyHostToDevice, h->stream));
   if (nd) CK(cudaMemcpyAsync(h->in_D.p, D_host, nd, cudaMemcpyHostToDevice, h->stream));
-  if (nb) CK(cudaMemcpyAsync(h->in_b.p, b_host, nb, cudaMemcpyHostToDevice, h->stream));
+  // b after the values and D (the factorisation needs those first), copied
+  // while the factorisation runs; the solve waits for it
+  CK(cudaEventRecord(h->copy_ev[0], h->stream));
+  CK(cudaStreamWaitEvent(h->copy_stream, h->copy_ev[0], 0));
+  if (nb) CK(cudaMemcpyAsync(h->in_b.p, b_host, nb, cudaMemcpyHostToDevice, h->copy_stream));
+  CK(cudaEventRecord(h->copy_ev[1], h->copy_stream));
   TRY(pisp_factor_perturbed(h, h->in_vals.as<double>(), h->in_D.as<double>(), t, K, precision));
+  CK(cudaStreamWaitEvent(h->stream, h->copy_ev[1], 0));
   TRY(pisp_solve(h, h->in_b.as<double>(), R, nullptr, h->out_x.as<double>(), sweeps));
   if (nb) CK(cudaMemcpyAsync(x_host, h->out_x.p, nb, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));

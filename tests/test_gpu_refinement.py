@@ -251,6 +251,27 @@ def test_profile_counts_only_covered_work(pisp, batch):
     assert fixed["refine_control"]["launches"] == 0
 
 
+def test_solve_host_pinned_matches_device(pisp, batch):
+    """pisp_solve_host copies b on a stream of its own while the factorisation
+    runs: with pinned host buffers (a real overlap) its x is the device path's,
+    bit for bit, call after call with new right-hand sides."""
+    import torch
+    insts, t, b, offs, refs = batch
+    sizes, rp, col, val, D = _concat(insts)
+    s = pisp.Solver(sizes, rp, col).set_refinement(STOP_TOL)
+    hv = torch.tensor(val).pin_memory().numpy()
+    hD = torch.tensor(D).pin_memory().numpy()
+    for seed in (1, 2):
+        bb = pfgen.rhs(sum(sizes), 8, seed)
+        hb = torch.tensor(bb).pin_memory().numpy()
+        hx = torch.empty(bb.shape, dtype=torch.float64).pin_memory().numpy()
+        s.solve_host(hv, hD, t, hb, "fp32", 10, out=hx)
+        s.factor(_dev(val), _dev(D), t, "fp32")
+        xd = s.solve(_dev(bb), sweeps=10).cpu().numpy()
+        assert np.array_equal(hx, xd)
+    s.close()
+
+
 @pytest.mark.parametrize("R", [1, 3, 260])
 def test_adaptive_odd_rhs_counts(pisp, R):
     """RHS counts that take the other paths of the per-instance maxima (R not
