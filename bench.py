@@ -442,18 +442,13 @@ def run_pisp(args, rank, world, local_rank):
     value = units * world * args.steps / (total_ms / 1e3)
     prof = arm.s.profile_read()
     stats = arm.s.stats()
-    # adaptive sweeps: captured in the graph they are one device-side loop
-    # (family sweep_loop; forward and backward then hold the first solve
-    # only); run eagerly, launch s of the solve and residual families covers
-    # only the instances still iterating, and the roofline counts full-launch
-    # equivalents (the fraction of front entries or rows each launch covered)
-    nsw, work, rows = arm.s.refinement_stats(sweeps, rows=True)
-    eager_gated = refine_tol > 0 and sweeps > 0 and not use_graph
-    gated = {"forward": float(work.sum()), "backward": float(work.sum()), "residual": float(rows.sum())}
+    # adaptive sweeps run as one device-side loop (family sweep_loop, not a
+    # kernel); forward and backward then hold the first solve only, whose
+    # launches cover every instance
+    nsw, _ = arm.s.refinement_stats(sweeps)
 
     def full_launches_per_step(f):
-        per = prof[f]["launches"] / args.steps
-        return per - sweeps + gated[f] if f in gated and eager_gated else per
+        return prof[f]["launches"] / args.steps
     if not use_graph:
         arm.s.profile(False)
     if rank != 0:
@@ -479,7 +474,6 @@ def run_pisp(args, rank, world, local_rank):
                 else "library count",
                 "library_bytes_per_launch": lib_bytes,
                 "avg_launch_us": round(1e3 * launch_ms, 3),
-                "launch_basis": "full-launch equivalents" if fam in gated and eager_gated else "launches",
                 "share_of_step": round(pf["ms"] / total_ms, 4) if world == 1 else None}
 
     def fam_roofline(f):
@@ -499,7 +493,6 @@ def run_pisp(args, rank, world, local_rank):
         mbf = min_bytes_per_launch(f, stats, K, R, p)
         return {"ms_per_step": round(v["ms"] / args.steps, 4),
                 "launches_per_step": v["launches"] / args.steps,
-                "full_launch_equivalents_per_step": round(fl, 4),
                 "min_GBps": (round(mbf * fl / (v["ms"] / args.steps / 1e3) / 1e9, 2)
                              if v["ms"] > 0 and mbf is not None else None),
                 "library_GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 2) if v["ms"] > 0 else 0.0}

@@ -335,11 +335,15 @@ int pisp_set_wait_limit(pisp_handle* h, int64_t polls, int32_t unreachable);
  * only d_1 = 0 stops an instance.
  * The instance stops when all its right-hand sides have converged or
  * stagnated; the later sweeps skip its rows and fronts (the solve kernels
- * walk only the work units of the instances still iterating).  tol = 0
- * restores fixed sweeps (every instance, every sweep).  Applies from the
- * next pisp_solve / pisp_refine / pisp_graph_capture (a captured step keeps
- * the mode it was captured with).  The transposed sweeps of pisp_adjoint
- * stay fixed.  Returns PISP_ERR_INVALID_ARG for tol < 0 or not finite. */
+ * walk only the work units of the instances still iterating).  The sweeps
+ * run as one device-side loop, a CUDA graph WHILE node that ends after the
+ * last sweep any instance takes: inside a stream capture (pisp_graph_capture,
+ * or the caller's own) as a node of the captured graph, otherwise as a graph
+ * launched once on the stream.  tol = 0 restores fixed sweeps (every
+ * instance, every sweep, plain launches).  Applies from the next pisp_solve /
+ * pisp_refine / pisp_graph_capture (a captured step keeps the mode it was
+ * captured with).  The transposed sweeps of pisp_adjoint stay fixed.
+ * Returns PISP_ERR_INVALID_ARG for tol < 0 or not finite. */
 int pisp_set_refinement(pisp_handle* h, double tol);
 
 /* The sweeps of the last pisp_solve (or of the last solve inside
@@ -454,10 +458,9 @@ enum {
   PISP_PROF_RESIDUAL = 4,     /* FP64 residuals of the sweeps */
   PISP_PROF_COMBINE = 5,      /* expansion-weighted combine */
   PISP_PROF_FACTOR = 6,       /* the whole factorisation in one launch (factor policy 4) */
-  PISP_PROF_REFINE = 7,       /* stopping tests of the adaptive sweeps (pisp_set_refinement) */
-  PISP_PROF_SWEEP_LOOP = 8,   /* adaptive sweeps captured as one device-side loop (residuals,
-                                 solves and stopping tests of every iteration) */
-  PISP_PROF_FAMILIES = 9
+  PISP_PROF_SWEEP_LOOP = 7,   /* the adaptive sweeps (pisp_set_refinement), one device-side loop:
+                                 residuals, correction solves and stopping tests of every iteration */
+  PISP_PROF_FAMILIES = 8
 };
 
 /* on != 0: start recording brackets (forgets the previous recording); the
@@ -467,9 +470,10 @@ int pisp_profile(pisp_handle* h, int32_t on);
 
 /* Synchronises the stream and adds the elapsed time, algorithmic bytes and
  * kernel launches of every recorded bracket to the per-family totals.  The
- * bytes of a launch of adaptive sweep s count only the instances that sweep
- * covered (front entries for the solves, rows for the residuals and the
- * stopping tests), as the last solve's pisp_refinement_stats gives them. */
+ * adaptive sweep loop counts the kernels of the iterations it ran and, per
+ * iteration, the bytes of the instances it covered (front entries for the
+ * solves, rows for the residuals and the stopping tests), as the last solve's
+ * pisp_refinement_stats gives them. */
 int pisp_profile_collect(pisp_handle* h);
 
 /* Per-family totals since the last pisp_profile_reset: device milliseconds,

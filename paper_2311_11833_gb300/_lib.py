@@ -82,7 +82,7 @@ _SIGS = {
     "pisp_profile_reset": (c_int32, [c_void_p]),
     "pisp_profile_name": (ctypes.c_char_p, [c_int32]),
 }
-PROF_FAMILIES = 9
+PROF_FAMILIES = 8
 
 _lib = None
 

@@ -132,11 +132,9 @@ struct pisp_handle {
     graph_valid = false;
   }
   // profiling: CUDA events bracketing each kernel family per level
-  // sweep >= 1: a launch of adaptive sweep `sweep` in a host loop (bytes for
-  // every instance, scaled at collection by the share the sweep covered);
-  // -1: a whole device-side sweep loop (launches per iteration, and the bytes
-  // of one sweep over every instance split into rows and solve work, scaled
-  // at collection per iteration)
+  // sweep = -1: a whole device-side sweep loop (launches per iteration, and
+  // the bytes of one sweep over every instance split into rows and solve
+  // work, scaled at collection per iteration by the share it covered)
   struct Bracket {
     int fam, e0, e1, launches;
     double bytes;
@@ -602,7 +600,7 @@ pisp::Shifts make_shifts(const pisp_handle* h, const double* w) {
 
 const char* kFamilyNames[PISP_PROF_FAMILIES] = {"factor_small", "factor_big", "forward",
                                                 "backward",     "residual",   "combine",
-                                                "factor_persistent", "refine_control", "sweep_loop"};
+                                                "factor_persistent", "sweep_loop"};
 
 // Event record that also works inside a stream capture: there it must become
 // an event-record node of the graph (external record) to be timed on replay.
@@ -631,11 +629,10 @@ int prof_begin(pisp_handle* h, cudaStream_t st = nullptr) {
 }
 
 // Closes the bracket on the stream it was opened on (default: the handle's).
-void prof_end(pisp_handle* h, int i, int fam, double bytes, int launches, cudaStream_t st = nullptr,
-              int sweep = 0) {
+void prof_end(pisp_handle* h, int i, int fam, double bytes, int launches, cudaStream_t st = nullptr) {
   if (i < 0 || launches <= 0) return;
   record_event(h, h->prof_ev[i + 1], st ? st : h->stream);
-  h->prof_br.push_back({fam, i, i + 1, launches, bytes, sweep, 0.0, 0.0});
+  h->prof_br.push_back({fam, i, i + 1, launches, bytes, 0, 0.0, 0.0});
 }
 
 int count(pisp_handle* h, int n) {
@@ -651,9 +648,9 @@ int count(pisp_handle* h, int n) {
 // or per-perturbation [N][K][R] (permuted order); results to `out`
 // (and added to `acc` when given).  Adaptive sweeps (persistent schedule):
 // act skips the fronts of instances that have stopped and the compacted unit
-// lists are walked; `sweep` tags the profiling brackets.
+// lists are walked.
 int solve_pass(pisp_handle* h, bool trans, const double* rhs, int rhs_mode, double* out,
-               double* acc, int32_t R, const uint8_t* act = nullptr, int sweep = 0) {
+               double* acc, int32_t R, const uint8_t* act = nullptr) {
   const int L = h->sym.n_levels;
   if (!trans && h->schedule == 0) {
     if (h->units_K != h->K || h->units_R != R) TRY(build_units(h, h->K, R));
@@ -676,7 +673,7 @@ int solve_pass(pisp_handle* h, bool trans, const double* rhs, int rhs_mode, doub
         h->fronts.p, rhs, rhs_mode, h->V.p, out, acc, R, h->K, h->units_maxF, h->solve_ctas, h->wait_polls,
         h->stream);
     TRY(count(h, n));
-    prof_end(h, pb, PISP_PROF_FORWARD, bf, n, nullptr, act ? sweep : 0);
+    prof_end(h, pb, PISP_PROF_FORWARD, bf, n);
     CK(cudaMemsetAsync(h->done.p, 0, nd, h->stream));
     pb = prof_begin(h);
     n = pisp::launch_solve_persistent(
@@ -685,7 +682,7 @@ int solve_pass(pisp_handle* h, bool trans, const double* rhs, int rhs_mode, doub
         h->fronts.p, rhs, rhs_mode, h->V.p, out, acc, R, h->K, h->units_maxF, h->solve_ctas, h->wait_polls,
         h->stream);
     TRY(count(h, n));
-    prof_end(h, pb, PISP_PROF_BACKWARD, bb, n, nullptr, act ? sweep : 0);
+    prof_end(h, pb, PISP_PROF_BACKWARD, bb, n);
     return PISP_OK;
   }
   for (int l = 0; l < L; ++l) {
@@ -748,71 +745,55 @@ double solve_bytes(const pisp_handle* h, int32_t R) {
   return b;
 }
 
-// One adaptive sweep for the instances still iterating: the FP64 residuals
-// of their rows, the gated solves of their corrections (compacted unit lists
-// of the persistent schedule; the per-level schedule solves every row, with
-// zero residuals outside the active set), the corrections added to their
-// solutions with the correction and solution sizes, the stopping test and
-// the active set and unit lists of the next sweep.  s_host: the sweep number in a host loop (brackets and launch
-// accounting), 0 inside a device-side loop (no brackets: a conditional body
-// holds no events).  has_cond: the stopping test drives the loop's
-// conditional `cond`.
+// One adaptive sweep for the instances still iterating, the body of the
+// device-side sweep loop: the FP64 residuals of their rows, the gated solves
+// of their corrections (compacted unit lists of the persistent schedule; the
+// per-level schedule solves every row, with zero residuals outside the active
+// set), the corrections added to their solutions with the correction and
+// solution sizes, the stopping test (which drives the loop's conditional
+// `cond`) and the active set and unit lists of the next sweep.  No profiling
+// brackets: a conditional body holds no events.
 int sweep_body(pisp_handle* h, const double* rhs, double* X_out, int32_t R, int32_t S, const pisp::Shifts& sh,
-               int s_host, cudaGraphConditionalHandle cond, int has_cond) {
-  const double N = (double)h->sym.N, KR = (double)h->K * R;
+               cudaGraphConditionalHandle cond) {
   const bool persistent = h->schedule == 0;
   const int32_t G = h->sym.G;
   uint8_t* act = h->r_act.as<uint8_t>();
   const pisp::ActiveSet as{act, h->r_nact.as<int32_t>(), h->r_ai.as<int32_t>(), h->r_arow.as<int64_t>(),
                            h->d_inst_off.as<int64_t>()};
-  int pb = s_host > 0 ? prof_begin(h) : -1;
-  int n = pisp::launch_residual_per_k(h->sd, h->vals.as<double>(), h->D.as<double>(), sh, rhs, X_out, R,
-                                      h->Rk.as<double>(), as, persistent ? pisp::kResActive : pisp::kResZeroStopped,
-                                      h->stream);
-  TRY(count(h, n));
-  prof_end(h, pb, PISP_PROF_RESIDUAL, h->sym.nnzA * 12.0 + N * 20.0 + N * R * 8.0 + 2.0 * N * KR * 8.0, n,
-           nullptr, s_host);
-  const bool prof_was = h->prof_on;
-  if (s_host == 0) h->prof_on = false;
+  TRY(count(h, pisp::launch_residual_per_k(h->sd, h->vals.as<double>(), h->D.as<double>(), sh, rhs, X_out, R,
+                                           h->Rk.as<double>(), as,
+                                           persistent ? pisp::kResActive : pisp::kResZeroStopped, h->stream)));
   // the corrections go to Y only: the stats launch below adds them to X
+  const bool prof_was = h->prof_on;
+  h->prof_on = false;
   const int rc = solve_pass(h, false, h->Rk.as<double>(), pisp::RHS_PER_K, h->Y.as<double>(), nullptr, R,
-                            persistent ? act : nullptr, s_host);
+                            persistent ? act : nullptr);
   h->prof_on = prof_was;
   TRY(rc);
-  pb = s_host > 0 ? prof_begin(h) : -1;
-  n = pisp::launch_refine_stats(h->sd, as, 0, X_out, h->Y.as<double>(), h->K, R, h->r_dmax.as<unsigned long long>(),
-                                h->r_xmax.as<unsigned long long>(), h->stream);
-  TRY(count(h, n));
-  int m = pisp::launch_refine_decide(G, R, h->sweep_tol, S, h->r_sweep.as<int32_t>(), cond, has_cond, act,
-                                     h->r_dmax.as<unsigned long long>(), h->r_xmax.as<unsigned long long>(),
-                                     h->r_prevd.as<double>(), h->r_nsw.as<int32_t>(), h->r_pre.as<int32_t>(),
-                                     h->r_nact.as<int32_t>(), h->r_ai.as<int32_t>(), h->r_arow.as<int64_t>(),
-                                     h->d_inst_off.as<int64_t>(), h->stream);
-  TRY(count(h, m));
-  if (persistent && s_host < S) {
-    const int c = pisp::launch_compact_units(
-        h->units_f.as<pisp::SolveUnit>(), h->rng_f.as<int32_t>(), h->n_units_f, h->units_fc.as<pisp::SolveUnit>(),
-        h->units_b.as<pisp::SolveUnit>(), h->rng_b.as<int32_t>(), h->n_units_b, h->units_bc.as<pisp::SolveUnit>(),
-        h->r_pre.as<int32_t>(), h->r_ccnt.as<int32_t>(), h->ucount.as<int32_t>(), h->stream);
-    TRY(count(h, c));
-    m += c;
-  }
-  prof_end(h, pb, PISP_PROF_REFINE, 3.0 * N * KR * 8.0, n + m, nullptr, s_host);
+  TRY(count(h, pisp::launch_refine_stats(h->sd, as, 0, X_out, h->Y.as<double>(), h->K, R,
+                                         h->r_dmax.as<unsigned long long>(), h->r_xmax.as<unsigned long long>(),
+                                         h->stream)));
+  TRY(count(h, pisp::launch_refine_decide(G, R, h->sweep_tol, S, h->r_sweep.as<int32_t>(), cond, 1, act,
+                                          h->r_dmax.as<unsigned long long>(), h->r_xmax.as<unsigned long long>(),
+                                          h->r_prevd.as<double>(), h->r_nsw.as<int32_t>(), h->r_pre.as<int32_t>(),
+                                          h->r_nact.as<int32_t>(), h->r_ai.as<int32_t>(), h->r_arow.as<int64_t>(),
+                                          h->d_inst_off.as<int64_t>(), h->stream)));
+  if (persistent)
+    TRY(count(h, pisp::launch_compact_units(
+                     h->units_f.as<pisp::SolveUnit>(), h->rng_f.as<int32_t>(), h->n_units_f,
+                     h->units_fc.as<pisp::SolveUnit>(), h->units_b.as<pisp::SolveUnit>(), h->rng_b.as<int32_t>(),
+                     h->n_units_b, h->units_bc.as<pisp::SolveUnit>(), h->r_pre.as<int32_t>(),
+                     h->r_ccnt.as<int32_t>(), h->ucount.as<int32_t>(), h->stream)));
   return PISP_OK;
 }
 
-// The adaptive sweeps as a device-side loop inside the stream capture in
-// progress on h->stream: a WHILE conditional node (its body one sweep_body,
-// captured on a side stream into the node's body graph) that runs while the
-// stopping test leaves an instance active, at most S times.
-int sweep_loop_node(pisp_handle* h, const double* rhs, double* X_out, int32_t R, int32_t S,
-                    const pisp::Shifts& sh) {
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  cudaGraph_t g = nullptr;
-  const cudaGraphNode_t* deps = nullptr;
-  size_t ndeps = 0;
-  CK(cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &g, &deps, nullptr, &ndeps));
-  if (cs != cudaStreamCaptureStatusActive || !g) return fail(h, PISP_ERR_CUDA, "no stream capture in progress");
+// The adaptive sweeps as a device-side loop: a WHILE conditional node added
+// to graph g after deps (its body one sweep_body, captured on a side stream
+// into the node's body graph) that runs while the stopping test leaves an
+// instance active, at most S times.
+int add_sweep_loop(pisp_handle* h, cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                   cudaGraphNode_t* node_out, const double* rhs, double* X_out, int32_t R, int32_t S,
+                   const pisp::Shifts& sh) {
   cudaGraphConditionalHandle cond = 0;
   CK(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
   cudaGraphNodeParams np{};
@@ -820,31 +801,59 @@ int sweep_loop_node(pisp_handle* h, const double* rhs, double* X_out, int32_t R,
   np.conditional.handle = cond;
   np.conditional.type = cudaGraphCondTypeWhile;
   np.conditional.size = 1;
-  cudaGraphNode_t node = nullptr;
   std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
-  CK(cudaGraphAddNode(&node, g, dv.data(), nullptr, dv.size(), &np));
+  CK(cudaGraphAddNode(node_out, g, dv.data(), nullptr, dv.size(), &np));
   cudaGraph_t body = np.conditional.phGraph_out[0];
   if (!h->body_stream) CK(cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking));
   CK(cudaStreamBeginCaptureToGraph(h->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   const cudaStream_t outer = h->stream;
   h->stream = h->body_stream;
   const int launches0 = h->launches;
-  const int rc = sweep_body(h, rhs, X_out, R, S, sh, 0, cond, 1);
+  const int rc = sweep_body(h, rhs, X_out, R, S, sh, cond);
   h->loop_kernels = h->launches - launches0;
   h->stream = outer;
   cudaGraph_t body_out = nullptr;
   const cudaError_t e = cudaStreamEndCapture(h->body_stream, &body_out);
   TRY(rc);
   if (e != cudaSuccess) return fail(h, PISP_ERR_CUDA, std::string("sweep loop capture: ") + cudaGetErrorString(e));
-  CK(cudaStreamUpdateCaptureDependencies(h->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return PISP_OK;
+}
+
+// The sweep loop on h->stream: inside a stream capture in progress, as a node
+// of the graph being captured; otherwise as a graph of its own, built,
+// launched once and destroyed (an executable graph destroyed in flight is
+// freed when it completes), its host-side construction overlapping the work
+// already queued.
+int run_sweep_loop(pisp_handle* h, const double* rhs, double* X_out, int32_t R, int32_t S, const pisp::Shifts& sh) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  CK(cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &g, &deps, nullptr, &ndeps));
+  cudaGraphNode_t node = nullptr;
+  if (cs == cudaStreamCaptureStatusActive) {
+    if (!g) return fail(h, PISP_ERR_CUDA, "stream capture without a graph");
+    TRY(add_sweep_loop(h, g, deps, ndeps, &node, rhs, X_out, R, S, sh));
+    CK(cudaStreamUpdateCaptureDependencies(h->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return PISP_OK;
+  }
+  CK(cudaGraphCreate(&g, 0));
+  int rc = add_sweep_loop(h, g, nullptr, 0, &node, rhs, X_out, R, S, sh);
+  cudaGraphExec_t ge = nullptr;
+  if (rc == PISP_OK && cudaGraphInstantiate(&ge, g, 0) != cudaSuccess)
+    rc = fail(h, PISP_ERR_CUDA, std::string("sweep loop instantiate: ") + cudaGetErrorString(cudaGetLastError()));
+  cudaGraphDestroy(g);
+  TRY(rc);
+  const cudaError_t e = cudaGraphLaunch(ge, h->stream);
+  cudaGraphExecDestroy(ge);
+  if (e != cudaSuccess) return fail(h, PISP_ERR_CUDA, std::string("sweep loop launch: ") + cudaGetErrorString(e));
   return PISP_OK;
 }
 
 // Per-perturbation solves of `rhs` (broadcast, original order) into X_out,
 // followed by at most `sweeps` FP64 residual corrections of every x_k: all of
 // them for every instance, or (pisp_set_refinement) per instance until its
-// stopping test holds, as a host loop, or as a device-side loop when the
-// stream is being captured.
+// stopping test holds, as a device-side loop.
 int solve_core(pisp_handle* h, const double* rhs, double* X_out, int32_t R, int32_t sweeps,
                const pisp::Shifts& sh) {
   TRY(solve_pass(h, false, rhs, pisp::RHS_BROADCAST, X_out, nullptr, R));
@@ -887,20 +896,14 @@ int solve_core(pisp_handle* h, const double* rhs, double* X_out, int32_t R, int3
                      h->units_fc.as<pisp::SolveUnit>(), h->units_b.as<pisp::SolveUnit>(), h->rng_b.as<int32_t>(),
                      h->n_units_b, h->units_bc.as<pisp::SolveUnit>(), h->r_pre.as<int32_t>(),
                      h->r_ccnt.as<int32_t>(), h->ucount.as<int32_t>(), h->stream)));
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  CK(cudaStreamIsCapturing(h->stream, &cs));
-  if (cs == cudaStreamCaptureStatusActive) {
-    const int pb = prof_begin(h);
-    TRY(sweep_loop_node(h, rhs, X_out, R, sweeps, sh));
-    h->last_loop = true;
-    if (pb >= 0) {  // the loop as one bracket; bytes and launches are scaled at collection
-      record_event(h, h->prof_ev[pb + 1], h->stream);
-      h->prof_br.push_back({PISP_PROF_SWEEP_LOOP, pb, pb + 1, h->loop_kernels, 0.0, -1,
-                            h->sym.nnzA * 12.0 + N * 20.0 + N * R * 8.0 + 5.0 * N * KR * 8.0, solve_bytes(h, R)});
-    }
-    return PISP_OK;
+  const int pb = prof_begin(h);
+  TRY(run_sweep_loop(h, rhs, X_out, R, sweeps, sh));
+  h->last_loop = true;
+  if (pb >= 0) {  // the loop as one bracket; bytes and launches are scaled at collection
+    record_event(h, h->prof_ev[pb + 1], h->stream);
+    h->prof_br.push_back({PISP_PROF_SWEEP_LOOP, pb, pb + 1, h->loop_kernels, 0.0, -1,
+                          h->sym.nnzA * 12.0 + N * 20.0 + N * R * 8.0 + 5.0 * N * KR * 8.0, solve_bytes(h, R)});
   }
-  for (int s = 1; s <= sweeps; ++s) TRY(sweep_body(h, rhs, X_out, R, sweeps, sh, s, 0, 0));
   return PISP_OK;
 }
 
@@ -1699,11 +1702,11 @@ int pisp_profile_collect(pisp_handle* h) {
   DeviceScope dev_scope_;
   TRY(set_device(h, dev_scope_));
   CK(cudaStreamSynchronize(h->stream));
-  int max_sweep = 0;
-  for (const auto& b : h->prof_br) max_sweep = std::max(max_sweep, b.sweep == -1 ? h->last_sweeps : b.sweep);
+  bool loop = false;
+  for (const auto& b : h->prof_br) loop = loop || b.sweep == -1;
   std::vector<int32_t> nsw;
   std::vector<double> fs, fr;
-  if (max_sweep > 0 && h->last_adaptive) TRY(sweep_fractions(h, max_sweep, nsw, fs, fr));
+  if (loop && h->last_adaptive) TRY(sweep_fractions(h, std::max(h->last_sweeps, 1), nsw, fs, fr));
   for (const auto& b : h->prof_br) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, h->prof_ev[b.e0], h->prof_ev[b.e1]));
@@ -1720,10 +1723,7 @@ int pisp_profile_collect(pisp_handle* h) {
       h->prof_launches[b.fam] += (int64_t)b.launches * iters;
       continue;
     }
-    double scale = 1.0;
-    if (b.sweep > 0 && !fs.empty())
-      scale = (b.fam == PISP_PROF_FORWARD || b.fam == PISP_PROF_BACKWARD) ? fs[b.sweep] : fr[b.sweep];
-    h->prof_bytes[b.fam] += b.bytes * scale;
+    h->prof_bytes[b.fam] += b.bytes;
     h->prof_launches[b.fam] += b.launches;
   }
   return PISP_OK;
