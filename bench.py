@@ -59,7 +59,7 @@ TRAFFIC_PER_LAUNCH = {
 BENCH = {
     "plain": dict(precision="fp64", sweeps=0, refine_tol=0.0),
     "precision": dict(precision="fp32", sweeps=8, refine_tol=1e-12),
-    "batching": dict(precision="fp32", sweeps=8, refine_tol=5e-12),
+    "batching": dict(precision="fp32", sweeps=8, refine_tol=1e-12),
     "differentiation": dict(precision="fp64", sweeps=0, refine_tol=0.0),
     "scale": dict(precision="fp32", sweeps=8, refine_tol=1e-12),
 }
