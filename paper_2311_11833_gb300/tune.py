@@ -155,10 +155,12 @@ def autotune(sizes, row_ptr, col, values, D, t, b, precision="fp32", sweeps=2, r
     inst = torch.repeat_interleave(torch.arange(len(sizes), device=b2.device),
                                    torch.as_tensor(np.asarray(sizes, np.int64), device=b2.device))
     # the accuracy reference: FP64 factors, default options, FP64 sweeps (two
-    # fixed, or adaptive up to four)
+    # fixed, or adaptive up to four and to a tolerance no looser than 1e-12,
+    # so that the reference sits at the FP64 floor whatever the candidates'
+    # stopping tolerance)
     sref = Solver(sizes, row_ptr, col)
     try:
-        sref.set_refinement(refine_tol)
+        sref.set_refinement(min(refine_tol, 1e-12) if refine_tol > 0 else 0.0)
         sref.factor(values, D, t, "fp64")
         ref = sref.solve(b2, sweeps=4 if refine_tol > 0 else 2).clone()
     finally:
