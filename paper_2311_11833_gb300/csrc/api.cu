@@ -770,7 +770,7 @@ int sweep_body(pisp_handle* h, const double* rhs, double* X_out, int32_t R, int3
                             persistent ? act : nullptr);
   h->prof_on = prof_was;
   TRY(rc);
-  TRY(count(h, pisp::launch_refine_stats(h->sd, as, 0, X_out, h->Y.as<double>(), h->K, R,
+  TRY(count(h, pisp::launch_refine_stats(h->sd, as, X_out, h->Y.as<double>(), h->K, R,
                                          h->r_dmax.as<unsigned long long>(), h->r_xmax.as<unsigned long long>(),
                                          h->stream)));
   TRY(count(h, pisp::launch_refine_decide(G, R, h->sweep_tol, S, h->r_sweep.as<int32_t>(), cond, 1, act,

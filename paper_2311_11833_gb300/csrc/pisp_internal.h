@@ -247,12 +247,11 @@ enum ResidualMode { kResAll = 0, kResZeroStopped = 1, kResActive = 2 };
 int launch_residual_per_k(const SymDev& sd, const double* vals, const double* D,
                           const Shifts& sh, const double* b, const double* X, int32_t R,
                           double* Rk, const ActiveSet& as, int mode, cudaStream_t st);
-// Per instance g of the active set (all != 0: every instance): X += Y on its
-// rows, then per RHS r the largest |Y| and |X| over its rows and all k,
-// atomically maxed into dmax/xmax [G][R] (zero on entry) as bit patterns.
-int launch_refine_stats(const SymDev& sd, const ActiveSet& as, int all, double* X, const double* Y,
-                        int32_t K, int32_t R, unsigned long long* dmax, unsigned long long* xmax,
-                        cudaStream_t st);
+// Per instance g of the active set: X += Y on its rows, then per RHS r the
+// largest |Y| and |X| over its rows and all k, atomically maxed into
+// dmax/xmax [G][R] (zero on entry) as bit patterns.
+int launch_refine_stats(const SymDev& sd, const ActiveSet& as, double* X, const double* Y, int32_t K, int32_t R,
+                        unsigned long long* dmax, unsigned long long* xmax, cudaStream_t st);
 // One CTA: the stopping test after sweep s = *sweep + 1 (s >= S: every
 // instance stops), *sweep = s, nsw[g] = the sweeps instance g took, dmax /
 // xmax zeroed again, then the active set: pre[g] = the active instances

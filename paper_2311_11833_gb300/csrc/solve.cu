@@ -1263,8 +1263,7 @@ __global__ void k_residual(SymDev sd, const double* __restrict__ vals, const dou
 // correction d_s and of the new solution, per right-hand side r:
 //   dmax[g][r] = max over its rows i and over k of |Y[pi][k][r]|,
 //   xmax[g][r] = max over its rows i and over k of |X[pi][k][r]|.
-// CTAs stride over chunks of kStatRows rows of the active set (all = 1:
-// of every instance).  Within an instance the rows' (i, k) pairs form a
+// CTAs stride over chunks of kStatRows rows of the active set.  Within an instance the rows' (i, k) pairs form a
 // matrix of R columns: thread t keeps column c = t % RB of a pass (RB =
 // min(R, 256)) and every (256/RB)-th pair, so a warp's loads are
 // contiguous; the per-column maxima meet in shared memory and then in one
@@ -1275,11 +1274,11 @@ constexpr int kStatThreads = 256;
 constexpr int kStatRows = 64;
 
 __global__ void __launch_bounds__(kStatThreads)
-k_refine_stats(SymDev sd, ActiveSet as, int all, double* __restrict__ X, const double* __restrict__ Y, int K,
-               int R, unsigned long long* __restrict__ dmax, unsigned long long* __restrict__ xmax) {
+k_refine_stats(SymDev sd, ActiveSet as, double* __restrict__ X, const double* __restrict__ Y, int K, int R,
+               unsigned long long* __restrict__ dmax, unsigned long long* __restrict__ xmax) {
   __shared__ unsigned long long s_d[kStatThreads], s_x[kStatThreads];
-  const int nact = all ? 0 : *as.nact;
-  const int64_t total = all ? sd.N : as.arow[nact];
+  const int nact = *as.nact;
+  const int64_t total = as.arow[nact];
   const int tid = threadIdx.x;
   const int RB = min(R, kStatThreads);
   const int nj = kStatThreads / RB;
@@ -1287,11 +1286,10 @@ k_refine_stats(SymDev sd, ActiveSet as, int all, double* __restrict__ X, const d
   for (int64_t a0 = (int64_t)blockIdx.x * kStatRows; a0 < total; a0 += (int64_t)gridDim.x * kStatRows) {
     const int64_t a1 = min(total, a0 + kStatRows);
     // the instances overlapping active rows [a0, a1), in order (CTA-uniform)
-    int q = all ? sd.row_inst[a0] : active_slot(as.arow, nact, a0);
+    int q = active_slot(as.arow, nact, a0);
     for (;; ++q) {
-      const int g = all ? q : as.ai[q];
-      const int64_t s0 = all ? as.inst_off[g] : as.arow[q];
-      const int64_t s1 = all ? as.inst_off[g + 1] : as.arow[q + 1];
+      const int g = as.ai[q];
+      const int64_t s0 = as.arow[q], s1 = as.arow[q + 1];
       const int64_t lo = max(a0, s0), hi = min(a1, s1);
       if (lo < hi) {
         // the instance's permuted rows are its original range: its (row, k)
@@ -1789,12 +1787,11 @@ int launch_residual_per_k(const SymDev& sd, const double* vals, const double* D,
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
-int launch_refine_stats(const SymDev& sd, const ActiveSet& as, int all, double* X, const double* Y,
-                        int32_t K, int32_t R, unsigned long long* dmax, unsigned long long* xmax,
-                        cudaStream_t st) {
+int launch_refine_stats(const SymDev& sd, const ActiveSet& as, double* X, const double* Y, int32_t K, int32_t R,
+                        unsigned long long* dmax, unsigned long long* xmax, cudaStream_t st) {
   if (sd.N == 0 || R < 1) return 0;
   const unsigned grid = std::min<unsigned>((unsigned)((sd.N + kStatRows - 1) / kStatRows), 32u * sm_count());
-  k_refine_stats<<<grid, kStatThreads, 0, st>>>(sd, as, all, X, Y, K, R, dmax, xmax);
+  k_refine_stats<<<grid, kStatThreads, 0, st>>>(sd, as, X, Y, K, R, dmax, xmax);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
