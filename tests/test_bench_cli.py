@@ -50,3 +50,40 @@ def test_minimum_bytes_count_indices_once_for_all_shifts():
     assert bench.min_bytes_per_launch("factor_small", st, K, R, p) is None
     # the whole factorisation: A's values, D, the pattern once, K factors
     assert bench.min_bytes_per_launch("factor_persistent", st, K, R, p) == 8 * 30 + 8 * 10 + 4 * (50 + 10) + K * p * 50
+
+
+def test_oracle_pool_matches_the_oracle_and_checks_every_instance():
+    """The bench's oracle references come from spawned worker processes (one
+    BLAS thread each): they equal the oracle run in this process up to the
+    rounding order of the BLAS threads (3e-12 entry-wise on the worst of these
+    instances, relative to each column's largest entry), and the check reports
+    every instance of the batch."""
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    import pfgen
+
+    insts = bench.workload_instances("batching", 0, 3)
+    t = pfgen.symmetric_shifts(4, 0.01)
+    sizes = [I.n for I in insts]
+    b = pfgen.rhs(sum(sizes), 2, 1)
+    refs = bench.oracle_refs(insts, t, b)
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    for g, I in enumerate(insts):
+        direct = oracle.x_hat(oracle.to_scipy(I), I.D, t, b[offs[g]:offs[g + 1]])
+        assert np.max(np.abs(refs[g] - direct).max(axis=0) / np.abs(direct).max(axis=0)) <= 1e-11
+
+    class Arm:  # the fields oracle_check reads
+        pass
+
+    arm = Arm()
+    arm.insts = insts
+    x = np.concatenate(refs).copy()
+    x[offs[1] + 3, 1] += 1e-6 * np.abs(refs[1][:, 1]).max()   # one wrong entry in instance 1
+    chk = bench.oracle_check(arm, refs, xs=x)
+    assert chk["instances"] == 3 and chk["results"] == 6
+    assert not chk["all_within_tol"]
+    bad = [p for p in chk["per_instance"] if max(p["entrywise"]) > bench.TOL]
+    assert [p["instance"] for p in bad] == [1]
