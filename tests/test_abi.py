@@ -263,3 +263,26 @@ def test_analyze_thread_cap_gives_the_same_structure(lib):
     assert c.rc == 1                                   # PISP_ERR_INVALID_ARG
     for h in (a, b, c):
         h.close()
+
+
+def test_refinement_calls_check_their_arguments(lib):
+    """pisp_set_refinement takes a finite tol >= 0 (no device needed);
+    pisp_refinement_stats reports NOT_FACTORED before any solve."""
+    h = ctypes.c_void_p()
+    assert lib.pisp_create(ctypes.byref(h), -1, None) == 0
+    for bad in (-1e-12, float("nan"), float("inf")):
+        assert lib.pisp_set_refinement(h, bad) == 1                     # INVALID_ARG
+    assert lib.pisp_set_refinement(h, 0.0) == 0
+    assert lib.pisp_set_refinement(h, 1e-12) == 0
+    assert lib.pisp_set_refinement(None, 1e-12) == 1
+    n = np.array([2], np.int32)
+    rp = np.array([0, 1, 2], np.int64)
+    col = np.array([0, 1], np.int32)
+    assert lib.pisp_analyze(h, 1, n.ctypes.data_as(ctypes.c_void_p), rp.ctypes.data_as(ctypes.c_void_p),
+                            col.ctypes.data_as(ctypes.c_void_p), None) == 0
+    nsw = np.zeros(1, np.int32)
+    work = np.zeros(4)
+    assert lib.pisp_refinement_stats(h, nsw.ctypes.data_as(ctypes.c_void_p), work.ctypes.data_as(ctypes.c_void_p),
+                                     None, 4) == 3                            # NOT_FACTORED: no solve yet
+    assert lib.pisp_refinement_stats(h, None, None, None, -1) == 1
+    lib.pisp_destroy(h)
