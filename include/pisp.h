@@ -21,8 +21,8 @@
  *  - Work is enqueued on the stream given to pisp_create and is ordered on
  *    it; only the queries that read device results back (pisp_get_status,
  *    pisp_refinement_stats, pisp_profile_collect, pisp_get_front /
- *    pivot_range, and pisp_get_stats after a captured adaptive sweep loop)
- *    and pisp_solve_host synchronise the stream.
+ *    pivot_range, and pisp_get_stats after adaptive sweeps) and
+ *    pisp_solve_host synchronise the stream.
  *  - A handle is not thread-safe; use one handle per host thread.
  *  - A call makes the handle's device current while it runs and restores
  *    the caller's current device before it returns.
@@ -139,9 +139,9 @@ typedef struct pisp_stats {
   int32_t etree_height;  /* height of the column elimination tree */
   int32_t K;             /* perturbations of the last factorisation */
   int32_t precision;     /* PISP_FP32 / PISP_FP64 of the last factorisation */
-  int32_t gpu_launches;  /* kernels launched by the last factor + solve calls (adaptive sweeps
-                            captured as a device-side loop: with the iterations the last run
-                            of the loop took; reading them synchronises the stream) */
+  int32_t gpu_launches;  /* kernels launched by the last factor + solve calls (adaptive sweeps,
+                            a device-side loop: with the iterations its last run took; reading
+                            them synchronises the stream) */
   double flops_factor;   /* per perturbation */
   double flops_solve;    /* per perturbation per RHS (forward + back) */
   double analyze_ms;     /* host time of pisp_analyze */

@@ -74,7 +74,7 @@ struct pisp_handle {
   double sweep_tol = 0.0;
   int32_t last_sweeps = 0;
   bool last_adaptive = false, any_solve = false;
-  bool last_loop = false;       // the last solve's sweeps were captured as a device-side loop
+  bool last_loop = false;       // the last solve's sweeps ran as a device-side loop
   int32_t loop_kernels = 0;     // kernels per iteration of that loop
   cudaStream_t body_stream = nullptr;  // captures the loop's body
   std::vector<double> inst_w;  // solve work of each instance (front entries)
@@ -1535,7 +1535,7 @@ int pisp_get_stats(const pisp_handle* h, pisp_stats* o) {
   o->precision = h->precision;
   o->gpu_launches = h->launches;
   if (h->last_loop && h->loop_kernels > 0 && h->r_sweep.p) {
-    // a device-side sweep loop was captured once: add its further iterations
+    // a device-side sweep loop counted its body once: add its further iterations
     pisp_handle* hh = const_cast<pisp_handle*>(h);
     DeviceScope dev_scope_;
     if (set_device(hh, dev_scope_) == PISP_OK) {
