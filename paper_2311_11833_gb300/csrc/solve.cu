@@ -1263,10 +1263,11 @@ __global__ void k_residual(SymDev sd, const double* __restrict__ vals, const dou
 // correction d_s and of the new solution, per right-hand side r:
 //   dmax[g][r] = max over its rows i and over k of |Y[pi][k][r]|,
 //   xmax[g][r] = max over its rows i and over k of |X[pi][k][r]|.
-// CTAs stride over chunks of kStatRows rows of the active set.  Within an instance the rows' (i, k) pairs form a
-// matrix of R columns: thread t keeps column c = t % RB of a pass (RB =
-// min(R, 256)) and every (256/RB)-th pair, so a warp's loads are
-// contiguous; the per-column maxima meet in shared memory and then in one
+// CTAs stride over chunks of kStatRows rows of the active set.  Within an
+// instance the rows' (i, k) pairs form a matrix of R columns: thread t keeps
+// column c = t % RB of a pass (RB = min(R, 256)) and every (256/RB)-th pair,
+// so a warp's loads are contiguous; the per-column maxima meet in shared
+// memory and then in one
 // 64-bit atomicMax per (g, r) on the bit patterns (non-negative doubles
 // order as their bit patterns, and a NaN orders above +inf, so a NaN never
 // reads as converged).
